@@ -1,0 +1,273 @@
+"""FP64 oracle of the binned kernel smoother (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  It shares
+no code with the CUDA path (``paper_2204_07716_gb300``) and never calls it.
+
+The heavy lifting is the plain C library ``oracle.c`` (direct O(N) sums per
+query point, Gaussian elimination in FP64).  This module adds the quantities
+built on top of those sums, each written from its definition in the paper:
+
+* ``grid_points``      the uniform grid of eq. 6, endpoints included.
+* ``moment_sums``      s_g and t_a of eq. 9 at arbitrary query points.
+* ``smooth_at``        mhat = e_1^T S^-1 t (eqs. 3, 10, 11) at query points.
+* ``smoother_diag``    S_ii = K_H(0) [S(x_i)^-1]_11, the i-th diagonal entry of
+                       the smoother matrix S of eq. 3 applied at the samples.
+* ``trace_exact``      tr(S_h), the DF of eq. 22.
+* ``fmc_trace``        Girard's fast Monte-Carlo estimate (Sec. 2.1) and the
+                       Hutchinson mean of w_p^T S w_p.
+* ``gcv``              eq. 22.
+* ``variance_pass``    eq. 23: a local-linear smooth of squared residuals.
+* ``get_hlist``        the bandwidth list helper of Sec. 4.
+* ``select_h``         the GCV argmin relaxed by ``dstd`` (Table 1).
+* ``probes``           the counter-based Gaussian probe generator.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.or_nmono.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.or_nmono.restype = ctypes.c_int
+        L.or_monomials.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.or_monomials.restype = ctypes.c_int
+        L.or_kernel.argtypes = [ctypes.c_int, dp, dp]
+        L.or_kernel.restype = ctypes.c_double
+        L.or_moment_sums.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int, dp, dp,
+                                     ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int]
+        L.or_moment_sums.restype = ctypes.c_int
+        L.or_lpr_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int,
+                                   dp, dp, dp]
+        L.or_lpr_solve.restype = ctypes.c_int
+        L.or_probes.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, dp]
+        L.or_probes.restype = None
+        L.or_splitmix64.argtypes = [ctypes.c_uint64]
+        L.or_splitmix64.restype = ctypes.c_uint64
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def nmono(d: int, deg: int) -> int:
+    return int(lib().or_nmono(d, deg))
+
+
+def monomials(d: int, deg: int) -> np.ndarray:
+    """Exponent table [nmono, d] in the oracle's (and the API's) order."""
+    m = nmono(d, deg)
+    e = np.zeros(m * d, dtype=np.int32)
+    lib().or_monomials(d, deg, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return e.reshape(m, d)
+
+
+def kernel(H: np.ndarray, z: np.ndarray) -> float:
+    H = _c64(H)
+    z = _c64(z)
+    return float(lib().or_kernel(H.shape[0], _dp(H), _dp(z)))
+
+
+def grid_points(grid_n: Sequence[int], lo: Sequence[float], hi: Sequence[float]) -> np.ndarray:
+    """All points of the eq. 6 grid, [prod(grid_n), d], last axis fastest.
+
+    g_{k,j} = lo_j + k (hi_j - lo_j) / (M_j - 1), endpoints included.
+    """
+    axes = []
+    for m, a, b in zip(grid_n, lo, hi):
+        if m == 1:
+            axes.append(np.array([a], dtype=np.float64))
+        else:
+            axes.append(a + np.arange(m, dtype=np.float64) * ((b - a) / (m - 1)))
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return np.stack([g.reshape(-1) for g in mesh], axis=1)
+
+
+def moment_sums(x: np.ndarray, c: np.ndarray, H: np.ndarray, deg: int,
+                q: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """s/t moment sums of eq. 9, [nq, nstr, nmono(d, deg)].
+
+    ``c`` is [nstr, n] (use ones for the s-fields, y for the t-fields).
+    """
+    x = _c64(x)
+    n, d = x.shape
+    c = _c64(np.atleast_2d(c))
+    q = _c64(np.atleast_2d(q))
+    H = _c64(H)
+    nm = nmono(d, deg)
+    out = np.zeros((q.shape[0], c.shape[0], nm))
+    rc = lib().or_moment_sums(d, n, _dp(x), c.shape[0], _dp(c), _dp(H), deg,
+                              q.shape[0], _dp(q), _dp(out), nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle moment sums failed ({rc}): H must be SPD, d in 1..3")
+    return out
+
+
+def lpr_solve(d: int, order: int, s: np.ndarray, t: np.ndarray):
+    """mhat = e_1^T S^-1 t and [S^-1]_11 from moment sums (eqs. 3, 11).
+
+    ``s`` [nq, nmono(d, 2 order)], ``t`` [nq, nrhs, nmono(d, order)].
+    Returns (mhat [nq, nrhs], sinv11 [nq]).
+    """
+    s = _c64(s)
+    t = _c64(t)
+    nq = s.shape[0]
+    nrhs = t.shape[1]
+    mh = np.zeros((nq, nrhs))
+    si = np.zeros(nq)
+    lib().or_lpr_solve(d, order, nq, _dp(s), nrhs, _dp(t), _dp(mh), _dp(si))
+    return mh, si
+
+
+def smooth_at(x: np.ndarray, y: np.ndarray, H: np.ndarray, order: int,
+              q: np.ndarray, nthreads: int = 0):
+    """Local-polynomial estimate at query points q.
+
+    Returns a dict with ``mhat`` [nq, nrhs], ``s`` [nq, ns] (s-fields),
+    ``t`` [nq, nrhs, nt] (t-fields) and ``sinv11`` [nq].
+    """
+    x = _c64(x)
+    d = x.shape[1]
+    y = _c64(np.atleast_2d(y))
+    nrhs = y.shape[0]
+    ones = np.ones((1, x.shape[0]))
+    s = moment_sums(x, ones, H, 2 * order, q, nthreads)[:, 0, :]
+    t = moment_sums(x, y, H, order, q, nthreads)
+    mh, si = lpr_solve(d, order, s, t)
+    return {"mhat": mh, "s": s, "t": t, "sinv11": si}
+
+
+def scale_field(x: np.ndarray, c: np.ndarray, H: np.ndarray, q: np.ndarray,
+                nthreads: int = 0) -> np.ndarray:
+    """a(q) = sum_i K_H(x_i - q) |c_i| : the natural size of a moment field."""
+    return moment_sums(x, np.abs(np.atleast_2d(c)), H, 0, q, nthreads)[:, :, 0]
+
+
+def smoother_diag(x: np.ndarray, H: np.ndarray, order: int, idx=None,
+                  nthreads: int = 0) -> np.ndarray:
+    """S_ii for i in idx (all samples by default).
+
+    With the smoother matrix of eq. 3 evaluated at q = x_i, row i is
+    e_1^T S(x_i)^-1 D^T W and its i-th entry is K_H(0) [S(x_i)^-1]_11,
+    because the i-th design row at q = x_i is e_1 (d(0) = (1, 0, ...)).
+    """
+    x = _c64(x)
+    d = x.shape[1]
+    q = x if idx is None else x[np.asarray(idx)]
+    r = smooth_at(x, np.zeros((1, x.shape[0])), H, order, q, nthreads)
+    return kernel(H, np.zeros(d)) * r["sinv11"]
+
+
+def trace_exact(x: np.ndarray, H: np.ndarray, order: int, nthreads: int = 0) -> float:
+    """tr(S_h) = sum_i S_ii (the DF in eq. 22)."""
+    return float(np.sum(smoother_diag(x, H, order, None, nthreads)))
+
+
+def apply_smoother(x: np.ndarray, v: np.ndarray, H: np.ndarray, order: int,
+                   idx=None, nthreads: int = 0) -> np.ndarray:
+    """(S_h v)_i at samples i in idx: the estimate of eq. 3 at q = x_i.
+
+    ``v`` is [nrhs, n]; returns [len(idx), nrhs].
+    """
+    x = _c64(x)
+    q = x if idx is None else x[np.asarray(idx)]
+    return smooth_at(x, v, H, order, q, nthreads)["mhat"]
+
+
+def fmc_trace(x: np.ndarray, w: np.ndarray, H: np.ndarray, order: int,
+              Sw: Optional[np.ndarray] = None, nthreads: int = 0):
+    """Fast Monte-Carlo DF (Sec. 2.1) with given probes w [np, n].
+
+    Step iii: (1/N) tr(I - S) ~ mean_p w_p^T (w_p - S w_p) / (w_p^T w_p),
+    hence tr(S) ~ N mean_p (w_p^T S w_p) / (w_p^T w_p)   (Girard).
+    Also returns the Hutchinson estimate mean_p w_p^T S w_p and the per-probe
+    numerators.
+    """
+    w = _c64(np.atleast_2d(w))
+    n = w.shape[1]
+    if Sw is None:
+        Sw = apply_smoother(x, w, H, order, None, nthreads).T   # [np, n]
+    num = np.sum(w * Sw, axis=1)
+    den = np.sum(w * w, axis=1)
+    return {"girard": float(n * np.mean(num / den)), "hutchinson": float(np.mean(num)),
+            "wSw": num, "ww": den}
+
+
+def gcv(rss: float, n: int, tr: float) -> float:
+    """Eq. 22: (RSS / N) / (tr(I - S) / N)^2."""
+    return (rss / n) / ((1.0 - tr / n) ** 2)
+
+
+def variance_pass(x: np.ndarray, y: np.ndarray, mhat_at_x: np.ndarray,
+                  H: np.ndarray, q: np.ndarray, order: int = 1, nthreads: int = 0) -> np.ndarray:
+    """Eq. 23: sigma^2(q) = local-linear smooth of r_i = |y_i - mhat(x_i)|^2."""
+    r = np.abs(np.atleast_2d(y) - np.atleast_2d(mhat_at_x)) ** 2
+    return smooth_at(x, r, H, order, q, nthreads)["mhat"]
+
+
+def get_hlist(n: int, lo: float, hi: float, spacing: str = "log") -> np.ndarray:
+    """Bandwidth candidates of Sec. 4 (get_hList): n values from lo to hi.
+
+    ``log`` spacing is 10**linspace(log10 lo, log10 hi, n) (MATLAB logspace),
+    ``lin`` is linspace(lo, hi, n).
+    """
+    if spacing == "log":
+        return 10.0 ** np.linspace(math.log10(lo), math.log10(hi), n)
+    return np.linspace(lo, hi, n)
+
+
+def select_h(gcv_values: Sequence[float], dstd: float = 0.0) -> int:
+    """Index of the selected bandwidth (Table 1, ``dstd``).
+
+    Reading of the garbled rule: take the largest candidate (candidates in
+    increasing order) whose GCV is within dstd * std(GCV) of the minimum;
+    dstd = 0 is the plain argmin, ties resolved toward the larger bandwidth.
+    """
+    g = np.asarray(gcv_values, dtype=np.float64)
+    thr = np.nanmin(g) + dstd * (np.nanstd(g) if dstd else 0.0)
+    ok = np.where(g <= thr)[0]
+    return int(ok.max())
+
+
+def probes(seed: int, n_probes: int, n: int) -> np.ndarray:
+    """Counter-based Gaussian probes [n_probes, n] (SplitMix64 + Box-Muller)."""
+    out = np.zeros((n_probes, n))
+    lib().or_probes(ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), n_probes, n, _dp(out))
+    return out
+
+
+def splitmix64(z: int) -> int:
+    return int(lib().or_splitmix64(ctypes.c_uint64(z & 0xFFFFFFFFFFFFFFFF)))

@@ -1,0 +1,262 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a library
+routine (scipy's Gaussian density, numpy least squares), a closed form, an
+invariant, derivatives of the density, brute force on tiny inputs, or values
+the paper prints.  A dropped term, a wrong sign, H in place of H^-1 or a
+transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_spd(rng, d, scale):
+    A = rng.standard_normal((d, d))
+    H = A @ A.T + d * np.eye(d)
+    return H * (scale ** 2 / np.mean(np.diag(H)))
+
+
+def test_monomial_order_is_combinations_with_replacement():
+    for d in (1, 2, 3):
+        for deg in range(0, 5):
+            e = oracle.monomials(d, deg)
+            expect = []
+            for k in range(deg + 1):
+                for tup in itertools.combinations_with_replacement(range(d), k):
+                    v = [0] * d
+                    for a in tup:
+                        v[a] += 1
+                    expect.append(v)
+            assert e.tolist() == expect
+            assert oracle.nmono(d, deg) == math.comb(d + deg, deg)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_single_point_numerator_is_the_gaussian_density(d):
+    # eq. 9 with one sample: t_0(g) = K_H(x_1 - g) y_1, K_H the N(0, H) density
+    rng = np.random.default_rng(1 + d)
+    H = rand_spd(rng, d, 0.1)
+    x = rng.random((1, d))
+    y = np.array([[1.7]])
+    q = rng.random((20, d))
+    t = oracle.moment_sums(x, y, H, 0, q)[:, 0, 0]
+    ref = 1.7 * stats.multivariate_normal(mean=x[0], cov=H).pdf(q)
+    np.testing.assert_allclose(t, ref, rtol=1e-13)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_first_and_second_moments_are_density_derivatives(d):
+    # grad_q s_0 = H^-1 s_(1) and H (grad grad^T s_0) H = s_(2) - H s_0, where
+    # s_(1), s_(2) are the first and second moments of (x_i - q).  This pins the
+    # sign (x_i - q) of eq. 4 and the exponent bookkeeping independently of eq. 9.
+    rng = np.random.default_rng(10 + d)
+    H = rand_spd(rng, d, 0.15)
+    x = rng.random((40, d))
+    q = rng.random((3, d))
+    ones = np.ones((1, 40))
+    m = oracle.moment_sums(x, ones, H, 2, q)[:, 0, :]
+    ex = oracle.monomials(d, 2)
+    first = [int(np.where((ex == np.eye(d, dtype=int)[j]).all(1))[0][0]) for j in range(d)]
+
+    def s0(p):
+        return oracle.moment_sums(x, ones, H, 0, p[None])[0, 0, 0]
+
+    h = 1e-4
+    for k in range(q.shape[0]):
+        grad = np.zeros(d)
+        hess = np.zeros((d, d))
+        for a in range(d):
+            ea = np.eye(d)[a] * h
+            grad[a] = (s0(q[k] + ea) - s0(q[k] - ea)) / (2 * h)
+            for b in range(d):
+                eb = np.eye(d)[b] * h
+                hess[a, b] = (s0(q[k] + ea + eb) - s0(q[k] + ea - eb)
+                              - s0(q[k] - ea + eb) + s0(q[k] - ea - eb)) / (4 * h * h)
+        s1 = m[k, first]
+        np.testing.assert_allclose(H @ grad, s1, rtol=1e-6, atol=1e-7 * np.abs(s1).max())
+        S2 = np.zeros((d, d))
+        for a in range(d):
+            for b in range(d):
+                e = np.zeros(d, dtype=int)
+                e[a] += 1
+                e[b] += 1
+                S2[a, b] = m[k, int(np.where((ex == e).all(1))[0][0])]
+        np.testing.assert_allclose(H @ hess @ H + H * m[k, 0], S2,
+                                   rtol=1e-4, atol=1e-5 * np.abs(S2).max())
+
+
+@pytest.mark.parametrize("d,order", [(1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)])
+def test_constant_response_is_returned(d, order):
+    rng = np.random.default_rng(20 + d + 3 * order)
+    x = rng.random((60, d))
+    H = rand_spd(rng, d, 0.2)
+    q = rng.random((15, d))
+    r = oracle.smooth_at(x, np.full((1, 60), -2.5), H, order, q)
+    np.testing.assert_allclose(r["mhat"], -2.5, rtol=1e-12)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_local_linear_reproduces_linear_m(d):
+    rng = np.random.default_rng(30 + d)
+    x = rng.random((80, d))
+    H = rand_spd(rng, d, 0.2)
+    a, b = 0.7, rng.standard_normal(d)
+    y = a + x @ b
+    q = rng.random((25, d))
+    r = oracle.smooth_at(x, y[None], H, 1, q)
+    np.testing.assert_allclose(r["mhat"][:, 0], a + q @ b, rtol=1e-10, atol=1e-11)
+    # NW does not reproduce a sloped line (boundary bias, Sec. 1): it must differ
+    r0 = oracle.smooth_at(x, y[None], H, 0, q)
+    assert np.max(np.abs(r0["mhat"][:, 0] - (a + q @ b))) > 1e-3
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_local_linear_equals_weighted_least_squares(d):
+    # eq. 2 minimised directly with numpy's least-squares routine
+    rng = np.random.default_rng(40 + d)
+    n = 50
+    x = rng.random((n, d))
+    H = rand_spd(rng, d, 0.25)
+    y = np.sin(4 * x[:, 0]) + rng.standard_normal(n) * 0.1
+    q = rng.random((6, d))
+    r = oracle.smooth_at(x, y[None], H, 1, q)
+    for k in range(q.shape[0]):
+        z = x - q[k]
+        w = stats.multivariate_normal(mean=np.zeros(d), cov=H).pdf(z).reshape(-1)
+        D = np.hstack([np.ones((n, 1)), z])
+        sw = np.sqrt(w)[:, None]
+        beta = np.linalg.lstsq(D * sw, y * sw[:, 0], rcond=None)[0]
+        np.testing.assert_allclose(r["mhat"][k, 0], beta[0], rtol=1e-9, atol=1e-12)
+    # NW is the weighted mean
+    r0 = oracle.smooth_at(x, y[None], H, 0, q)
+    for k in range(q.shape[0]):
+        w = stats.multivariate_normal(mean=np.zeros(d), cov=H).pdf(x - q[k]).reshape(-1)
+        np.testing.assert_allclose(r0["mhat"][k, 0], np.sum(w * y) / np.sum(w), rtol=1e-12)
+
+
+@pytest.mark.parametrize("d,order", [(1, 0), (2, 0), (1, 1), (2, 1), (3, 1)])
+def test_smoother_diagonal_and_trace_match_explicit_matrix(d, order):
+    # Build S column by column by smoothing unit vectors, compare diag(S)
+    rng = np.random.default_rng(50 + d + order)
+    n = 30
+    x = rng.random((n, d))
+    H = rand_spd(rng, d, 0.3)
+    S = oracle.apply_smoother(x, np.eye(n), H, order)   # S[i, j] = (S e_j)_i
+    np.testing.assert_allclose(np.diag(S), oracle.smoother_diag(x, H, order), rtol=1e-10)
+    np.testing.assert_allclose(np.trace(S), oracle.trace_exact(x, H, order), rtol=1e-10)
+    np.testing.assert_allclose(S.sum(axis=1), 1.0, rtol=1e-10)     # rows reproduce constants
+    if order == 0:
+        s0 = oracle.moment_sums(x, np.ones((1, n)), H, 0, x)[:, 0, 0]
+        k0 = stats.multivariate_normal(mean=np.zeros(d), cov=H).pdf(np.zeros(d))
+        np.testing.assert_allclose(np.diag(S), k0 / s0, rtol=1e-12)
+
+
+def test_single_sample_trace_is_one():
+    for d in (1, 2, 3):
+        x = np.full((1, d), 0.4)
+        assert abs(oracle.trace_exact(x, np.eye(d) * 0.01, 0) - 1.0) < 1e-14
+
+
+def test_gcv_vanishes_for_reproduced_response():
+    rng = np.random.default_rng(7)
+    x = rng.random((40, 2))
+    y = 1.0 - 2.0 * x[:, 0] + 0.5 * x[:, 1]
+    H = np.diag([0.05, 0.08])
+    m = oracle.apply_smoother(x, y[None], H, 1)[:, 0]
+    rss = float(np.sum((y - m) ** 2))
+    assert rss < 1e-20
+    tr = oracle.trace_exact(x, H, 1)
+    assert oracle.gcv(rss, 40, tr) < 1e-20
+    # eq. 22 on a hand-made case
+    assert oracle.gcv(8.0, 4, 2.0) == pytest.approx((8.0 / 4) / (0.5 ** 2))
+
+
+def test_fmc_trace_is_unbiased():
+    # Sec. 2.1: E[w^T S w] = tr(S) for w ~ N(0, I); mean over 3000 probes lies
+    # within 4 standard errors of the exact trace.
+    rng = np.random.default_rng(99)
+    n = 200
+    x = rng.random((n, 1))
+    H = np.array([[0.03 ** 2]])
+    S = oracle.apply_smoother(x, np.eye(n), H, 0)
+    exact = np.trace(S)
+    assert exact == pytest.approx(oracle.trace_exact(x, H, 0), rel=1e-10)
+    w = oracle.probes(12345, 3000, n)
+    r = oracle.fmc_trace(x, w, H, 0, Sw=(S @ w.T).T)
+    se = np.std(r["wSw"]) / math.sqrt(3000)
+    assert abs(r["hutchinson"] - exact) < 4 * se
+    assert abs(r["girard"] - exact) < 4 * se * 1.5
+
+
+def test_probe_generator_is_standard_normal():
+    z = oracle.probes(2024, 4, 50_000)
+    for p in range(4):
+        assert stats.kstest(z[p], "norm").pvalue > 1e-4
+        assert abs(z[p].mean()) < 5 / math.sqrt(50_000)
+        assert abs(z[p].var() - 1) < 0.03
+    c = np.corrcoef(z)
+    assert np.max(np.abs(c - np.eye(4))) < 0.02
+    # SplitMix64 is a bijection on 64-bit words: no collisions on a run of counters
+    outs = {oracle.splitmix64(k) for k in range(5000)}
+    assert len(outs) == 5000
+
+
+def test_get_hlist_reproduces_printed_bessel_values():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "get_hlist_bessel.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for n, lo, hi, sp, idx, val in rows:
+        h = oracle.get_hlist(int(n), float(lo), float(hi), sp)
+        assert round(h[int(idx) - 1], 6 if float(val) < 0.1 else 5) == pytest.approx(float(val), abs=1e-12)
+    # original-scale h = normalised h * std(x): the two printed pairs share the ratio
+    assert 0.26178 / 0.046416 == pytest.approx(0.72843 / 0.12915, rel=1e-4)
+
+
+def test_select_h_dstd_rule():
+    g = [5.0, 3.0, 2.0, 2.0, 4.0]
+    assert oracle.select_h(g, 0.0) == 3          # ties go to the larger h
+    assert oracle.select_h([5.0, 2.0, 2.1, 9.0], 0.0) == 1
+    # relaxed: anything within dstd*std of the min qualifies, the largest h wins
+    s = float(np.std([5.0, 2.0, 2.1, 9.0]))
+    assert oracle.select_h([5.0, 2.0, 2.1, 9.0], 0.15 / s) == 2
+    assert oracle.select_h([5.0, 2.0, 2.1, 9.0], 0.05 / s) == 1
+
+
+def test_variance_pass_reproduces_constant_and_linear_residuals():
+    rng = np.random.default_rng(5)
+    x = rng.random((70, 2))
+    y = rng.standard_normal(70)
+    q = rng.random((10, 2))
+    H = np.diag([0.1 ** 2, 0.12 ** 2])
+    m = y - 0.3 * np.sign(rng.standard_normal(70))      # |y - m|^2 == 0.09
+    v = oracle.variance_pass(x, y[None], m[None], H, q)
+    np.testing.assert_allclose(v[:, 0], 0.09, rtol=1e-12)
+    r = 0.5 + x[:, 0] - 0.25 * x[:, 1]                  # |y - m|^2 linear in x
+    v = oracle.variance_pass(x, np.sqrt(r)[None], np.zeros((1, 70)), H, q)
+    np.testing.assert_allclose(v[:, 0], 0.5 + q[:, 0] - 0.25 * q[:, 1], rtol=1e-10)
+
+
+def test_kde_integrates_to_one():
+    # eq. 8: s_0 / N is a density (Gaussian K has unit mass)
+    rng = np.random.default_rng(3)
+    x = 0.3 + 0.4 * rng.random((25, 2))
+    H = np.diag([0.03 ** 2, 0.02 ** 2])
+    g = oracle.grid_points((201, 201), (0, 0), (1, 1))
+    s0 = oracle.moment_sums(x, np.ones((1, 25)), H, 0, g)[:, 0, 0]
+    assert np.sum(s0) * (1 / 200) ** 2 / 25 == pytest.approx(1.0, rel=1e-6)
+
+
+def test_grid_points_eq6():
+    g = oracle.grid_points((3, 5), (0.0, -1.0), (1.0, 1.0))
+    assert g.shape == (15, 2)
+    np.testing.assert_allclose(g[:5, 1], [-1, -0.5, 0, 0.5, 1])
+    np.testing.assert_allclose(g[::5, 0], [0, 0.5, 1])
