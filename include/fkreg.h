@@ -1,0 +1,261 @@
+/*
+ * fkreg.h - C ABI of the GB300 NUFFT kernel smoother.
+ *
+ * The library computes, for N scattered samples x_i in R^d (d = 1..3) with
+ * responses y_i, the local-polynomial kernel regression of
+ * "FKreg: A MATLAB toolbox for fast Multivariate Kernel Regression":
+ *
+ *   s_g(q) = sum_i K_H(x_i - q) (x_i - q)^g        |g| <= 2l   (Sec. 1.1, eq. 9)
+ *   t_a(q) = sum_i K_H(x_i - q) (x_i - q)^a y_i    |a| <= l    (eq. 9)
+ *   mhat(q) = e_1^T S(q)^-1 t(q),   S_ab = s_(a+b)             (eqs. 3, 11)
+ *
+ * with the Gaussian kernel K_H(z) = (2 pi)^(-d/2) |H|^(-1/2) exp(-z^T H^-1 z / 2)
+ * (the scaled kernel of Sec. 1), at the points q of a uniform grid (eq. 6) and
+ * at the samples themselves.  The sums are evaluated to a requested tolerance
+ * by type-1 NUFFT spreading (Sec. 1.2, eqs. 16-20), a Fourier-domain multiply
+ * by the transform of the moment kernels z^g K_H(z), and inverse FFTs
+ * (eq. 21); values at the samples use the type-2 (uniform to non-uniform)
+ * NUFFT that Sec. 1.1 mentions.  On top of the sums the library gives the
+ * fast Monte-Carlo trace of the smoother matrix (Sec. 2.1), GCV (eq. 22) and
+ * the conditional-variance pass (eq. 23).
+ *
+ * Conventions shared by every call:
+ *  - Every pointer named *_dev is DEVICE memory owned by the caller.  The
+ *    library never allocates device memory: all scratch lives in the
+ *    workspace the caller hands to fkreg_set_workspace.  Host pointers are
+ *    read during the call only.
+ *  - Every call that takes a `stream` (a cudaStream_t passed as void*; NULL =
+ *    legacy default stream) is asynchronous on that stream.  Results are valid
+ *    after the stream is synchronised.
+ *  - No call aborts, traps or prints.  Argument errors return immediately with
+ *    a status and a message in fkreg_last_error().  Errors detected on the
+ *    device (a sample outside the grid box or not finite) set an error word
+ *    that fkreg_sync_status() reports as FKREG_ERR_DEVICE.
+ *  - Arrays are C-contiguous.  Samples are [n][d] (row-major, "AoS").  Grid
+ *    arrays are [..., M_1, ..., M_d] with the last axis fastest.  Complex
+ *    values are interleaved (re, im).  The floating type of every float
+ *    array is the plan's precision: float for FKREG_F32, double for FKREG_F64.
+ *  - Monomials z^g are ordered by total degree and, inside one degree, as
+ *    non-decreasing index tuples: 1, z1, .., zd, z1 z1, z1 z2, .., zd zd.
+ *    ns = C(d + 2l, 2l) s-fields and nt = C(d + l, l) t-fields per response.
+ */
+#ifndef FKREG_H
+#define FKREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fkreg_plan_s* fkreg_plan;
+
+typedef enum {
+  FKREG_OK = 0,
+  FKREG_ERR_INVALID_ARG = 1,  /* bad sizes, non-SPD H, NULL where required   */
+  FKREG_ERR_UNSUPPORTED = 2,  /* a valid request this build does not handle  */
+  FKREG_ERR_WORKSPACE = 3,    /* workspace missing, too small or misaligned  */
+  FKREG_ERR_CUDA = 4,         /* a CUDA runtime call failed                  */
+  FKREG_ERR_CUFFT = 5,        /* a cuFFT call failed                         */
+  FKREG_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up          */
+  FKREG_ERR_DEVICE = 7,       /* device flagged a bad sample (NaN, outside)  */
+  FKREG_ERR_STATE = 8         /* call order violated (e.g. smooth before set_points) */
+} fkreg_status;
+
+enum { FKREG_F32 = 0, FKREG_F64 = 1 };
+enum { FKREG_SPREAD_ES = 0, FKREG_SPREAD_GAUSS = 1 };
+enum { FKREG_KERNEL_GAUSSIAN = 0 };
+
+/* fkreg_opts.flags */
+enum {
+  FKREG_GCV_EXACT_TRACE = 1   /* GCV uses the exact trace K_H(0) sum_i [S(x_i)^-1]_11
+                                 instead of Girard's Monte-Carlo estimate */
+};
+
+/*
+ * Problem description (the arguments of cv_fkreg in Sec. 4 and Table 1).
+ *   dim            d, 1..3
+ *   order          l: 0 = Nadaraya-Watson (eq. 7), 1 = local linear (eq. 3)
+ *   kernel         FKREG_KERNEL_GAUSSIAN (the only kernel whose transform the
+ *                  tolerance controls; Table 1's compact kernels -> UNSUPPORTED)
+ *   spread_kernel  NUFFT spreading kernel: exponential of semicircle (default)
+ *                  or the Gaussian of Sec. 1.2 eq. 17 (about twice as wide)
+ *   precision      FKREG_F32 (spreading, FFT, interpolation in float, FP64
+ *                  per-point solves and reductions) or FKREG_F64 (all double)
+ *   y_complex      0: real responses; 1: complex responses (interleaved)
+ *   grid_n/lo/hi   the grid of eq. 6 per axis: grid_n[j] >= 2 points from
+ *                  grid_lo[j] to grid_hi[j], endpoints included.  Samples
+ *                  must lie inside [lo, hi] (callers clip beforehand).
+ *   n_bw, H        host array [n_bw][d][d] of SPD bandwidth matrices (a
+ *                  per-axis standard deviation sigma_j means H = diag(sigma^2))
+ *   n_rhs          responses that share the geometry (stacked right-hand sides)
+ *   max_probes     largest number of Monte-Carlo probes a later fkreg_df uses
+ *   tol            NUFFT tolerance (e.g. 1e-6 for F32, 1e-12 for F64)
+ *   mask_rho       grid points with s_0(g) < mask_rho * max_g s_0 are masked
+ *                  (NaN estimate, mask byte 0); 0 selects the default 1e-3
+ *   tile           spreading tile edge in fine-grid cells per axis (0 = auto)
+ *   flags          FKREG_GCV_EXACT_TRACE
+ */
+typedef struct {
+  int dim;
+  int order;
+  int kernel;
+  int spread_kernel;
+  int precision;
+  int y_complex;
+  int64_t grid_n[3];
+  double grid_lo[3];
+  double grid_hi[3];
+  int n_bw;
+  const double* H;
+  int n_rhs;
+  int max_probes;
+  double tol;
+  double mask_rho;
+  int tile;
+  int flags;
+} fkreg_opts;
+
+/*
+ * Geometry the planner derives (host only; for inspection and tests).
+ *   delta[j]   grid spacing (hi - lo) / (M_j - 1)            (eq. 6)
+ *   period[j]  P_j = L_j delta_j >= (hi - lo) + kernel tail: the period of the
+ *              Fourier series, chosen so no wrap-around reaches the box
+ *              (the role of the zero padding of eq. 18)
+ *   ldft[j]    L_j, length of the inverse DFT onto the grid lattice (eq. 21)
+ *   modes[j]   K_j, even; Fourier modes |k_j| <= K_j/2 - 1 are kept
+ *   nf[j]      fine (oversampled) grid of the type-1 spreading, >= 2 K_j
+ *   w, beta    spreading width in fine cells and ES shape parameter
+ *   tile[j]    spreading tile edge; nbins[j] = ceil(nf / tile)
+ *   inv_h[j]   the factor nf_j / P_j that maps x - lo to fine-grid units,
+ *              rounded to the plan precision (the bin rule uses it)
+ */
+typedef struct {
+  int dim;
+  double delta[3];
+  double period[3];
+  int64_t ldft[3];
+  int64_t modes[3];
+  int64_t nf[3];
+  int w;
+  double beta;
+  int64_t tile[3];
+  int64_t nbins[3];
+  double inv_h[3];
+  int ns;          /* s-fields */
+  int nt;          /* t-fields per response */
+} fkreg_geometry;
+
+/*
+ * Output buffers of fkreg_smooth / fkreg_df (device; any may be NULL).
+ *   mhat_grid  [n_bw][n_rhs][M]   estimate of eq. 11 on the grid (complex if y_complex)
+ *   mask       [n_bw][M] uint8    1 where s_0(g) >= mask_rho * max s_0
+ *   moments    [n_bw][ns + n_rhs*nt][M]  s-fields then t-fields of eq. 9 on the
+ *              grid (t-fields complex if y_complex)
+ *   mhat_at_x  [n_bw][n_rhs][n]   (S_h y)_i at the samples, ORIGINAL order
+ *   rss        [n_bw][n_rhs] double  ||y - S_h y||^2 (numerator of eq. 22)
+ *   trace      [n_bw][3] double   Girard estimate N mean_p(w^T S w / w^T w)
+ *              (Sec. 2.1), Hutchinson mean_p w^T S w, and the exact trace
+ *              K_H(0) sum_i [S(x_i)^-1]_11 (fkreg_df only)
+ *   gcv        [n_bw][n_rhs] double  eq. 22 (fkreg_df only)
+ */
+typedef struct {
+  void* mhat_grid;
+  uint8_t* mask;
+  void* moments;
+  void* mhat_at_x;
+  double* rss;
+  double* trace;
+  double* gcv;
+} fkreg_outputs;
+
+/* Host-only: validate opts and compute the geometry. No CUDA call is made. */
+fkreg_status fkreg_geometry_query(const fkreg_opts* opts, fkreg_geometry* out);
+
+/*
+ * Host-only: the Fourier transform of the spreading kernel,
+ * phihat[k] = integral over |z| <= w/2 of phi(z) cos(2 pi k z / nf) dz for
+ * k = 0..nk-1 (Gauss-Legendre quadrature in FP64).  The deconvolution of
+ * eq. 20 divides by it.  kind: FKREG_SPREAD_ES or FKREG_SPREAD_GAUSS.
+ */
+fkreg_status fkreg_spread_kernel_ft(int kind, int w, double beta, int64_t nf,
+                                    int64_t nk, double* phihat);
+
+/*
+ * Create a plan for up to max_n samples.  Computes the geometry and the
+ * spreading-kernel tables on the host and creates the cuFFT plans (needs a
+ * current CUDA device).  The plan owns host tables and cuFFT handles only.
+ */
+fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan* out);
+
+/* Bytes of device workspace the plan needs (256-byte aligned start). */
+fkreg_status fkreg_workspace_bytes(fkreg_plan plan, size_t* bytes);
+
+/* Hand the plan its workspace and upload the small tables (async on stream). */
+fkreg_status fkreg_set_workspace(fkreg_plan plan, void* ws_dev, size_t bytes, void* stream);
+
+/*
+ * Bin and sort the samples x_dev [n][d] (plan precision), n <= max_n.
+ * Each sample gets the bin of its fine-grid cell (floor of
+ * fl(fl(x_j - lo_j) * inv_h_j), computed with round-to-nearest IEEE
+ * operations and no fused multiply-add) and the samples are reordered by a
+ * stable counting sort: the permutation is unique and bit-exact.  All later
+ * calls share this geometry until the next fkreg_set_points.
+ */
+fkreg_status fkreg_set_points(fkreg_plan plan, int64_t n, const void* x_dev, void* stream);
+
+/*
+ * Copy the sort result: perm_dev[s] = original index of the s-th sorted
+ * sample (uint32, n entries) and bin_start_dev (uint32, nbins+1 entries,
+ * exclusive prefix sum of the bin counts).  Either pointer may be NULL.
+ */
+fkreg_status fkreg_get_sort(fkreg_plan plan, uint32_t* perm_dev, uint32_t* bin_start_dev,
+                            int64_t* nbins, void* stream);
+
+/*
+ * Smooth the responses y_dev [n_rhs][n] (complex interleaved if y_complex)
+ * for every bandwidth of the plan: grid estimates and/or values at the
+ * samples, per the non-NULL members of `out` (trace and gcv are ignored).
+ */
+fkreg_status fkreg_smooth(fkreg_plan plan, const void* y_dev, const fkreg_outputs* out,
+                          void* stream);
+
+/*
+ * Smooth y together with n_probes Gaussian probe vectors w_p (Sec. 2.1) and
+ * return the DF estimates and GCV (eq. 22) for every bandwidth, plus any of
+ * the smoothing outputs.  probes_dev [n_probes][n] (plan precision, ORIGINAL
+ * sample order) or NULL: then probe (p, i) is drawn on the device from the
+ * counter-based generator c = splitmix64(seed XOR splitmix64((p << 40) XOR i)),
+ * u1 = ((c >> 11) + 1) 2^-53, u2 = (splitmix64(c) >> 11) 2^-53,
+ * w = sqrt(-2 ln u1) cos(2 pi u2).  n_probes <= max_probes.
+ */
+fkreg_status fkreg_df(fkreg_plan plan, const void* y_dev, int n_probes, uint64_t seed,
+                      const void* probes_dev, const fkreg_outputs* out, void* stream);
+
+/*
+ * Conditional-variance pass (Sec. 3, eq. 23): smooth r_i = |y_i - mhat(x_i)|^2
+ * with the plan's order and bandwidths, reusing the s-field spectrum of the
+ * last fkreg_smooth / fkreg_df on these points.  mhat_at_x_dev is that call's
+ * mhat_at_x output [n_bw][n_rhs][n] (original order); bandwidth b's residuals
+ * are smoothed with bandwidth b.  sigma2_grid_dev [n_bw][n_rhs][M] (real).
+ */
+fkreg_status fkreg_variance(fkreg_plan plan, const void* y_dev, const void* mhat_at_x_dev,
+                            void* sigma2_grid_dev, void* stream);
+
+/* Synchronise the stream and report device-detected errors (then clear them). */
+fkreg_status fkreg_sync_status(fkreg_plan plan, void* stream);
+
+/* Message of the last failing call on this plan ("" if none). */
+const char* fkreg_last_error(fkreg_plan plan);
+
+/* Message of the last failing plan-less call (geometry query, create). */
+const char* fkreg_global_error(void);
+
+void fkreg_plan_destroy(fkreg_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FKREG_H */

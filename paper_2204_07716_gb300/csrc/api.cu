@@ -1,0 +1,467 @@
+// C ABI: plan lifetime, workspace layout and the stage launcher.
+//
+// One fkreg_smooth / fkreg_df call runs, on the caller's stream:
+//   strengths (density 1, responses, probes) in sorted order
+//   -> type-1 spreading -> forward FFT (cuFFT)
+//   -> grid stage: kernel multiply + fold -> inverse FFT -> FP64 grid solve
+//   -> sample stage, per bandwidth: kernel multiply / deconvolve onto that
+//      bandwidth's fine grid -> inverse FFT -> interpolation + at-sample
+//      solve + reductions
+//   -> DF / GCV finalisation.
+// No host synchronisation happens inside a call.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+using fk::Region;
+
+namespace {
+
+std::string g_last_error;
+std::mutex g_mu;
+
+fkreg_status set_global_error(fkreg_status st, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_last_error = msg;
+  return st;
+}
+
+fkreg_status plan_err(fkreg_plan_s* P, fkreg_status st, const std::string& msg) {
+  if (P) P->err = msg;
+  return st;
+}
+
+fkreg_status cuda_err(fkreg_plan_s* P, cudaError_t e, const char* where) {
+  return plan_err(P, FKREG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+
+struct Layout {
+  size_t cur = 0;
+  void take(Region& r, size_t bytes) {
+    cur = (cur + kAlign - 1) / kAlign * kAlign;
+    r.off = cur;
+    r.bytes = bytes;
+    cur += std::max<size_t>(bytes, 1);
+  }
+};
+
+int64_t half_cells(const int64_t* n, int d) {
+  int64_t h = 1;
+  for (int a = 0; a < d; ++a) h *= (a == d - 1) ? (n[a] / 2 + 1) : n[a];
+  return h;
+}
+
+int64_t full_cells(const int64_t* n, int d) {
+  int64_t h = 1;
+  for (int a = 0; a < d; ++a) h *= n[a];
+  return h;
+}
+
+}  // namespace
+
+namespace fk {
+
+// kind 0: forward R2C, kind 1: inverse C2R
+fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, cufftHandle* h) {
+  auto key = std::make_tuple(kind, dims[0], P->d > 1 ? dims[1] : 1, P->d > 2 ? dims[2] : 1, batch);
+  auto it = P->ffts.find(key);
+  if (it != P->ffts.end()) {
+    *h = it->second;
+    return FKREG_OK;
+  }
+  cufftHandle hd;
+  if (cufftCreate(&hd) != CUFFT_SUCCESS) return plan_err(P, FKREG_ERR_CUFFT, "cufftCreate failed");
+  cufftSetAutoAllocation(hd, 0);
+  long long n[3] = {dims[0], dims[1], dims[2]};
+  cufftType type;
+  if (P->prec == FKREG_F32)
+    type = kind == 0 ? CUFFT_R2C : CUFFT_C2R;
+  else
+    type = kind == 0 ? CUFFT_D2Z : CUFFT_Z2D;
+  size_t work = 0;
+  cufftResult r = cufftMakePlanMany64(hd, P->d, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &work);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(hd);
+    return plan_err(P, FKREG_ERR_CUFFT, "cufftMakePlanMany64 failed (" + std::to_string(int(r)) + ")");
+  }
+  if (P->ws && work > P->r_fftwork.bytes) {
+    cufftDestroy(hd);
+    return plan_err(P, FKREG_ERR_WORKSPACE, "cuFFT work area larger than the reserved region");
+  }
+  if (P->ws) cufftSetWorkArea(hd, P->ws + P->r_fftwork.off);
+  P->fft_work_reserved = std::max(P->fft_work_reserved, work);
+  P->ffts[key] = hd;
+  *h = hd;
+  return FKREG_OK;
+}
+
+}  // namespace fk
+
+extern "C" {
+
+fkreg_status fkreg_geometry_query(const fkreg_opts* opts, fkreg_geometry* out) {
+  std::string err;
+  fkreg_status st = fk::compute_geometry(opts, out, &err, nullptr, nullptr, nullptr, nullptr);
+  if (st != FKREG_OK) set_global_error(st, err);
+  return st;
+}
+
+fkreg_status fkreg_spread_kernel_ft(int kind, int w, double beta, int64_t nf, int64_t nk,
+                                    double* phihat) {
+  if (!phihat || w < 2 || w > 32 || nf < 2 || nk < 0 || !(beta > 0))
+    return set_global_error(FKREG_ERR_INVALID_ARG, "fkreg_spread_kernel_ft: bad arguments");
+  if (kind != FKREG_SPREAD_ES && kind != FKREG_SPREAD_GAUSS)
+    return set_global_error(FKREG_ERR_INVALID_ARG, "fkreg_spread_kernel_ft: bad kind");
+  fk::spread_phihat(kind, w, beta, nf, nk, phihat);
+  return FKREG_OK;
+}
+
+const char* fkreg_global_error(void) { return g_last_error.c_str(); }
+
+fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan* out) {
+  if (!out) return set_global_error(FKREG_ERR_INVALID_ARG, "out must be non-NULL");
+  *out = nullptr;
+  if (max_n < 0 || max_n > (int64_t(1) << 31))
+    return set_global_error(FKREG_ERR_INVALID_ARG, "max_n must lie in [0, 2^31]");
+  auto* P = new fkreg_plan_s();
+  std::string err;
+  fkreg_status st = fk::compute_geometry(opts, &P->g, &err, &P->bw, &P->tab, P->phi1_off, &P->geo);
+  if (st != FKREG_OK) {
+    delete P;
+    return set_global_error(st, err);
+  }
+  P->o = *opts;
+  const int d = opts->dim;
+  P->H.assign(opts->H, opts->H + size_t(opts->n_bw) * d * d);
+  P->o.H = P->H.data();
+  P->max_n = max_n;
+  P->d = d;
+  P->order = opts->order;
+  P->prec = opts->precision;
+  P->tsize = P->prec == FKREG_F32 ? 4 : 8;
+  P->ns = P->g.ns;
+  P->nt = P->g.nt;
+  P->p = P->nt;
+  P->nbw = opts->n_bw;
+  P->nrhs = opts->n_rhs;
+  P->nrhs_real = opts->n_rhs * (opts->y_complex ? 2 : 1);
+  P->max_probes = opts->max_probes;
+  P->mono.n = P->ns;
+  P->mono.nt = P->nt;
+  fk::monomials(d, 2 * P->order, P->mono.e);
+  P->smax = 1 + P->nrhs_real + P->max_probes;
+  P->f2max = P->ns + (P->nrhs_real + P->max_probes) * P->nt;
+  P->fgrid = P->ns + P->nrhs_real * P->nt;
+  P->nacc = P->nrhs_real + 2 * P->max_probes + 1;
+  if (P->nacc > 512) {
+    delete P;
+    return set_global_error(FKREG_ERR_UNSUPPORTED, "n_rhs (real parts) + 2 max_probes must be <= 511");
+  }
+  if (P->nt * (P->nrhs_real + P->max_probes) + P->ns > 4096) {
+    delete P;
+    return set_global_error(FKREG_ERR_UNSUPPORTED, "too many fields");
+  }
+  int64_t nb = 1;
+  for (int a = 0; a < d; ++a) nb *= P->g.nbins[a];
+  P->nbins_total = nb;
+  P->nsub_max = nb + (max_n + fk::kSubMax - 1) / fk::kSubMax;
+  P->nblk_interp = 152 * 8;
+  // tile + halo must fit shared memory for one strength
+  {
+    size_t cells = 1;
+    for (int a = 0; a < d; ++a) cells *= size_t(P->g.tile[a] + 2 * ((P->g.w + 1) / 2));
+    if (cells * P->tsize > 200 * 1024) {
+      delete P;
+      return set_global_error(FKREG_ERR_UNSUPPORTED, "spreading tile too large for shared memory");
+    }
+  }
+  // device
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete P;
+    return set_global_error(FKREG_ERR_CUDA, "no CUDA device");
+  }
+  // workspace layout
+  const size_t T = P->tsize;
+  const int64_t nf_cells = full_cells(P->g.nf, d), nf_half = half_cells(P->g.nf, d);
+  const int64_t l_cells = full_cells(P->g.ldft, d), l_half = half_cells(P->g.ldft, d);
+  int64_t t2_cells = 1, t2_half = 1;
+  for (const auto& B : P->bw) {
+    t2_cells = std::max(t2_cells, full_cells(B.nf, d));
+    t2_half = std::max(t2_half, half_cells(B.nf, d));
+  }
+  const int64_t ntiles = (max_n + 4095) / 4096;
+  const int64_t scan_len = std::max<int64_t>(256 * ntiles, nb + 1);
+  Layout L;
+  L.take(P->r_err, 256);
+  L.take(P->r_bw, sizeof(fk::BwDev) * P->nbw);
+  L.take(P->r_tab, sizeof(double) * std::max<size_t>(1, P->tab.size()));
+  L.take(P->r_xs, T * d * std::max<int64_t>(1, max_n));
+  for (Region* r : {&P->r_keys0, &P->r_vals0, &P->r_keys1, &P->r_vals1})
+    L.take(*r, 4 * std::max<int64_t>(1, max_n));
+  L.take(P->r_counts, 4 * nb);
+  L.take(P->r_binstart, 4 * (nb + 1));
+  L.take(P->r_nsub, 4 * nb);
+  L.take(P->r_substart, 4 * (nb + 1));
+  L.take(P->r_subbin, 4 * P->nsub_max);
+  L.take(P->r_subfirst, 4 * P->nsub_max);
+  L.take(P->r_hist, 4 * (256 * ntiles + 1));
+  L.take(P->r_scan, 4 * (scan_len / 1024 + 2));
+  L.take(P->r_str, T * P->smax * std::max<int64_t>(1, max_n));
+  L.take(P->r_fine, T * P->smax * nf_cells);
+  L.take(P->r_spec, 2 * T * P->smax * nf_half);
+  L.take(P->r_gspec, 2 * T * size_t(P->nbw) * P->fgrid * l_half);
+  L.take(P->r_gfield, T * size_t(P->nbw) * P->fgrid * l_cells);
+  L.take(P->r_t2spec, 2 * T * size_t(P->f2max) * t2_half);
+  L.take(P->r_t2field, T * size_t(P->f2max) * t2_cells);
+  L.take(P->r_part, sizeof(double) * size_t(P->nblk_interp + 1) * P->nbw * P->nacc);
+  L.take(P->r_smax, 8 * size_t(P->nbw));
+  // cuFFT plans for the standard passes (work sizes decide the reserved area)
+  {
+    int64_t dims[3];
+    cufftHandle h;
+    std::vector<int> fwd_batches = {1 + P->nrhs_real, P->nrhs};
+    if (P->max_probes > 0) fwd_batches.push_back(P->smax);
+    for (int bt : fwd_batches) {
+      for (int a = 0; a < 3; ++a) dims[a] = P->g.nf[a];
+      if ((st = fk::fft_get(P, 0, dims, bt, &h)) != FKREG_OK) {
+        std::string m = P->err;
+        fkreg_plan_destroy(P);
+        return set_global_error(st, m);
+      }
+    }
+    for (int a = 0; a < 3; ++a) dims[a] = P->g.ldft[a];
+    for (int bt : {P->nbw * P->fgrid, P->ns + P->nrhs * P->nt}) {
+      if ((st = fk::fft_get(P, 1, dims, bt, &h)) != FKREG_OK) {
+        std::string m = P->err;
+        fkreg_plan_destroy(P);
+        return set_global_error(st, m);
+      }
+    }
+    for (const auto& B : P->bw) {
+      for (int a = 0; a < 3; ++a) dims[a] = B.nf[a];
+      std::vector<int> bts = {P->ns + P->nrhs_real * P->nt};
+      if (P->max_probes > 0) bts.push_back(P->f2max);
+      for (int bt : bts)
+        if ((st = fk::fft_get(P, 1, dims, bt, &h)) != FKREG_OK) {
+          std::string m = P->err;
+          fkreg_plan_destroy(P);
+          return set_global_error(st, m);
+        }
+    }
+  }
+  L.take(P->r_fftwork, std::max<size_t>(P->fft_work_reserved, 256));
+  P->ws_bytes = L.cur + kAlign;
+  *out = P;
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_workspace_bytes(fkreg_plan P, size_t* bytes) {
+  if (!P || !bytes) return FKREG_ERR_INVALID_ARG;
+  *bytes = P->ws_bytes;
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_set_workspace(fkreg_plan P, void* ws, size_t bytes, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (!ws) return plan_err(P, FKREG_ERR_WORKSPACE, "workspace pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign)
+    return plan_err(P, FKREG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < P->ws_bytes)
+    return plan_err(P, FKREG_ERR_WORKSPACE,
+                    "workspace too small: need " + std::to_string(P->ws_bytes) + " bytes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  P->ws = static_cast<char*>(ws);
+  P->ws_given = bytes;
+  for (auto& kv : P->ffts)
+    if (cufftSetWorkArea(kv.second, P->ws + P->r_fftwork.off) != CUFFT_SUCCESS)
+      return plan_err(P, FKREG_ERR_CUFFT, "cufftSetWorkArea failed");
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->ws + P->r_err.off, 0, 256, s)) != cudaSuccess) return cuda_err(P, e, "memset");
+  if ((e = cudaMemcpyAsync(P->ws + P->r_bw.off, P->bw.data(), sizeof(fk::BwDev) * P->nbw,
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_err(P, e, "upload bandwidth table");
+  if (!P->tab.empty() &&
+      (e = cudaMemcpyAsync(P->ws + P->r_tab.off, P->tab.data(), sizeof(double) * P->tab.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_err(P, e, "upload tables");
+  // the host tables must outlive the copies: wait for them
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(P, e, "sync");
+  P->points_set = false;
+  P->dens_valid = false;
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_set_points(fkreg_plan P, int64_t n, const void* x, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (!P->ws) return plan_err(P, FKREG_ERR_STATE, "fkreg_set_workspace must come first");
+  if (n < 0 || n > P->max_n) return plan_err(P, FKREG_ERR_INVALID_ARG, "n must lie in [0, max_n]");
+  if (n > 0 && !x) return plan_err(P, FKREG_ERR_INVALID_ARG, "x is NULL");
+  P->n = n;
+  P->points_set = false;
+  P->dens_valid = false;
+  cudaError_t e = fk::run_sort(P, n, x, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_err(P, e, "bin sort");
+  P->points_set = true;
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_get_sort(fkreg_plan P, uint32_t* perm, uint32_t* bin_start, int64_t* nbins,
+                            void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (nbins) *nbins = P->nbins_total;
+  if (!P->points_set) return plan_err(P, FKREG_ERR_STATE, "fkreg_set_points must come first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (perm && P->n > 0 &&
+      (e = cudaMemcpyAsync(perm, fk::perm_ptr(P), 4 * P->n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_err(P, e, "copy perm");
+  if (bin_start &&
+      (e = cudaMemcpyAsync(bin_start, P->ws + P->r_binstart.off, 4 * (P->nbins_total + 1),
+                           cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_err(P, e, "copy bin_start");
+  return FKREG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+fkreg_status exec_fft(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, void* in, void* out,
+                      cudaStream_t s) {
+  cufftHandle h;
+  fkreg_status st = fk::fft_get(P, kind, dims, batch, &h);
+  if (st != FKREG_OK) return st;
+  if (cufftSetStream(h, s) != CUFFT_SUCCESS) return plan_err(P, FKREG_ERR_CUFFT, "cufftSetStream failed");
+  cufftResult r;
+  if (P->prec == FKREG_F32) {
+    r = kind == 0 ? cufftExecR2C(h, static_cast<cufftReal*>(in), static_cast<cufftComplex*>(out))
+                  : cufftExecC2R(h, static_cast<cufftComplex*>(in), static_cast<cufftReal*>(out));
+  } else {
+    r = kind == 0 ? cufftExecD2Z(h, static_cast<cufftDoubleReal*>(in), static_cast<cufftDoubleComplex*>(out))
+                  : cufftExecZ2D(h, static_cast<cufftDoubleComplex*>(in), static_cast<cufftDoubleReal*>(out));
+  }
+  if (r != CUFFT_SUCCESS) return plan_err(P, FKREG_ERR_CUFFT, "cuFFT exec failed (" + std::to_string(int(r)) + ")");
+  return FKREG_OK;
+}
+
+#define FK_CHECK(call, what)                         \
+  do {                                               \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) return cuda_err(P, _e, what); \
+  } while (0)
+#define FK_STATUS(call)                 \
+  do {                                  \
+    fkreg_status _s = (call);           \
+    if (_s != FKREG_OK) return _s;      \
+  } while (0)
+
+fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t seed, const void* probes,
+                      const fkreg_outputs* out, bool want_df, cudaStream_t s) {
+  if (!P->ws) return plan_err(P, FKREG_ERR_STATE, "fkreg_set_workspace must come first");
+  if (!P->points_set) return plan_err(P, FKREG_ERR_STATE, "fkreg_set_points must come first");
+  if (P->n > 0 && !y) return plan_err(P, FKREG_ERR_INVALID_ARG, "y is NULL");
+  if (n_probes < 0 || n_probes > P->max_probes)
+    return plan_err(P, FKREG_ERR_INVALID_ARG, "n_probes must lie in [0, max_probes]");
+  const int d = P->d;
+  const int S = 1 + P->nrhs_real + n_probes;
+  const size_t T = P->tsize;
+  const int64_t nf_cells = full_cells(P->g.nf, d);
+  (void)nf_cells;
+  P->dens_valid = false;
+  FK_CHECK(fk::run_gather_strengths(P, y, 0, n_probes, seed, probes, 1, s), "strengths");
+  FK_CHECK(fk::run_spread(P, 0, S, s), "spread");
+  FK_STATUS(exec_fft(P, 0, P->g.nf, S, P->ws + P->r_fine.off, P->ws + P->r_spec.off, s));
+  const bool grid = out && (out->mhat_grid || out->mask || out->moments);
+  if (grid) {
+    FK_CHECK(fk::run_kmul_grid(P, 0, 1, P->nrhs_real, 0, P->nbw, P->ws + P->r_gspec.off, s), "kmul grid");
+    FK_STATUS(exec_fft(P, 1, P->g.ldft, P->nbw * P->fgrid, P->ws + P->r_gspec.off,
+                       P->ws + P->r_gfield.off, s));
+    FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, nullptr, out, nullptr, s), "grid solve");
+  }
+  const bool at = want_df || n_probes > 0 || (out && (out->mhat_at_x || out->rss));
+  if (at) {
+    const int n_rhs_str = P->nrhs_real + n_probes;
+    const int f2 = P->ns + n_rhs_str * P->nt;
+    for (int b = 0; b < P->nbw; ++b) {
+      FK_CHECK(fk::run_kmul_t2(P, b, 0, 1, n_rhs_str, s), "kmul type-2");
+      FK_STATUS(exec_fft(P, 1, P->bw[b].nf, f2, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
+      FK_CHECK(fk::run_interp(P, b, P->nrhs_real, n_probes, y, out ? out->mhat_at_x : nullptr, s),
+               "interpolation");
+    }
+    FK_CHECK(fk::run_finalize(P, n_probes, out, s), "finalize");
+  }
+  (void)T;
+  P->dens_valid = true;
+  return FKREG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fkreg_status fkreg_smooth(fkreg_plan P, const void* y, const fkreg_outputs* out, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  return pipeline(P, y, 0, 0, nullptr, out, false, static_cast<cudaStream_t>(stream));
+}
+
+fkreg_status fkreg_df(fkreg_plan P, const void* y, int n_probes, uint64_t seed, const void* probes,
+                      const fkreg_outputs* out, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (n_probes < 1) return plan_err(P, FKREG_ERR_INVALID_ARG, "fkreg_df needs n_probes >= 1");
+  return pipeline(P, y, n_probes, seed, probes, out, true, static_cast<cudaStream_t>(stream));
+}
+
+fkreg_status fkreg_variance(fkreg_plan P, const void* y, const void* mhat_at_x, void* sigma2,
+                            void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (!P->dens_valid)
+    return plan_err(P, FKREG_ERR_STATE, "fkreg_variance must follow fkreg_smooth/fkreg_df on the same points");
+  if (P->n > 0 && (!y || !mhat_at_x)) return plan_err(P, FKREG_ERR_INVALID_ARG, "y and mhat_at_x are required");
+  if (!sigma2) return plan_err(P, FKREG_ERR_INVALID_ARG, "sigma2_grid is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d = P->d;
+  const int64_t nf_cells = full_cells(P->g.nf, d), nf_half = half_cells(P->g.nf, d);
+  const int R = P->nrhs;
+  for (int b = 0; b < P->nbw; ++b) {
+    FK_CHECK(fk::run_residual_strengths(P, y, mhat_at_x, b, 1, s), "residuals");
+    FK_CHECK(fk::run_spread(P, 1, R, s), "spread");
+    FK_STATUS(exec_fft(P, 0, P->g.nf, R, P->ws + P->r_fine.off + P->tsize * nf_cells,
+                       P->ws + P->r_spec.off + 2 * P->tsize * nf_half, s));
+    FK_CHECK(fk::run_kmul_grid(P, 0, 1, R, b, 1, P->ws + P->r_gspec.off, s), "kmul grid");
+    FK_STATUS(exec_fft(P, 1, P->g.ldft, P->ns + R * P->nt, P->ws + P->r_gspec.off,
+                       P->ws + P->r_gfield.off, s));
+    FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, sigma2, s), "grid solve");
+  }
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_sync_status(fkreg_plan P, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_err(P, e, "stream");
+  if (!P->ws) return FKREG_OK;
+  int word = 0;
+  if ((e = cudaMemcpy(&word, P->ws + P->r_err.off, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_err(P, e, "read error word");
+  if (word) {
+    cudaMemset(P->ws + P->r_err.off, 0, sizeof(int));
+    return plan_err(P, FKREG_ERR_DEVICE, "a sample lies outside the grid box or is not finite");
+  }
+  return FKREG_OK;
+}
+
+const char* fkreg_last_error(fkreg_plan P) { return P ? P->err.c_str() : ""; }
+
+void fkreg_plan_destroy(fkreg_plan P) {
+  if (!P) return;
+  for (auto& kv : P->ffts) cufftDestroy(kv.second);
+  delete P;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations shared by the planner, the kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fkreg.h"
+
+namespace fk {
+
+constexpr int kMaxD = 3;
+constexpr int kMaxMono = 10;     // monomials of degree <= 2 in 3-D
+constexpr int kMaxP = 4;         // unknowns of the local-linear system in 3-D
+constexpr int kSubMax = 1024;    // samples per spreading sub-problem
+constexpr int kRadixBits = 8;
+
+// Geometry of the whole plan, passed to kernels by value.
+struct GeoDev {
+  int d;
+  int w;            // spreading width (fine cells)
+  int pad;          // ceil(w/2): tile halo on each side
+  int skind;        // FKREG_SPREAD_ES / FKREG_SPREAD_GAUSS
+  double beta;      // ES shape, or Gaussian exponent factor
+  int64_t nf[3];    // type-1 fine grid
+  int64_t L[3];     // inverse-DFT length onto the grid lattice
+  int64_t M[3];     // output grid points
+  int64_t K[3];     // type-1 modes (kept: |k| <= K/2 - 1)
+  double P[3];      // period
+  double lo[3];
+  double hi[3];
+  double inv_h[3];  // nf / P (double; the T-rounded copy is inv_h_t)
+  float inv_h_f[3];
+  int64_t tile[3];
+  int64_t nbins[3];
+};
+
+// One bandwidth, stored in the workspace (device reads it).
+struct BwDev {
+  double H[9];
+  double sigma[3];     // sqrt(H_jj)
+  double k0;           // K_H(0)
+  int64_t K[3];        // modes this bandwidth needs
+  int64_t nf[3];       // type-2 fine grid for this bandwidth
+  double inv_h[3];     // nf_b / P
+  int64_t phi2_off[3]; // offset (doubles) of 1/phihat tables (k >= 0) for type-2
+};
+
+// Monomial exponents (degree <= 2) for device code.
+struct MonoTab {
+  int n;               // monomials of degree <= 2l  (s-fields)
+  int nt;              // monomials of degree <= l   (t-fields)
+  int e[kMaxMono][kMaxD];
+};
+
+struct Region {
+  size_t off = 0, bytes = 0;
+};
+
+}  // namespace fk
+
+struct fkreg_plan_s {
+  fkreg_opts o{};
+  std::vector<double> H;        // [nbw][d][d]
+  fkreg_geometry g{};
+  fk::GeoDev geo{};
+  fk::MonoTab mono{};
+  int64_t max_n = 0;
+  int d = 0, order = 0, prec = 0, ns = 0, nt = 0, p = 0;
+  int nbw = 0, nrhs = 0, nrhs_real = 0, max_probes = 0;
+  int smax = 0;                 // strengths of the largest pass
+  int f2max = 0;                // type-2 fields of the largest pass
+  int fgrid = 0;                // grid fields (ns + nrhs_real * nt)
+  size_t tsize = 4;             // sizeof(T)
+  std::vector<fk::BwDev> bw;    // host copy of the bandwidth table
+  std::vector<double> tab;      // 1/phihat tables (type-1 per axis, then type-2)
+  int64_t phi1_off[3] = {0, 0, 0};
+  int64_t nbins_total = 0;
+  int64_t nsub_max = 0;
+  int64_t nblk_interp = 0;      // blocks of the interpolation kernel (partials)
+  int nacc = 0;                 // accumulators per (block, bandwidth)
+
+  // workspace regions
+  fk::Region r_err, r_bw, r_tab, r_xs, r_keys0, r_vals0, r_keys1, r_vals1, r_counts,
+      r_binstart, r_nsub, r_substart, r_subbin, r_subfirst, r_hist, r_scan, r_str,
+      r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork;
+  size_t ws_bytes = 0;
+  size_t fft_work_reserved = 0;
+  char* ws = nullptr;
+  size_t ws_given = 0;
+
+  // cuFFT plan cache: (kind, n0, n1, n2, batch) -> handle
+  std::map<std::tuple<int, int64_t, int64_t, int64_t, int>, cufftHandle> ffts;
+
+  // state
+  int64_t n = 0;
+  bool points_set = false;
+  bool dens_valid = false;
+  int perm_in_vals1 = 0;        // which ping-pong buffer holds the permutation
+  std::string err;
+  int device = -1;
+};
+
+namespace fk {
+
+// planner.cpp
+fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::string* err,
+                              std::vector<BwDev>* bw, std::vector<double>* tab,
+                              int64_t phi1_off[3], GeoDev* geo);
+double spread_phi(int kind, int w, double beta, double z);
+void spread_phihat(int kind, int w, double beta, int64_t nf, int64_t nk, double* out);
+int nmono(int d, int deg);
+void monomials(int d, int deg, int (*e)[kMaxD]);
+int64_t next_fast(int64_t n);
+
+// sort.cu
+cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s);
+
+// spread.cu
+cudaError_t run_spread(fkreg_plan_s* P, int s0, int ns_count, cudaStream_t s);
+cudaError_t run_gather_strengths(fkreg_plan_s* P, const void* y, int first_str, int n_probes,
+                                 uint64_t seed, const void* probes, int with_density,
+                                 cudaStream_t s);
+cudaError_t run_residual_strengths(fkreg_plan_s* P, const void* y, const void* mhat_at_x,
+                                   int b, int first_str, cudaStream_t s);
+
+// spectral.cu
+cudaError_t run_kmul_grid(fkreg_plan_s* P, int str_dens, int str_rhs, int nrhs_fields,
+                          int bw_first, int bw_count, void* out_spec, cudaStream_t s);
+cudaError_t run_kmul_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
+                        cudaStream_t s);
+
+// solve.cu
+cudaError_t run_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int nrhs_fields,
+                           const void* y_complex_flag_dummy, const fkreg_outputs* out,
+                           void* sigma2, cudaStream_t s);
+cudaError_t run_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, const void* y,
+                       void* mhat_at_x, cudaStream_t s);
+cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out,
+                         cudaStream_t s);
+
+const uint32_t* perm_ptr(fkreg_plan_s* P);
+
+// fft helpers (api.cu)
+fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, cufftHandle* h);
+
+template <typename T>
+T* wsp(fkreg_plan_s* P, const Region& r) {
+  return reinterpret_cast<T*>(P->ws + r.off);
+}
+
+}  // namespace fk

@@ -1,0 +1,320 @@
+// Bin assignment and stable counting sort of the samples.
+//
+// Every sample gets the spreading bin that holds its fine-grid cell:
+//   u_j   = fl(fl(x_j - lo_j) * inv_h_j)      (round-to-nearest, no FMA)
+//   c_j   = min(floor(u_j), nf_j - 1)
+//   bin   = row-major index of (c_j / tile_j)
+// The samples are then ordered by bin with a least-significant-digit radix
+// sort (8-bit digits).  Each pass is a stable counting sort: per-tile digit
+// histograms, one exclusive scan over (digit, tile), and a scatter that ranks
+// equal digits inside a tile in index order with warp match masks.  The
+// resulting permutation is therefore unique: bin first, original index second.
+// The paper bins the samples onto the grid too (Sec. 1.1, O(N) gridding); the
+// counting sort is this implementation's own device-side organisation of it.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace fk {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;                      // keys per thread per tile
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per tile
+constexpr int kScanThreads = 256;
+constexpr int kScanChunk = 1024;                     // elements per scan block
+
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T inv_h_of(const GeoDev& g, int j);
+template <>
+__device__ __forceinline__ float inv_h_of<float>(const GeoDev& g, int j) { return g.inv_h_f[j]; }
+template <>
+__device__ __forceinline__ double inv_h_of<double>(const GeoDev& g, int j) { return g.inv_h[j]; }
+
+template <typename T>
+__global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
+                                uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                uint32_t* __restrict__ counts, int* __restrict__ errw) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t key = 0;
+  bool bad = false;
+  for (int j = 0; j < g.d; ++j) {
+    T xv = x[i * g.d + j];
+    const T lo = T(g.lo[j]), hi = T(g.hi[j]);
+    if (!(xv >= lo && xv <= hi)) {
+      bad = true;
+      xv = lo;
+    }
+    const T u = mul_rn(sub_rn(xv, lo), inv_h_of<T>(g, j));
+    int64_t c = int64_t(floor(u));
+    if (c < 0) c = 0;
+    if (c > g.nf[j] - 1) c = g.nf[j] - 1;
+    key = key * uint32_t(g.nbins[j]) + uint32_t(c / g.tile[j]);
+  }
+  if (bad) atomicOr(errw, 1);
+  keys[i] = key;
+  vals[i] = uint32_t(i);
+  atomicAdd(&counts[key], 1u);
+}
+
+// ---- exclusive scan of uint32 (three kernels, any length) ----------------
+__global__ void scan_block_sums(const uint32_t* __restrict__ in, int64_t n,
+                                uint32_t* __restrict__ sums) {
+  __shared__ uint32_t red[kScanThreads / 32];
+  const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+  uint32_t s = 0;
+  for (int k = threadIdx.x; k < kScanChunk; k += kScanThreads) {
+    int64_t i = base + k;
+    if (i < n) s += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of `sums` in place by one block, chunk after chunk.
+__global__ void scan_sums_single(uint32_t* __restrict__ sums, int64_t nb, uint32_t* total) {
+  __shared__ uint32_t buf[1024];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    uint32_t v = (i < nb) ? sums[i] : 0u;
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    // Hillis-Steele inclusive scan
+    for (int o = 1; o < 1024; o <<= 1) {
+      uint32_t t = (threadIdx.x >= o) ? buf[threadIdx.x - o] : 0u;
+      __syncthreads();
+      buf[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) sums[i] = carry + buf[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += buf[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// out[i] = offset(block) + exclusive prefix inside the block; in may alias out.
+__global__ void scan_apply(const uint32_t* in, int64_t n, const uint32_t* __restrict__ sums,
+                           uint32_t* out) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+  constexpr int per = kScanChunk / kScanThreads;  // 4 consecutive elements per thread
+  uint32_t v[per];
+  uint32_t run = 0;
+  for (int k = 0; k < per; ++k) {
+    int64_t i = base + threadIdx.x * per + k;
+    v[k] = (i < n) ? in[i] : 0u;
+    run += v[k];
+  }
+  // warp inclusive scan of per-thread totals
+  uint32_t inc = run;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t woff = 0;
+  for (int w = 0; w < warp; ++w) woff += wsum[w];
+  uint32_t off = sums[blockIdx.x] + woff + inc - run;
+  for (int k = 0; k < per; ++k) {
+    int64_t i = base + threadIdx.x * per + k;
+    if (i < n) out[i] = off;
+    off += v[k];
+  }
+}
+
+// ---- radix sort passes ---------------------------------------------------
+__global__ void radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                              int64_t ntiles, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    int64_t i = base + int64_t(r) * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[int64_t(threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void radix_downsweep(const uint32_t* __restrict__ keys_in,
+                                const uint32_t* __restrict__ vals_in, int64_t n, int shift,
+                                int64_t ntiles, const uint32_t* __restrict__ hist_scanned,
+                                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+  __shared__ uint32_t wcnt[kSortThreads / 32][257];
+  __shared__ uint32_t base_off[256];
+  __shared__ uint32_t running[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  running[tid] = hist_scanned[int64_t(tid) * ntiles + blockIdx.x];
+  const int64_t tbase = int64_t(blockIdx.x) * kSortTile;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < kSortRounds; ++r) {
+    for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][tid] = 0;
+    if (tid == 0)
+      for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][256] = 0;
+    __syncthreads();
+    const int64_t i = tbase + int64_t(r) * kSortThreads + tid;
+    const bool valid = i < n;
+    uint32_t key = 0, val = 0, dig = 256;
+    if (valid) {
+      key = keys_in[i];
+      val = vals_in[i];
+      dig = (key >> shift) & 255u;
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+    const uint32_t rank = __popc(peers & lt_mask);
+    if ((peers & lt_mask) == 0) wcnt[warp][dig] = __popc(peers);  // lowest lane of the group
+    __syncthreads();
+    {
+      uint32_t run = 0;
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        uint32_t t = wcnt[w][tid];
+        wcnt[w][tid] = run;
+        run += t;
+      }
+      base_off[tid] = running[tid];
+      running[tid] += run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = base_off[dig] + wcnt[warp][dig] + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void gather_coords_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
+                                     const uint32_t* __restrict__ perm, T* __restrict__ xs) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t i = perm[s];
+  for (int j = 0; j < g.d; ++j) {
+    T xv = x[int64_t(i) * g.d + j];
+    const T lo = T(g.lo[j]), hi = T(g.hi[j]);
+    if (!(xv >= lo && xv <= hi)) xv = lo;
+    xs[int64_t(j) * n + s] = sub_rn(xv, lo);
+  }
+}
+
+__global__ void nsub_kernel(const uint32_t* __restrict__ counts, int64_t nbins,
+                            uint32_t* __restrict__ nsub) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  nsub[b] = (counts[b] + kSubMax - 1) / kSubMax;
+}
+
+__global__ void fill_sub_kernel(const uint32_t* __restrict__ bin_start, int64_t nbins,
+                                const uint32_t* __restrict__ sub_start,
+                                uint32_t* __restrict__ sub_bin, uint32_t* __restrict__ sub_first) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const uint32_t s0 = sub_start[b], s1 = sub_start[b + 1];
+  for (uint32_t k = s0; k < s1; ++k) {
+    sub_bin[k] = uint32_t(b);
+    sub_first[k] = bin_start[b] + (k - s0) * kSubMax;
+  }
+}
+
+// exclusive scan of in[0..n) into out[0..n], out[n] = total
+cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* scratch,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+  const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  scan_block_sums<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, scratch);
+  scan_sums_single<<<1, 1024, 0, s>>>(scratch, nb, out + n);
+  scan_apply<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, scratch, out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) {
+  const GeoDev& g = P->geo;
+  uint32_t* keys0 = wsp<uint32_t>(P, P->r_keys0);
+  uint32_t* vals0 = wsp<uint32_t>(P, P->r_vals0);
+  uint32_t* keys1 = wsp<uint32_t>(P, P->r_keys1);
+  uint32_t* vals1 = wsp<uint32_t>(P, P->r_vals1);
+  uint32_t* counts = wsp<uint32_t>(P, P->r_counts);
+  uint32_t* bstart = wsp<uint32_t>(P, P->r_binstart);
+  uint32_t* scratch = wsp<uint32_t>(P, P->r_scan);
+  int* errw = wsp<int>(P, P->r_err);
+  const int64_t nbins = P->nbins_total;
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * nbins, s);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    const unsigned blocks = unsigned((n + 255) / 256);
+    if (P->prec == FKREG_F32)
+      bin_keys_kernel<float><<<blocks, 256, 0, s>>>(g, n, static_cast<const float*>(x), keys0, vals0,
+                                                    counts, errw);
+    else
+      bin_keys_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), keys0,
+                                                     vals0, counts, errw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // radix passes over the significant bits of the bin index
+  int bits = 0;
+  while ((int64_t(1) << bits) < nbins) ++bits;
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  uint32_t* hist = wsp<uint32_t>(P, P->r_hist);
+  uint32_t *kin = keys0, *vin = vals0, *kout = keys1, *vout = vals1;
+  int in_is_1 = 0;
+  for (int p = 0; p < passes && n > 0; ++p) {
+    const int shift = p * kRadixBits;
+    radix_upsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, n, shift, ntiles, hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan(hist, hist, 256 * ntiles, scratch, s)) != cudaSuccess) return e;
+    radix_downsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, vin, n, shift, ntiles, hist, kout,
+                                                              vout);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+    in_is_1 ^= 1;
+  }
+  P->perm_in_vals1 = in_is_1;
+  if ((e = exclusive_scan(counts, bstart, nbins, scratch, s)) != cudaSuccess) return e;
+  if (n > 0) {
+    const unsigned blocks = unsigned((n + 255) / 256);
+    if (P->prec == FKREG_F32)
+      gather_coords_kernel<float><<<blocks, 256, 0, s>>>(g, n, static_cast<const float*>(x), vin,
+                                                         wsp<float>(P, P->r_xs));
+    else
+      gather_coords_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), vin,
+                                                          wsp<double>(P, P->r_xs));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // spreading sub-problems: at most kSubMax samples each
+  uint32_t* nsub = wsp<uint32_t>(P, P->r_nsub);
+  uint32_t* sstart = wsp<uint32_t>(P, P->r_substart);
+  const unsigned bb = unsigned((nbins + 255) / 256);
+  nsub_kernel<<<bb, 256, 0, s>>>(counts, nbins, nsub);
+  if ((e = exclusive_scan(nsub, sstart, nbins, scratch, s)) != cudaSuccess) return e;
+  fill_sub_kernel<<<bb, 256, 0, s>>>(bstart, nbins, sstart, wsp<uint32_t>(P, P->r_subbin),
+                                     wsp<uint32_t>(P, P->r_subfirst));
+  return cudaGetLastError();
+}
+
+}  // namespace fk

@@ -1,0 +1,320 @@
+// Fourier-domain kernel multiply with deconvolution (Sec. 1.1 "convolution
+// ... in the frequency domain", eq. 20 deconvolution).
+//
+// After the forward FFT of the fine grid, B_k ~ phihat(k) F_k with
+// F_k = sum_i c_i exp(-2 pi i k (x_i - lo) / P).  A moment field
+// T_g(q) = sum_i c_i K_H(x_i - q) (x_i - q)^g is the correlation of the point
+// measure with w_g(z) = z^g K_H(z), so on the period P
+//   T_g(lo + m delta) = sum_k A_g[k] exp(2 pi i k m / L),
+//   A_g[k] = F_k W_g(k/P) / prod_j P_j,
+//   W_g(xi) = integral w_g(z) exp(+2 pi i xi.z) dz:
+//     g = 0        : G(xi) = exp(-2 pi^2 xi^T H xi)
+//     g = e_a      : 2 pi i (H xi)_a G(xi)
+//     g = e_a + e_c: (H_ac - 4 pi^2 (H xi)_a (H xi)_c) G(xi)
+// (the transforms of the Gaussian and its first two moments).
+// Grid stage: A is folded modulo L onto the half spectrum of a length-L
+// real inverse DFT (exact aliasing when the kept modes exceed L).
+// Type-2 stage: A / phihat_b is placed on the per-bandwidth fine grid
+// (zero elsewhere) for the interpolation back to the samples.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace fk {
+
+namespace {
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<float> {
+  using type = float2;
+};
+template <>
+struct Cx<double> {
+  using type = double2;
+};
+
+template <typename C, typename T>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// F_q at signed mode kk from the R2C half spectrum of the type-1 fine grid.
+template <typename T, typename C>
+__device__ __forceinline__ C fetch_F(const GeoDev& g, const C* __restrict__ F, const int64_t kk[3],
+                                     int D) {
+  const int64_t last = kk[D - 1];
+  const bool neg = last < 0;
+  int64_t idx = 0;
+  for (int a = 0; a < D; ++a) {
+    int64_t k = neg ? -kk[a] : kk[a];
+    int64_t n = (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
+    if (a < D - 1) {
+      k %= g.nf[a];
+      if (k < 0) k += g.nf[a];
+    }
+    idx = idx * n + k;
+  }
+  C v = F[idx];
+  if (neg) v.y = -v.y;
+  return v;
+}
+
+// multiplier data for one mode and bandwidth
+template <typename T>
+struct ModeMul {
+  T G;
+  T hx[3];
+};
+
+template <typename T>
+__device__ __forceinline__ ModeMul<T> mode_mul(const GeoDev& g, const BwDev& B, const int64_t kk[3],
+                                               int D) {
+  ModeMul<T> m;
+  T xi[3] = {T(0), T(0), T(0)};
+  for (int a = 0; a < D; ++a) xi[a] = T(kk[a]) / T(g.P[a]);
+  T q = T(0);
+  for (int a = 0; a < 3; ++a) {
+    T s = T(0);
+    for (int c = 0; c < D; ++c) s += T(B.H[a * 3 + c]) * xi[c];
+    m.hx[a] = (a < D) ? s : T(0);
+    q += xi[a] * m.hx[a];
+  }
+  const T twopi = T(6.283185307179586476925286766559);
+  m.G = exp(-T(0.5) * twopi * twopi * q);
+  return m;
+}
+
+// accumulate base * W_g for the first nf monomials
+template <typename T, typename C>
+__device__ __forceinline__ void acc_fields(C* acc, C base, const ModeMul<T>& m, const BwDev& B,
+                                           const MonoTab& mono, int nfields) {
+  const T twopi = T(6.283185307179586476925286766559);
+  for (int f = 0; f < nfields; ++f) {
+    int deg = mono.e[f][0] + mono.e[f][1] + mono.e[f][2];
+    if (deg == 0) {
+      acc[f].x += base.x;
+      acc[f].y += base.y;
+    } else if (deg == 1) {
+      int a = mono.e[f][0] ? 0 : (mono.e[f][1] ? 1 : 2);
+      const T s = twopi * m.hx[a];  // multiply by i * s
+      acc[f].x += -base.y * s;
+      acc[f].y += base.x * s;
+    } else {
+      int a = -1, c = -1;
+      for (int j = 0; j < 3; ++j)
+        for (int r = 0; r < mono.e[f][j]; ++r) {
+          if (a < 0)
+            a = j;
+          else
+            c = j;
+        }
+      const T s = T(B.H[a * 3 + c]) - twopi * twopi * m.hx[a] * m.hx[c];
+      acc[f].x += base.x * s;
+      acc[f].y += base.y * s;
+    }
+  }
+}
+
+// Grid stage: thread per (half-spectrum index j on the L grid, bandwidth, strength q).
+template <typename T, int D>
+__global__ void kmul_grid_kernel(GeoDev g, const BwDev* __restrict__ bwt,
+                                 const double* __restrict__ tab, int64_t phi1_0, int64_t phi1_1,
+                                 int64_t phi1_2, MonoTab mono, const typename Cx<T>::type* __restrict__ F,
+                                 int64_t fine_half, int str_dens, int str_rhs, int nrhs_fields,
+                                 int bw_first, int bw_count, int fgrid, int64_t lhalf,
+                                 typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
+  const int nq = (str_dens >= 0 ? 1 : 0) + nrhs_fields;
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t total = lhalf * bw_count * nq;
+  if (gid >= total) return;
+  const int64_t j = gid % lhalf;
+  const int q = int((gid / lhalf) % nq);
+  const int bb = int(gid / (lhalf * nq));
+  const BwDev& B = bwt[bw_first + bb];
+  const bool dens = (str_dens >= 0) && q == 0;
+  const int strength = dens ? str_dens : str_rhs + (q - (str_dens >= 0 ? 1 : 0));
+  const int nfld = dens ? mono.n : mono.nt;
+  const int fbase = dens ? 0 : ((str_dens >= 0 ? mono.n : 0) + (q - (str_dens >= 0 ? 1 : 0)) * mono.nt);
+  const C* Fq = F + int64_t(strength) * fine_half;
+  // output multi-index
+  int64_t jj[3] = {0, 0, 0};
+  {
+    int64_t rem = j;
+    for (int a = D - 1; a >= 0; --a) {
+      const int64_t n = (a == D - 1) ? (g.L[a] / 2 + 1) : g.L[a];
+      jj[a] = rem % n;
+      rem /= n;
+    }
+  }
+  // alias ranges
+  int64_t k0[3], cnt[3];
+  for (int a = 0; a < D; ++a) {
+    const int64_t hk = B.K[a] / 2 - 1;
+    const int64_t lo = -hk;
+    int64_t r = (jj[a] - lo) % g.L[a];
+    if (r < 0) r += g.L[a];
+    k0[a] = lo + r;
+    cnt[a] = (k0[a] > hk) ? 0 : ((hk - k0[a]) / g.L[a] + 1);
+  }
+  C acc[kMaxMono];
+  for (int f = 0; f < kMaxMono; ++f) acc[f] = C{T(0), T(0)};
+  const int64_t phi1[3] = {phi1_0, phi1_1, phi1_2};
+  T invP = T(1);
+  for (int a = 0; a < D; ++a) invP /= T(g.P[a]);
+  const int64_t c1 = (D > 1) ? cnt[1] : 1, c2 = (D > 2) ? cnt[2] : 1;
+  for (int64_t i0 = 0; i0 < cnt[0]; ++i0)
+    for (int64_t i1 = 0; i1 < c1; ++i1)
+      for (int64_t i2 = 0; i2 < c2; ++i2) {
+        int64_t kk[3] = {k0[0] + i0 * g.L[0], 0, 0};
+        if (D > 1) kk[1] = k0[1] + i1 * g.L[1];
+        if (D > 2) kk[2] = k0[2] + i2 * g.L[2];
+        T dec = invP;
+        for (int a = 0; a < D; ++a) dec *= T(tab[phi1[a] + (kk[a] < 0 ? -kk[a] : kk[a])]);
+        const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
+        C base = fetch_F<T, C>(g, Fq, kk, D);
+        const T s = dec * m.G;
+        base.x *= s;
+        base.y *= s;
+        acc_fields<T, C>(acc, base, m, B, mono, nfld);
+      }
+  for (int f = 0; f < nfld; ++f) out[(int64_t(bb) * fgrid + fbase + f) * lhalf + j] = acc[f];
+}
+
+// Type-2 stage for one bandwidth: thread per (fine half-spectrum index, strength q).
+template <typename T, int D>
+__global__ void kmul_t2_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
+                               const double* __restrict__ tab, int64_t phi1_0, int64_t phi1_1,
+                               int64_t phi1_2, MonoTab mono, const typename Cx<T>::type* __restrict__ F,
+                               int64_t fine_half, int str_dens, int str_rhs, int n_rhs_str,
+                               int64_t t2half, typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
+  const int nq = 1 + n_rhs_str;
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= t2half * nq) return;
+  const int64_t j = gid % t2half;
+  const int q = int(gid / t2half);
+  const BwDev& B = bwt[b];
+  const bool dens = q == 0;
+  const int strength = dens ? str_dens : str_rhs + q - 1;
+  const int nfld = dens ? mono.n : mono.nt;
+  const int fbase = dens ? 0 : mono.n + (q - 1) * mono.nt;
+  int64_t kk[3] = {0, 0, 0};
+  bool inside = true;
+  {
+    int64_t rem = j;
+    for (int a = D - 1; a >= 0; --a) {
+      const int64_t n = (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+      int64_t idx = rem % n;
+      rem /= n;
+      int64_t k = (a == D - 1) ? idx : (idx < (B.nf[a] + 1) / 2 ? idx : idx - B.nf[a]);
+      kk[a] = k;
+      if ((k < 0 ? -k : k) > B.K[a] / 2 - 1) inside = false;
+    }
+  }
+  C acc[kMaxMono];
+  for (int f = 0; f < kMaxMono; ++f) acc[f] = C{T(0), T(0)};
+  if (inside) {
+    const int64_t phi1[3] = {phi1_0, phi1_1, phi1_2};
+    T dec = T(1);
+    for (int a = 0; a < D; ++a) {
+      const int64_t ak = kk[a] < 0 ? -kk[a] : kk[a];
+      dec *= T(tab[phi1[a] + ak] * tab[B.phi2_off[a] + ak] / g.P[a]);
+    }
+    const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
+    C base = fetch_F<T, C>(g, F + int64_t(strength) * fine_half, kk, D);
+    const T s = dec * m.G;
+    base.x *= s;
+    base.y *= s;
+    acc_fields<T, C>(acc, base, m, B, mono, nfld);
+  }
+  for (int f = 0; f < nfld; ++f) out[int64_t(fbase + f) * t2half + j] = acc[f];
+}
+
+template <typename T>
+cudaError_t launch_grid(fkreg_plan_s* P, int str_dens, int str_rhs, int nrhs_fields, int bw_first,
+                        int bw_count, void* out, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const GeoDev& g = P->geo;
+  const int D = P->d;
+  int64_t lhalf = 1, fhalf = 1;
+  for (int a = 0; a < D; ++a) {
+    lhalf *= (a == D - 1) ? (g.L[a] / 2 + 1) : g.L[a];
+    fhalf *= (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
+  }
+  const int nq = (str_dens >= 0 ? 1 : 0) + nrhs_fields;
+  const int64_t total = lhalf * bw_count * nq;
+  const unsigned blocks = unsigned((total + 255) / 256);
+  const int fgrid = (str_dens >= 0 ? P->ns : 0) + nrhs_fields * P->nt;
+  auto* F = wsp<C>(P, P->r_spec);
+  auto* bwt = wsp<BwDev>(P, P->r_bw);
+  auto* tab = wsp<double>(P, P->r_tab);
+  C* o = static_cast<C*>(out);
+#define FK_KG(DD)                                                                                  \
+  kmul_grid_kernel<T, DD><<<blocks, 256, 0, st>>>(g, bwt, tab, P->phi1_off[0], P->phi1_off[1],      \
+                                                  P->phi1_off[2], P->mono, F, fhalf, str_dens,      \
+                                                  str_rhs, nrhs_fields, bw_first, bw_count, fgrid, \
+                                                  lhalf, o)
+  if (D == 1)
+    FK_KG(1);
+  else if (D == 2)
+    FK_KG(2);
+  else
+    FK_KG(3);
+#undef FK_KG
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
+                      cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const GeoDev& g = P->geo;
+  const int D = P->d;
+  const BwDev& B = P->bw[b];
+  int64_t t2half = 1, fhalf = 1;
+  for (int a = 0; a < D; ++a) {
+    t2half *= (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+    fhalf *= (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
+  }
+  const int64_t total = t2half * (1 + n_rhs_str);
+  const unsigned blocks = unsigned((total + 255) / 256);
+  auto* F = wsp<C>(P, P->r_spec);
+  auto* bwt = wsp<BwDev>(P, P->r_bw);
+  auto* tab = wsp<double>(P, P->r_tab);
+  C* o = wsp<C>(P, P->r_t2spec);
+#define FK_KT(DD)                                                                               \
+  kmul_t2_kernel<T, DD><<<blocks, 256, 0, st>>>(g, bwt, b, tab, P->phi1_off[0], P->phi1_off[1], \
+                                                P->phi1_off[2], P->mono, F, fhalf, str_dens,    \
+                                                str_rhs, n_rhs_str, t2half, o)
+  if (D == 1)
+    FK_KT(1);
+  else if (D == 2)
+    FK_KT(2);
+  else
+    FK_KT(3);
+#undef FK_KT
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_kmul_grid(fkreg_plan_s* P, int str_dens, int str_rhs, int nrhs_fields, int bw_first,
+                          int bw_count, void* out_spec, cudaStream_t st) {
+  return P->prec == FKREG_F32
+             ? launch_grid<float>(P, str_dens, str_rhs, nrhs_fields, bw_first, bw_count, out_spec, st)
+             : launch_grid<double>(P, str_dens, str_rhs, nrhs_fields, bw_first, bw_count, out_spec, st);
+}
+
+cudaError_t run_kmul_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
+                        cudaStream_t st) {
+  return P->prec == FKREG_F32 ? launch_t2<float>(P, b, str_dens, str_rhs, n_rhs_str, st)
+                              : launch_t2<double>(P, b, str_dens, str_rhs, n_rhs_str, st);
+}
+
+}  // namespace fk

@@ -1,0 +1,292 @@
+// Type-1 spreading (the gridding of Sec. 1.2, eqs. 16-17) and strength setup.
+//
+// fine_s[m] = sum_i c_{s,i} prod_j phi(m_j - u_ij),  u_ij = (x_ij - lo_j) nf_j / P_j,
+// periodic in m_j (mod nf_j).  One CTA owns one sub-problem: up to kSubMax
+// sorted samples of one bin.  It accumulates their contributions into a
+// shared-memory copy of the bin's tile plus a halo of ceil(w/2) cells per
+// side, with shared-memory atomics, and then adds the tile to the fine grid
+// in global memory with one atomic per non-zero cell.  Strengths are handled
+// in chunks that fit the shared-memory budget.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace fk {
+
+namespace {
+
+constexpr int kSpreadThreads = 256;
+constexpr int kMaxChunk = 8;
+constexpr int kMaxW = 24;
+
+template <typename T>
+__device__ __forceinline__ T inv_h_of(const GeoDev& g, int j);
+template <>
+__device__ __forceinline__ float inv_h_of<float>(const GeoDev& g, int j) { return g.inv_h_f[j]; }
+template <>
+__device__ __forceinline__ double inv_h_of<double>(const GeoDev& g, int j) { return g.inv_h[j]; }
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// Spreading kernel value at offset z (fine cells).
+template <typename T>
+__device__ __forceinline__ T phi(int kind, int w, T beta, T z) {
+  if (kind == FKREG_SPREAD_ES) {
+    const T t = T(2) * z / T(w);
+    const T a = T(1) - t * t;
+    return a > T(0) ? exp(beta * (sqrt(a) - T(1))) : T(0);
+  }
+  return (fabs(z) <= T(0.5) * T(w)) ? exp(-beta * z * z) : T(0);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kSpreadThreads)
+spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict__ str, int s0,
+              int scount, int chunk, const uint32_t* __restrict__ sub_bin,
+              const uint32_t* __restrict__ sub_first, const uint32_t* __restrict__ bin_start,
+              const uint32_t* __restrict__ sub_total, T* __restrict__ fine) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const uint32_t k = blockIdx.x;
+  if (k >= *sub_total) return;
+  const uint32_t b = sub_bin[k];
+  const uint32_t first = sub_first[k];
+  const uint32_t last = min(first + uint32_t(kSubMax), bin_start[b + 1]);
+  // bin multi-index (axis 0 slowest)
+  int64_t bj[3] = {0, 0, 0};
+  {
+    int64_t rem = b;
+    for (int j = D - 1; j >= 0; --j) {
+      bj[j] = rem % g.nbins[j];
+      rem /= g.nbins[j];
+    }
+  }
+  int64_t o[3] = {0, 0, 0};
+  int W[3] = {1, 1, 1};
+  for (int j = 0; j < D; ++j) {
+    o[j] = bj[j] * g.tile[j] - g.pad;
+    W[j] = int(g.tile[j]) + 2 * g.pad;
+  }
+  const int cells = W[0] * W[1] * W[2];
+  const int w = g.w;
+  const T beta = T(g.beta);
+  const T halfw = T(0.5) * T(w);
+  const int64_t fine_cells = g.nf[0] * g.nf[1] * g.nf[2];
+
+  for (int c0 = 0; c0 < scount; c0 += chunk) {
+    const int cn = min(chunk, scount - c0);
+    for (int idx = threadIdx.x; idx < cn * cells; idx += blockDim.x) sm[idx] = T(0);
+    __syncthreads();
+    for (uint32_t p = first + threadIdx.x; p < last; p += blockDim.x) {
+      T wt[D][kMaxW];
+      int l[3] = {0, 0, 0};
+      for (int j = 0; j < D; ++j) {
+        const T u = mul_rn(xs[int64_t(j) * n + p], inv_h_of<T>(g, j));
+        const T f0 = ceil(u - halfw);
+        l[j] = int(int64_t(f0) - o[j]);
+        for (int t = 0; t < w; ++t) wt[j][t] = phi<T>(g.skind, w, beta, (f0 + T(t)) - u);
+      }
+      T cv[kMaxChunk];
+      for (int c = 0; c < cn; ++c) cv[c] = str[int64_t(s0 + c0 + c) * n + p];
+      if (D == 1) {
+        for (int t0 = 0; t0 < w; ++t0) {
+          const int idx = l[0] + t0;
+          for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + idx], cv[c] * wt[0][t0]);
+        }
+      } else if (D == 2) {
+        for (int t0 = 0; t0 < w; ++t0) {
+          const int row = (l[0] + t0) * W[1] + l[1];
+          for (int t1 = 0; t1 < w; ++t1) {
+            const T v = wt[0][t0] * wt[D - 1][t1];
+            for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + row + t1], cv[c] * v);
+          }
+        }
+      } else {
+        for (int t0 = 0; t0 < w; ++t0)
+          for (int t1 = 0; t1 < w; ++t1) {
+            const int row = ((l[0] + t0) * W[1] + (l[1] + t1)) * W[2] + l[2];
+            const T v01 = wt[0][t0] * wt[1 % D][t1];
+            for (int t2 = 0; t2 < w; ++t2) {
+              const T v = v01 * wt[D - 1][t2];
+              for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + row + t2], cv[c] * v);
+            }
+          }
+      }
+    }
+    __syncthreads();
+    // flush the tile (periodic wrap) into the fine grid
+    for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+      int rem = idx;
+      int64_t gidx = 0;
+      int lj[3];
+      for (int j = 2; j >= 0; --j) {
+        lj[j] = rem % W[j];
+        rem /= W[j];
+      }
+      for (int j = 0; j < 3; ++j) {
+        int64_t m = 0;
+        if (j < D) {
+          m = (o[j] + lj[j]) % g.nf[j];
+          if (m < 0) m += g.nf[j];
+        }
+        gidx = gidx * g.nf[j] + m;
+      }
+      for (int c = 0; c < cn; ++c) {
+        const T v = sm[c * cells + idx];
+        if (v != T(0)) atomicAdd(&fine[int64_t(s0 + c0 + c) * fine_cells + gidx], v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- strengths in sorted order --------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Gaussian probe value for (probe p, original index i): counter-based
+// SplitMix64 words, Box-Muller transform in FP64.
+__device__ __forceinline__ double probe_value(uint64_t seed, int p, uint32_t i) {
+  const uint64_t ctr = (uint64_t(p) << 40) ^ uint64_t(i);
+  const uint64_t c = splitmix64(seed ^ splitmix64(ctr));
+  const uint64_t c2 = splitmix64(c);
+  const double u1 = (double(c >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = double(c2 >> 11) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+template <typename T>
+__global__ void gather_strengths_kernel(int64_t n, const uint32_t* __restrict__ perm,
+                                        const T* __restrict__ y, int n_rhs, int y_complex,
+                                        int with_density, int n_probes, uint64_t seed,
+                                        const T* __restrict__ probes, T* __restrict__ str,
+                                        int first) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t i = perm[s];
+  int k = first;
+  if (with_density) str[int64_t(k++) * n + s] = T(1);
+  for (int r = 0; r < n_rhs; ++r) {
+    if (y_complex) {
+      str[int64_t(k++) * n + s] = y[(int64_t(r) * n + i) * 2 + 0];
+      str[int64_t(k++) * n + s] = y[(int64_t(r) * n + i) * 2 + 1];
+    } else {
+      str[int64_t(k++) * n + s] = y[int64_t(r) * n + i];
+    }
+  }
+  for (int p = 0; p < n_probes; ++p) {
+    const T v = probes ? probes[int64_t(p) * n + i] : T(probe_value(seed, p, i));
+    str[int64_t(k++) * n + s] = v;
+  }
+}
+
+// r_i = |y_i - mhat_b(x_i)|^2 for every response (eq. 23), sorted order.
+template <typename T>
+__global__ void residual_strengths_kernel(int64_t n, const uint32_t* __restrict__ perm,
+                                          const T* __restrict__ y, const T* __restrict__ mh,
+                                          int n_rhs, int y_complex, int b, T* __restrict__ str,
+                                          int first) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t i = perm[s];
+  for (int r = 0; r < n_rhs; ++r) {
+    T v;
+    if (y_complex) {
+      const int64_t yi = (int64_t(r) * n + i) * 2;
+      const int64_t mi = ((int64_t(b) * n_rhs + r) * n + i) * 2;
+      const T dr = y[yi] - mh[mi], di = y[yi + 1] - mh[mi + 1];
+      v = dr * dr + di * di;
+    } else {
+      const T dr = y[int64_t(r) * n + i] - mh[(int64_t(b) * n_rhs + r) * n + i];
+      v = dr * dr;
+    }
+    str[int64_t(first + r) * n + s] = v;
+  }
+}
+
+template <typename T, int D>
+cudaError_t launch_spread(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
+  const GeoDev& g = P->geo;
+  int cells = 1;
+  for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
+  const size_t per = size_t(cells) * sizeof(T);
+  const size_t budget = 100 * 1024;
+  int chunk = int(std::max<size_t>(1, std::min<size_t>(budget / per, kMaxChunk)));
+  chunk = std::min(chunk, scount);
+  const size_t smem = per * chunk;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(spread_kernel<T, D>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned(P->nsub_max);
+  const uint32_t* sub_total = wsp<uint32_t>(P, P->r_substart) + P->nbins_total;
+  spread_kernel<T, D><<<grid, kSpreadThreads, smem, st>>>(
+      g, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_str), s0, scount, chunk,
+      wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
+      wsp<uint32_t>(P, P->r_binstart), sub_total, wsp<T>(P, P->r_fine));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread_d(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
+  switch (P->d) {
+    case 1: return launch_spread<T, 1>(P, s0, scount, st);
+    case 2: return launch_spread<T, 2>(P, s0, scount, st);
+    default: return launch_spread<T, 3>(P, s0, scount, st);
+  }
+}
+
+}  // namespace
+
+const uint32_t* perm_ptr(fkreg_plan_s* P) {
+  return P->perm_in_vals1 ? wsp<uint32_t>(P, P->r_vals1) : wsp<uint32_t>(P, P->r_vals0);
+}
+
+cudaError_t run_spread(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
+  const int64_t fine_cells = P->geo.nf[0] * P->geo.nf[1] * P->geo.nf[2];
+  cudaError_t e = cudaMemsetAsync(P->ws + P->r_fine.off + size_t(s0) * fine_cells * P->tsize, 0,
+                                  size_t(scount) * fine_cells * P->tsize, st);
+  if (e != cudaSuccess || P->n == 0 || scount == 0) return e;
+  return P->prec == FKREG_F32 ? launch_spread_d<float>(P, s0, scount, st)
+                              : launch_spread_d<double>(P, s0, scount, st);
+}
+
+cudaError_t run_gather_strengths(fkreg_plan_s* P, const void* y, int first_str, int n_probes,
+                                 uint64_t seed, const void* probes, int with_density,
+                                 cudaStream_t st) {
+  if (P->n == 0) return cudaSuccess;
+  const unsigned blocks = unsigned((P->n + 255) / 256);
+  const uint32_t* perm = perm_ptr(P);
+  if (P->prec == FKREG_F32)
+    gather_strengths_kernel<float><<<blocks, 256, 0, st>>>(
+        P->n, perm, static_cast<const float*>(y), P->nrhs, P->o.y_complex, with_density, n_probes,
+        seed, static_cast<const float*>(probes), wsp<float>(P, P->r_str), first_str);
+  else
+    gather_strengths_kernel<double><<<blocks, 256, 0, st>>>(
+        P->n, perm, static_cast<const double*>(y), P->nrhs, P->o.y_complex, with_density, n_probes,
+        seed, static_cast<const double*>(probes), wsp<double>(P, P->r_str), first_str);
+  return cudaGetLastError();
+}
+
+cudaError_t run_residual_strengths(fkreg_plan_s* P, const void* y, const void* mhat_at_x, int b,
+                                   int first_str, cudaStream_t st) {
+  if (P->n == 0) return cudaSuccess;
+  const unsigned blocks = unsigned((P->n + 255) / 256);
+  const uint32_t* perm = perm_ptr(P);
+  if (P->prec == FKREG_F32)
+    residual_strengths_kernel<float><<<blocks, 256, 0, st>>>(
+        P->n, perm, static_cast<const float*>(y), static_cast<const float*>(mhat_at_x), P->nrhs,
+        P->o.y_complex, b, wsp<float>(P, P->r_str), first_str);
+  else
+    residual_strengths_kernel<double><<<blocks, 256, 0, st>>>(
+        P->n, perm, static_cast<const double*>(y), static_cast<const double*>(mhat_at_x), P->nrhs,
+        P->o.y_complex, b, wsp<double>(P, P->r_str), first_str);
+  return cudaGetLastError();
+}
+
+}  // namespace fk

@@ -1,0 +1,329 @@
+"""Thin Python binding of libfkreg.so (argument marshalling only).
+
+Every computation happens inside the CUDA library; this module only builds
+the C structs, hands device pointers of torch tensors and the current CUDA
+stream to the C ABI declared in ``include/fkreg.h``, and raises on a non-OK
+status.  There is no CPU fallback: if the library is missing the import of
+a plan fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Iterable, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfkreg.so")
+
+FKREG_F32, FKREG_F64 = 0, 1
+FKREG_SPREAD_ES, FKREG_SPREAD_GAUSS = 0, 1
+FKREG_GCV_EXACT_TRACE = 1
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA", 5: "CUFFT",
+          6: "TIMEOUT", 7: "DEVICE", 8: "STATE"}
+
+EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
+           "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
+           "fkreg_smooth", "fkreg_df", "fkreg_variance", "fkreg_sync_status",
+           "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("spread_kernel", ctypes.c_int), ("precision", ctypes.c_int),
+                ("y_complex", ctypes.c_int), ("grid_n", ctypes.c_int64 * 3),
+                ("grid_lo", ctypes.c_double * 3), ("grid_hi", ctypes.c_double * 3),
+                ("n_bw", ctypes.c_int), ("H", ctypes.POINTER(ctypes.c_double)),
+                ("n_rhs", ctypes.c_int), ("max_probes", ctypes.c_int), ("tol", ctypes.c_double),
+                ("mask_rho", ctypes.c_double), ("tile", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("delta", ctypes.c_double * 3),
+                ("period", ctypes.c_double * 3), ("ldft", ctypes.c_int64 * 3),
+                ("modes", ctypes.c_int64 * 3), ("nf", ctypes.c_int64 * 3), ("w", ctypes.c_int),
+                ("beta", ctypes.c_double), ("tile", ctypes.c_int64 * 3),
+                ("nbins", ctypes.c_int64 * 3), ("inv_h", ctypes.c_double * 3),
+                ("ns", ctypes.c_int), ("nt", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        d = self.dim
+        out = {"dim": d, "w": self.w, "beta": self.beta, "ns": self.ns, "nt": self.nt}
+        for k in ("delta", "period", "ldft", "modes", "nf", "tile", "nbins", "inv_h"):
+            out[k] = list(getattr(self, k))[:d]
+        return out
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [("mhat_grid", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("moments", ctypes.c_void_p), ("mhat_at_x", ctypes.c_void_p),
+                ("rss", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("gcv", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+class FkregError(RuntimeError):
+    pass
+
+
+def load():
+    """Load libfkreg.so (build it first with paper_2204_07716_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FkregError(f"{LIB_PATH} is missing: run paper_2204_07716_gb300.build.build() "
+                         "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.fkreg_geometry_query.argtypes = [ctypes.POINTER(Opts), ctypes.POINTER(Geometry)]
+    L.fkreg_spread_kernel_ft.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64, i64,
+                                         ctypes.POINTER(ctypes.c_double)]
+    L.fkreg_plan_create.argtypes = [ctypes.POINTER(Opts), i64, ctypes.POINTER(vp)]
+    L.fkreg_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.fkreg_set_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.fkreg_set_points.argtypes = [vp, i64, vp, vp]
+    L.fkreg_get_sort.argtypes = [vp, vp, vp, ctypes.POINTER(i64), vp]
+    L.fkreg_smooth.argtypes = [vp, vp, ctypes.POINTER(Outputs), vp]
+    L.fkreg_df.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(Outputs), vp]
+    L.fkreg_variance.argtypes = [vp, vp, vp, vp, vp]
+    L.fkreg_sync_status.argtypes = [vp, vp]
+    L.fkreg_last_error.argtypes = [vp]
+    L.fkreg_last_error.restype = ctypes.c_char_p
+    L.fkreg_global_error.argtypes = []
+    L.fkreg_global_error.restype = ctypes.c_char_p
+    L.fkreg_plan_destroy.argtypes = [vp]
+    L.fkreg_plan_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def make_opts(d: int, order: int, grid_n: Sequence[int], lo: Sequence[float],
+              hi: Sequence[float], H: np.ndarray, n_rhs: int = 1, max_probes: int = 0,
+              tol: float = 1e-6, precision: str = "f32", y_complex: bool = False,
+              spread_kernel: str = "es", mask_rho: float = 0.0, tile: int = 0,
+              flags: int = 0):
+    """Build an Opts struct; returns (opts, keepalive) -- keep both alive."""
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1, d, d))
+    o = Opts()
+    o.dim, o.order, o.kernel = d, order, 0
+    o.spread_kernel = FKREG_SPREAD_ES if spread_kernel == "es" else FKREG_SPREAD_GAUSS
+    o.precision = FKREG_F32 if precision == "f32" else FKREG_F64
+    o.y_complex = int(bool(y_complex))
+    for j in range(3):
+        o.grid_n[j] = int(grid_n[j]) if j < d else 1
+        o.grid_lo[j] = float(lo[j]) if j < d else 0.0
+        o.grid_hi[j] = float(hi[j]) if j < d else 1.0
+    o.n_bw = H.shape[0]
+    o.H = H.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    o.n_rhs, o.max_probes, o.tol = n_rhs, max_probes, tol
+    o.mask_rho, o.tile, o.flags = mask_rho, tile, flags
+    return o, H
+
+
+def geometry(**kw) -> dict:
+    """Planner geometry (host only, no GPU needed)."""
+    L = load()
+    o, keep = make_opts(**kw)
+    g = Geometry()
+    st = L.fkreg_geometry_query(ctypes.byref(o), ctypes.byref(g))
+    if st != 0:
+        raise FkregError(f"{STATUS.get(st, st)}: {L.fkreg_global_error().decode()}")
+    return g.as_dict()
+
+
+def spread_kernel_ft(kind: str, w: int, beta: float, nf: int, nk: int) -> np.ndarray:
+    L = load()
+    out = np.zeros(nk)
+    st = L.fkreg_spread_kernel_ft(FKREG_SPREAD_ES if kind == "es" else FKREG_SPREAD_GAUSS, w,
+                                  beta, nf, nk, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != 0:
+        raise FkregError(L.fkreg_global_error().decode())
+    return out
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class Plan:
+    """One smoothing problem on one GPU.  Owns a torch workspace tensor.
+
+    The methods mirror the C calls: ``set_points`` (bin + stable sort),
+    ``smooth``, ``df`` (Monte-Carlo DF + GCV), ``variance`` (eq. 23).
+    """
+
+    def __init__(self, d: int, order: int, grid_n, lo, hi, H, max_n: int, n_rhs: int = 1,
+                 max_probes: int = 0, tol: float = 1e-6, precision: str = "f32",
+                 y_complex: bool = False, spread_kernel: str = "es", mask_rho: float = 0.0,
+                 tile: int = 0, flags: int = 0, device=None):
+        import torch
+        self.torch = torch
+        self.L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.d, self.order, self.n_rhs = d, order, n_rhs
+        self.grid_n = tuple(int(v) for v in grid_n)
+        self.M = int(np.prod(self.grid_n))
+        self.max_probes = max_probes
+        self.precision = precision
+        self.y_complex = bool(y_complex)
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+        self.cdtype = torch.complex64 if precision == "f32" else torch.complex128
+        self._opts, self._keep = make_opts(d, order, grid_n, lo, hi, H, n_rhs, max_probes, tol,
+                                           precision, y_complex, spread_kernel, mask_rho, tile,
+                                           flags)
+        self.n_bw = self._opts.n_bw
+        g = Geometry()
+        self._check_global(self.L.fkreg_geometry_query(ctypes.byref(self._opts), ctypes.byref(g)))
+        self.geom = g.as_dict()
+        self.ns, self.nt = g.ns, g.nt
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._check_global(self.L.fkreg_plan_create(ctypes.byref(self._opts), int(max_n),
+                                                        ctypes.byref(h)))
+        self.h = h
+        nbytes = ctypes.c_size_t()
+        self._check(self.L.fkreg_workspace_bytes(self.h, ctypes.byref(nbytes)))
+        self.ws_bytes = int(nbytes.value)
+        self._ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self._check(self.L.fkreg_set_workspace(self.h, ctypes.c_void_p(self._ws_ptr),
+                                               self.ws_bytes, self._stream()))
+        self.n = 0
+
+    # -- helpers -----------------------------------------------------------
+    def _stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _check_global(self, st):
+        if st != 0:
+            raise FkregError(f"{STATUS.get(st, st)}: {self.L.fkreg_global_error().decode()}")
+
+    def _check(self, st):
+        if st != 0:
+            raise FkregError(f"{STATUS.get(st, st)}: {self.L.fkreg_last_error(self.h).decode()}")
+
+    def _as_dev(self, a, complex_ok=False):
+        t = self.torch
+        if not isinstance(a, t.Tensor):
+            a = t.as_tensor(np.asarray(a))
+        if a.is_complex():
+            if not complex_ok:
+                raise FkregError("complex input where real expected")
+            a = a.to(self.cdtype)
+            a = t.view_as_real(a)
+        else:
+            a = a.to(self.dtype)
+        return a.to(self.device).contiguous()
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.fkreg_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls -------------------------------------------------------------
+    def set_points(self, x):
+        x = self._as_dev(x)
+        n = int(x.shape[0])
+        self._x = x
+        self._check(self.L.fkreg_set_points(self.h, n, ctypes.c_void_p(x.data_ptr()), self._stream()))
+        self.n = n
+
+    def sync(self):
+        self._check(self.L.fkreg_sync_status(self.h, self._stream()))
+
+    def get_sort(self):
+        t = self.torch
+        nb = ctypes.c_int64()
+        self.L.fkreg_get_sort(self.h, None, None, ctypes.byref(nb), self._stream())
+        perm = t.empty(max(self.n, 1), dtype=t.int32, device=self.device)
+        bstart = t.empty(int(nb.value) + 1, dtype=t.int32, device=self.device)
+        self._check(self.L.fkreg_get_sort(self.h, ctypes.c_void_p(perm.data_ptr()),
+                                          ctypes.c_void_p(bstart.data_ptr()), ctypes.byref(nb),
+                                          self._stream()))
+        return perm[: self.n], bstart
+
+    def _outputs(self, want: Iterable[str], df: bool) -> Dict[str, object]:
+        t = self.torch
+        want = set(want)
+        o = {}
+        cplx = self.y_complex
+        M, nb, R, n = self.M, self.n_bw, self.n_rhs, self.n
+        fdt = self.cdtype if cplx else self.dtype
+        if "mhat_grid" in want:
+            o["mhat_grid"] = t.empty((nb, R) + self.grid_n, dtype=fdt, device=self.device)
+        if "mask" in want:
+            o["mask"] = t.empty((nb,) + self.grid_n, dtype=t.uint8, device=self.device)
+        if "moments" in want:
+            per = self.ns + R * self.nt * (2 if cplx else 1)
+            o["moments"] = t.empty((nb, per) + self.grid_n, dtype=self.dtype, device=self.device)
+        if "mhat_at_x" in want:
+            o["mhat_at_x"] = t.empty((nb, R, max(n, 1)), dtype=fdt, device=self.device)
+        if "rss" in want or df:
+            o["rss"] = t.empty((nb, R), dtype=t.float64, device=self.device)
+        if df:
+            o["trace"] = t.empty((nb, 3), dtype=t.float64, device=self.device)
+            o["gcv"] = t.empty((nb, R), dtype=t.float64, device=self.device)
+        return o
+
+    def _struct(self, o) -> Outputs:
+        s = Outputs()
+        for k in ("mhat_grid", "mask", "moments", "mhat_at_x", "rss", "trace", "gcv"):
+            setattr(s, k, o[k].data_ptr() if k in o else None)
+        return s
+
+    def _y(self, y):
+        y = self._as_dev(y, complex_ok=self.y_complex)
+        if self.y_complex and y.dim() == 2:      # [n, 2] from a 1-D complex vector
+            y = y.unsqueeze(0)
+        if not self.y_complex and y.dim() == 1:
+            y = y.unsqueeze(0)
+        return y.contiguous()
+
+    def smooth(self, y, want=("mhat_grid", "mask")) -> Dict[str, object]:
+        y = self._y(y)
+        o = self._outputs(want, df=False)
+        s = self._struct(o)
+        self._check(self.L.fkreg_smooth(self.h, ctypes.c_void_p(y.data_ptr()), ctypes.byref(s),
+                                        self._stream()))
+        self._y_keep = y
+        return o
+
+    def df(self, y, n_probes: int, seed: int = 0, probes=None,
+           want=("mhat_grid", "mask")) -> Dict[str, object]:
+        y = self._y(y)
+        pr = None
+        if probes is not None:
+            pr = self._as_dev(probes)
+        o = self._outputs(want, df=True)
+        s = self._struct(o)
+        self._check(self.L.fkreg_df(self.h, ctypes.c_void_p(y.data_ptr()), int(n_probes),
+                                    ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                    None if pr is None else ctypes.c_void_p(pr.data_ptr()),
+                                    ctypes.byref(s), self._stream()))
+        self._y_keep = (y, pr)
+        return o
+
+    def variance(self, y, mhat_at_x):
+        t = self.torch
+        y = self._y(y)
+        mh = self._as_dev(mhat_at_x, complex_ok=self.y_complex)
+        out = t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
+        self._check(self.L.fkreg_variance(self.h, ctypes.c_void_p(y.data_ptr()),
+                                          ctypes.c_void_p(mh.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), self._stream()))
+        self._y_keep = (y, mh)
+        return out

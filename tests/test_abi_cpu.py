@@ -1,0 +1,94 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every declared
+symbol, validates arguments, and its host planner is right.  No GPU needed."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2204_07716_gb300 import build as fkbuild
+from paper_2204_07716_gb300 import fkreg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fkbuild.build()
+    return fkreg.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fkreg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fkreg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(fkreg.EXPORTS)
+
+
+def opts(**kw):
+    base = dict(d=2, order=1, grid_n=(256, 256), lo=(0, 0), hi=(1, 1),
+                H=np.diag([0.01 ** 2, 0.015 ** 2]), tol=1e-6)
+    base.update(kw)
+    return base
+
+
+def test_geometry_covers_tail_and_spectrum(lib):
+    g = fkreg.geometry(**opts())
+    assert g["w"] == 7 and g["ns"] == 6 and g["nt"] == 3
+    for j, sig in enumerate((0.01, 0.015)):
+        delta = 1 / 255
+        assert g["delta"][j] == pytest.approx(delta)
+        # period covers the box plus the kernel tail (no wrap into the box)
+        assert g["period"][j] >= 1.0 + 5.5 * sig
+        assert g["period"][j] == pytest.approx(g["ldft"][j] * delta)
+        # kept modes resolve the Gaussian multiplier to below tol
+        kmax = g["modes"][j] // 2 - 1
+        xi = kmax / g["period"][j]
+        assert math.exp(-2 * math.pi ** 2 * sig ** 2 * xi ** 2) < 1e-6
+        assert g["nf"][j] >= 2 * g["modes"][j] and g["nf"][j] % 2 == 0
+        assert g["inv_h"][j] == pytest.approx(g["nf"][j] / g["period"][j], rel=1e-7)
+
+
+def test_width_follows_tolerance(lib):
+    for tol, w in ((1e-6, 7), (1e-9, 10), (1e-12, 13), (1e-3, 4)):
+        assert fkreg.geometry(**opts(tol=tol))["w"] == w
+    assert fkreg.geometry(**opts(tol=1e-6, spread_kernel="gauss"))["w"] == 14
+
+
+def test_invalid_arguments_are_reported(lib):
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
+        fkreg.geometry(**opts(H=np.array([[1.0, 2.0], [2.0, 1.0]]) * 1e-4))   # not SPD
+    with pytest.raises(fkreg.FkregError, match="UNSUPPORTED"):
+        fkreg.geometry(**opts(order=2))
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
+        fkreg.geometry(**opts(grid_n=(1, 256)))
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
+        fkreg.geometry(**opts(tol=0.5))
+
+
+@pytest.mark.parametrize("kind", ["es", "gauss"])
+def test_spread_kernel_transform_matches_adaptive_quadrature(lib, kind):
+    w = 7 if kind == "es" else 14
+    beta = 2.30 * w if kind == "es" else 3 * math.pi / (4 * (w // 2))
+    nf = 96
+    ph = fkreg.spread_kernel_ft(kind, w, beta, nf, 24)
+
+    def phi(z):
+        if kind == "es":
+            t = 2 * z / w
+            return math.exp(beta * (math.sqrt(max(0.0, 1 - t * t)) - 1)) if abs(t) <= 1 else 0.0
+        return math.exp(-beta * z * z) if abs(z) <= w / 2 else 0.0
+
+    for k in range(24):
+        ref = integrate.quad(lambda z: phi(z) * math.cos(2 * math.pi * k * z / nf), -w / 2, w / 2,
+                             limit=400, epsabs=1e-15, epsrel=1e-13)[0]
+        assert ph[k] == pytest.approx(ref, rel=1e-10, abs=1e-14)

@@ -1,0 +1,319 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars (normwise errors defined in parity_util):
+  FP64, tol 1e-12 -> 1e-10;  FP64, tol 1e-9 -> 1e-8;  FP32, tol 1e-6 -> 1e-5.
+Bin counts and permutations are compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_07716_gb300 import inputs
+from parity_util import field_error, field_scale_sigma, mhat_error, sample_grid_indices
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BAR = {("f64", 1e-12): 1e-10, ("f64", 1e-9): 1e-8, ("f32", 1e-6): 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2204_07716_gb300 import build
+    build.build()
+    oracle.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def plan_for(w, n_probes=0, **kw):
+    from paper_2204_07716_gb300.fkreg import Plan
+    return Plan(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=max(w.n, 1), n_rhs=w.y.shape[0],
+                max_probes=n_probes, tol=w.tol, precision=w.precision, **kw)
+
+
+def as_seen(w):
+    """x, y exactly as the device sees them (rounded to the plan precision)."""
+    if w.precision == "f32":
+        x = w.x.astype(np.float32).astype(np.float64)
+        y = w.y.astype(np.complex64 if np.iscomplexobj(w.y) else np.float32)
+        y = y.astype(np.complex128 if np.iscomplexobj(w.y) else np.float64)
+        return x, y
+    return w.x, w.y
+
+
+def check_grid(w, out, b=0, idx=None, bar=None):
+    """Compare mhat and the moment fields on (a subset of) the grid."""
+    bar = bar or BAR[(w.precision, w.tol)]
+    x, y = as_seen(w)
+    H = w.H[b]
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    if idx is None:
+        idx = np.arange(gp.shape[0])
+    q = gp[idx]
+    r = oracle.smooth_at(x, y, H, w.order, q)
+    a1 = oracle.scale_field(x, np.ones((1, w.n)), H, q)[:, 0]
+    ay = oracle.scale_field(x, y, H, q)
+    mg = out["mhat_grid"][b].reshape(y.shape[0], -1).cpu().numpy()[:, idx]
+    mask = out["mask"][b].reshape(-1).cpu().numpy()[idx].astype(bool)
+    errs = {}
+    for rr in range(y.shape[0]):
+        errs[f"mhat{rr}"] = mhat_error(mg[rr], r["mhat"][:, rr], r["s"][:, 0], ay[:, rr], mask)
+    if "moments" in out:
+        mom = out["moments"][b].reshape(out["moments"].shape[1], -1).cpu().numpy()[:, idx]
+        ex = oracle.monomials(w.d, 2 * w.order)
+        for f in range(r["s"].shape[1]):
+            errs[f"s{f}"] = field_error(mom[f], r["s"][:, f], a1, field_scale_sigma(H, ex[f]))
+        for rr in range(y.shape[0]):
+            for f in range(r["t"].shape[2]):
+                g = mom[r["s"].shape[1] + rr * r["t"].shape[2] + f]
+                errs[f"t{rr}_{f}"] = field_error(g, r["t"][:, rr, f], ay[:, rr],
+                                                 field_scale_sigma(H, ex[f]))
+    # masked points have too little density; the oracle agrees they are sparse
+    s0max = np.max(r["s"][:, 0])
+    assert np.all(r["s"][~mask, 0] < 2e-3 * max(s0max, 1e-300) + 1e-300) or idx.size < gp.shape[0]
+    worst = max(errs.values())
+    assert worst <= bar, {k: f"{v:.2e}" for k, v in errs.items()}
+    return errs
+
+
+# ---------------------------------------------------------------- sorting ----
+def cpu_keys(x, geom, precision):
+    ft = np.float32 if precision == "f32" else np.float64
+    d = x.shape[1]
+    key = np.zeros(x.shape[0], dtype=np.int64)
+    for j in range(d):
+        xp = (x[:, j].astype(ft) - ft(0.0)).astype(ft)
+        u = (xp * ft(geom["inv_h"][j])).astype(ft)
+        c = np.floor(u).astype(np.int64)
+        c = np.clip(c, 0, geom["nf"][j] - 1)
+        key = key * geom["nbins"][j] + c // geom["tile"][j]
+    return key
+
+
+@pytest.mark.parametrize("case", ["d1", "d2clip", "d3", "dups", "one"])
+def test_sort_is_bit_exact(case):
+    if case == "d1":
+        w = inputs.nw1d()
+    elif case == "d2clip":
+        w = inputs.ll2d(n=200_000)
+    elif case == "d3":
+        w = inputs.random_small(1, 3, 50_000, 16, 0, [0.05], precision="f32", tol=1e-6)
+    elif case == "dups":
+        w = inputs.random_small(2, 2, 30_000, 32, 1, [0.03], precision="f32", tol=1e-6)
+        w.x[::3] = w.x[0]          # many identical locations
+        w.x[1::7, 0] = 1.0         # points on the upper boundary
+    else:
+        w = inputs.random_small(3, 2, 1, 16, 0, [0.1])
+    p = plan_for(w)
+    p.set_points(torch.tensor(w.x))
+    perm, bstart = p.get_sort()
+    p.sync()
+    key = cpu_keys(w.x, p.geom, w.precision)
+    ref = np.argsort(key, kind="stable")
+    assert np.array_equal(perm.cpu().numpy().astype(np.int64), ref)
+    nb = int(np.prod(p.geom["nbins"]))
+    counts = np.bincount(key, minlength=nb)
+    ref_start = np.concatenate([[0], np.cumsum(counts)])
+    assert np.array_equal(bstart.cpu().numpy().astype(np.int64), ref_start)
+    assert bstart.cpu().numpy()[-1] == w.n
+
+
+# ------------------------------------------------------------ grid parity ----
+def smooth(w, want=("mhat_grid", "mask", "moments")):
+    p = plan_for(w)
+    p.set_points(torch.tensor(w.x))
+    out = p.smooth(torch.tensor(w.y), want=want)
+    p.sync()
+    return p, out
+
+
+def test_nw1d_fp64_full():
+    # 1-D Nadaraya-Watson, N = 10^4, 256 grid points, FP64, tol 1e-9
+    w = inputs.nw1d()
+    _, out = smooth(w)
+    check_grid(w, out)
+
+
+def test_nw1d_fp64_tol12():
+    w = inputs.nw1d(tol=1e-12)
+    _, out = smooth(w)
+    check_grid(w, out)
+
+
+@pytest.mark.parametrize("d,order,grid,sig", [(1, 1, 200, 0.01), (2, 0, 40, 0.03), (2, 1, 40, 0.03),
+                                              (3, 0, 12, 0.06), (3, 1, 12, 0.07)])
+def test_fp64_tol12_all_dims(d, order, grid, sig):
+    w = inputs.random_small(10 + d + order, d, 3000, grid, order, [sig], precision="f64", tol=1e-12)
+    _, out = smooth(w)
+    check_grid(w, out)
+
+
+@pytest.mark.parametrize("d,order,grid,sig", [(1, 0, 300, 0.01), (2, 1, 64, 0.02), (3, 0, 16, 0.05),
+                                              (3, 1, 16, 0.06)])
+def test_fp32_tol6_all_dims(d, order, grid, sig):
+    w = inputs.random_small(20 + d + order, d, 20_000, grid, order, [sig], precision="f32", tol=1e-6)
+    _, out = smooth(w)
+    check_grid(w, out)
+
+
+def test_full_bandwidth_matrix():
+    w = inputs.random_small(31, 2, 4000, 40, 1, [0.04], precision="f64", tol=1e-12, full_h=True)
+    _, out = smooth(w)
+    check_grid(w, out)
+
+
+def test_bandwidth_sweep_with_narrow_kernels():
+    # narrow bandwidths fold the spectrum onto the grid lattice (modes > L)
+    w = inputs.random_small(32, 1, 5000, 64, 0, np.logspace(-2.5, -1, 5), precision="f64", tol=1e-12)
+    p, out = smooth(w)
+    g = p.geom
+    for b in range(w.n_bw):
+        check_grid(w, out, b=b)
+
+
+def test_stacked_and_complex_responses():
+    w = inputs.random_small(33, 1, 3000, 80, 1, [0.03], precision="f64", tol=1e-12, n_rhs=3)
+    _, out = smooth(w)
+    check_grid(w, out)
+    # complex y = (re, im) smoothed as two real responses
+    wc = inputs.random_small(34, 2, 3000, 32, 1, [0.05], precision="f64", tol=1e-12)
+    yc = wc.y[0] + 1j * np.sin(5 * wc.x[:, 1])
+    from paper_2204_07716_gb300.fkreg import Plan
+    p = Plan(2, 1, wc.grid_n, wc.lo, wc.hi, wc.H, max_n=wc.n, n_rhs=1, tol=1e-12,
+             precision="f64", y_complex=True)
+    p.set_points(torch.tensor(wc.x))
+    out = p.smooth(torch.tensor(yc), want=("mhat_grid", "mask"))
+    p.sync()
+    mg = out["mhat_grid"][0, 0].reshape(-1).cpu().numpy()
+    for part, yy in (("re", yc.real), ("im", yc.imag)):
+        wr = inputs.Workload("c", 2, wc.x, yy[None], wc.grid_n, wc.lo, wc.hi, wc.H, 1, 1e-12, "f64")
+        o2 = {"mhat_grid": torch.tensor((mg.real if part == "re" else mg.imag).reshape((1, 1) + wc.grid_n)),
+              "mask": out["mask"]}
+        check_grid(wr, o2)
+
+
+def test_ll2d_full_size_sampled():
+    # 2-D local linear, N = 10^6, 256^2 grid, FP32, tol 1e-6 (sampled grid points)
+    w = inputs.ll2d()
+    _, out = smooth(w)
+    idx = sample_grid_indices(w.grid_n, 300, seed=1)
+    check_grid(w, out, idx=idx)
+
+
+# --------------------------------------------------------- sample parity ----
+def test_at_samples_rss_and_exact_trace():
+    w = inputs.random_small(40, 2, 3000, 32, 1, [0.05], precision="f64", tol=1e-12)
+    p = plan_for(w, n_probes=1)
+    p.set_points(torch.tensor(w.x))
+    z = oracle.probes(7, 1, w.n)
+    out = p.df(torch.tensor(w.y), 1, probes=torch.tensor(z), want=("mhat_at_x",))
+    p.sync()
+    r = oracle.smooth_at(w.x, w.y, w.H[0], 1, w.x)
+    ay = oracle.scale_field(w.x, w.y, w.H[0], w.x)
+    mh = out["mhat_at_x"][0, 0].cpu().numpy()
+    assert mhat_error(mh, r["mhat"][:, 0], r["s"][:, 0], ay[:, 0]) < 1e-10
+    rss_o = float(np.sum((w.y[0] - r["mhat"][:, 0]) ** 2))
+    assert out["rss"][0, 0].item() == pytest.approx(rss_o, rel=1e-9)
+    tr_o = oracle.trace_exact(w.x, w.H[0], 1)
+    assert out["trace"][0, 2].item() == pytest.approx(tr_o, rel=1e-9)
+
+
+@pytest.mark.parametrize("d,order", [(1, 0), (2, 1), (3, 0)])
+def test_df_and_gcv_with_given_probes(d, order):
+    grid = {1: 64, 2: 24, 3: 10}[d]
+    w = inputs.random_small(50 + d, d, 2500, grid, order, [0.04, 0.08], precision="f64", tol=1e-12)
+    npb = 4
+    z = oracle.probes(11, npb, w.n)
+    p = plan_for(w, n_probes=npb)
+    p.set_points(torch.tensor(w.x))
+    out = p.df(torch.tensor(w.y), npb, probes=torch.tensor(z), want=())
+    p.sync()
+    for b in range(w.n_bw):
+        Sz = oracle.apply_smoother(w.x, z, w.H[b], order).T
+        f = oracle.fmc_trace(w.x, z, w.H[b], order, Sw=Sz)
+        scale = np.sum(np.abs(z) * np.abs(Sz)) / npb
+        assert abs(out["trace"][b, 1].item() - f["hutchinson"]) <= 1e-10 * scale
+        assert out["trace"][b, 0].item() == pytest.approx(f["girard"], rel=1e-9)
+        m = oracle.apply_smoother(w.x, w.y, w.H[b], order)[:, 0]
+        rss = float(np.sum((w.y[0] - m) ** 2))
+        assert out["rss"][b, 0].item() == pytest.approx(rss, rel=1e-9)
+        assert out["gcv"][b, 0].item() == pytest.approx(oracle.gcv(rss, w.n, f["girard"]), rel=1e-8)
+
+
+def test_device_probes_follow_the_counter_generator():
+    w = inputs.random_small(60, 1, 4000, 64, 0, [0.03], precision="f64", tol=1e-12)
+    p = plan_for(w, n_probes=3)
+    p.set_points(torch.tensor(w.x))
+    a = p.df(torch.tensor(w.y), 3, seed=12345, want=())
+    tr_dev = a["trace"].cpu().numpy().copy()
+    z = oracle.probes(12345, 3, w.n)
+    b = p.df(torch.tensor(w.y), 3, probes=torch.tensor(z), want=())
+    p.sync()
+    np.testing.assert_allclose(tr_dev, b["trace"].cpu().numpy(), rtol=1e-12)
+
+
+def test_fp32_df_sweep():
+    w = inputs.nw3d_df(n=30_000, grid=16, n_bw=4, n_probes=4)
+    z = w.probes
+    p = plan_for(w, n_probes=4)
+    p.set_points(torch.tensor(w.x))
+    out = p.df(torch.tensor(w.y), 4, probes=torch.tensor(z), want=())
+    p.sync()
+    x, y = as_seen(w)
+    z32 = z.astype(np.float32).astype(np.float64)
+    for b in range(w.n_bw):
+        Sz = oracle.apply_smoother(x, z32, w.H[b], 0).T
+        f = oracle.fmc_trace(x, z32, w.H[b], 0, Sw=Sz)
+        scale = np.sum(np.abs(z32) * np.abs(Sz)) / 4
+        assert abs(out["trace"][b, 1].item() - f["hutchinson"]) <= 1e-5 * scale
+        tr = oracle.trace_exact(x, w.H[b], 0)
+        assert out["trace"][b, 2].item() == pytest.approx(tr, rel=1e-5)
+
+
+# --------------------------------------------------------- variance pass ----
+def test_variance_pass():
+    w = inputs.random_small(70, 1, 3000, 100, 1, [0.04], precision="f64", tol=1e-12)
+    p = plan_for(w)
+    p.set_points(torch.tensor(w.x))
+    out = p.smooth(torch.tensor(w.y), want=("mhat_at_x",))
+    s2 = p.variance(torch.tensor(w.y), out["mhat_at_x"])
+    p.sync()
+    mh = out["mhat_at_x"][0, 0].cpu().numpy()
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    ro = oracle.variance_pass(w.x, w.y, mh[None], w.H[0], gp, order=1)
+    r = (w.y[0] - mh) ** 2
+    s0 = oracle.moment_sums(w.x, np.ones((1, w.n)), w.H[0], 0, gp)[:, 0, 0]
+    ar = oracle.scale_field(w.x, r[None], w.H[0], gp)[:, 0]
+    valid = s0 >= 2e-3 * s0.max()
+    assert mhat_error(s2[0, 0].cpu().numpy(), ro[:, 0], s0, ar, valid) < 1e-10
+
+
+# ------------------------------------------------------------ edge cases ----
+def test_empty_and_single_sample():
+    w = inputs.random_small(80, 2, 1, 20, 0, [0.1], precision="f64", tol=1e-12)
+    p = plan_for(w)
+    p.set_points(torch.zeros((0, 2), dtype=torch.float64))
+    out = p.smooth(torch.zeros((1, 0), dtype=torch.float64), want=("mhat_grid", "mask"))
+    p.sync()
+    assert out["mask"].sum().item() == 0
+    assert torch.isnan(out["mhat_grid"]).all()
+    p.set_points(torch.tensor(w.x))
+    out = p.smooth(torch.tensor([[2.5]], dtype=torch.float64), want=("mhat_grid", "mask"))
+    p.sync()
+    m = out["mhat_grid"][0, 0][out["mask"][0].bool()]
+    assert m.numel() > 0
+    assert torch.allclose(m, torch.full_like(m, 2.5), rtol=1e-9)
+
+
+def test_points_outside_the_box_are_flagged():
+    from paper_2204_07716_gb300.fkreg import FkregError
+    w = inputs.random_small(81, 1, 100, 20, 0, [0.1], precision="f64", tol=1e-12)
+    w.x[5, 0] = 1.5
+    w.x[9, 0] = float("nan")
+    p = plan_for(w)
+    p.set_points(torch.tensor(w.x))
+    with pytest.raises(FkregError, match="DEVICE"):
+        p.sync()
+    p.sync()   # the error word was cleared
