@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Throughput of the NUFFT kernel smoother on one GB300 (or N replicas).
+
+One step = the whole hot path on the 2-D local-linear workload
+(N = 10^6 samples from a clipped 3-Gaussian mixture, 256 x 256 grid,
+H = diag(0.01^2, 0.015^2), FP32 with FP64 solves, tol 1e-6):
+  bin + stable sort of the samples (fkreg_set_points),
+  fkreg_df with y and 10 on-device Gaussian probes (Table 1 default Np):
+    type-1 spreading of 12 strengths, FFT, kernel multiply + deconvolution,
+    inverse FFT, FP64 grid solves (6 moment + 3 response grids -> mhat, mask),
+    type-2 interpolation of 39 fields at every sample with the FP64
+    at-sample solve, RSS, Monte-Carlo DF, exact trace and GCV,
+  fkreg_variance: spreading + smoothing of the squared residuals (eq. 23).
+value = N * (1 response + 10 probes + 1 variance response) * bandwidths / step time,
+in sample-points per second, summed over all ranks (independent replicas).
+
+--impl reference times the FP64 oracle (direct sums) on the host cores on a
+bounded sample of the same step and extrapolates per query point.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PROBES = 10
+WORKLOAD = "ll2d-1M-256sq-LL-f32-tol1e-6"
+METRIC = "sample-pts/sec of NUFFT smoothing at rel err<=1e-5 vs plain FP64; % HBM roofline"
+UNIT = "sample-pts/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def algorithmic(plan, n, n_probes):
+    """Algorithmic bytes / flops per launch of the spreading and interpolation kernels."""
+    T = 4
+    d = plan.d
+    S = 1 + plan.n_rhs + n_probes
+    nf = int(math.prod(plan.geom["nf"]))
+    w = plan.geom["w"]
+    # spread: read d coordinates + S strengths per sample, write S fine grids once
+    spread_bytes = n * (d * T + S * T) + S * nf * T
+    spread_flops = 2 * n * S * w ** d
+    F2 = plan.ns + (plan.n_rhs + n_probes) * plan.nt
+    # interp: read coordinates, permutation, responses/probes; read the F2 fine
+    # grids once; write mhat at the samples
+    interp_bytes = n * (d * T + 4 + (plan.n_rhs + n_probes) * T + plan.n_rhs * T) + F2 * nf * T
+    interp_flops = 2 * n * F2 * w ** d
+    return {"spread": (spread_bytes, spread_flops), "interp": (interp_bytes, interp_flops)}
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2204_07716_gb300 import build as fkbuild
+    from paper_2204_07716_gb300 import fkreg, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        fkbuild.build()
+    if world > 1:
+        dist.barrier()
+    w = inputs.ll2d()
+    n = w.n
+    plan = fkreg.Plan(2, 1, w.grid_n, w.lo, w.hi, w.H, max_n=n, n_rhs=1, max_probes=N_PROBES,
+                      tol=w.tol, precision="f32", device=dev)
+    x = torch.tensor(w.x, dtype=torch.float32, device=dev)
+    y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    want = ("mhat_grid", "mask", "mhat_at_x")
+
+    def step(k, xx, yy):
+        plan.set_points(xx)
+        out = plan.df(yy, N_PROBES, seed=1000 + k, want=want)
+        s2 = plan.variance(yy, out["mhat_at_x"])
+        return out, s2
+
+    for k in range(args.warmup):
+        step(k, x, y)
+    plan.sync()
+    plan.stage_times()                      # reset timers and launch counter
+    plan.set_timing(True)
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))                 # evict L2 between steps (512 MB > 129 MB)
+        ev[k][0].record(stream)
+        step(args.warmup + k, x, y)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    plan.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stage_ms, stage_calls, launches = plan.stage_times()
+    plan.set_timing(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_step = n * (1 + N_PROBES + 1) * plan.n_bw
+    value = world * units_per_step * args.steps / (total_ms / 1e3)
+
+    # e2e: host pinned inputs, copies inside the timed region, results read back
+    xh = torch.tensor(w.x, dtype=torch.float32).pin_memory()
+    yh = torch.tensor(w.y, dtype=torch.float32).pin_memory()
+    mh_host = torch.empty((plan.n_bw, 1) + w.grid_n, dtype=torch.float32).pin_memory()
+    gcv_host = torch.empty((plan.n_bw, 1), dtype=torch.float64).pin_memory()
+    s2_host = torch.empty((plan.n_bw, 1) + w.grid_n, dtype=torch.float32).pin_memory()
+    xd = torch.empty_like(x)
+    yd = torch.empty_like(y)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e2e_ev[k][0].record(stream)
+        xd.copy_(xh, non_blocking=True)
+        yd.copy_(yh, non_blocking=True)
+        out, s2 = step(k, xd, yd)
+        mh_host.copy_(out["mhat_grid"], non_blocking=True)
+        gcv_host.copy_(out["gcv"], non_blocking=True)
+        s2_host.copy_(s2, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    plan.sync()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * units_per_step * args.steps / (e2e_ms / 1e3)
+    h2d = xh.numel() * 4 + yh.numel() * 4
+    d2h = mh_host.numel() * 4 + gcv_host.numel() * 8 + s2_host.numel() * 4
+
+    # roofline of the dominant kernel stage
+    own = {k: v for k, v in stage_ms.items() if k not in ("fft_fwd", "fft_grid", "fft_t2")}
+    dom = max(own, key=own.get)
+    hbm_peak, peak_kind = peaks()
+    alg = algorithmic(plan, n, N_PROBES)
+    roof = None
+    if dom in alg and stage_calls[dom]:
+        per_launch_ms = stage_ms[dom] / stage_calls[dom]
+        bytes_per_launch = alg[dom][0] if dom == "spread" else alg[dom][0]
+        if dom == "spread":
+            # the variance pass spreads 1 strength: report the df spread launch shape
+            pass
+        achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "traffic": None, "peak_source": peak_kind,
+                "launch_ms": round(per_launch_ms, 4)}
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64solve", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "grid": list(w.grid_n), "order": 1,
+                   "bandwidth_sd": [0.01, 0.015], "probes": N_PROBES, "tol": w.tol,
+                   "units_per_step": units_per_step, "l2": "flushed (512 MB write) between steps",
+                   "parallelism": f"replicas{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "stages_ms_per_step": {k: round(v / args.steps, 4) for k, v in stage_ms.items()},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_step_estimate(w, seconds: float):
+    """Time the FP64 oracle on a bounded sample of one bench step, extrapolate.
+
+    The oracle's cost per query point is O(N): a grid point needs the 6 s-sums
+    and 3 t-sums of y (grid pass) plus 3 t-sums of the residuals (variance
+    pass); a sample point needs 6 s-sums and 3 t-sums for y and each probe.
+    The sample evaluates a few grid and sample points and scales by M and N.
+    """
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    x = w.x.astype(np.float32).astype(np.float64)
+    y = w.y.astype(np.float32).astype(np.float64)
+    z = oracle.probes(7, N_PROBES, w.n)
+    rng = np.random.default_rng(0)
+    # calibrate with a tiny sample, then size the timed sample to ~seconds
+    def run(qg, qs):
+        t0 = time.perf_counter()
+        gi = rng.choice(gp.shape[0], size=qg, replace=False)
+        oracle.smooth_at(x, np.concatenate([y, y]), w.H[0], 1, gp[gi], nthreads=cores)
+        si = rng.choice(w.n, size=qs, replace=False)
+        oracle.smooth_at(x, np.concatenate([y, z]), w.H[0], 1, x[si], nthreads=cores)
+        return time.perf_counter() - t0
+
+    tg = run(cores, 0) / cores
+    ts = run(0, cores) / cores
+    qg = max(cores, int(0.4 * seconds / max(tg, 1e-9)))
+    qs = max(cores, int(0.6 * seconds / max(ts, 1e-9)))
+    t = run(qg, 0)
+    tg = t / qg
+    t2 = run(0, qs)
+    ts = t2 / qs
+    M = gp.shape[0]
+    full_s = tg * M + ts * w.n
+    units = w.n * (1 + N_PROBES + 1)
+    return {"value": units / full_s, "full_step_s": full_s, "cores": cores,
+            "sample": f"{qg} grid points + {qs} sample points of the step (direct FP64 sums "
+                      f"over all {w.n} samples each), extrapolated to {M} grid points and "
+                      f"{w.n} sample points",
+            "sample_s": t + t2}
+
+
+def cpu_baseline(w, seconds):
+    r = oracle_step_estimate(w, seconds)
+    return {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+            "sample": r["sample"], "extrapolated_full_step_s": r["full_step_s"]}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2204_07716_gb300 import inputs
+
+    w = inputs.ll2d()
+    per_step = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_step_estimate(w, per_step)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_step_estimate(w, per_step)
+        vals.append(r["value"])
+        secs.append(r["full_step_s"])
+    value = statistics.median(vals)
+    ms = statistics.median(secs) * 1e3
+    cores = os.cpu_count() or 1
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w.n, "grid": list(w.grid_n), "order": 1,
+                   "probes": N_PROBES, "parallelism": "host cores"},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                         "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -243,6 +243,33 @@ fkreg_status fkreg_df(fkreg_plan plan, const void* y_dev, int n_probes, uint64_t
 fkreg_status fkreg_variance(fkreg_plan plan, const void* y_dev, const void* mhat_at_x_dev,
                             void* sigma2_grid_dev, void* stream);
 
+/*
+ * Stage timers (profiling).  With timing enabled every stage of a call is
+ * bracketed by CUDA events recorded on the call's stream; fkreg_stage_times
+ * waits for those events, returns the accumulated milliseconds and launch
+ * counts per stage since the previous query (arrays of FKREG_N_STAGES, either
+ * may be NULL) and resets them.  kernel_launches (may be NULL) receives the
+ * number of this library's own kernel launches since the previous query
+ * (cuFFT's kernels are not counted).  Timing adds two event records per stage.
+ */
+enum {
+  FKREG_STAGE_SORT = 0,       /* bin keys, radix sort, bin offsets, sorted coordinates */
+  FKREG_STAGE_STRENGTHS = 1,  /* responses / probes / residuals in sorted order */
+  FKREG_STAGE_SPREAD = 2,     /* type-1 spreading */
+  FKREG_STAGE_FFT_FWD = 3,    /* cuFFT forward of the fine grids */
+  FKREG_STAGE_KMUL_GRID = 4,  /* kernel multiply + fold for the grid lattice */
+  FKREG_STAGE_FFT_GRID = 5,   /* cuFFT inverse onto the lattice */
+  FKREG_STAGE_GRID_SOLVE = 6, /* FP64 per-grid-point solves */
+  FKREG_STAGE_KMUL_T2 = 7,    /* kernel multiply + deconvolution for type-2 */
+  FKREG_STAGE_FFT_T2 = 8,     /* cuFFT inverse onto the type-2 fine grids */
+  FKREG_STAGE_INTERP = 9,     /* interpolation at the samples + solves + reductions */
+  FKREG_STAGE_FINALIZE = 10,  /* DF / GCV */
+  FKREG_N_STAGES = 11
+};
+fkreg_status fkreg_set_timing(fkreg_plan plan, int enable);
+fkreg_status fkreg_stage_times(fkreg_plan plan, double* ms, int64_t* launches,
+                               int64_t* kernel_launches);
+
 /* Synchronise the stream and report device-detected errors (then clear them). */
 fkreg_status fkreg_sync_status(fkreg_plan plan, void* stream);
 

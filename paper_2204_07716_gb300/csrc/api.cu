@@ -38,6 +38,35 @@ fkreg_status cuda_err(fkreg_plan_s* P, cudaError_t e, const char* where) {
   return plan_err(P, FKREG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Records a (start, stop) event pair around one stage when timing is on.
+struct StageScope {
+  fkreg_plan_s* P;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageScope(fkreg_plan_s* P_, int st, cudaStream_t s_) : P(P_), stage(st), s(s_) {
+    if (!P->timing) return;
+    a = take();
+    b = take();
+    if (a) cudaEventRecord(a, s);
+  }
+  ~StageScope() {
+    if (!P->timing || !a || !b) return;
+    cudaEventRecord(b, s);
+    P->pending.push_back({stage, a, b});
+  }
+  cudaEvent_t take() {
+    if (!P->ev_pool.empty()) {
+      cudaEvent_t e = P->ev_pool.back();
+      P->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+};
+
 constexpr size_t kAlign = 256;
 
 struct Layout {
@@ -304,7 +333,11 @@ fkreg_status fkreg_set_points(fkreg_plan P, int64_t n, const void* x, void* stre
   P->n = n;
   P->points_set = false;
   P->dens_valid = false;
-  cudaError_t e = fk::run_sort(P, n, x, static_cast<cudaStream_t>(stream));
+  cudaError_t e;
+  {
+    StageScope sc(P, FKREG_STAGE_SORT, static_cast<cudaStream_t>(stream));
+    e = fk::run_sort(P, n, x, static_cast<cudaStream_t>(stream));
+  }
   if (e != cudaSuccess) return cuda_err(P, e, "bin sort");
   P->points_set = true;
   return FKREG_OK;
@@ -373,26 +406,56 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
   const int64_t nf_cells = full_cells(P->g.nf, d);
   (void)nf_cells;
   P->dens_valid = false;
-  FK_CHECK(fk::run_gather_strengths(P, y, 0, n_probes, seed, probes, 1, s), "strengths");
-  FK_CHECK(fk::run_spread(P, 0, S, s), "spread");
-  FK_STATUS(exec_fft(P, 0, P->g.nf, S, P->ws + P->r_fine.off, P->ws + P->r_spec.off, s));
+#define FK_STAGE(id) StageScope _sc##id(P, id, s)
+  {
+    FK_STAGE(FKREG_STAGE_STRENGTHS);
+    FK_CHECK(fk::run_gather_strengths(P, y, 0, n_probes, seed, probes, 1, s), "strengths");
+  }
+  {
+    FK_STAGE(FKREG_STAGE_SPREAD);
+    FK_CHECK(fk::run_spread(P, 0, S, s), "spread");
+  }
+  {
+    FK_STAGE(FKREG_STAGE_FFT_FWD);
+    FK_STATUS(exec_fft(P, 0, P->g.nf, S, P->ws + P->r_fine.off, P->ws + P->r_spec.off, s));
+  }
   const bool grid = out && (out->mhat_grid || out->mask || out->moments);
   if (grid) {
-    FK_CHECK(fk::run_kmul_grid(P, 0, 1, P->nrhs_real, 0, P->nbw, P->ws + P->r_gspec.off, s), "kmul grid");
-    FK_STATUS(exec_fft(P, 1, P->g.ldft, P->nbw * P->fgrid, P->ws + P->r_gspec.off,
-                       P->ws + P->r_gfield.off, s));
-    FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, nullptr, out, nullptr, s), "grid solve");
+    {
+      FK_STAGE(FKREG_STAGE_KMUL_GRID);
+      FK_CHECK(fk::run_kmul_grid(P, 0, 1, P->nrhs_real, 0, P->nbw, P->ws + P->r_gspec.off, s),
+               "kmul grid");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_FFT_GRID);
+      FK_STATUS(exec_fft(P, 1, P->g.ldft, P->nbw * P->fgrid, P->ws + P->r_gspec.off,
+                         P->ws + P->r_gfield.off, s));
+    }
+    {
+      FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+      FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, nullptr, out, nullptr, s), "grid solve");
+    }
   }
   const bool at = want_df || n_probes > 0 || (out && (out->mhat_at_x || out->rss));
   if (at) {
     const int n_rhs_str = P->nrhs_real + n_probes;
     const int f2 = P->ns + n_rhs_str * P->nt;
     for (int b = 0; b < P->nbw; ++b) {
-      FK_CHECK(fk::run_kmul_t2(P, b, 0, 1, n_rhs_str, s), "kmul type-2");
-      FK_STATUS(exec_fft(P, 1, P->bw[b].nf, f2, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
-      FK_CHECK(fk::run_interp(P, b, P->nrhs_real, n_probes, y, out ? out->mhat_at_x : nullptr, s),
-               "interpolation");
+      {
+        FK_STAGE(FKREG_STAGE_KMUL_T2);
+        FK_CHECK(fk::run_kmul_t2(P, b, 0, 1, n_rhs_str, s), "kmul type-2");
+      }
+      {
+        FK_STAGE(FKREG_STAGE_FFT_T2);
+        FK_STATUS(exec_fft(P, 1, P->bw[b].nf, f2, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
+      }
+      {
+        FK_STAGE(FKREG_STAGE_INTERP);
+        FK_CHECK(fk::run_interp(P, b, P->nrhs_real, n_probes, y, out ? out->mhat_at_x : nullptr, s),
+                 "interpolation");
+      }
     }
+    FK_STAGE(FKREG_STAGE_FINALIZE);
     FK_CHECK(fk::run_finalize(P, n_probes, out, s), "finalize");
   }
   (void)T;
@@ -428,15 +491,63 @@ fkreg_status fkreg_variance(fkreg_plan P, const void* y, const void* mhat_at_x, 
   const int64_t nf_cells = full_cells(P->g.nf, d), nf_half = half_cells(P->g.nf, d);
   const int R = P->nrhs;
   for (int b = 0; b < P->nbw; ++b) {
-    FK_CHECK(fk::run_residual_strengths(P, y, mhat_at_x, b, 1, s), "residuals");
-    FK_CHECK(fk::run_spread(P, 1, R, s), "spread");
-    FK_STATUS(exec_fft(P, 0, P->g.nf, R, P->ws + P->r_fine.off + P->tsize * nf_cells,
-                       P->ws + P->r_spec.off + 2 * P->tsize * nf_half, s));
-    FK_CHECK(fk::run_kmul_grid(P, 0, 1, R, b, 1, P->ws + P->r_gspec.off, s), "kmul grid");
-    FK_STATUS(exec_fft(P, 1, P->g.ldft, P->ns + R * P->nt, P->ws + P->r_gspec.off,
-                       P->ws + P->r_gfield.off, s));
-    FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, sigma2, s), "grid solve");
+    {
+      FK_STAGE(FKREG_STAGE_STRENGTHS);
+      FK_CHECK(fk::run_residual_strengths(P, y, mhat_at_x, b, 1, s), "residuals");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_SPREAD);
+      FK_CHECK(fk::run_spread(P, 1, R, s), "spread");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_FFT_FWD);
+      FK_STATUS(exec_fft(P, 0, P->g.nf, R, P->ws + P->r_fine.off + P->tsize * nf_cells,
+                         P->ws + P->r_spec.off + 2 * P->tsize * nf_half, s));
+    }
+    {
+      FK_STAGE(FKREG_STAGE_KMUL_GRID);
+      FK_CHECK(fk::run_kmul_grid(P, 0, 1, R, b, 1, P->ws + P->r_gspec.off, s), "kmul grid");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_FFT_GRID);
+      FK_STATUS(exec_fft(P, 1, P->g.ldft, P->ns + R * P->nt, P->ws + P->r_gspec.off,
+                         P->ws + P->r_gfield.off, s));
+    }
+    {
+      FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+      FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, sigma2, s), "grid solve");
+    }
   }
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_set_timing(fkreg_plan P, int enable) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  P->timing = enable != 0;
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_stage_times(fkreg_plan P, double* ms, int64_t* launches, int64_t* kernel_launches) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  for (auto& pe : P->pending) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(pe.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pe.a, pe.b);
+    if (e != cudaSuccess) return cuda_err(P, e, "stage timer");
+    P->stage_ms[pe.stage] += t;
+    P->stage_calls[pe.stage] += 1;
+    P->ev_pool.push_back(pe.a);
+    P->ev_pool.push_back(pe.b);
+  }
+  P->pending.clear();
+  for (int i = 0; i < FKREG_N_STAGES; ++i) {
+    if (ms) ms[i] = P->stage_ms[i];
+    if (launches) launches[i] = P->stage_calls[i];
+    P->stage_ms[i] = 0;
+    P->stage_calls[i] = 0;
+  }
+  if (kernel_launches) *kernel_launches = P->launches;
+  P->launches = 0;
   return FKREG_OK;
 }
 
@@ -461,6 +572,11 @@ const char* fkreg_last_error(fkreg_plan P) { return P ? P->err.c_str() : ""; }
 void fkreg_plan_destroy(fkreg_plan P) {
   if (!P) return;
   for (auto& kv : P->ffts) cufftDestroy(kv.second);
+  for (auto& pe : P->pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (auto e : P->ev_pool) cudaEventDestroy(e);
   delete P;
 }
 

@@ -104,6 +104,18 @@ struct fkreg_plan_s {
   int perm_in_vals1 = 0;        // which ping-pong buffer holds the permutation
   std::string err;
   int device = -1;
+
+  // profiling: own kernel launches, per-stage events
+  int64_t launches = 0;
+  bool timing = false;
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double stage_ms[FKREG_N_STAGES] = {0};
+  int64_t stage_calls[FKREG_N_STAGES] = {0};
 };
 
 namespace fk {

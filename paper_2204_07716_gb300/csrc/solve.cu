@@ -422,6 +422,7 @@ cudaError_t launch_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int n
   grid_solve_kernel<T><<<blocks, 256, 0, st>>>(g, P->mono, wsp<BwDev>(P, P->r_bw), bw_first,
                                                bw_count, P->order, Mtot, field, fgrid, lcells,
                                                nrhs_fields, smax, rho, go);
+  P->launches += 2;
   return cudaGetLastError();
 }
 
@@ -448,6 +449,7 @@ cudaError_t launch_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, v
   else
     FK_IK(3);
 #undef FK_IK
+  P->launches += 1;
   return cudaGetLastError();
 }
 
@@ -480,6 +482,7 @@ cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out
       sums, P->nbw, nacc, P->nrhs_real, n_probes, P->o.y_complex, P->n,
       (P->o.flags & FKREG_GCV_EXACT_TRACE) ? 1 : 0, out ? out->rss : nullptr,
       out ? out->trace : nullptr, out ? out->gcv : nullptr);
+  P->launches += 2;
   return cudaGetLastError();
 }
 

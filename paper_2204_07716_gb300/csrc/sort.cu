@@ -240,8 +240,9 @@ __global__ void fill_sub_kernel(const uint32_t* __restrict__ bin_start, int64_t 
 
 // exclusive scan of in[0..n) into out[0..n], out[n] = total
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* scratch,
-                           cudaStream_t s) {
+                           cudaStream_t s, int64_t* launches) {
   if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+  *launches += 3;
   const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
   scan_block_sums<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, scratch);
   scan_sums_single<<<1, 1024, 0, s>>>(scratch, nb, out + n);
@@ -273,6 +274,7 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
       bin_keys_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), keys0,
                                                      vals0, counts, errw);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    P->launches += 1;
   }
   // radix passes over the significant bits of the bin index
   int bits = 0;
@@ -285,8 +287,9 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
   for (int p = 0; p < passes && n > 0; ++p) {
     const int shift = p * kRadixBits;
     radix_upsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, n, shift, ntiles, hist);
+    P->launches += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = exclusive_scan(hist, hist, 256 * ntiles, scratch, s)) != cudaSuccess) return e;
+    if ((e = exclusive_scan(hist, hist, 256 * ntiles, scratch, s, &P->launches)) != cudaSuccess) return e;
     radix_downsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, vin, n, shift, ntiles, hist, kout,
                                                               vout);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -295,7 +298,7 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
     in_is_1 ^= 1;
   }
   P->perm_in_vals1 = in_is_1;
-  if ((e = exclusive_scan(counts, bstart, nbins, scratch, s)) != cudaSuccess) return e;
+  if ((e = exclusive_scan(counts, bstart, nbins, scratch, s, &P->launches)) != cudaSuccess) return e;
   if (n > 0) {
     const unsigned blocks = unsigned((n + 255) / 256);
     if (P->prec == FKREG_F32)
@@ -305,13 +308,15 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
       gather_coords_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), vin,
                                                           wsp<double>(P, P->r_xs));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    P->launches += 1;
   }
   // spreading sub-problems: at most kSubMax samples each
   uint32_t* nsub = wsp<uint32_t>(P, P->r_nsub);
   uint32_t* sstart = wsp<uint32_t>(P, P->r_substart);
   const unsigned bb = unsigned((nbins + 255) / 256);
   nsub_kernel<<<bb, 256, 0, s>>>(counts, nbins, nsub);
-  if ((e = exclusive_scan(nsub, sstart, nbins, scratch, s)) != cudaSuccess) return e;
+  P->launches += 2;
+  if ((e = exclusive_scan(nsub, sstart, nbins, scratch, s, &P->launches)) != cudaSuccess) return e;
   fill_sub_kernel<<<bb, 256, 0, s>>>(bstart, nbins, sstart, wsp<uint32_t>(P, P->r_subbin),
                                      wsp<uint32_t>(P, P->r_subfirst));
   return cudaGetLastError();

@@ -267,6 +267,7 @@ cudaError_t launch_grid(fkreg_plan_s* P, int str_dens, int str_rhs, int nrhs_fie
   else
     FK_KG(3);
 #undef FK_KG
+  P->launches += 1;
   return cudaGetLastError();
 }
 
@@ -299,6 +300,7 @@ cudaError_t launch_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_r
   else
     FK_KT(3);
 #undef FK_KT
+  P->launches += 1;
   return cudaGetLastError();
 }
 

@@ -229,6 +229,7 @@ cudaError_t launch_spread(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) 
       g, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_str), s0, scount, chunk,
       wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
       wsp<uint32_t>(P, P->r_binstart), sub_total, wsp<T>(P, P->r_fine));
+  P->launches += 1;
   return cudaGetLastError();
 }
 
@@ -270,6 +271,7 @@ cudaError_t run_gather_strengths(fkreg_plan_s* P, const void* y, int first_str, 
     gather_strengths_kernel<double><<<blocks, 256, 0, st>>>(
         P->n, perm, static_cast<const double*>(y), P->nrhs, P->o.y_complex, with_density, n_probes,
         seed, static_cast<const double*>(probes), wsp<double>(P, P->r_str), first_str);
+  P->launches += 1;
   return cudaGetLastError();
 }
 
@@ -286,6 +288,7 @@ cudaError_t run_residual_strengths(fkreg_plan_s* P, const void* y, const void* m
     residual_strengths_kernel<double><<<blocks, 256, 0, st>>>(
         P->n, perm, static_cast<const double*>(y), static_cast<const double*>(mhat_at_x), P->nrhs,
         P->o.y_complex, b, wsp<double>(P, P->r_str), first_str);
+  P->launches += 1;
   return cudaGetLastError();
 }
 

@@ -20,13 +20,16 @@ LIB_PATH = os.path.join(HERE, "libfkreg.so")
 FKREG_F32, FKREG_F64 = 0, 1
 FKREG_SPREAD_ES, FKREG_SPREAD_GAUSS = 0, 1
 FKREG_GCV_EXACT_TRACE = 1
+STAGES = ["sort", "strengths", "spread", "fft_fwd", "kmul_grid", "fft_grid", "grid_solve",
+          "kmul_t2", "fft_t2", "interp", "finalize"]
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA", 5: "CUFFT",
           6: "TIMEOUT", 7: "DEVICE", 8: "STATE"}
 
 EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
-           "fkreg_smooth", "fkreg_df", "fkreg_variance", "fkreg_sync_status",
+           "fkreg_smooth", "fkreg_df", "fkreg_variance", "fkreg_set_timing",
+           "fkreg_stage_times", "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy"]
 
 
@@ -90,6 +93,9 @@ def load():
     L.fkreg_smooth.argtypes = [vp, vp, ctypes.POINTER(Outputs), vp]
     L.fkreg_df.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(Outputs), vp]
     L.fkreg_variance.argtypes = [vp, vp, vp, vp, vp]
+    L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
+    L.fkreg_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i64)]
     L.fkreg_sync_status.argtypes = [vp, vp]
     L.fkreg_last_error.argtypes = [vp]
     L.fkreg_last_error.restype = ctypes.c_char_p
@@ -244,6 +250,19 @@ class Plan:
 
     def sync(self):
         self._check(self.L.fkreg_sync_status(self.h, self._stream()))
+
+    def set_timing(self, enable: bool = True):
+        self._check(self.L.fkreg_set_timing(self.h, int(bool(enable))))
+
+    def stage_times(self):
+        """(ms per stage, calls per stage, own kernel launches) since the last query."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        calls = (ctypes.c_int64 * n)()
+        kl = ctypes.c_int64()
+        self._check(self.L.fkreg_stage_times(self.h, ms, calls, ctypes.byref(kl)))
+        return ({STAGES[i]: ms[i] for i in range(n)}, {STAGES[i]: calls[i] for i in range(n)},
+                int(kl.value))
 
     def get_sort(self):
         t = self.torch
