@@ -270,6 +270,39 @@ fkreg_status fkreg_set_timing(fkreg_plan plan, int enable);
 fkreg_status fkreg_stage_times(fkreg_plan plan, double* ms, int64_t* launches,
                                int64_t* kernel_launches);
 
+/*
+ * Allocation-free stable bin sort.  The paper has no counterpart: this is an
+ * entry point for callers that cannot allocate device memory while they run
+ * (a host program whose memory pool owns every device byte, a plug-in that
+ * is handed buffers but no allocator, a loop that forbids allocation after
+ * start-up).  It computes the same permutation and bin offsets as
+ * fkreg_set_points + fkreg_get_sort, but keeps its scratch in a device array
+ * that the library owns (about 4.3 MB, held on every GPU that loads the
+ * library until the process exits) instead of a workspace.
+ *   geom           geometry from fkreg_geometry_query (dim, nf, tile, nbins,
+ *                  inv_h are used)
+ *   grid_lo/hi     host [dim], the grid box of the plan options
+ *   precision      FKREG_F32 or FKREG_F64: the type of x_dev
+ *   n              samples, 0 <= n <= 262144 (2^18); at most 65536 bins
+ *   x_dev          [n][dim] samples (device)
+ *   perm_dev       [n] uint32 out: original index of the s-th sorted sample
+ *   bin_start_dev  [nbins + 1] uint32 out: exclusive prefix sum of bin counts
+ *   bad_dev        optional int32 out: 1 if a sample lay outside the box or
+ *                  was not finite (it is then sorted into the first bin along
+ *                  that axis), else 0
+ * Larger n or more bins return FKREG_ERR_INVALID_ARG before anything runs.
+ * The call allocates nothing.  Its first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array and the array keeps the previous call's contents
+ * (the call clears what must start at zero), so calls whose work overlaps on
+ * the GPU (other streams, other host threads) race: serialise them.
+ */
+fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const double* grid_lo,
+                                   const double* grid_hi, int precision, int64_t n,
+                                   const void* x_dev, uint32_t* perm_dev, uint32_t* bin_start_dev,
+                                   int32_t* bad_dev, void* stream);
+
 /* Synchronise the stream and report device-detected errors (then clear them). */
 fkreg_status fkreg_sync_status(fkreg_plan plan, void* stream);
 

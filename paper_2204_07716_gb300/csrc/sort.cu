@@ -13,6 +13,8 @@
 // counting sort is this implementation's own device-side organisation of it.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace fk {
@@ -322,4 +324,133 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+// ---- bin sort with library-owned static scratch ----------------------------
+// Some callers cannot allocate device memory once they are running: a host
+// program whose memory pool owns every device byte, a plug-in that is given
+// buffers but no allocator, or a latency-critical loop that forbids
+// allocation after start-up.  For them the stable bin sort has a variant
+// whose scratch lives in this file-scope device array instead of a caller
+// workspace.  Every GPU that loads the library holds the array until exit.
+namespace {
+
+constexpr int64_t kStaticMaxN = int64_t(1) << 18;      // samples per call
+constexpr int64_t kStaticMaxBins = int64_t(1) << 16;   // spreading bins
+constexpr int64_t kStaticTiles = (kStaticMaxN + kSortTile - 1) / kSortTile;
+constexpr int64_t kStaticScanLen =
+    (256 * kStaticTiles > kStaticMaxBins + 1) ? 256 * kStaticTiles : kStaticMaxBins + 1;
+// word offsets inside the array (each region starts on a 256-byte boundary)
+constexpr int64_t kOffKeys0 = 0;
+constexpr int64_t kOffVals0 = kOffKeys0 + kStaticMaxN;
+constexpr int64_t kOffKeys1 = kOffVals0 + kStaticMaxN;
+constexpr int64_t kOffVals1 = kOffKeys1 + kStaticMaxN;
+constexpr int64_t kOffCounts = kOffVals1 + kStaticMaxN;
+constexpr int64_t kOffHist = kOffCounts + kStaticMaxBins;
+constexpr int64_t kOffScan = kOffHist + ((256 * kStaticTiles + 1 + 63) / 64) * 64;
+constexpr int64_t kOffErr = kOffScan + ((kStaticScanLen / 1024 + 2 + 63) / 64) * 64;
+constexpr int64_t kStaticWords = kOffErr + 64;
+
+static __device__ __align__(256) uint32_t g_sort_scratch[kStaticWords];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+uint32_t* g_static_base[kMaxDevices] = {nullptr};
+
+}  // namespace
+
 }  // namespace fk
+
+extern "C" fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const double* grid_lo,
+                                              const double* grid_hi, int precision, int64_t n,
+                                              const void* x_dev, uint32_t* perm_dev,
+                                              uint32_t* bin_start_dev, int32_t* bad_dev,
+                                              void* stream) {
+  using namespace fk;
+  if (!geom || !grid_lo || !grid_hi) return FKREG_ERR_INVALID_ARG;
+  const int d = geom->dim;
+  if (d < 1 || d > 3) return FKREG_ERR_INVALID_ARG;
+  if (precision != FKREG_F32 && precision != FKREG_F64) return FKREG_ERR_INVALID_ARG;
+  if (n < 0 || n > kStaticMaxN) return FKREG_ERR_INVALID_ARG;
+  if ((n > 0 && !x_dev) || !perm_dev || !bin_start_dev) return FKREG_ERR_INVALID_ARG;
+  int64_t nbins = 1;
+  for (int j = 0; j < d; ++j) {
+    if (geom->nf[j] < 1 || geom->tile[j] < 1 || geom->nbins[j] < 1 ||
+        geom->nbins[j] != (geom->nf[j] + geom->tile[j] - 1) / geom->tile[j] ||
+        !(geom->inv_h[j] > 0) || !(grid_hi[j] > grid_lo[j]))
+      return FKREG_ERR_INVALID_ARG;
+    nbins *= geom->nbins[j];
+  }
+  if (nbins > kStaticMaxBins) return FKREG_ERR_INVALID_ARG;
+  // one-time set-up per device: the device address of the array (host code
+  // cannot use the symbol itself, which names a host-side shadow)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FKREG_ERR_CUDA;
+  uint32_t* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_base[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return FKREG_ERR_CUDA;
+      g_static_base[dev] = static_cast<uint32_t*>(p);
+    }
+    base = g_static_base[dev];
+  }
+  GeoDev g{};
+  g.d = d;
+  for (int j = 0; j < 3; ++j) {
+    g.nf[j] = j < d ? geom->nf[j] : 1;
+    g.tile[j] = j < d ? geom->tile[j] : 1;
+    g.nbins[j] = j < d ? geom->nbins[j] : 1;
+    g.lo[j] = j < d ? grid_lo[j] : 0.0;
+    g.hi[j] = j < d ? grid_hi[j] : 0.0;
+    g.inv_h[j] = j < d ? geom->inv_h[j] : 1.0;
+    g.inv_h_f[j] = float(g.inv_h[j]);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t* keys0 = base + kOffKeys0;
+  uint32_t* vals0 = base + kOffVals0;
+  uint32_t* keys1 = base + kOffKeys1;
+  uint32_t* vals1 = base + kOffVals1;
+  uint32_t* counts = base + kOffCounts;
+  uint32_t* hist = base + kOffHist;
+  uint32_t* scan = base + kOffScan;
+  int* errw = reinterpret_cast<int*>(base + kOffErr);
+  int64_t launches = 0;
+  // the array keeps the previous call's contents: zero what must start at zero
+  if (cudaMemsetAsync(counts, 0, sizeof(uint32_t) * nbins, s) != cudaSuccess) return FKREG_ERR_CUDA;
+  if (cudaMemsetAsync(errw, 0, sizeof(int), s) != cudaSuccess) return FKREG_ERR_CUDA;
+  if (n > 0) {
+    const unsigned blocks = unsigned((n + 255) / 256);
+    if (precision == FKREG_F32)
+      bin_keys_kernel<float><<<blocks, 256, 0, s>>>(g, n, static_cast<const float*>(x_dev), keys0,
+                                                    vals0, counts, errw);
+    else
+      bin_keys_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x_dev), keys0,
+                                                     vals0, counts, errw);
+    if (cudaGetLastError() != cudaSuccess) return FKREG_ERR_CUDA;
+  }
+  int bits = 0;
+  while ((int64_t(1) << bits) < nbins) ++bits;
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  uint32_t *kin = keys0, *vin = vals0, *kout = keys1, *vout = vals1;
+  for (int p = 0; p < passes && n > 0; ++p) {
+    const int shift = p * kRadixBits;
+    radix_upsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, n, shift, ntiles, hist);
+    if (cudaGetLastError() != cudaSuccess) return FKREG_ERR_CUDA;
+    if (exclusive_scan(hist, hist, 256 * ntiles, scan, s, &launches) != cudaSuccess) return FKREG_ERR_CUDA;
+    radix_downsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, vin, n, shift, ntiles, hist, kout,
+                                                              vout);
+    if (cudaGetLastError() != cudaSuccess) return FKREG_ERR_CUDA;
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  if (exclusive_scan(counts, bin_start_dev, nbins, scan, s, &launches) != cudaSuccess) return FKREG_ERR_CUDA;
+  if (n > 0 && cudaMemcpyAsync(perm_dev, vin, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s) !=
+                   cudaSuccess)
+    return FKREG_ERR_CUDA;
+  if (bad_dev && cudaMemcpyAsync(bad_dev, errw, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) !=
+                     cudaSuccess)
+    return FKREG_ERR_CUDA;
+  return FKREG_OK;
+}
+

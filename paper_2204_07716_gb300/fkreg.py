@@ -29,7 +29,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA"
 EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
            "fkreg_smooth", "fkreg_df", "fkreg_variance", "fkreg_set_timing",
-           "fkreg_stage_times", "fkreg_sync_status",
+           "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy"]
 
 
@@ -96,6 +96,9 @@ def load():
     L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
     L.fkreg_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]
+    L.fkreg_bin_sort_static.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int, i64, vp, vp,
+                                        vp, vp, vp]
     L.fkreg_sync_status.argtypes = [vp, vp]
     L.fkreg_last_error.argtypes = [vp]
     L.fkreg_last_error.restype = ctypes.c_char_p
