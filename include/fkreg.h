@@ -227,8 +227,10 @@ fkreg_status fkreg_smooth(fkreg_plan plan, const void* y_dev, const fkreg_output
  * the smoothing outputs.  probes_dev [n_probes][n] (plan precision, ORIGINAL
  * sample order) or NULL: then probe (p, i) is drawn on the device from the
  * counter-based generator c = splitmix64(seed XOR splitmix64((p << 40) XOR i)),
- * u1 = ((c >> 11) + 1) 2^-53, u2 = (splitmix64(c) >> 11) 2^-53,
- * w = sqrt(-2 ln u1) cos(2 pi u2).  n_probes <= max_probes.
+ * then Box-Muller w = sqrt(-2 ln u1) cos(2 pi u2) in the plan precision:
+ * FKREG_F64: u1 = ((c >> 11) + 1) 2^-53, u2 = (splitmix64(c) >> 11) 2^-53;
+ * FKREG_F32: u1 = ((c >> 40) + 1) 2^-24, u2 = (splitmix64(c) >> 40) 2^-24.
+ * n_probes <= max_probes.
  */
 fkreg_status fkreg_df(fkreg_plan plan, const void* y_dev, int n_probes, uint64_t seed,
                       const void* probes_dev, const fkreg_outputs* out, void* stream);

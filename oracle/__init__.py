@@ -69,6 +69,9 @@ def lib():
         L.or_lpr_solve.restype = ctypes.c_int
         L.or_probes.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, dp]
         L.or_probes.restype = None
+        L.or_probes_f32.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_float)]
+        L.or_probes_f32.restype = None
         L.or_splitmix64.argtypes = [ctypes.c_uint64]
         L.or_splitmix64.restype = ctypes.c_uint64
         _lib = L
@@ -262,8 +265,17 @@ def select_h(gcv_values: Sequence[float], dstd: float = 0.0) -> int:
     return int(ok.max())
 
 
-def probes(seed: int, n_probes: int, n: int) -> np.ndarray:
-    """Counter-based Gaussian probes [n_probes, n] (SplitMix64 + Box-Muller)."""
+def probes(seed: int, n_probes: int, n: int, precision: str = "f64") -> np.ndarray:
+    """Counter-based Gaussian probes [n_probes, n] (SplitMix64 + Box-Muller).
+
+    ``precision="f32"`` evaluates the single-precision variant (24-bit
+    uniforms, float arithmetic) and returns float32 values.
+    """
+    if precision == "f32":
+        out32 = np.zeros((n_probes, n), dtype=np.float32)
+        lib().or_probes_f32(ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), n_probes, n,
+                            out32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        return out32
     out = np.zeros((n_probes, n))
     lib().or_probes(ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), n_probes, n, _dp(out))
     return out

@@ -286,4 +286,21 @@ void or_probes(uint64_t seed, int np, int64_t n, double* out) {
     }
 }
 
+/*
+ * The same probes evaluated in single precision (the generator an FP32 plan
+ * draws on the device): 24-bit uniforms u1 = ((c >> 40) + 1) 2^-24,
+ * u2 = (splitmix64(c) >> 40) 2^-24, Box-Muller in float.
+ */
+void or_probes_f32(uint64_t seed, int np, int64_t n, float* out) {
+  for (int p = 0; p < np; ++p)
+    for (int64_t i = 0; i < n; ++i) {
+      uint64_t ctr = ((uint64_t)p << 40) ^ (uint64_t)i;
+      uint64_t c = splitmix64(seed ^ splitmix64(ctr));
+      uint64_t c2 = splitmix64(c);
+      float u1 = (float)((uint32_t)(c >> 40) + 1u) * 0x1.0p-24f;
+      float u2 = (float)(uint32_t)(c2 >> 40) * 0x1.0p-24f;
+      out[(int64_t)p * n + i] = sqrtf(-2.0f * logf(u1)) * cosf(2.0f * (float)M_PI * u2);
+    }
+}
+
 uint64_t or_splitmix64(uint64_t z) { return splitmix64(z); }

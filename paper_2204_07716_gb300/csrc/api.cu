@@ -95,7 +95,7 @@ int64_t full_cells(const int64_t* n, int d) {
 
 namespace fk {
 
-// kind 0: forward R2C, kind 1: inverse C2R
+// kind 0: forward R2C, kind 1: inverse C2R, kind 2: inverse C2R with outputs interleaved
 fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, cufftHandle* h) {
   auto key = std::make_tuple(kind, dims[0], P->d > 1 ? dims[1] : 1, P->d > 2 ? dims[2] : 1, batch);
   auto it = P->ffts.find(key);
@@ -113,7 +113,19 @@ fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, 
   else
     type = kind == 0 ? CUFFT_D2Z : CUFFT_Z2D;
   size_t work = 0;
-  cufftResult r = cufftMakePlanMany64(hd, P->d, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &work);
+  cufftResult r;
+  if (kind == 2) {
+    // inverse transform whose outputs are interleaved per cell: element
+    // (field b, cell m) lands at m * batch + b
+    long long inembed[3] = {n[0], n[1], n[2]};
+    inembed[P->d - 1] = n[P->d - 1] / 2 + 1;
+    long long onembed[3] = {n[0], n[1], n[2]};
+    long long idist = 1;
+    for (int a = 0; a < P->d; ++a) idist *= inembed[a];
+    r = cufftMakePlanMany64(hd, P->d, n, inembed, 1, idist, onembed, batch, 1, type, batch, &work);
+  } else {
+    r = cufftMakePlanMany64(hd, P->d, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &work);
+  }
   if (r != CUFFT_SUCCESS) {
     cufftDestroy(hd);
     return plan_err(P, FKREG_ERR_CUFFT, "cufftMakePlanMany64 failed (" + std::to_string(int(r)) + ")");
@@ -276,7 +288,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
       std::vector<int> bts = {P->ns + P->nrhs_real * P->nt};
       if (P->max_probes > 0) bts.push_back(P->f2max);
       for (int bt : bts)
-        if ((st = fk::fft_get(P, 1, dims, bt, &h)) != FKREG_OK) {
+        if ((st = fk::fft_get(P, 2, dims, bt, &h)) != FKREG_OK) {
           std::string m = P->err;
           fkreg_plan_destroy(P);
           return set_global_error(st, m);
@@ -447,7 +459,7 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
       }
       {
         FK_STAGE(FKREG_STAGE_FFT_T2);
-        FK_STATUS(exec_fft(P, 1, P->bw[b].nf, f2, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
+        FK_STATUS(exec_fft(P, 2, P->bw[b].nf, f2, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
       }
       {
         FK_STAGE(FKREG_STAGE_INTERP);

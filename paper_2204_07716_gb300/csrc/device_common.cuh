@@ -1,0 +1,149 @@
+// Device helpers shared by the spreading, interpolation and solve kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace fk {
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T inv_h_of(const GeoDev& g, int j);
+template <>
+__device__ __forceinline__ float inv_h_of<float>(const GeoDev& g, int j) { return g.inv_h_f[j]; }
+template <>
+__device__ __forceinline__ double inv_h_of<double>(const GeoDev& g, int j) { return g.inv_h[j]; }
+
+// Spreading kernel phi at offset z (fine cells): exponential of semicircle
+// exp(beta (sqrt(1 - (2z/w)^2) - 1)) on |z| <= w/2, or the truncated Gaussian
+// exp(-beta z^2) of eq. 17.
+template <typename T>
+__device__ __forceinline__ T phi(int kind, int w, T beta, T z) {
+  if (kind == FKREG_SPREAD_ES) {
+    const T t = T(2) * z / T(w);
+    const T a = T(1) - t * t;
+    return a > T(0) ? exp(beta * (sqrt(a) - T(1))) : T(0);
+  }
+  return (fabs(z) <= T(0.5) * T(w)) ? exp(-beta * z * z) : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T sel3(int ax, T a, T b, T c) {
+  return ax == 0 ? a : (ax == 1 ? b : c);
+}
+
+__device__ __forceinline__ int64_t wrap_idx(int64_t m, int64_t nf) {
+  return m < 0 ? m + nf : (m >= nf ? m - nf : m);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Solve S a = e_1 (p x p, FP64, partial pivoting). Returns false if singular.
+__device__ __forceinline__ bool solve_e1(int p, double S[kMaxP][kMaxP], double a[kMaxP]) {
+  double r[kMaxP];
+  for (int i = 0; i < p; ++i) r[i] = (i == 0) ? 1.0 : 0.0;
+  for (int c = 0; c < p; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < p; ++i)
+      if (fabs(S[i][c]) > fabs(S[piv][c])) piv = i;
+    if (!(fabs(S[piv][c]) > 0.0)) return false;
+    if (piv != c) {
+      for (int j = 0; j < p; ++j) {
+        double t = S[c][j];
+        S[c][j] = S[piv][j];
+        S[piv][j] = t;
+      }
+      double t = r[c];
+      r[c] = r[piv];
+      r[piv] = t;
+    }
+    for (int i = c + 1; i < p; ++i) {
+      const double f = S[i][c] / S[c][c];
+      for (int j = c; j < p; ++j) S[i][j] -= f * S[c][j];
+      r[i] -= f * r[c];
+    }
+  }
+  for (int i = p - 1; i >= 0; --i) {
+    double v = r[i];
+    for (int j = i + 1; j < p; ++j) v -= S[i][j] * a[j];
+    a[i] = v / S[i][i];
+  }
+  return isfinite(a[0]);
+}
+
+__device__ __forceinline__ int mono_index(const MonoTab& m, int nm, int e0, int e1, int e2) {
+  for (int k = 0; k < nm; ++k)
+    if (m.e[k][0] == e0 && m.e[k][1] == e1 && m.e[k][2] == e2) return k;
+  return 0;
+}
+
+// sigma^g for the t-field monomial a
+__device__ __forceinline__ double tscale(const MonoTab& mono, int a, const double* sigma) {
+  double sc = 1.0;
+  for (int j = 0; j < 3; ++j)
+    for (int r = 0; r < mono.e[a][j]; ++r) sc *= sigma[j];
+  return sc;
+}
+
+// Scaled normal matrix S~_ab = s_(a+b) / sigma^(a+b) from the s-fields, and
+// a = S~^-1 e_1 (the intercept is unchanged by the scaling), by elimination.
+__device__ __forceinline__ bool lpr_weights(const MonoTab& mono, int p, const double* s,
+                                            const double* sigma, double a[kMaxP]) {
+  double S[kMaxP][kMaxP];
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) {
+      const int e0 = mono.e[i][0] + mono.e[j][0];
+      const int e1 = mono.e[i][1] + mono.e[j][1];
+      const int e2 = mono.e[i][2] + mono.e[j][2];
+      const int k = mono_index(mono, mono.n, e0, e1, e2);
+      double sc = 1.0;
+      for (int r = 0; r < e0; ++r) sc *= sigma[0];
+      for (int r = 0; r < e1; ++r) sc *= sigma[1];
+      for (int r = 0; r < e2; ++r) sc *= sigma[2];
+      S[i][j] = s[k] / sc;
+    }
+  return solve_e1(p, S, a);
+}
+
+// Same result with closed forms for p <= 3 (one division).
+__device__ __forceinline__ bool lpr_weights_fast(const MonoTab& mono, int p, const double* s,
+                                                 const double* sigma, double a[kMaxP]) {
+  if (p == 1) {
+    a[0] = 1.0 / s[0];
+    return s[0] > 0.0;
+  }
+  if (p == 2) {  // 1-D local linear
+    const double s01 = s[1] / sigma[0], s11 = s[2] / (sigma[0] * sigma[0]);
+    const double det = s[0] * s11 - s01 * s01;
+    if (!(det > 0.0)) return false;
+    const double inv = 1.0 / det;
+    a[0] = s11 * inv;
+    a[1] = -s01 * inv;
+    return isfinite(a[0]);
+  }
+  if (p == 3) {  // 2-D local linear, s-fields 1, z1, z2, z1z1, z1z2, z2z2
+    const double g0 = sigma[0], g1 = sigma[1];
+    const double s00 = s[0], s01 = s[1] / g0, s02 = s[2] / g1;
+    const double s11 = s[3] / (g0 * g0), s12 = s[4] / (g0 * g1), s22 = s[5] / (g1 * g1);
+    const double c0 = s11 * s22 - s12 * s12;
+    const double c1 = s12 * s02 - s01 * s22;
+    const double c2 = s01 * s12 - s11 * s02;
+    const double det = s00 * c0 + s01 * c1 + s02 * c2;
+    if (!(det > 0.0)) return false;
+    const double inv = 1.0 / det;
+    a[0] = c0 * inv;
+    a[1] = c1 * inv;
+    a[2] = c2 * inv;
+    return isfinite(a[0]);
+  }
+  return lpr_weights(mono, p, s, sigma, a);
+}
+
+}  // namespace fk

@@ -226,6 +226,8 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
     w = 2 * m;
     beta = 3.0 * M_PI / (4.0 * m);
   }
+  if (d * w > 64)
+    return fail(err, FKREG_ERR_UNSUPPORTED, "spreading width too large for this dimension (dim * w <= 64)");
   g->w = w;
   g->beta = beta;
 
@@ -287,7 +289,8 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
       const int64_t cand[] = {2048, 64, 32, 16, 12, 8, 6, 4, 2};
       t = 2;
       for (int64_t c : cand) {
-        if ((d == 2 && c > 32) || (d == 3 && c > 16)) continue;
+        // 2-D tiles of 16 keep the interpolation window of a bin cache-sized
+        if ((d == 2 && c > 16) || (d == 3 && c > 16)) continue;
         int64_t cells = 1;
         for (int a = 0; a < d; ++a) cells *= (c + pad2);
         if (cells * tsz <= 96 * 1024) {
@@ -317,6 +320,19 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
   double nb = 1;
   for (int j = 0; j < d; ++j) nb *= double(g->nbins[j]);
   if (nb > 4.0e9) return fail(err, FKREG_ERR_UNSUPPORTED, "too many spreading bins (raise tile)");
+  // cell indices of the fine grids are 32-bit inside the kernels
+  {
+    double c1 = 1;
+    for (int j = 0; j < d; ++j) c1 *= double(g->nf[j]);
+    double c2 = 0;
+    for (int b = 0; b < nbw; ++b) {
+      double cb = 1;
+      for (int j = 0; j < d; ++j) cb *= double(bws[b].nf[j]);
+      c2 = std::max(c2, cb);
+    }
+    if (c1 >= 2.0e9 || c2 >= 2.0e9)
+      return fail(err, FKREG_ERR_UNSUPPORTED, "fine grid too large (more than 2^31 cells)");
+  }
 
   // 1/phihat tables: type-1 per axis, then per bandwidth per axis (k >= 0 half)
   if (tab) {

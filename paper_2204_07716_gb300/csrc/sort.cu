@@ -43,6 +43,7 @@ template <typename T>
 __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                 uint32_t* __restrict__ counts, int* __restrict__ errw) {
+  // counts == nullptr: the caller counts with bin_count_shared
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t key = 0;
@@ -63,7 +64,22 @@ __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
   if (bad) atomicOr(errw, 1);
   keys[i] = key;
   vals[i] = uint32_t(i);
-  atomicAdd(&counts[key], 1u);
+  if (counts) atomicAdd(&counts[key], 1u);
+}
+
+// Bin counts through a per-block shared-memory histogram (few bins: the
+// global counters would otherwise see heavy contention).
+__global__ void bin_count_shared(const uint32_t* __restrict__ keys, int64_t n, int64_t nbins,
+                                 uint32_t* __restrict__ counts) {
+  extern __shared__ uint32_t h[];
+  for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    atomicAdd(&h[keys[i]], 1u);
+  __syncthreads();
+  for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x)
+    if (h[b]) atomicAdd(&counts[b], h[b]);
 }
 
 // ---- exclusive scan of uint32 (three kernels, any length) ----------------
@@ -269,14 +285,22 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
   if (e != cudaSuccess) return e;
   if (n > 0) {
     const unsigned blocks = unsigned((n + 255) / 256);
+    const bool shared_hist = nbins <= 8192;
+    uint32_t* gcounts = shared_hist ? nullptr : counts;
     if (P->prec == FKREG_F32)
       bin_keys_kernel<float><<<blocks, 256, 0, s>>>(g, n, static_cast<const float*>(x), keys0, vals0,
-                                                    counts, errw);
+                                                    gcounts, errw);
     else
       bin_keys_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), keys0,
-                                                     vals0, counts, errw);
+                                                     vals0, gcounts, errw);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     P->launches += 1;
+    if (shared_hist) {
+      const unsigned hb = unsigned(std::min<int64_t>((n + 4095) / 4096, 152 * 4));
+      bin_count_shared<<<hb, 512, sizeof(uint32_t) * nbins, s>>>(keys0, n, nbins, counts);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      P->launches += 1;
+    }
   }
   // radix passes over the significant bits of the bin index
   int bits = 0;

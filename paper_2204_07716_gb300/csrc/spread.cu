@@ -2,13 +2,17 @@
 //
 // fine_s[m] = sum_i c_{s,i} prod_j phi(m_j - u_ij),  u_ij = (x_ij - lo_j) nf_j / P_j,
 // periodic in m_j (mod nf_j).  One CTA owns one sub-problem: up to kSubMax
-// sorted samples of one bin.  It accumulates their contributions into a
-// shared-memory copy of the bin's tile plus a halo of ceil(w/2) cells per
-// side, with shared-memory atomics, and then adds the tile to the fine grid
-// in global memory with one atomic per non-zero cell.  Strengths are handled
-// in chunks that fit the shared-memory budget.
+// sorted samples of one bin.  Each thread takes one sample at a time and adds
+// its w^d window into a shared-memory copy of the bin's tile plus a halo of
+// ceil(w/2) cells per side (shared-memory atomics); the CTA then adds the tile
+// to the fine grid in global memory with one atomic per non-zero cell.
+// Strengths go in chunks that fit the shared-memory budget.  W > 0 fixes the
+// width at compile time (unrolled window, weights in registers).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace fk {
@@ -17,30 +21,9 @@ namespace {
 
 constexpr int kSpreadThreads = 256;
 constexpr int kMaxChunk = 8;
-constexpr int kMaxW = 24;
+constexpr int kMaxWRun = 24;
 
-template <typename T>
-__device__ __forceinline__ T inv_h_of(const GeoDev& g, int j);
-template <>
-__device__ __forceinline__ float inv_h_of<float>(const GeoDev& g, int j) { return g.inv_h_f[j]; }
-template <>
-__device__ __forceinline__ double inv_h_of<double>(const GeoDev& g, int j) { return g.inv_h[j]; }
-
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-
-// Spreading kernel value at offset z (fine cells).
-template <typename T>
-__device__ __forceinline__ T phi(int kind, int w, T beta, T z) {
-  if (kind == FKREG_SPREAD_ES) {
-    const T t = T(2) * z / T(w);
-    const T a = T(1) - t * t;
-    return a > T(0) ? exp(beta * (sqrt(a) - T(1))) : T(0);
-  }
-  return (fabs(z) <= T(0.5) * T(w)) ? exp(-beta * z * z) : T(0);
-}
-
-template <typename T, int D>
+template <typename T, int D, int W>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict__ str, int s0,
               int scount, int chunk, const uint32_t* __restrict__ sub_bin,
@@ -53,7 +36,6 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
   const uint32_t b = sub_bin[k];
   const uint32_t first = sub_first[k];
   const uint32_t last = min(first + uint32_t(kSubMax), bin_start[b + 1]);
-  // bin multi-index (axis 0 slowest)
   int64_t bj[3] = {0, 0, 0};
   {
     int64_t rem = b;
@@ -63,73 +45,112 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
     }
   }
   int64_t o[3] = {0, 0, 0};
-  int W[3] = {1, 1, 1};
+  int W3[3] = {1, 1, 1};
   for (int j = 0; j < D; ++j) {
     o[j] = bj[j] * g.tile[j] - g.pad;
-    W[j] = int(g.tile[j]) + 2 * g.pad;
+    W3[j] = int(g.tile[j]) + 2 * g.pad;
   }
-  const int cells = W[0] * W[1] * W[2];
-  const int w = g.w;
+  const int cells = W3[0] * W3[1] * W3[2];
+  const int w = W > 0 ? W : g.w;
   const T beta = T(g.beta);
   const T halfw = T(0.5) * T(w);
   const int64_t fine_cells = g.nf[0] * g.nf[1] * g.nf[2];
+  constexpr int WR = W > 0 ? W : kMaxWRun;
 
   for (int c0 = 0; c0 < scount; c0 += chunk) {
     const int cn = min(chunk, scount - c0);
     for (int idx = threadIdx.x; idx < cn * cells; idx += blockDim.x) sm[idx] = T(0);
     __syncthreads();
     for (uint32_t p = first + threadIdx.x; p < last; p += blockDim.x) {
-      T wt[D][kMaxW];
+      T wt[D][WR];
       int l[3] = {0, 0, 0};
+#pragma unroll
       for (int j = 0; j < D; ++j) {
         const T u = mul_rn(xs[int64_t(j) * n + p], inv_h_of<T>(g, j));
         const T f0 = ceil(u - halfw);
         l[j] = int(int64_t(f0) - o[j]);
-        for (int t = 0; t < w; ++t) wt[j][t] = phi<T>(g.skind, w, beta, (f0 + T(t)) - u);
+        const T off = f0 - u;
+        if constexpr (W > 0) {
+#pragma unroll
+          for (int t = 0; t < W; ++t) wt[j][t] = phi<T>(g.skind, w, beta, off + T(t));
+        } else {
+          for (int t = 0; t < w; ++t) wt[j][t] = phi<T>(g.skind, w, beta, off + T(t));
+        }
       }
       T cv[kMaxChunk];
-      for (int c = 0; c < cn; ++c) cv[c] = str[int64_t(s0 + c0 + c) * n + p];
-      if (D == 1) {
-        for (int t0 = 0; t0 < w; ++t0) {
-          const int idx = l[0] + t0;
-          for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + idx], cv[c] * wt[0][t0]);
-        }
-      } else if (D == 2) {
-        for (int t0 = 0; t0 < w; ++t0) {
-          const int row = (l[0] + t0) * W[1] + l[1];
-          for (int t1 = 0; t1 < w; ++t1) {
-            const T v = wt[0][t0] * wt[D - 1][t1];
-            for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + row + t1], cv[c] * v);
+#pragma unroll
+      for (int c = 0; c < kMaxChunk; ++c) cv[c] = c < cn ? str[int64_t(s0 + c0 + c) * n + p] : T(0);
+      if constexpr (W > 0) {
+        if (D == 1) {
+#pragma unroll
+          for (int t0 = 0; t0 < W; ++t0) {
+            const int idx = l[0] + t0;
+#pragma unroll
+            for (int c = 0; c < kMaxChunk; ++c)
+              if (c < cn) atomicAdd(&sm[c * cells + idx], cv[c] * wt[0][t0]);
           }
-        }
-      } else {
-        for (int t0 = 0; t0 < w; ++t0)
-          for (int t1 = 0; t1 < w; ++t1) {
-            const int row = ((l[0] + t0) * W[1] + (l[1] + t1)) * W[2] + l[2];
-            const T v01 = wt[0][t0] * wt[1 % D][t1];
-            for (int t2 = 0; t2 < w; ++t2) {
-              const T v = v01 * wt[D - 1][t2];
-              for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + row + t2], cv[c] * v);
+        } else if (D == 2) {
+#pragma unroll
+          for (int t0 = 0; t0 < W; ++t0) {
+            const int row = (l[0] + t0) * W3[1] + l[1];
+            const T w0 = wt[0][t0];
+#pragma unroll
+            for (int t1 = 0; t1 < W; ++t1) {
+              const T v = w0 * wt[D - 1][t1];
+#pragma unroll
+              for (int c = 0; c < kMaxChunk; ++c)
+                if (c < cn) atomicAdd(&sm[c * cells + row + t1], cv[c] * v);
             }
           }
+        } else {
+#pragma unroll 1
+          for (int t0 = 0; t0 < W; ++t0)
+#pragma unroll
+            for (int t1 = 0; t1 < W; ++t1) {
+              const int row = ((l[0] + t0) * W3[1] + (l[1] + t1)) * W3[2] + l[2];
+              const T v01 = wt[0][t0] * wt[1 % D][t1];
+#pragma unroll
+              for (int t2 = 0; t2 < W; ++t2) {
+                const T v = v01 * wt[D - 1][t2];
+#pragma unroll
+                for (int c = 0; c < kMaxChunk; ++c)
+                  if (c < cn) atomicAdd(&sm[c * cells + row + t2], cv[c] * v);
+              }
+            }
+        }
+      } else {
+        // runtime width: plain loops over the window
+        int ncw = 1;
+        for (int j = 0; j < D; ++j) ncw *= w;
+#pragma unroll 1
+        for (int cidx = 0; cidx < ncw; ++cidx) {
+          int rem = cidx, lidx = 0, mult = 1;
+          T v = T(1);
+          for (int j = D - 1; j >= 0; --j) {
+            const int t = rem % w;
+            rem /= w;
+            v *= wt[j][t];
+            lidx += (l[j] + t) * mult;
+            mult *= W3[j];
+          }
+#pragma unroll 1
+          for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + lidx], cv[c] * v);
+        }
       }
     }
     __syncthreads();
     // flush the tile (periodic wrap) into the fine grid
     for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
       int rem = idx;
-      int64_t gidx = 0;
       int lj[3];
       for (int j = 2; j >= 0; --j) {
-        lj[j] = rem % W[j];
-        rem /= W[j];
+        lj[j] = rem % W3[j];
+        rem /= W3[j];
       }
+      int64_t gidx = 0;
       for (int j = 0; j < 3; ++j) {
         int64_t m = 0;
-        if (j < D) {
-          m = (o[j] + lj[j]) % g.nf[j];
-          if (m < 0) m += g.nf[j];
-        }
+        if (j < D) m = wrap_idx(o[j] + lj[j], g.nf[j]);
         gidx = gidx * g.nf[j] + m;
       }
       for (int c = 0; c < cn; ++c) {
@@ -138,6 +159,51 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
       }
     }
     __syncthreads();
+  }
+}
+
+template <typename T, int D, int W>
+cudaError_t launch_spread_w(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
+  const GeoDev& g = P->geo;
+  int cells = 1;
+  for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
+  const size_t per = size_t(cells) * sizeof(T);
+  const size_t budget = 100 * 1024;
+  int chunk = int(std::max<size_t>(1, std::min<size_t>(budget / per, kMaxChunk)));
+  chunk = std::min(chunk, scount);
+  const size_t smem = per * chunk;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(spread_kernel<T, D, W>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned(P->nsub_max);
+  const uint32_t* sub_total = wsp<uint32_t>(P, P->r_substart) + P->nbins_total;
+  spread_kernel<T, D, W><<<grid, kSpreadThreads, smem, st>>>(
+      g, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_str), s0, scount, chunk,
+      wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
+      wsp<uint32_t>(P, P->r_binstart), sub_total, wsp<T>(P, P->r_fine));
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t launch_spread(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
+  const int w = P->geo.w;
+  if (w == 7) return launch_spread_w<T, D, 7>(P, s0, scount, st);
+  if constexpr (sizeof(T) == 8 && D < 3) {
+    if (w == 10) return launch_spread_w<T, D, 10>(P, s0, scount, st);
+    if (w == 13) return launch_spread_w<T, D, 13>(P, s0, scount, st);
+  }
+  if (w > kMaxWRun) return cudaErrorInvalidValue;
+  return launch_spread_w<T, D, 0>(P, s0, scount, st);
+}
+
+template <typename T>
+cudaError_t launch_spread_d(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
+  switch (P->d) {
+    case 1: return launch_spread<T, 1>(P, s0, scount, st);
+    case 2: return launch_spread<T, 2>(P, s0, scount, st);
+    default: return launch_spread<T, 3>(P, s0, scount, st);
   }
 }
 
@@ -150,14 +216,27 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
 }
 
 // Gaussian probe value for (probe p, original index i): counter-based
-// SplitMix64 words, Box-Muller transform in FP64.
-__device__ __forceinline__ double probe_value(uint64_t seed, int p, uint32_t i) {
+// SplitMix64 words and the Box-Muller transform, evaluated in the plan
+// precision (53-bit uniforms in FP64, 24-bit uniforms in FP32).
+template <typename T>
+__device__ __forceinline__ T probe_value(uint64_t seed, int p, uint32_t i);
+template <>
+__device__ __forceinline__ double probe_value<double>(uint64_t seed, int p, uint32_t i) {
   const uint64_t ctr = (uint64_t(p) << 40) ^ uint64_t(i);
   const uint64_t c = splitmix64(seed ^ splitmix64(ctr));
   const uint64_t c2 = splitmix64(c);
   const double u1 = (double(c >> 11) + 1.0) * 0x1.0p-53;
   const double u2 = double(c2 >> 11) * 0x1.0p-53;
   return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+template <>
+__device__ __forceinline__ float probe_value<float>(uint64_t seed, int p, uint32_t i) {
+  const uint64_t ctr = (uint64_t(p) << 40) ^ uint64_t(i);
+  const uint64_t c = splitmix64(seed ^ splitmix64(ctr));
+  const uint64_t c2 = splitmix64(c);
+  const float u1 = float(uint32_t(c >> 40) + 1u) * 0x1.0p-24f;
+  const float u2 = float(uint32_t(c2 >> 40)) * 0x1.0p-24f;
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
 template <typename T>
@@ -180,7 +259,7 @@ __global__ void gather_strengths_kernel(int64_t n, const uint32_t* __restrict__ 
     }
   }
   for (int p = 0; p < n_probes; ++p) {
-    const T v = probes ? probes[int64_t(p) * n + i] : T(probe_value(seed, p, i));
+    const T v = probes ? probes[int64_t(p) * n + i] : probe_value<T>(seed, p, i);
     str[int64_t(k++) * n + s] = v;
   }
 }
@@ -206,39 +285,6 @@ __global__ void residual_strengths_kernel(int64_t n, const uint32_t* __restrict_
       v = dr * dr;
     }
     str[int64_t(first + r) * n + s] = v;
-  }
-}
-
-template <typename T, int D>
-cudaError_t launch_spread(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
-  const GeoDev& g = P->geo;
-  int cells = 1;
-  for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
-  const size_t per = size_t(cells) * sizeof(T);
-  const size_t budget = 100 * 1024;
-  int chunk = int(std::max<size_t>(1, std::min<size_t>(budget / per, kMaxChunk)));
-  chunk = std::min(chunk, scount);
-  const size_t smem = per * chunk;
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(spread_kernel<T, D>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  const unsigned grid = unsigned(P->nsub_max);
-  const uint32_t* sub_total = wsp<uint32_t>(P, P->r_substart) + P->nbins_total;
-  spread_kernel<T, D><<<grid, kSpreadThreads, smem, st>>>(
-      g, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_str), s0, scount, chunk,
-      wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
-      wsp<uint32_t>(P, P->r_binstart), sub_total, wsp<T>(P, P->r_fine));
-  P->launches += 1;
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_spread_d(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
-  switch (P->d) {
-    case 1: return launch_spread<T, 1>(P, s0, scount, st);
-    case 2: return launch_spread<T, 2>(P, s0, scount, st);
-    default: return launch_spread<T, 3>(P, s0, scount, st);
   }
 }
 

@@ -254,6 +254,18 @@ def test_device_probes_follow_the_counter_generator():
     np.testing.assert_allclose(tr_dev, b["trace"].cpu().numpy(), rtol=1e-12)
 
 
+def test_fp32_device_probes_follow_the_single_precision_generator():
+    w = inputs.random_small(61, 2, 20_000, 32, 1, [0.04], precision="f32", tol=1e-6)
+    p = plan_for(w, n_probes=3)
+    p.set_points(torch.tensor(w.x))
+    a = p.df(torch.tensor(w.y), 3, seed=777, want=())
+    tr_dev = a["trace"].cpu().numpy().copy()
+    z = oracle.probes(777, 3, w.n, precision="f32")
+    b = p.df(torch.tensor(w.y), 3, probes=torch.tensor(z), want=())
+    p.sync()
+    np.testing.assert_allclose(tr_dev[:, :2], b["trace"].cpu().numpy()[:, :2], rtol=1e-5)
+
+
 def test_fp32_df_sweep():
     w = inputs.nw3d_df(n=30_000, grid=16, n_bw=4, n_probes=4)
     z = w.probes

@@ -205,6 +205,12 @@ def test_probe_generator_is_standard_normal():
         assert abs(z[p].var() - 1) < 0.03
     c = np.corrcoef(z)
     assert np.max(np.abs(c - np.eye(4))) < 0.02
+    z32 = oracle.probes(2024, 2, 50_000, precision="f32")
+    assert z32.dtype == np.float32
+    for p in range(2):
+        assert stats.kstest(z32[p].astype(np.float64), "norm").pvalue > 1e-4
+    # the single-precision variant draws from the same counters (24-bit uniforms)
+    assert np.corrcoef(z[0], z32[0].astype(np.float64))[0, 1] > 0.999
     # SplitMix64 is a bijection on 64-bit words: no collisions on a run of counters
     outs = {oracle.splitmix64(k) for k in range(5000)}
     assert len(outs) == 5000
