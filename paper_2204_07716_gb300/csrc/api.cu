@@ -122,7 +122,8 @@ fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, 
     long long onembed[3] = {n[0], n[1], n[2]};
     long long idist = 1;
     for (int a = 0; a < P->d; ++a) idist *= inembed[a];
-    r = cufftMakePlanMany64(hd, P->d, n, inembed, 1, idist, onembed, batch, 1, type, batch, &work);
+    const long long rec = fk::t2_record_stride(batch);
+    r = cufftMakePlanMany64(hd, P->d, n, inembed, 1, idist, onembed, rec, 1, type, batch, &work);
   } else {
     r = cufftMakePlanMany64(hd, P->d, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &work);
   }
@@ -258,7 +259,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   L.take(P->r_gspec, 2 * T * size_t(P->nbw) * P->fgrid * l_half);
   L.take(P->r_gfield, T * size_t(P->nbw) * P->fgrid * l_cells);
   L.take(P->r_t2spec, 2 * T * size_t(P->f2max) * t2_half);
-  L.take(P->r_t2field, T * size_t(P->f2max) * t2_cells);
+  L.take(P->r_t2field, T * size_t(fk::t2_record_stride(P->f2max)) * t2_cells);
   L.take(P->r_part, sizeof(double) * size_t(P->nblk_interp + 1) * P->nbw * P->nacc);
   L.take(P->r_smax, 8 * size_t(P->nbw));
   // cuFFT plans for the standard passes (work sizes decide the reserved area)
@@ -574,6 +575,7 @@ fkreg_status fkreg_sync_status(fkreg_plan P, void* stream) {
     return cuda_err(P, e, "read error word");
   if (word) {
     cudaMemset(P->ws + P->r_err.off, 0, sizeof(int));
+    if (word & 2) return plan_err(P, FKREG_ERR_TIMEOUT, "a bounded device-side wait gave up");
     return plan_err(P, FKREG_ERR_DEVICE, "a sample lies outside the grid box or is not finite");
   }
   return FKREG_OK;

@@ -157,6 +157,7 @@ cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out
                          cudaStream_t s);
 
 const uint32_t* perm_ptr(fkreg_plan_s* P);
+int t2_record_stride(int F2);
 
 // fft helpers (api.cu)
 fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, cufftHandle* h);

@@ -9,7 +9,24 @@
 //   wSw_p      = sum_i w_pi (S w_p)_i,  ww_p = sum_i w_pi^2   (Sec. 2.1)
 //   tr_exact   = K_H(0) sum_i [S(x_i)^-1]_11                  (diagonal of S_h)
 // Block partials are summed in a fixed order, so results are deterministic.
+//
+// Fields are stored interleaved per fine-grid cell ([cell][rec], rec >= F2
+// a multiple of 4), so a warp gathers one sample at a time with its lanes
+// spread over the fields: every load of the 32 lanes is one contiguous run.
+// A warp walks a group of 32 consecutive sorted samples, parks each sample's
+// field values in shared memory, and then each lane takes one sample for the
+// FP64 solve and the reductions.  Fields go in passes of pass_f; pass 0 holds
+// the s-fields.
+//
+// Two kernels share that structure.  The TMA kernel takes one spreading
+// sub-problem (samples of one bin) at a time, copies the bin's window of the
+// field grid (all fields) into shared memory with bulk asynchronous copies
+// completing on an mbarrier, and gathers from there.  The global kernel
+// gathers straight from the (cache-resident) field grid and serves 3-D and
+// windows that do not fit shared memory.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -18,28 +35,307 @@ namespace fk {
 
 namespace {
 
-constexpr int kI2Warps = 4;
+constexpr int kI2Warps = 16;   // global kernel: warps per block (upper bound)
+constexpr int kTWarps = 8;     // TMA kernel: warps per block
 constexpr int kMaxAcc = 512;
-constexpr int kMaxCh = 4;     // 32-field chunks per pass (pass_f <= 128)
-constexpr int kMaxWRun = 32;  // runtime-width fallback
+constexpr int kMaxWRun = 32;   // runtime-width fallback
+constexpr uint32_t kMaxSpin = 1u << 22;  // bounded mbarrier wait
 
-// Fields are stored interleaved per fine-grid cell ([cell][F2]), so a warp
-// gathers one sample at a time with its lanes spread over the fields: every
-// load of the 32 lanes is one contiguous run.  A warp walks a group of 32
-// consecutive sorted samples (one bin, nearby cells, cache-resident), parks
-// each sample's field values in shared memory, and then each lane takes one
-// sample for the FP64 solve and the reductions.  Fields go in passes of
-// pass_f so the staging buffer stays small; pass 0 holds the s-fields.
-// W > 0 fixes the spreading width at compile time (unrolled window, weights
-// in registers); W == 0 is the runtime-width fallback.
-template <typename T, int D, int W>
+// ---- bulk-copy / mbarrier primitives (inline PTX) --------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return uint32_t(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(m))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// ---- per-sample window geometry ---------------------------------------------
+template <typename T, int D>
+struct SampleWin {
+  int i0, i1, i2;   // first cell of the window per axis (unwrapped)
+  T wl0, wl1;       // lane-distributed 1-D kernel values (axis l / w, tap l % w)
+};
+
+template <typename T, int D>
+__device__ __forceinline__ SampleWin<T, D> sample_window(const GeoDev& g, int w, T beta, T halfw,
+                                                         T ih0, T ih1, T ih2, T x0, T x1, T x2,
+                                                         int lane) {
+  SampleWin<T, D> sw;
+  T off0, off1 = T(0), off2 = T(0);
+  {
+    const T u = x0 * ih0;
+    const T f = ceil(u - halfw);
+    sw.i0 = int(f);
+    off0 = f - u;
+  }
+  sw.i1 = 0;
+  sw.i2 = 0;
+  if (D > 1) {
+    const T u = x1 * ih1;
+    const T f = ceil(u - halfw);
+    sw.i1 = int(f);
+    off1 = f - u;
+  }
+  if (D > 2) {
+    const T u = x2 * ih2;
+    const T f = ceil(u - halfw);
+    sw.i2 = int(f);
+    off2 = f - u;
+  }
+  const int ax = lane / w, t = lane % w;
+  sw.wl0 = ax < D ? phi<T>(g.skind, w, beta, sel3<T>(ax, off0, off1, off2) + T(t)) : T(0);
+  const int l2 = lane + 32, ax2 = l2 / w, t2 = l2 % w;
+  sw.wl1 = ax2 < D ? phi<T>(g.skind, w, beta, sel3<T>(ax2, off0, off1, off2) + T(t2)) : T(0);
+  return sw;
+}
+
+// Gather fields [f_first, f_first + fcount) of one sample from the global
+// field grid (periodic wrap).  Lanes cover the fields.
+template <typename T, int D, int W, int NCH>
+__device__ __forceinline__ void gather_global(const T* __restrict__ fld, int64_t rec, int f_first,
+                                              int fcount, int lane, const SampleWin<T, D>& sw,
+                                              int w, int nf0, int nf1, int nf2, T* cellw,
+                                              T acc[NCH]) {
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) acc[ch] = T(0);
+  const T* fb = fld + f_first + lane;
+  if constexpr (W > 0) {
+    T wa[D][W];
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        const int l = d * W + t;
+        wa[d][t] = l < 32 ? __shfl_sync(0xffffffffu, sw.wl0, l) : __shfl_sync(0xffffffffu, sw.wl1, l - 32);
+      }
+    const int ilast = D == 1 ? sw.i0 : (D == 2 ? sw.i1 : sw.i2);
+    const int nlast = D == 1 ? nf0 : (D == 2 ? nf1 : nf2);
+    int64_t clf[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) clf[t] = wrap_idx(ilast + t, nlast) * rec;
+    if (D == 1) {
+#pragma unroll
+      for (int t0 = 0; t0 < W; ++t0) {
+        const T* q = fb + clf[t0];
+        const T v = wa[0][t0];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch)
+          if (lane + ch * 32 < fcount) acc[ch] += __ldg(q + ch * 32) * v;
+      }
+    } else if (D == 2) {
+#pragma unroll
+      for (int t0 = 0; t0 < W; ++t0) {
+        const T* rowp = fb + wrap_idx(sw.i0 + t0, nf0) * nf1 * rec;
+        const T w0 = wa[0][t0];
+#pragma unroll
+        for (int t1 = 0; t1 < W; ++t1) {
+          const T* q = rowp + clf[t1];
+          const T v = w0 * wa[D - 1][t1];
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch)
+            if (lane + ch * 32 < fcount) acc[ch] += __ldg(q + ch * 32) * v;
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int t0 = 0; t0 < W; ++t0) {
+        const int64_t r0 = wrap_idx(sw.i0 + t0, nf0) * nf1;
+#pragma unroll
+        for (int t1 = 0; t1 < W; ++t1) {
+          const T* rowp = fb + (r0 + wrap_idx(sw.i1 + t1, nf1)) * nf2 * rec;
+          const T w01 = wa[0][t0] * wa[1 % D][t1];
+#pragma unroll
+          for (int t2 = 0; t2 < W; ++t2) {
+            const T* q = rowp + clf[t2];
+            const T v = w01 * wa[D - 1][t2];
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch)
+              if (lane + ch * 32 < fcount) acc[ch] += __ldg(q + ch * 32) * v;
+          }
+        }
+      }
+    }
+  } else {
+    // runtime width: tensor-product cell weights through shared memory
+    int ncw = 1;
+    for (int j = 0; j < D; ++j) ncw *= w;
+    for (int c0 = 0; c0 < ncw; c0 += 32) {
+      const int c = c0 + lane;
+      int rem = c < ncw ? c : 0;
+      T v = T(1);
+      for (int d = D - 1; d >= 0; --d) {
+        const int t = rem % w;
+        rem /= w;
+        const int l = d * w + t;
+        const T a0 = __shfl_sync(0xffffffffu, sw.wl0, l & 31);
+        const T a1 = __shfl_sync(0xffffffffu, sw.wl1, l & 31);
+        v *= (l < 32) ? a0 : a1;
+      }
+      if (c < ncw) cellw[c] = v;
+    }
+    __syncwarp();
+    for (int c = 0; c < ncw; ++c) {
+      int rem = c;
+      int64_t cell = 0, mult = 1;
+      for (int d = D - 1; d >= 0; --d) {
+        const int t = rem % w;
+        rem /= w;
+        const int id = d == 0 ? sw.i0 : (d == 1 ? sw.i1 : sw.i2);
+        const int nfd = d == 0 ? nf0 : (d == 1 ? nf1 : nf2);
+        cell += wrap_idx(id + t, nfd) * mult;
+        mult *= nfd;
+      }
+      const T* q = fb + cell * rec;
+      const T v = cellw[c];
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch)
+        if (lane + ch * 32 < fcount) acc[ch] += q[ch * 32] * v;
+    }
+    __syncwarp();
+  }
+}
+
+// Gather from a window staged in shared memory: win[(l0 * e1 + l1) * rec + f],
+// (l0, l1) = (i0 - o0, i1 - o1) already checked to lie inside the window.
+template <typename T, int D, int W, int NCH>
+__device__ __forceinline__ void gather_smem(const T* win, int rec, int e1, int l0, int l1,
+                                            int f_first, int fcount, int lane,
+                                            const SampleWin<T, D>& sw, T acc[NCH]) {
+  static_assert(D <= 2 && W > 0, "shared-memory gather serves 1-D and 2-D with a fixed width");
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) acc[ch] = T(0);
+  T wa[D][W];
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const int l = d * W + t;
+      wa[d][t] = l < 32 ? __shfl_sync(0xffffffffu, sw.wl0, l) : __shfl_sync(0xffffffffu, sw.wl1, l - 32);
+    }
+  const T* fb = win + f_first + lane;
+  if (D == 1) {
+    const T* q0 = fb + l0 * rec;
+#pragma unroll
+    for (int t0 = 0; t0 < W; ++t0) {
+      const T v = wa[0][t0];
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch)
+        if (lane + ch * 32 < fcount) acc[ch] += q0[t0 * rec + ch * 32] * v;
+    }
+  } else {
+#pragma unroll
+    for (int t0 = 0; t0 < W; ++t0) {
+      const T* rowp = fb + ((l0 + t0) * e1 + l1) * rec;
+      const T w0 = wa[0][t0];
+#pragma unroll
+      for (int t1 = 0; t1 < W; ++t1) {
+        const T v = w0 * wa[D - 1][t1];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch)
+          if (lane + ch * 32 < fcount) acc[ch] += rowp[t1 * rec + ch * 32] * v;
+      }
+    }
+  }
+}
+
+// Per-group epilogue state shared by both kernels.
+struct GroupCtx {
+  int ns, nt, p, nq, n_rhs_real, n_probes, cplx, n_rhs_out, nacc, order, b;
+};
+
+// Phase B of one pass: lane = sample (valid when lane < cnt).  Solves on pass 0,
+// then forms mhat for this pass's responses / probes and accumulates.
+template <typename T>
+__device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mono, const BwDev& B,
+                                            const T* my, int pass, int q_done, int q_in, int lane,
+                                            bool valid, int64_t s, int64_t n,
+                                            const T* __restrict__ str,
+                                            const uint32_t* __restrict__ perm,
+                                            T* __restrict__ mhat_at_x, const T* tsc, T af[kMaxP],
+                                            double* red) {
+  if (pass == 0) {
+    double a[kMaxP] = {0, 0, 0, 0};
+    bool ok = false;
+    if (valid) {
+      double sv[kMaxMono];
+      for (int k = 0; k < c.ns; ++k) sv[k] = double(my[k]);
+      if (c.order == 0) {
+        ok = sv[0] > 0.0;
+        a[0] = ok ? 1.0 / sv[0] : 0.0;
+      } else {
+        ok = lpr_weights_fast(mono, c.p, sv, B.sigma, a);
+      }
+    }
+    for (int k = 0; k < c.p; ++k) af[k] = ok ? T(a[k]) * tsc[k] : T(0);
+    const double tv = warp_sum_t<double>((valid && ok) ? B.k0 * a[0] : 0.0);
+    if (lane == 0) red[c.nacc - 1] += tv;
+  }
+  const int fq0 = pass == 0 ? c.ns : 0;
+  const uint32_t orig = valid ? perm[s] : 0u;
+  for (int qq = 0; qq < q_in; ++qq) {
+    const int q = q_done + qq;
+    T mh = T(0);
+    for (int k = 0; k < c.p; ++k) mh += af[k] * my[fq0 + qq * c.nt + k];
+    const T cv = valid ? str[int64_t(1 + q) * n + s] : T(0);
+    if (q < c.n_rhs_real) {
+      const T r = valid ? cv - mh : T(0);
+      const T v = warp_sum_t<T>(r * r);
+      if (lane == 0) red[q] += double(v);
+      if (valid && mhat_at_x) {
+        const int mult = c.cplx ? 2 : 1;
+        const int rr = q / mult, pt = q % mult;
+        mhat_at_x[((int64_t(c.b) * c.n_rhs_out + rr) * n + orig) * mult + pt] = mh;
+      }
+    } else {
+      const int pp = q - c.n_rhs_real;
+      const T v1 = warp_sum_t<T>(valid ? cv * mh : T(0));
+      const T v2 = warp_sum_t<T>(valid ? cv * cv : T(0));
+      if (lane == 0) {
+        red[c.n_rhs_real + pp] += double(v1);
+        red[c.n_rhs_real + c.n_probes + pp] += double(v2);
+      }
+    }
+  }
+}
+
+// ---- kernel 1: gathers from the global field grid ---------------------------
+template <typename T, int D, int W, int NCH>
 __global__ void __launch_bounds__(kI2Warps * 32)
 interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int order, int64_t n,
               const T* __restrict__ xs, const T* __restrict__ str, const uint32_t* __restrict__ perm,
-              const T* __restrict__ fld, int F2, int pass_f, int n_rhs_real, int n_probes, int cplx,
-              int n_rhs_out, T* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part) {
+              const T* __restrict__ fld, int rec, int F2, int pass_f, int n_rhs_real, int n_probes,
+              int cplx, int n_rhs_out, T* __restrict__ mhat_at_x, int nacc, int nbw,
+              double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = int(blockDim.x >> 5);
   const int w = W > 0 ? W : g.w;
   int ncw = 1;
   for (int j = 0; j < D; ++j) ncw *= w;
@@ -47,8 +343,8 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   const int bstride = pass_f + 1;
   double* red_all = reinterpret_cast<double*>(smem_raw);
   double* red = red_all + warp * nacc;
-  T* cellw = reinterpret_cast<T*>(red_all + kI2Warps * nacc) + warp * ncw;
-  T* buf = reinterpret_cast<T*>(red_all + kI2Warps * nacc) + kI2Warps * ncw + warp * 32 * bstride;
+  T* cellw = reinterpret_cast<T*>(red_all + nwarps * nacc) + warp * ncw;
+  T* buf = reinterpret_cast<T*>(red_all + nwarps * nacc) + nwarps * ncw + warp * 32 * bstride;
   for (int a = lane; a < nacc; a += 32) red[a] = 0.0;
   __syncwarp();
   const BwDev& B = bwt[b];
@@ -56,13 +352,16 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   const T ih0 = T(B.inv_h[0]), ih1 = T(D > 1 ? B.inv_h[1] : 1.0), ih2 = T(D > 2 ? B.inv_h[2] : 1.0);
   const T beta = T(g.beta);
   const T halfw = T(0.5) * T(w);
-  const int ns = mono.n, nt = mono.nt, p = nt;
-  const int nq = n_rhs_real + n_probes;
+  GroupCtx c{mono.n, mono.nt, mono.nt, n_rhs_real + n_probes, n_rhs_real, n_probes, cplx,
+             n_rhs_out, nacc, order, b};
   T tsc[kMaxP];
-  for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
+  for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
+  // each block walks one contiguous run of sample groups (neighbouring bins)
   const int64_t ngroups = (n + 31) / 32;
-  const int64_t gstride = int64_t(gridDim.x) * kI2Warps;
-  for (int64_t grp = int64_t(blockIdx.x) * kI2Warps + warp; grp < ngroups; grp += gstride) {
+  const int64_t per_block = (ngroups + gridDim.x - 1) / gridDim.x;
+  const int64_t g_begin = int64_t(blockIdx.x) * per_block;
+  const int64_t g_end = min(ngroups, g_begin + per_block);
+  for (int64_t grp = g_begin + warp; grp < g_end; grp += nwarps) {
     const int64_t s0 = grp * 32;
     const int cnt = int(min(int64_t(32), n - s0));
     const int64_t s = s0 + lane;
@@ -70,11 +369,9 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
     T af[kMaxP] = {T(0), T(0), T(0), T(0)};
     int q_done = 0, f_first = 0;
     for (int pass = 0; f_first < F2; ++pass) {
-      const int q_in = pass == 0 ? min(nq, (pass_f - ns) / nt) : min(nq - q_done, pass_f / nt);
-      const int f_last = (pass == 0 ? ns : f_first) + q_in * nt;
+      const int q_in = pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt) : min(c.nq - q_done, pass_f / c.nt);
+      const int f_last = (pass == 0 ? c.ns : f_first) + q_in * c.nt;
       const int fcount = f_last - f_first;
-      const int nch = (fcount + 31) / 32;
-      // ---- phase A: warp-cooperative gather, one sample at a time ----
       T xn0 = xs[s0], xn1 = D > 1 ? xs[n + s0] : T(0), xn2 = D > 2 ? xs[2 * n + s0] : T(0);
       for (int j = 0; j < cnt; ++j) {
         const T x0 = xn0, x1 = xn1, x2 = xn2;
@@ -83,178 +380,17 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
           if (D > 1) xn1 = xs[n + s0 + j + 1];
           if (D > 2) xn2 = xs[2 * n + s0 + j + 1];
         }
-        int i0, i1 = 0, i2 = 0;
-        T off0, off1 = T(0), off2 = T(0);
-        {
-          const T u = x0 * ih0;
-          const T f = ceil(u - halfw);
-          i0 = int(f);
-          off0 = f - u;
-        }
-        if (D > 1) {
-          const T u = x1 * ih1;
-          const T f = ceil(u - halfw);
-          i1 = int(f);
-          off1 = f - u;
-        }
-        if (D > 2) {
-          const T u = x2 * ih2;
-          const T f = ceil(u - halfw);
-          i2 = int(f);
-          off2 = f - u;
-        }
-        // 1-D kernel values: lane l holds axis l / w, tap l % w (two rounds)
-        T wl0, wl1;
-        {
-          const int ax = lane / w, t = lane % w;
-          wl0 = ax < D ? phi<T>(g.skind, w, beta, sel3<T>(ax, off0, off1, off2) + T(t)) : T(0);
-          const int l2 = lane + 32, ax2 = l2 / w, t2 = l2 % w;
-          wl1 = ax2 < D ? phi<T>(g.skind, w, beta, sel3<T>(ax2, off0, off1, off2) + T(t2)) : T(0);
-        }
-        T acc[kMaxCh];
+        const SampleWin<T, D> sw =
+            sample_window<T, D>(g, w, beta, halfw, ih0, ih1, ih2, x0, x1, x2, lane);
+        T acc[NCH];
+        gather_global<T, D, W, NCH>(fld, rec, f_first, fcount, lane, sw, w, nf0, nf1, nf2, cellw, acc);
 #pragma unroll
-        for (int ch = 0; ch < kMaxCh; ++ch) acc[ch] = T(0);
-        const T* fb = fld + f_first + lane;
-        if constexpr (W > 0) {
-          T wa[D][W > 0 ? W : 1];
-#pragma unroll
-          for (int d = 0; d < D; ++d)
-#pragma unroll
-            for (int t = 0; t < W; ++t) {
-              const int l = d * W + t;
-              wa[d][t] = l < 32 ? __shfl_sync(0xffffffffu, wl0, l) : __shfl_sync(0xffffffffu, wl1, l - 32);
-            }
-          int cl[W > 0 ? W : 1];
-#pragma unroll
-          for (int t = 0; t < W; ++t) cl[t] = int(wrap_idx(D == 1 ? i0 + t : (D == 2 ? i1 + t : i2 + t),
-                                                          D == 1 ? nf0 : (D == 2 ? nf1 : nf2)));
-          if (D == 1) {
-#pragma unroll
-            for (int t0 = 0; t0 < W; ++t0) {
-              const T* q = fb + int64_t(cl[t0]) * F2;
-              const T v = wa[0][t0];
-#pragma unroll
-              for (int ch = 0; ch < kMaxCh; ++ch)
-                if (ch < nch && lane + ch * 32 < fcount) acc[ch] += __ldg(q + ch * 32) * v;
-            }
-          } else if (D == 2) {
-#pragma unroll
-            for (int t0 = 0; t0 < W; ++t0) {
-              const int row = int(wrap_idx(i0 + t0, nf0)) * nf1;
-              const T w0 = wa[0][t0];
-#pragma unroll
-              for (int t1 = 0; t1 < W; ++t1) {
-                const T* q = fb + int64_t(row + cl[t1]) * F2;
-                const T v = w0 * wa[D - 1][t1];
-#pragma unroll
-                for (int ch = 0; ch < kMaxCh; ++ch)
-                  if (ch < nch && lane + ch * 32 < fcount) acc[ch] += __ldg(q + ch * 32) * v;
-              }
-            }
-          } else {
-#pragma unroll 1
-            for (int t0 = 0; t0 < W; ++t0) {
-              const int r0 = int(wrap_idx(i0 + t0, nf0)) * nf1;
-#pragma unroll
-              for (int t1 = 0; t1 < W; ++t1) {
-                const int r1 = (r0 + int(wrap_idx(i1 + t1, nf1))) * nf2;
-                const T w01 = wa[0][t0] * wa[1 % D][t1];
-#pragma unroll
-                for (int t2 = 0; t2 < W; ++t2) {
-                  const T* q = fb + int64_t(r1 + cl[t2]) * F2;
-                  const T v = w01 * wa[D - 1][t2];
-#pragma unroll
-                  for (int ch = 0; ch < kMaxCh; ++ch)
-                    if (ch < nch && lane + ch * 32 < fcount) acc[ch] += __ldg(q + ch * 32) * v;
-                }
-              }
-            }
-          }
-        } else {
-          // runtime width: tensor-product cell weights through shared memory
-          for (int c0 = 0; c0 < ncw; c0 += 32) {
-            const int c = c0 + lane;
-            int rem = c < ncw ? c : 0;
-            T v = T(1);
-            for (int d = D - 1; d >= 0; --d) {
-              const int t = rem % w;
-              rem /= w;
-              const int l = d * w + t;
-              const T a0 = __shfl_sync(0xffffffffu, wl0, l & 31);
-              const T a1 = __shfl_sync(0xffffffffu, wl1, l & 31);
-              v *= (l < 32) ? a0 : a1;
-            }
-            if (c < ncw) cellw[c] = v;
-          }
-          __syncwarp();
-          for (int c = 0; c < ncw; ++c) {
-            int rem = c;
-            int64_t cell = 0, mult = 1;
-            for (int d = D - 1; d >= 0; --d) {
-              const int t = rem % w;
-              rem /= w;
-              const int id = d == 0 ? i0 : (d == 1 ? i1 : i2);
-              const int nfd = d == 0 ? nf0 : (d == 1 ? nf1 : nf2);
-              cell += wrap_idx(id + t, nfd) * mult;
-              mult *= nfd;
-            }
-            const T* q = fb + cell * F2;
-            const T v = cellw[c];
-#pragma unroll
-            for (int ch = 0; ch < kMaxCh; ++ch)
-              if (ch < nch && lane + ch * 32 < fcount) acc[ch] += q[ch * 32] * v;
-          }
-        }
-#pragma unroll
-        for (int ch = 0; ch < kMaxCh; ++ch)
-          if (ch < nch && lane + ch * 32 < fcount) buf[j * bstride + lane + ch * 32] = acc[ch];
+        for (int ch = 0; ch < NCH; ++ch)
+          if (lane + ch * 32 < fcount) buf[j * bstride + lane + ch * 32] = acc[ch];
         __syncwarp();
       }
-      // ---- phase B: one lane per sample ----
-      const T* my = buf + lane * bstride;
-      if (pass == 0) {
-        double a[kMaxP] = {0, 0, 0, 0};
-        bool ok = false;
-        if (valid) {
-          double sv[kMaxMono];
-          for (int k = 0; k < ns; ++k) sv[k] = double(my[k]);
-          if (order == 0) {
-            ok = sv[0] > 0.0;
-            a[0] = ok ? 1.0 / sv[0] : 0.0;
-          } else {
-            ok = lpr_weights_fast(mono, p, sv, B.sigma, a);
-          }
-        }
-        for (int k = 0; k < p; ++k) af[k] = ok ? T(a[k]) * tsc[k] : T(0);
-        const double tv = warp_sum_t<double>((valid && ok) ? B.k0 * a[0] : 0.0);
-        if (lane == 0) red[nacc - 1] += tv;
-      }
-      const int fq0 = pass == 0 ? ns : 0;
-      const uint32_t orig = valid ? perm[s] : 0u;
-      for (int qq = 0; qq < q_in; ++qq) {
-        const int q = q_done + qq;
-        T mh = T(0);
-        for (int k = 0; k < p; ++k) mh += af[k] * my[fq0 + qq * nt + k];
-        const T c = valid ? str[int64_t(1 + q) * n + s] : T(0);
-        if (q < n_rhs_real) {
-          const T r = valid ? c - mh : T(0);
-          const T v = warp_sum_t<T>(r * r);
-          if (lane == 0) red[q] += double(v);
-          if (valid && mhat_at_x) {
-            const int mult = cplx ? 2 : 1;
-            const int rr = q / mult, pt = q % mult;
-            mhat_at_x[((int64_t(b) * n_rhs_out + rr) * n + orig) * mult + pt] = mh;
-          }
-        } else {
-          const int pp = q - n_rhs_real;
-          const T v1 = warp_sum_t<T>(valid ? c * mh : T(0));
-          const T v2 = warp_sum_t<T>(valid ? c * c : T(0));
-          if (lane == 0) {
-            red[n_rhs_real + pp] += double(v1);
-            red[n_rhs_real + n_probes + pp] += double(v2);
-          }
-        }
-      }
+      finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n, str,
+                     perm, mhat_at_x, tsc, af, red);
       __syncwarp();
       q_done += q_in;
       f_first = f_last;
@@ -263,7 +399,145 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   __syncthreads();
   for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
     double t = 0.0;
-    for (int wv = 0; wv < kI2Warps; ++wv) t += red_all[wv * nacc + a];
+    for (int wv = 0; wv < nwarps; ++wv) t += red_all[wv * nacc + a];
+    part[(int64_t(blockIdx.x) * nbw + b) * nacc + a] = t;
+  }
+}
+
+// ---- kernel 2: bin windows staged in shared memory by bulk copies ----------
+// One block takes spreading sub-problems (samples of one bin) in turn.  The
+// bin's window of the field grid, [wm0][wm1][rec] cells x fields, is copied
+// row by row with cp.async.bulk (periodic wrap splits a row in two), the
+// copies complete on an mbarrier, and the warps gather from shared memory.
+// The wait is bounded: if it gives up, the block raises the timeout bit of
+// the error word, waits once more (bounded) for its copies, and exits.
+template <typename T, int D, int W, int NCH>
+__global__ void __launch_bounds__(kTWarps * 32)
+interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int order,
+                  int64_t n, const T* __restrict__ xs, const T* __restrict__ str,
+                  const uint32_t* __restrict__ perm, const T* __restrict__ fld, int rec, int F2,
+                  int pass_f, int n_rhs_real, int n_probes, int cplx, int n_rhs_out,
+                  T* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part,
+                  const uint32_t* __restrict__ sub_bin, const uint32_t* __restrict__ sub_first,
+                  const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ sub_total,
+                  int wm0, int wm1, int* __restrict__ errw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = int(blockDim.x >> 5);
+  const int bstride = pass_f + 1;
+  const size_t win_bytes = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
+  T* win = reinterpret_cast<T*>(smem_raw);
+  double* red_all = reinterpret_cast<double*>(smem_raw + win_bytes);
+  double* red = red_all + warp * nacc;
+  T* buf = reinterpret_cast<T*>(red_all + nwarps * nacc) + warp * 32 * bstride;
+  for (int a = lane; a < nacc; a += 32) red[a] = 0.0;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const BwDev& B = bwt[b];
+  const int nf0 = int(B.nf[0]), nf1 = D > 1 ? int(B.nf[1]) : 1;
+  const T ih0 = T(B.inv_h[0]), ih1 = T(D > 1 ? B.inv_h[1] : 1.0);
+  const double r0 = double(B.nf[0]) / double(g.nf[0]);
+  const double r1 = D > 1 ? double(B.nf[1]) / double(g.nf[1]) : 1.0;
+  const T beta = T(g.beta);
+  const T halfw = T(0.5) * T(W);
+  GroupCtx c{mono.n, mono.nt, mono.nt, n_rhs_real + n_probes, n_rhs_real, n_probes, cplx,
+             n_rhs_out, nacc, order, b};
+  T tsc[kMaxP];
+  for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
+  uint32_t parity = 0;
+  const uint32_t nsub = *sub_total;
+  bool failed = false;
+  for (uint32_t k = blockIdx.x; k < nsub; k += gridDim.x) {
+    const uint32_t bin = sub_bin[k];
+    const uint32_t first = sub_first[k];
+    const uint32_t last = min(first + uint32_t(kSubMax), bin_start[bin + 1]);
+    const int64_t bj0 = D > 1 ? int64_t(bin) / g.nbins[1] : int64_t(bin);
+    const int64_t bj1 = D > 1 ? int64_t(bin) % g.nbins[1] : 0;
+    const int o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - 1;
+    const int o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - 1 : 0;
+    if (threadIdx.x == 0) {
+      fence_proxy_async();  // earlier reads of the window come before the new copies
+      mbar_expect_tx(&mbar, uint32_t(size_t(wm0) * wm1 * rec * sizeof(T)));
+      for (int r = 0; r < (D > 1 ? wm0 : 1); ++r) {
+        // axis of the contiguous segment: axis 1 in 2-D, axis 0 in 1-D
+        const int oseg = D > 1 ? o1 : o0;
+        const int nseg = D > 1 ? nf1 : nf0;
+        const int eseg = D > 1 ? wm1 : wm0;
+        const int64_t rowbase = D > 1 ? wrap_idx(o0 + r, nf0) * int64_t(nf1) : 0;
+        const int start = int(wrap_idx(oseg, nseg));
+        const int len = min(eseg, nseg - start);
+        T* dst = win + size_t(r) * eseg * rec;
+        bulk_g2s(dst, fld + (rowbase + start) * rec, uint32_t(size_t(len) * rec * sizeof(T)), &mbar);
+        if (len < eseg)
+          bulk_g2s(dst + size_t(len) * rec, fld + rowbase * rec,
+                   uint32_t(size_t(eseg - len) * rec * sizeof(T)), &mbar);
+      }
+    }
+    bool ok = false;
+    for (uint32_t it = 0; it < kMaxSpin && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(errw, 2);
+      bool late = false;
+      for (uint32_t it = 0; it < kMaxSpin && !late; ++it) late = mbar_try_wait(&mbar, parity);
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    const int ngr = int((last - first + 31) / 32);
+    for (int gi = warp; gi < ngr; gi += nwarps) {
+      const int64_t s0 = int64_t(first) + int64_t(gi) * 32;
+      const int cnt = int(min(int64_t(32), int64_t(last) - s0));
+      const int64_t s = s0 + lane;
+      const bool valid = lane < cnt;
+      T af[kMaxP] = {T(0), T(0), T(0), T(0)};
+      int q_done = 0, f_first = 0;
+      for (int pass = 0; f_first < F2; ++pass) {
+        const int q_in =
+            pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt) : min(c.nq - q_done, pass_f / c.nt);
+        const int f_last = (pass == 0 ? c.ns : f_first) + q_in * c.nt;
+        const int fcount = f_last - f_first;
+        T xn0 = xs[s0], xn1 = D > 1 ? xs[n + s0] : T(0);
+        for (int j = 0; j < cnt; ++j) {
+          const T x0 = xn0, x1 = xn1;
+          if (j + 1 < cnt) {
+            xn0 = xs[s0 + j + 1];
+            if (D > 1) xn1 = xs[n + s0 + j + 1];
+          }
+          const SampleWin<T, D> sw =
+              sample_window<T, D>(g, W, beta, halfw, ih0, ih1, T(1), x0, x1, T(0), lane);
+          const int l0 = sw.i0 - o0, l1 = D > 1 ? sw.i1 - o1 : 0;
+          const bool inside =
+              l0 >= 0 && l0 + W <= wm0 && (D == 1 || (l1 >= 0 && l1 + W <= wm1));
+          T acc[NCH];
+          if (inside)
+            gather_smem<T, D, W, NCH>(win, rec, D > 1 ? wm1 : 1, l0, l1, f_first, fcount, lane, sw,
+                                      acc);
+          else
+            gather_global<T, D, W, NCH>(fld, rec, f_first, fcount, lane, sw, W, nf0, nf1, 1,
+                                        nullptr, acc);
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch)
+            if (lane + ch * 32 < fcount) buf[j * bstride + lane + ch * 32] = acc[ch];
+          __syncwarp();
+        }
+        finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n, str,
+                       perm, mhat_at_x, tsc, af, red);
+        __syncwarp();
+        q_done += q_in;
+        f_first = f_last;
+      }
+    }
+    __syncthreads();  // every read of this window is done before the next copies
+  }
+  if (failed) return;
+  __syncthreads();
+  for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
+    double t = 0.0;
+    for (int wv = 0; wv < nwarps; ++wv) t += red_all[wv * nacc + a];
     part[(int64_t(blockIdx.x) * nbw + b) * nacc + a] = t;
   }
 }
@@ -323,32 +597,72 @@ __global__ void finalize_kernel(const double* __restrict__ sums, int nbw, int na
   }
 }
 
-template <typename T, int D, int W>
+// Window extent of a bin on bandwidth b's fine grid (cells, per axis): covers
+// every window of a sample in the bin with one cell of slack on each side.
+inline int tma_window(const GeoDev& g, const BwDev& B, int j) {
+  const double r = double(B.nf[j]) / double(g.nf[j]);
+  return int(std::ceil(double(g.tile[j]) * r)) + 2 * g.pad + 3;
+}
+
+template <typename T>
+inline int record_stride(int F2) {
+  return (F2 + 3) / 4 * 4;
+}
+
+template <typename T, int D, int W, int NCH>
 cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
-                            cudaStream_t st, unsigned blocks, int nacc, int F2, int pass_f) {
+                            cudaStream_t st, int nacc, int F2) {
+  constexpr int pass_f = 32 * NCH;
+  const int rec = record_stride<T>(F2);
+  const unsigned blocks = unsigned(P->nblk_interp);
+  const size_t buf_warp = sizeof(T) * 32 * (pass_f + 1) + sizeof(double) * nacc;
+  if constexpr (D <= 2 && W > 0) {
+    const BwDev& B = P->bw[b];
+    const int wm0 = tma_window(P->geo, B, 0);
+    const int wm1 = D > 1 ? tma_window(P->geo, B, 1) : 1;
+    const size_t win = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
+    const size_t smem = win + buf_warp * kTWarps;
+    const bool fits = wm0 <= B.nf[0] && (D == 1 || wm1 <= B.nf[1]) && smem <= 220 * 1024;
+    if (fits) {
+      cudaError_t e = cudaFuncSetAttribute(interp_tma_kernel<T, D, W, NCH>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      interp_tma_kernel<T, D, W, NCH><<<blocks, kTWarps * 32, smem, st>>>(
+          P->geo, P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, wsp<T>(P, P->r_xs),
+          wsp<T>(P, P->r_str), perm_ptr(P), wsp<T>(P, P->r_t2field), rec, F2, pass_f, n_rhs_real,
+          n_probes, P->o.y_complex, P->nrhs, static_cast<T*>(mhat_at_x), nacc, P->nbw,
+          wsp<double>(P, P->r_part), wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
+          wsp<uint32_t>(P, P->r_binstart), wsp<uint32_t>(P, P->r_substart) + P->nbins_total, wm0,
+          wm1, wsp<int>(P, P->r_err));
+      P->launches += 1;
+      return cudaGetLastError();
+    }
+  }
   int ncw = 1;
   for (int j = 0; j < D; ++j) ncw *= P->geo.w;
   if (W > 0) ncw = 0;
-  const size_t smem = sizeof(double) * kI2Warps * nacc + sizeof(T) * kI2Warps * ncw +
-                      sizeof(T) * kI2Warps * 32 * (pass_f + 1);
-  if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(interp_kernel<T, D, W>,
+  // warps per block: as many as fit (up to kI2Warps) in the shared-memory budget
+  const size_t per_warp = buf_warp + sizeof(T) * ncw;
+  const int nwarps = int(std::min<size_t>(kI2Warps, (200 * 1024) / per_warp));
+  if (nwarps < 1) return cudaErrorInvalidConfiguration;
+  const size_t smem = per_warp * nwarps;
+  cudaError_t e = cudaFuncSetAttribute(interp_kernel<T, D, W, NCH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  interp_kernel<T, D, W><<<blocks, kI2Warps * 32, smem, st>>>(
+  interp_kernel<T, D, W, NCH><<<blocks, nwarps * 32, smem, st>>>(
       P->geo, P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, wsp<T>(P, P->r_xs),
-      wsp<T>(P, P->r_str), perm_ptr(P), wsp<T>(P, P->r_t2field), F2, pass_f, n_rhs_real, n_probes,
-      P->o.y_complex, P->nrhs, static_cast<T*>(mhat_at_x), nacc, P->nbw, wsp<double>(P, P->r_part));
+      wsp<T>(P, P->r_str), perm_ptr(P), wsp<T>(P, P->r_t2field), rec, F2, pass_f, n_rhs_real,
+      n_probes, P->o.y_complex, P->nrhs, static_cast<T*>(mhat_at_x), nacc, P->nbw,
+      wsp<double>(P, P->r_part));
   P->launches += 1;
   return cudaGetLastError();
 }
 
-template <typename T, int D>
+template <typename T, int D, int NCH>
 cudaError_t launch_interp_d(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
-                            cudaStream_t st, unsigned blocks, int nacc, int F2, int pass_f) {
+                            cudaStream_t st, int nacc, int F2) {
   const int w = P->geo.w;
-#define FK_W(WW) \
-  return launch_interp_w<T, D, WW>(P, b, n_rhs_real, n_probes, mhat_at_x, st, blocks, nacc, F2, pass_f)
+#define FK_W(WW) return launch_interp_w<T, D, WW, NCH>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2)
   if (w == 7) FK_W(7);
   if constexpr (sizeof(T) == 8 && D < 3) {
     if (w == 10) FK_W(10);
@@ -362,22 +676,20 @@ template <typename T>
 cudaError_t launch_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, void* mhat_at_x,
                           cudaStream_t st) {
   const int n_rhs_real = n_rhs_str;
-  const int64_t groups = (P->n + 31) / 32;
-  const unsigned blocks =
-      unsigned(std::min<int64_t>((groups + kI2Warps - 1) / kI2Warps, P->nblk_interp));
   const int nacc = n_rhs_real + 2 * n_probes + 1;
   if (nacc > kMaxAcc) return cudaErrorInvalidValue;
-  if (blocks == 0) return cudaSuccess;
   const int F2 = P->ns + (n_rhs_real + n_probes) * P->nt;
-  int pass_f = (int(sizeof(T)) == 4) ? 128 : 64;
-  pass_f = std::min(pass_f, ((F2 + 31) / 32) * 32);
-  pass_f = std::max(pass_f, P->ns + P->nt);
   if (P->d * P->geo.w > 64 || P->geo.w > kMaxWRun) return cudaErrorInvalidValue;
-  switch (P->d) {
-    case 1: return launch_interp_d<T, 1>(P, b, n_rhs_real, n_probes, mhat_at_x, st, blocks, nacc, F2, pass_f);
-    case 2: return launch_interp_d<T, 2>(P, b, n_rhs_real, n_probes, mhat_at_x, st, blocks, nacc, F2, pass_f);
-    default: return launch_interp_d<T, 3>(P, b, n_rhs_real, n_probes, mhat_at_x, st, blocks, nacc, F2, pass_f);
+  // fields per pass: 64 (float) or 32 (double)
+  const bool two = sizeof(T) == 4 && F2 > 32;
+  if (two) {
+    if (P->d == 1) return launch_interp_d<T, 1, 2>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2);
+    if (P->d == 2) return launch_interp_d<T, 2, 2>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2);
+    return launch_interp_d<T, 3, 2>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2);
   }
+  if (P->d == 1) return launch_interp_d<T, 1, 1>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2);
+  if (P->d == 2) return launch_interp_d<T, 2, 1>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2);
+  return launch_interp_d<T, 3, 1>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2);
 }
 
 }  // namespace
@@ -392,8 +704,7 @@ cudaError_t run_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, cons
 cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out, cudaStream_t st) {
   const int nacc = P->nrhs_real + 2 * n_probes + 1;
   double* sums = wsp<double>(P, P->r_part) + P->nblk_interp * int64_t(P->nbw) * P->nacc;
-  const int64_t groups = (P->n + 31) / 32;
-  const int64_t nblk = std::min<int64_t>((groups + kI2Warps - 1) / kI2Warps, P->nblk_interp);
+  const int64_t nblk = P->nblk_interp;
   const int tot = P->nbw * nacc;
   reduce_partials<<<tot, 256, 0, st>>>(wsp<double>(P, P->r_part), nblk, P->nbw, nacc, sums);
   cudaError_t e = cudaGetLastError();
@@ -405,5 +716,9 @@ cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out
   P->launches += 2;
   return cudaGetLastError();
 }
+
+// Field record stride of the type-2 grids for F2 fields (multiple of 4 so
+// every cell record starts on a 16-byte boundary for the bulk copies).
+int t2_record_stride(int F2) { return (F2 + 3) / 4 * 4; }
 
 }  // namespace fk

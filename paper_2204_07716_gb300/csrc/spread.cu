@@ -23,6 +23,22 @@ constexpr int kSpreadThreads = 256;
 constexpr int kMaxChunk = 8;
 constexpr int kMaxWRun = 24;
 
+// Shared-memory accumulator of the tile.  FP32 plans accumulate in 32-bit
+// fixed point (native integer shared-memory atomics); the scale of each
+// strength is 2^30 / sum_i |c_i| over the sub-problem, so no cell can
+// overflow (every spreading weight is <= 1) and one rounding step is
+// sum_i |c_i| / 2^31.  FP64 plans accumulate doubles directly.
+template <typename T>
+struct TileAcc {
+  using type = T;
+  static __device__ __forceinline__ void add(T* p, T v) { atomicAdd(p, v); }
+};
+template <>
+struct TileAcc<float> {
+  using type = int;
+  static __device__ __forceinline__ void add(int* p, float v) { atomicAdd(p, __float2int_rn(v)); }
+};
+
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict__ str, int s0,
@@ -30,7 +46,10 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
               const uint32_t* __restrict__ sub_first, const uint32_t* __restrict__ bin_start,
               const uint32_t* __restrict__ sub_total, T* __restrict__ fine) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+  using A = typename TileAcc<T>::type;
+  A* sm = reinterpret_cast<A*>(smem_raw);
+  __shared__ T s_scale[kMaxChunk], s_inv[kMaxChunk];
+  __shared__ T s_red[kSpreadThreads / 32][kMaxChunk];
   const uint32_t k = blockIdx.x;
   if (k >= *sub_total) return;
   const uint32_t b = sub_bin[k];
@@ -59,7 +78,33 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
 
   for (int c0 = 0; c0 < scount; c0 += chunk) {
     const int cn = min(chunk, scount - c0);
-    for (int idx = threadIdx.x; idx < cn * cells; idx += blockDim.x) sm[idx] = T(0);
+    for (int idx = threadIdx.x; idx < cn * cells; idx += blockDim.x) sm[idx] = A(0);
+    if (sizeof(A) == 4) {
+      // fixed-point scale per strength: 2^30 / sum |c| over this sub-problem
+      T part[kMaxChunk];
+#pragma unroll
+      for (int c = 0; c < kMaxChunk; ++c) part[c] = T(0);
+      for (uint32_t p = first + threadIdx.x; p < last; p += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < kMaxChunk; ++c)
+          if (c < cn) part[c] += fabs(str[int64_t(s0 + c0 + c) * n + p]);
+#pragma unroll
+      for (int c = 0; c < kMaxChunk; ++c) {
+        const T v = warp_sum_t<T>(part[c]);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5][c] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < kMaxChunk) {
+        T tot = T(0);
+        for (int wv = 0; wv < kSpreadThreads / 32; ++wv) tot += s_red[wv][threadIdx.x];
+        const T sc = tot > T(0) ? T(1073741824.0) / tot : T(0);
+        s_scale[threadIdx.x] = sc;
+        s_inv[threadIdx.x] = tot > T(0) ? tot / T(1073741824.0) : T(0);
+      }
+    } else if (threadIdx.x < kMaxChunk) {
+      s_scale[threadIdx.x] = T(1);
+      s_inv[threadIdx.x] = T(1);
+    }
     __syncthreads();
     for (uint32_t p = first + threadIdx.x; p < last; p += blockDim.x) {
       T wt[D][WR];
@@ -79,7 +124,8 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
       }
       T cv[kMaxChunk];
 #pragma unroll
-      for (int c = 0; c < kMaxChunk; ++c) cv[c] = c < cn ? str[int64_t(s0 + c0 + c) * n + p] : T(0);
+      for (int c = 0; c < kMaxChunk; ++c)
+        cv[c] = c < cn ? str[int64_t(s0 + c0 + c) * n + p] * s_scale[c] : T(0);
       if constexpr (W > 0) {
         if (D == 1) {
 #pragma unroll
@@ -87,7 +133,7 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
             const int idx = l[0] + t0;
 #pragma unroll
             for (int c = 0; c < kMaxChunk; ++c)
-              if (c < cn) atomicAdd(&sm[c * cells + idx], cv[c] * wt[0][t0]);
+              if (c < cn) TileAcc<T>::add(&sm[c * cells + idx], cv[c] * wt[0][t0]);
           }
         } else if (D == 2) {
 #pragma unroll
@@ -99,7 +145,7 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
               const T v = w0 * wt[D - 1][t1];
 #pragma unroll
               for (int c = 0; c < kMaxChunk; ++c)
-                if (c < cn) atomicAdd(&sm[c * cells + row + t1], cv[c] * v);
+                if (c < cn) TileAcc<T>::add(&sm[c * cells + row + t1], cv[c] * v);
             }
           }
         } else {
@@ -114,7 +160,7 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
                 const T v = v01 * wt[D - 1][t2];
 #pragma unroll
                 for (int c = 0; c < kMaxChunk; ++c)
-                  if (c < cn) atomicAdd(&sm[c * cells + row + t2], cv[c] * v);
+                  if (c < cn) TileAcc<T>::add(&sm[c * cells + row + t2], cv[c] * v);
               }
             }
         }
@@ -134,7 +180,7 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
             mult *= W3[j];
           }
 #pragma unroll 1
-          for (int c = 0; c < cn; ++c) atomicAdd(&sm[c * cells + lidx], cv[c] * v);
+          for (int c = 0; c < cn; ++c) TileAcc<T>::add(&sm[c * cells + lidx], cv[c] * v);
         }
       }
     }
@@ -154,8 +200,8 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
         gidx = gidx * g.nf[j] + m;
       }
       for (int c = 0; c < cn; ++c) {
-        const T v = sm[c * cells + idx];
-        if (v != T(0)) atomicAdd(&fine[int64_t(s0 + c0 + c) * fine_cells + gidx], v);
+        const A a = sm[c * cells + idx];
+        if (a != A(0)) atomicAdd(&fine[int64_t(s0 + c0 + c) * fine_cells + gidx], T(a) * s_inv[c]);
       }
     }
     __syncthreads();
