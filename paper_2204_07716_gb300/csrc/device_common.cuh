@@ -23,7 +23,7 @@ __device__ __forceinline__ double inv_h_of<double>(const GeoDev& g, int j) { ret
 template <typename T>
 __device__ __forceinline__ T phi(int kind, int w, T beta, T z) {
   if (kind == FKREG_SPREAD_ES) {
-    const T t = T(2) * z / T(w);
+    const T t = z * (T(2) / T(w));
     const T a = T(1) - t * t;
     return a > T(0) ? exp(beta * (sqrt(a) - T(1))) : T(0);
   }
@@ -112,15 +112,16 @@ __device__ __forceinline__ bool lpr_weights(const MonoTab& mono, int p, const do
   return solve_e1(p, S, a);
 }
 
-// Same result with closed forms for p <= 3 (one division).
+// Same result with closed forms for p <= 3 (one division); isg = 1 / sigma.
 __device__ __forceinline__ bool lpr_weights_fast(const MonoTab& mono, int p, const double* s,
-                                                 const double* sigma, double a[kMaxP]) {
+                                                 const double* sigma, const double* isg,
+                                                 double a[kMaxP]) {
   if (p == 1) {
     a[0] = 1.0 / s[0];
     return s[0] > 0.0;
   }
   if (p == 2) {  // 1-D local linear
-    const double s01 = s[1] / sigma[0], s11 = s[2] / (sigma[0] * sigma[0]);
+    const double s01 = s[1] * isg[0], s11 = s[2] * (isg[0] * isg[0]);
     const double det = s[0] * s11 - s01 * s01;
     if (!(det > 0.0)) return false;
     const double inv = 1.0 / det;
@@ -129,9 +130,9 @@ __device__ __forceinline__ bool lpr_weights_fast(const MonoTab& mono, int p, con
     return isfinite(a[0]);
   }
   if (p == 3) {  // 2-D local linear, s-fields 1, z1, z2, z1z1, z1z2, z2z2
-    const double g0 = sigma[0], g1 = sigma[1];
-    const double s00 = s[0], s01 = s[1] / g0, s02 = s[2] / g1;
-    const double s11 = s[3] / (g0 * g0), s12 = s[4] / (g0 * g1), s22 = s[5] / (g1 * g1);
+    const double h0 = isg[0], h1 = isg[1];
+    const double s00 = s[0], s01 = s[1] * h0, s02 = s[2] * h1;
+    const double s11 = s[3] * (h0 * h0), s12 = s[4] * (h0 * h1), s22 = s[5] * (h1 * h1);
     const double c0 = s11 * s22 - s12 * s12;
     const double c1 = s12 * s02 - s01 * s22;
     const double c2 = s01 * s12 - s11 * s02;

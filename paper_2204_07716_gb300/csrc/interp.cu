@@ -265,6 +265,61 @@ __device__ __forceinline__ void gather_smem(const T* win, int rec, int e1, int l
   }
 }
 
+// Two samples at once from a staged window, FP32, every field in one pass
+// (F2 <= 64): lane l accumulates fields 2l and 2l+1 with 8-byte shared loads,
+// and the two samples' independent chains hide each other's latency.
+template <int D, int W>
+__device__ __forceinline__ void gather_smem_pair(const float* win, int rec, int e1, int la0,
+                                                 int la1, int lb0, int lb1, int lane, bool active,
+                                                 const SampleWin<float, D>& swa,
+                                                 const SampleWin<float, D>& swb, float2& acca,
+                                                 float2& accb) {
+  float wa[D][W], wb[D][W];
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const int l = d * W + t;
+      wa[d][t] = l < 32 ? __shfl_sync(0xffffffffu, swa.wl0, l) : __shfl_sync(0xffffffffu, swa.wl1, l - 32);
+      wb[d][t] = l < 32 ? __shfl_sync(0xffffffffu, swb.wl0, l) : __shfl_sync(0xffffffffu, swb.wl1, l - 32);
+    }
+  acca = make_float2(0.f, 0.f);
+  accb = make_float2(0.f, 0.f);
+  if (!active) return;
+  const float* fa = win + 2 * lane;
+  if (D == 1) {
+#pragma unroll
+    for (int t0 = 0; t0 < W; ++t0) {
+      const float2 va = *reinterpret_cast<const float2*>(fa + (la0 + t0) * rec);
+      const float2 vb = *reinterpret_cast<const float2*>(fa + (lb0 + t0) * rec);
+      acca.x += va.x * wa[0][t0];
+      acca.y += va.y * wa[0][t0];
+      accb.x += vb.x * wb[0][t0];
+      accb.y += vb.y * wb[0][t0];
+    }
+  } else {
+#pragma unroll
+    for (int t0 = 0; t0 < W; ++t0) {
+      const float* ra = fa + ((la0 + t0) * e1 + la1) * rec;
+      const float* rb = fa + ((lb0 + t0) * e1 + lb1) * rec;
+      float2 ra2 = make_float2(0.f, 0.f), rb2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t1 = 0; t1 < W; ++t1) {
+        const float2 va = *reinterpret_cast<const float2*>(ra + t1 * rec);
+        const float2 vb = *reinterpret_cast<const float2*>(rb + t1 * rec);
+        ra2.x += va.x * wa[D - 1][t1];
+        ra2.y += va.y * wa[D - 1][t1];
+        rb2.x += vb.x * wb[D - 1][t1];
+        rb2.y += vb.y * wb[D - 1][t1];
+      }
+      acca.x += ra2.x * wa[0][t0];
+      acca.y += ra2.y * wa[0][t0];
+      accb.x += rb2.x * wb[0][t0];
+      accb.y += rb2.y * wb[0][t0];
+    }
+  }
+}
+
 // Per-group epilogue state shared by both kernels.
 struct GroupCtx {
   int ns, nt, p, nq, n_rhs_real, n_probes, cplx, n_rhs_out, nacc, order, b;
@@ -290,7 +345,8 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
         ok = sv[0] > 0.0;
         a[0] = ok ? 1.0 / sv[0] : 0.0;
       } else {
-        ok = lpr_weights_fast(mono, c.p, sv, B.sigma, a);
+        const double isg[3] = {1.0 / B.sigma[0], 1.0 / B.sigma[1], 1.0 / B.sigma[2]};
+        ok = lpr_weights_fast(mono, c.p, sv, B.sigma, isg, a);
       }
     }
     for (int k = 0; k < c.p; ++k) af[k] = ok ? T(a[k]) * tsc[k] : T(0);
@@ -500,8 +556,58 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
             pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt) : min(c.nq - q_done, pass_f / c.nt);
         const int f_last = (pass == 0 ? c.ns : f_first) + q_in * c.nt;
         const int fcount = f_last - f_first;
+        bool paired = false;
+        if constexpr (sizeof(T) == 4) {
+          // every field in one pass: two samples at a time, 8-byte loads
+          if (F2 <= 64 && fcount == F2) {
+            paired = true;
+            for (int j = 0; j < cnt; j += 2) {
+              const int jb = j + 1 < cnt ? j + 1 : j;
+              const T xa0 = xs[s0 + j], xa1 = D > 1 ? xs[n + s0 + j] : T(0);
+              const T xb0 = xs[s0 + jb], xb1 = D > 1 ? xs[n + s0 + jb] : T(0);
+              const SampleWin<T, D> swa =
+                  sample_window<T, D>(g, W, beta, halfw, ih0, ih1, T(1), xa0, xa1, T(0), lane);
+              const SampleWin<T, D> swb =
+                  sample_window<T, D>(g, W, beta, halfw, ih0, ih1, T(1), xb0, xb1, T(0), lane);
+              const int la0 = swa.i0 - o0, la1 = D > 1 ? swa.i1 - o1 : 0;
+              const int lb0 = swb.i0 - o0, lb1 = D > 1 ? swb.i1 - o1 : 0;
+              const bool in_a = la0 >= 0 && la0 + W <= wm0 && (D == 1 || (la1 >= 0 && la1 + W <= wm1));
+              const bool in_b = lb0 >= 0 && lb0 + W <= wm0 && (D == 1 || (lb1 >= 0 && lb1 + W <= wm1));
+              if (in_a && in_b) {
+                float2 acca, accb;
+                gather_smem_pair<D, W>(reinterpret_cast<const float*>(win), rec, D > 1 ? wm1 : 1,
+                                       la0, la1, lb0, lb1, lane, 2 * lane < rec, swa, swb, acca,
+                                       accb);
+                T* oa = buf + j * bstride + 2 * lane;
+                T* ob = buf + jb * bstride + 2 * lane;
+                if (2 * lane < fcount) oa[0] = acca.x;
+                if (2 * lane + 1 < fcount) oa[1] = acca.y;
+                if (jb != j) {
+                  if (2 * lane < fcount) ob[0] = accb.x;
+                  if (2 * lane + 1 < fcount) ob[1] = accb.y;
+                }
+              } else {
+                for (int h = 0; h < (jb != j ? 2 : 1); ++h) {
+                  const SampleWin<T, D>& sw = h == 0 ? swa : swb;
+                  const int l0 = h == 0 ? la0 : lb0, l1 = h == 0 ? la1 : lb1;
+                  T acc[NCH];
+                  if (h == 0 ? in_a : in_b)
+                    gather_smem<T, D, W, NCH>(win, rec, D > 1 ? wm1 : 1, l0, l1, f_first, fcount,
+                                              lane, sw, acc);
+                  else
+                    gather_global<T, D, W, NCH>(fld, rec, f_first, fcount, lane, sw, W, nf0, nf1, 1,
+                                                nullptr, acc);
+#pragma unroll
+                  for (int ch = 0; ch < NCH; ++ch)
+                    if (lane + ch * 32 < fcount) buf[(j + h) * bstride + lane + ch * 32] = acc[ch];
+                }
+              }
+              __syncwarp();
+            }
+          }
+        }
         T xn0 = xs[s0], xn1 = D > 1 ? xs[n + s0] : T(0);
-        for (int j = 0; j < cnt; ++j) {
+        for (int j = 0; j < (paired ? 0 : cnt); ++j) {
           const T x0 = xn0, x1 = xn1;
           if (j + 1 < cnt) {
             xn0 = xs[s0 + j + 1];

@@ -3,8 +3,8 @@
 // At every grid point the s- and t-fields give the normal equations
 // S(g) beta = t(g) of eqs. 3 / 11 (S_ab = s_(a+b)).  They are assembled in
 // FP64 in the scaled basis u = diag(sigma)^-1 (x_i - g), which leaves the
-// intercept unchanged, solved by Gaussian elimination with partial pivoting,
-// and mhat = e_1^T S^-1 t.  Grid points whose density s_0 is below
+// intercept unchanged, solved in closed form (p <= 3) or by Gaussian
+// elimination with partial pivoting (p = 4), and mhat = e_1^T S^-1 t.  Grid points whose density s_0 is below
 // mask_rho * max s_0 are masked (NaN estimate, mask 0).
 #include <cuda_runtime.h>
 
@@ -18,8 +18,10 @@ namespace {
 template <typename T>
 __global__ void smax_kernel(GeoDev g, int64_t Mtot, const T* __restrict__ field, int fgrid,
                             int64_t lcells, T* __restrict__ smax, int bw_count) {
-  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gid >= Mtot * bw_count) return;
+  // every lane stays to the end (warp shuffles below); out-of-range lanes add 0
+  const int64_t gid0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool in_range = gid0 < Mtot * bw_count;
+  const int64_t gid = in_range ? gid0 : Mtot * bw_count - 1;
   const int64_t m = gid % Mtot;
   const int bb = int(gid / Mtot);
   int64_t rem = m, lidx = 0, mi[3];
@@ -28,13 +30,33 @@ __global__ void smax_kernel(GeoDev g, int64_t Mtot, const T* __restrict__ field,
     rem /= g.M[a];
   }
   for (int a = 0; a < 3; ++a) lidx = lidx * g.L[a] + mi[a];
-  T v = field[(int64_t(bb) * fgrid) * lcells + lidx];
-  if (!(v > T(0))) return;
-  if (sizeof(T) == 4)
-    atomicMax(reinterpret_cast<unsigned int*>(smax + bb), __float_as_uint(float(v)));
-  else
-    atomicMax(reinterpret_cast<unsigned long long*>(smax + bb),
-              (unsigned long long)__double_as_longlong(double(v)));
+  T v = in_range ? field[(int64_t(bb) * fgrid) * lcells + lidx] : T(0);
+  if (!(v > T(0))) v = T(0);
+  // block maximum first, then one atomic per block (all threads of a block
+  // share the bandwidth unless a block straddles two of them: then per warp)
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int bb0 = __shfl_sync(0xffffffffu, bb, 0);
+  const bool uniform = __all_sync(0xffffffffu, bb == bb0);
+  if ((threadIdx.x & 31) == 0 && v > T(0)) {
+    if (!uniform) {
+      // rare: the warp spans two bandwidths; fall back to per-thread atomics below
+    } else if (sizeof(T) == 4) {
+      atomicMax(reinterpret_cast<unsigned int*>(smax + bb), __float_as_uint(float(v)));
+    } else {
+      atomicMax(reinterpret_cast<unsigned long long*>(smax + bb),
+                (unsigned long long)__double_as_longlong(double(v)));
+    }
+  }
+  if (!uniform && in_range) {
+    T vv = field[(int64_t(bb) * fgrid) * lcells + lidx];
+    if (vv > T(0)) {
+      if (sizeof(T) == 4)
+        atomicMax(reinterpret_cast<unsigned int*>(smax + bb), __float_as_uint(float(vv)));
+      else
+        atomicMax(reinterpret_cast<unsigned long long*>(smax + bb),
+                  (unsigned long long)__double_as_longlong(double(vv)));
+    }
+  }
 }
 
 struct GridOut {
@@ -74,7 +96,10 @@ __global__ void grid_solve_kernel(GeoDev g, MonoTab mono, const BwDev* __restric
     if (order == 0)
       a[0] = 1.0 / s[0];
     else
-      ok = lpr_weights(mono, p, s, B.sigma, a);
+    {
+      const double isg[3] = {1.0 / B.sigma[0], 1.0 / B.sigma[1], 1.0 / B.sigma[2]};
+      ok = lpr_weights_fast(mono, p, s, B.sigma, isg, a);
+    }
   }
   const T nan = T(__longlong_as_double(0x7ff8000000000000LL));
   const int mult = out.cplx ? 2 : 1;
