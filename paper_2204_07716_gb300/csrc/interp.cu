@@ -36,7 +36,7 @@ namespace fk {
 namespace {
 
 constexpr int kI2Warps = 16;   // global kernel: warps per block (upper bound)
-constexpr int kTWarps = 8;     // TMA kernel: warps per block
+constexpr int kTWarps = 16;    // TMA kernel: warps per block (upper bound)
 constexpr int kMaxAcc = 512;
 constexpr int kMaxWRun = 32;   // runtime-width fallback
 constexpr uint32_t kMaxSpin = 1u << 22;  // bounded mbarrier wait
@@ -340,7 +340,8 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
     bool ok = false;
     if (valid) {
       double sv[kMaxMono];
-      for (int k = 0; k < c.ns; ++k) sv[k] = double(my[k]);
+#pragma unroll
+      for (int k = 0; k < kMaxMono; ++k) sv[k] = k < c.ns ? double(my[k]) : 0.0;
       if (c.order == 0) {
         ok = sv[0] > 0.0;
         a[0] = ok ? 1.0 / sv[0] : 0.0;
@@ -349,7 +350,8 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
         ok = lpr_weights_fast(mono, c.p, sv, B.sigma, isg, a);
       }
     }
-    for (int k = 0; k < c.p; ++k) af[k] = ok ? T(a[k]) * tsc[k] : T(0);
+#pragma unroll
+    for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
     const double tv = warp_sum_t<double>((valid && ok) ? B.k0 * a[0] : 0.0);
     if (lane == 0) red[c.nacc - 1] += tv;
   }
@@ -358,7 +360,9 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
   for (int qq = 0; qq < q_in; ++qq) {
     const int q = q_done + qq;
     T mh = T(0);
-    for (int k = 0; k < c.p; ++k) mh += af[k] * my[fq0 + qq * c.nt + k];
+#pragma unroll
+    for (int k = 0; k < kMaxP; ++k)
+      if (k < c.p) mh += af[k] * my[fq0 + qq * c.nt + k];
     const T cv = valid ? str[int64_t(1 + q) * n + s] : T(0);
     if (q < c.n_rhs_real) {
       const T r = valid ? cv - mh : T(0);
@@ -411,6 +415,7 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   GroupCtx c{mono.n, mono.nt, mono.nt, n_rhs_real + n_probes, n_rhs_real, n_probes, cplx,
              n_rhs_out, nacc, order, b};
   T tsc[kMaxP];
+#pragma unroll
   for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
   // each block walks one contiguous run of sample groups (neighbouring bins)
   const int64_t ngroups = (n + 31) / 32;
@@ -476,12 +481,12 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
                   T* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part,
                   const uint32_t* __restrict__ sub_bin, const uint32_t* __restrict__ sub_first,
                   const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ sub_total,
-                  int wm0, int wm1, int* __restrict__ errw) {
+                  int wm0, int wm1, int lo_slack, int bstride_in, int* __restrict__ errw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = int(blockDim.x >> 5);
-  const int bstride = pass_f + 1;
+  const int bstride = bstride_in;
   const size_t win_bytes = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
   T* win = reinterpret_cast<T*>(smem_raw);
   double* red_all = reinterpret_cast<double*>(smem_raw + win_bytes);
@@ -503,6 +508,7 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
   GroupCtx c{mono.n, mono.nt, mono.nt, n_rhs_real + n_probes, n_rhs_real, n_probes, cplx,
              n_rhs_out, nacc, order, b};
   T tsc[kMaxP];
+#pragma unroll
   for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
   uint32_t parity = 0;
   const uint32_t nsub = *sub_total;
@@ -513,8 +519,8 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
     const uint32_t last = min(first + uint32_t(kSubMax), bin_start[bin + 1]);
     const int64_t bj0 = D > 1 ? int64_t(bin) / g.nbins[1] : int64_t(bin);
     const int64_t bj1 = D > 1 ? int64_t(bin) % g.nbins[1] : 0;
-    const int o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - 1;
-    const int o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - 1 : 0;
+    const int o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - lo_slack;
+    const int o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - lo_slack : 0;
     if (threadIdx.x == 0) {
       fence_proxy_async();  // earlier reads of the window come before the new copies
       mbar_expect_tx(&mbar, uint32_t(size_t(wm0) * wm1 * rec * sizeof(T)));
@@ -587,11 +593,9 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
                   if (2 * lane + 1 < fcount) ob[1] = accb.y;
                 }
               } else {
-                for (int h = 0; h < (jb != j ? 2 : 1); ++h) {
-                  const SampleWin<T, D>& sw = h == 0 ? swa : swb;
-                  const int l0 = h == 0 ? la0 : lb0, l1 = h == 0 ? la1 : lb1;
+                auto one = [&](const SampleWin<T, D>& sw, int l0, int l1, bool in, int jj) {
                   T acc[NCH];
-                  if (h == 0 ? in_a : in_b)
+                  if (in)
                     gather_smem<T, D, W, NCH>(win, rec, D > 1 ? wm1 : 1, l0, l1, f_first, fcount,
                                               lane, sw, acc);
                   else
@@ -599,8 +603,10 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
                                                 nullptr, acc);
 #pragma unroll
                   for (int ch = 0; ch < NCH; ++ch)
-                    if (lane + ch * 32 < fcount) buf[(j + h) * bstride + lane + ch * 32] = acc[ch];
-                }
+                    if (lane + ch * 32 < fcount) buf[jj * bstride + lane + ch * 32] = acc[ch];
+                };
+                one(swa, la0, la1, in_a, j);
+                if (jb != j) one(swb, lb0, lb1, in_b, jb);
               }
               __syncwarp();
             }
@@ -705,9 +711,14 @@ __global__ void finalize_kernel(const double* __restrict__ sums, int nbw, int na
 
 // Window extent of a bin on bandwidth b's fine grid (cells, per axis): covers
 // every window of a sample in the bin with one cell of slack on each side.
+// On the spreading grid itself (r = 1) the window is exact: origin
+// b T - pad, extent T + w + 1.  Other grids get one more cell of slack on each
+// side for the rounding of the rescaled coordinates (a sample whose window
+// still falls outside is gathered from global memory).
+inline int tma_slack(const GeoDev& g, const BwDev& B, int j) { return B.nf[j] == g.nf[j] ? 0 : 1; }
 inline int tma_window(const GeoDev& g, const BwDev& B, int j) {
   const double r = double(B.nf[j]) / double(g.nf[j]);
-  return int(std::ceil(double(g.tile[j]) * r)) + 2 * g.pad + 3;
+  return int(std::ceil(double(g.tile[j]) * r)) + g.w + 1 + 2 * tma_slack(g, B, j);
 }
 
 template <typename T>
@@ -727,19 +738,27 @@ cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
     const int wm0 = tma_window(P->geo, B, 0);
     const int wm1 = D > 1 ? tma_window(P->geo, B, 1) : 1;
     const size_t win = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
-    const size_t smem = win + buf_warp * kTWarps;
-    const bool fits = wm0 <= B.nf[0] && (D == 1 || wm1 <= B.nf[1]) && smem <= 220 * 1024;
+    const int slack = std::max(tma_slack(P->geo, B, 0), D > 1 ? tma_slack(P->geo, B, 1) : 0);
+    // staging stride: the record when every field fits one pass, odd for
+    // conflict-free column reads
+    const int span = F2 <= pass_f ? F2 : pass_f;
+    const int bstride = span | 1;
+    const size_t per_warp = sizeof(T) * 32 * bstride + sizeof(double) * nacc;
+    const size_t budget = 220 * 1024;
+    const int nw = win < budget ? int(std::min<size_t>(kTWarps, (budget - win) / per_warp)) : 0;
+    const size_t smem = win + per_warp * size_t(nw);
+    const bool fits = wm0 <= B.nf[0] && (D == 1 || wm1 <= B.nf[1]) && nw >= 4;
     if (fits) {
       cudaError_t e = cudaFuncSetAttribute(interp_tma_kernel<T, D, W, NCH>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
-      interp_tma_kernel<T, D, W, NCH><<<blocks, kTWarps * 32, smem, st>>>(
+      interp_tma_kernel<T, D, W, NCH><<<blocks, nw * 32, smem, st>>>(
           P->geo, P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, wsp<T>(P, P->r_xs),
           wsp<T>(P, P->r_str), perm_ptr(P), wsp<T>(P, P->r_t2field), rec, F2, pass_f, n_rhs_real,
           n_probes, P->o.y_complex, P->nrhs, static_cast<T*>(mhat_at_x), nacc, P->nbw,
           wsp<double>(P, P->r_part), wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
           wsp<uint32_t>(P, P->r_binstart), wsp<uint32_t>(P, P->r_substart) + P->nbins_total, wm0,
-          wm1, wsp<int>(P, P->r_err));
+          wm1, slack, bstride, wsp<int>(P, P->r_err));
       P->launches += 1;
       return cudaGetLastError();
     }

@@ -39,7 +39,7 @@ struct TileAcc<float> {
   static __device__ __forceinline__ void add(int* p, float v) { atomicAdd(p, __float2int_rn(v)); }
 };
 
-template <typename T, int D, int W>
+template <typename T, int D, int W, int CN>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict__ str, int s0,
               int scount, int chunk, const uint32_t* __restrict__ sub_bin,
@@ -76,32 +76,32 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
   const int64_t fine_cells = g.nf[0] * g.nf[1] * g.nf[2];
   constexpr int WR = W > 0 ? W : kMaxWRun;
 
-  for (int c0 = 0; c0 < scount; c0 += chunk) {
-    const int cn = min(chunk, scount - c0);
+  // one launch handles CN strengths [s0, s0 + CN) (scount and chunk are CN)
+  for (int c0 = 0; c0 < 1; ++c0) {
+    constexpr int cn = CN;
     for (int idx = threadIdx.x; idx < cn * cells; idx += blockDim.x) sm[idx] = A(0);
     if (sizeof(A) == 4) {
       // fixed-point scale per strength: 2^30 / sum |c| over this sub-problem
-      T part[kMaxChunk];
+      T part[CN];
 #pragma unroll
-      for (int c = 0; c < kMaxChunk; ++c) part[c] = T(0);
+      for (int c = 0; c < CN; ++c) part[c] = T(0);
       for (uint32_t p = first + threadIdx.x; p < last; p += blockDim.x)
 #pragma unroll
-        for (int c = 0; c < kMaxChunk; ++c)
-          if (c < cn) part[c] += fabs(str[int64_t(s0 + c0 + c) * n + p]);
+        for (int c = 0; c < CN; ++c) part[c] += fabs(str[int64_t(s0 + c0 + c) * n + p]);
 #pragma unroll
-      for (int c = 0; c < kMaxChunk; ++c) {
+      for (int c = 0; c < CN; ++c) {
         const T v = warp_sum_t<T>(part[c]);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5][c] = v;
       }
       __syncthreads();
-      if (threadIdx.x < kMaxChunk) {
+      if (threadIdx.x < CN) {
         T tot = T(0);
         for (int wv = 0; wv < kSpreadThreads / 32; ++wv) tot += s_red[wv][threadIdx.x];
         const T sc = tot > T(0) ? T(1073741824.0) / tot : T(0);
         s_scale[threadIdx.x] = sc;
         s_inv[threadIdx.x] = tot > T(0) ? tot / T(1073741824.0) : T(0);
       }
-    } else if (threadIdx.x < kMaxChunk) {
+    } else if (threadIdx.x < CN) {
       s_scale[threadIdx.x] = T(1);
       s_inv[threadIdx.x] = T(1);
     }
@@ -122,18 +122,16 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
           for (int t = 0; t < w; ++t) wt[j][t] = phi<T>(g.skind, w, beta, off + T(t));
         }
       }
-      T cv[kMaxChunk];
+      T cv[CN];
 #pragma unroll
-      for (int c = 0; c < kMaxChunk; ++c)
-        cv[c] = c < cn ? str[int64_t(s0 + c0 + c) * n + p] * s_scale[c] : T(0);
+      for (int c = 0; c < CN; ++c) cv[c] = str[int64_t(s0 + c0 + c) * n + p] * s_scale[c];
       if constexpr (W > 0) {
         if (D == 1) {
 #pragma unroll
           for (int t0 = 0; t0 < W; ++t0) {
             const int idx = l[0] + t0;
 #pragma unroll
-            for (int c = 0; c < kMaxChunk; ++c)
-              if (c < cn) TileAcc<T>::add(&sm[c * cells + idx], cv[c] * wt[0][t0]);
+            for (int c = 0; c < CN; ++c) TileAcc<T>::add(&sm[c * cells + idx], cv[c] * wt[0][t0]);
           }
         } else if (D == 2) {
 #pragma unroll
@@ -144,8 +142,7 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
             for (int t1 = 0; t1 < W; ++t1) {
               const T v = w0 * wt[D - 1][t1];
 #pragma unroll
-              for (int c = 0; c < kMaxChunk; ++c)
-                if (c < cn) TileAcc<T>::add(&sm[c * cells + row + t1], cv[c] * v);
+              for (int c = 0; c < CN; ++c) TileAcc<T>::add(&sm[c * cells + row + t1], cv[c] * v);
             }
           }
         } else {
@@ -159,8 +156,7 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
               for (int t2 = 0; t2 < W; ++t2) {
                 const T v = v01 * wt[D - 1][t2];
 #pragma unroll
-                for (int c = 0; c < kMaxChunk; ++c)
-                  if (c < cn) TileAcc<T>::add(&sm[c * cells + row + t2], cv[c] * v);
+                for (int c = 0; c < CN; ++c) TileAcc<T>::add(&sm[c * cells + row + t2], cv[c] * v);
               }
             }
         }
@@ -208,28 +204,57 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
   }
 }
 
+template <typename T, int D, int W, int CN>
+cudaError_t launch_spread_cn(fkreg_plan_s* P, int s0, cudaStream_t st) {
+  const GeoDev& g = P->geo;
+  int cells = 1;
+  for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
+  const size_t smem = size_t(cells) * sizeof(typename TileAcc<T>::type) * CN;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(spread_kernel<T, D, W, CN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned(P->nsub_max);
+  const uint32_t* sub_total = wsp<uint32_t>(P, P->r_substart) + P->nbins_total;
+  spread_kernel<T, D, W, CN><<<grid, kSpreadThreads, smem, st>>>(
+      g, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_str), s0, CN, CN,
+      wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
+      wsp<uint32_t>(P, P->r_binstart), sub_total, wsp<T>(P, P->r_fine));
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+// Strengths go in launches of 8, 4, 2 or 1 (compile-time chunk sizes, as
+// many as the shared-memory budget allows per launch).
 template <typename T, int D, int W>
 cudaError_t launch_spread_w(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
   const GeoDev& g = P->geo;
   int cells = 1;
   for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
-  const size_t per = size_t(cells) * sizeof(T);
-  const size_t budget = 100 * 1024;
-  int chunk = int(std::max<size_t>(1, std::min<size_t>(budget / per, kMaxChunk)));
-  chunk = std::min(chunk, scount);
-  const size_t smem = per * chunk;
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(spread_kernel<T, D, W>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  const unsigned grid = unsigned(P->nsub_max);
-  const uint32_t* sub_total = wsp<uint32_t>(P, P->r_substart) + P->nbins_total;
-  spread_kernel<T, D, W><<<grid, kSpreadThreads, smem, st>>>(
-      g, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_str), s0, scount, chunk,
-      wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
-      wsp<uint32_t>(P, P->r_binstart), sub_total, wsp<T>(P, P->r_fine));
-  P->launches += 1;
-  return cudaGetLastError();
+  const size_t per = size_t(cells) * sizeof(typename TileAcc<T>::type);
+  const int cap = int(std::max<size_t>(1, std::min<size_t>((100 * 1024) / per, kMaxChunk)));
+  int done = 0;
+  while (done < scount) {
+    const int rem = std::min(scount - done, cap);
+    cudaError_t e;
+    int used;
+    if (rem >= 8) {
+      e = launch_spread_cn<T, D, W, 8>(P, s0 + done, st);
+      used = 8;
+    } else if (rem >= 4) {
+      e = launch_spread_cn<T, D, W, 4>(P, s0 + done, st);
+      used = 4;
+    } else if (rem >= 2) {
+      e = launch_spread_cn<T, D, W, 2>(P, s0 + done, st);
+      used = 2;
+    } else {
+      e = launch_spread_cn<T, D, W, 1>(P, s0 + done, st);
+      used = 1;
+    }
+    if (e != cudaSuccess) return e;
+    done += used;
+  }
+  return cudaSuccess;
 }
 
 template <typename T, int D>
