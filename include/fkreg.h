@@ -69,8 +69,9 @@ enum { FKREG_KERNEL_GAUSSIAN = 0 };
 
 /* fkreg_opts.flags */
 enum {
-  FKREG_GCV_EXACT_TRACE = 1   /* GCV uses the exact trace K_H(0) sum_i [S(x_i)^-1]_11
+  FKREG_GCV_EXACT_TRACE = 1,  /* GCV uses the exact trace K_H(0) sum_i [S(x_i)^-1]_11
                                  instead of Girard's Monte-Carlo estimate */
+  FKREG_WANT_BACKWARD = 2     /* reserve workspace and FFT plans for fkreg_backward */
 };
 
 /*
@@ -95,7 +96,7 @@ enum {
  *   mask_rho       grid points with s_0(g) < mask_rho * max_g s_0 are masked
  *                  (NaN estimate, mask byte 0); 0 selects the default 1e-3
  *   tile           spreading tile edge in fine-grid cells per axis (0 = auto)
- *   flags          FKREG_GCV_EXACT_TRACE
+ *   flags          FKREG_GCV_EXACT_TRACE, FKREG_WANT_BACKWARD
  */
 typedef struct {
   int dim;
@@ -246,6 +247,29 @@ fkreg_status fkreg_variance(fkreg_plan plan, const void* y_dev, const void* mhat
                             void* sigma2_grid_dev, void* stream);
 
 /*
+ * Gradient of GCV (eq. 22) for bandwidth b, with the Monte-Carlo trace of
+ * Sec. 2.1 over n_probes fixed probes (given, or drawn as in fkreg_df from
+ * seed), with respect to the log bandwidths, the responses and the samples.
+ * Runs the forward fkreg_df itself, then the hand-written backward: the
+ * adjoints of the moment fields at the samples (FP64 per-sample solves),
+ * derivative fields for d/dlog sigma_j and the evaluation-point gradient, and
+ * one adjoint spreading pass (the adjoint of type-2 interpolation is type-1
+ * spreading) for the source-side d/dx and for d/dy.
+ * Requires a plan created with FKREG_WANT_BACKWARD, n_rhs = 1, real y,
+ * diagonal H (H = diag(sigma^2), the derivative is in log sigma_j) and the
+ * Monte-Carlo trace (no FKREG_GCV_EXACT_TRACE); otherwise
+ * FKREG_ERR_UNSUPPORTED.
+ *   y_dev       [n] responses;  probes_dev [n_probes][n] or NULL (seeded)
+ *   gcv_dev     double, the GCV value of bandwidth b (may be NULL)
+ *   dlogh_dev   [dim] double, dGCV / dlog sigma_j (may be NULL)
+ *   dy_dev      [n] dGCV / dy_i, original order (may be NULL)
+ *   dx_dev      [n][dim] dGCV / dx_i, original order (may be NULL)
+ */
+fkreg_status fkreg_backward(fkreg_plan plan, const void* y_dev, int n_probes, uint64_t seed,
+                            const void* probes_dev, int b, double* gcv_dev, double* dlogh_dev,
+                            void* dy_dev, void* dx_dev, void* stream);
+
+/*
  * Stage timers (profiling).  With timing enabled every stage of a call is
  * bracketed by CUDA events recorded on the call's stream; fkreg_stage_times
  * waits for those events, returns the accumulated milliseconds and launch
@@ -266,7 +290,8 @@ enum {
   FKREG_STAGE_FFT_T2 = 8,     /* cuFFT inverse onto the type-2 fine grids */
   FKREG_STAGE_INTERP = 9,     /* interpolation at the samples + solves + reductions */
   FKREG_STAGE_FINALIZE = 10,  /* DF / GCV */
-  FKREG_N_STAGES = 11
+  FKREG_STAGE_BACKWARD = 11,  /* derivative fields, adjoints, adjoint spreading */
+  FKREG_N_STAGES = 12
 };
 fkreg_status fkreg_set_timing(fkreg_plan plan, int enable);
 fkreg_status fkreg_stage_times(fkreg_plan plan, double* ms, int64_t* launches,

@@ -200,6 +200,11 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   P->f2max = P->ns + (P->nrhs_real + P->max_probes) * P->nt;
   P->fgrid = P->ns + P->nrhs_real * P->nt;
   P->nacc = P->nrhs_real + 2 * P->max_probes + 1;
+  P->backward = (opts->flags & FKREG_WANT_BACKWARD) != 0;
+  P->f2bwd = P->ns + (1 + P->max_probes) * P->nt;
+  const int nout_bwd = 1 + (2 + P->max_probes) * opts->dim;
+  const int strengths_total = P->smax + (P->backward ? P->f2bwd : 0);
+  const int t2_fields = std::max(P->f2max, P->backward ? std::max(P->f2bwd, nout_bwd) : 0);
   if (P->nacc > 512) {
     delete P;
     return set_global_error(FKREG_ERR_UNSUPPORTED, "n_rhs (real parts) + 2 max_probes must be <= 511");
@@ -253,15 +258,22 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   L.take(P->r_subfirst, 4 * P->nsub_max);
   L.take(P->r_hist, 4 * (256 * ntiles + 1));
   L.take(P->r_scan, 4 * (scan_len / 1024 + 2));
-  L.take(P->r_str, T * P->smax * std::max<int64_t>(1, max_n));
-  L.take(P->r_fine, T * P->smax * nf_cells);
-  L.take(P->r_spec, 2 * T * P->smax * nf_half);
+  L.take(P->r_str, T * strengths_total * std::max<int64_t>(1, max_n));
+  L.take(P->r_fine, T * strengths_total * nf_cells);
+  L.take(P->r_spec, 2 * T * strengths_total * nf_half);
   L.take(P->r_gspec, 2 * T * size_t(P->nbw) * P->fgrid * l_half);
   L.take(P->r_gfield, T * size_t(P->nbw) * P->fgrid * l_cells);
-  L.take(P->r_t2spec, 2 * T * size_t(P->f2max) * t2_half);
-  L.take(P->r_t2field, T * size_t(fk::t2_record_stride(P->f2max)) * t2_cells);
+  L.take(P->r_t2spec, 2 * T * size_t(t2_fields) * t2_half);
+  L.take(P->r_t2field, T * size_t(fk::t2_record_stride(t2_fields)) * t2_cells);
   L.take(P->r_part, sizeof(double) * size_t(P->nblk_interp + 1) * P->nbw * P->nacc);
   L.take(P->r_smax, 8 * size_t(P->nbw));
+  if (P->backward) {
+    const int64_t nn = std::max<int64_t>(1, max_n);
+    L.take(P->r_bV, T * size_t(1 + 2 * d) * std::max(P->f2bwd, nout_bwd) * nn);
+    L.take(P->r_bdx, T * size_t(d + 1) * nn);
+    L.take(P->r_bsc, 8 * 16);
+    L.take(P->r_bpart, 8 * 3 * size_t((nn + 255) / 256 + 1));
+  }
   // cuFFT plans for the standard passes (work sizes decide the reserved area)
   {
     int64_t dims[3];
@@ -284,10 +296,22 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
         return set_global_error(st, m);
       }
     }
+    if (P->backward) {
+      for (int a = 0; a < 3; ++a) dims[a] = P->g.nf[a];
+      if ((st = fk::fft_get(P, 0, dims, P->f2bwd, &h)) != FKREG_OK) {
+        std::string m = P->err;
+        fkreg_plan_destroy(P);
+        return set_global_error(st, m);
+      }
+    }
     for (const auto& B : P->bw) {
       for (int a = 0; a < 3; ++a) dims[a] = B.nf[a];
       std::vector<int> bts = {P->ns + P->nrhs_real * P->nt};
       if (P->max_probes > 0) bts.push_back(P->f2max);
+      if (P->backward) {
+        bts.push_back(P->f2bwd);
+        bts.push_back(nout_bwd);
+      }
       for (int bt : bts)
         if ((st = fk::fft_get(P, 2, dims, bt, &h)) != FKREG_OK) {
           std::string m = P->err;
@@ -490,6 +514,65 @@ fkreg_status fkreg_df(fkreg_plan P, const void* y, int n_probes, uint64_t seed, 
   if (!P) return FKREG_ERR_INVALID_ARG;
   if (n_probes < 1) return plan_err(P, FKREG_ERR_INVALID_ARG, "fkreg_df needs n_probes >= 1");
   return pipeline(P, y, n_probes, seed, probes, out, true, static_cast<cudaStream_t>(stream));
+}
+
+fkreg_status fkreg_backward(fkreg_plan P, const void* y, int n_probes, uint64_t seed,
+                            const void* probes, int b, double* gcv, double* dlogh, void* dy,
+                            void* dx, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (!P->backward)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward needs a plan created with FKREG_WANT_BACKWARD");
+  if (P->nrhs != 1 || P->o.y_complex)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward supports one real response");
+  if (P->o.flags & FKREG_GCV_EXACT_TRACE)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward differentiates the Monte-Carlo trace");
+  if (n_probes < 1 || n_probes > P->max_probes)
+    return plan_err(P, FKREG_ERR_INVALID_ARG, "n_probes must lie in [1, max_probes]");
+  if (b < 0 || b >= P->nbw) return plan_err(P, FKREG_ERR_INVALID_ARG, "bandwidth index out of range");
+  {
+    const double* Hb = P->H.data() + size_t(b) * P->d * P->d;
+    for (int i = 0; i < P->d; ++i)
+      for (int j = 0; j < P->d; ++j)
+        if (i != j && Hb[i * P->d + j] != 0.0)
+          return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward needs a diagonal bandwidth matrix");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  fkreg_outputs out{};
+  FK_STATUS(pipeline(P, y, n_probes, seed, probes, &out, true, s));
+  if (P->n == 0) return FKREG_OK;
+  const int d = P->d;
+  const int R = 1 + n_probes;
+  const int F2 = P->ns + R * P->nt;
+  const int nout = 1 + (1 + R) * d;
+  const int64_t n = P->n;
+  const size_t T = P->tsize;
+  const int64_t nf_cells = full_cells(P->g.nf, d), nf_half = half_cells(P->g.nf, d);
+  FK_STAGE(FKREG_STAGE_BACKWARD);
+  FK_CHECK(fk::run_loss_scalars(P, b, n_probes, s), "loss scalars");
+  // values, evaluation-point gradients, bandwidth derivatives of the fields
+  for (int mode = 0; mode < 1 + 2 * d; ++mode) {
+    const int kind = mode == 0 ? 0 : (mode <= d ? 1 : 2);
+    const int axis = mode == 0 ? 0 : (mode <= d ? mode - 1 : mode - 1 - d);
+    FK_CHECK(fk::run_kmul_t2_mode(P, b, 0, 1, R, kind, axis, s), "derivative spectra");
+    FK_STATUS(exec_fft(P, 2, P->bw[b].nf, F2, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
+    FK_CHECK(fk::run_gather_fields(P, b, F2, P->ws + P->r_bV.off + T * size_t(mode) * F2 * n, s),
+             "gather fields");
+  }
+  FK_CHECK(fk::run_adjoint(P, b, n_probes, s), "adjoints");
+  // adjoint spreading of Qbar (strengths smax .. smax + F2)
+  FK_CHECK(fk::run_spread(P, P->smax, F2, s), "adjoint spread");
+  FK_STATUS(exec_fft(P, 0, P->g.nf, F2, P->ws + P->r_fine.off + T * P->smax * nf_cells,
+                     P->ws + P->r_spec.off + 2 * T * P->smax * nf_half, s));
+  FK_CHECK(fk::run_kmul_adj(P, b, P->smax, 1 + R, s), "adjoint spectra");
+  FK_STATUS(exec_fft(P, 2, P->bw[b].nf, nout, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
+  FK_CHECK(fk::run_gather_fields(P, b, nout, P->ws + P->r_bV.off, s), "gather adjoint fields");
+  FK_CHECK(fk::run_combine(P, n_probes, dy, dx, dlogh, s), "combine");
+  if (gcv) {
+    cudaError_t e = cudaMemcpyAsync(gcv, P->ws + P->r_bsc.off + 2 * sizeof(double), sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_err(P, e, "copy gcv");
+  }
+  return FKREG_OK;
 }
 
 fkreg_status fkreg_variance(fkreg_plan P, const void* y, const void* mhat_at_x, void* sigma2,

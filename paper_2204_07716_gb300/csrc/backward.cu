@@ -1,0 +1,402 @@
+// Hand-written backward of GCV (eq. 22) with respect to log h, y and x.
+//
+// With the Monte-Carlo trace of Sec. 2.1 (fixed probes w_p),
+//   GCV = (RSS / N) / (1 - tr / N)^2,  RSS = sum_i (y_i - mhat_y(x_i))^2,
+//   tr  = (N / Np) sum_p sum_i w_pi mhat_p(x_i) / (w_p^T w_p),
+// and mhat_r(x_i) = e_1^T S(x_i)^-1 t_r(x_i) (eq. 3).  Every field value at a
+// sample, Q_(i,f) = sum_j c_(f,j) w_f(x_j - x_i) with w_f(z) = z^g_f K_H(z), gets
+// an adjoint Qbar_(i,f) = dGCV / dQ_(i,f):
+//   t-fields of response r : g_(r,i) a_i             (a = S^-1 e_1)
+//   s-field g              : -sum_(a+b=g) a_a bbar_b  (bbar = sum_r g_r S^-1 t_r)
+// with g_y = -2 L_RSS (y_i - mhat_y), g_p = L_tr (N / Np) w_pi / (w_p^T w_p).
+// Then
+//   d/dlog sigma_j = sum_i Qbar_i . dQ_i/dlog sigma_j      (derivative fields at x_i)
+//   d/dx_i (target) = sum_f Qbar_(i,f) grad_q Q_f(x_i)      (gradient fields at x_i)
+//   d/dx_j (source) = sum_c c_(c,j) sum_(f in c) sum_i Qbar_(i,f) grad w_f(x_j - x_i)
+//   d/dy_j          = 2 L_RSS (y_j - mhat_y(x_j)) + sum_(f in y) sum_i Qbar_(i,f) w_f(x_j - x_i)
+// The last two are NUFFT convolutions of the adjoints spread as strengths.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "gather.cuh"
+#include "internal.h"
+
+namespace fk {
+
+namespace {
+
+constexpr int kGWarps = 8;
+constexpr int kE1Threads = 256;
+
+// Gather F fields (record stride rec) at every sorted sample into V[f][n].
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(kGWarps * 32)
+gather_fields_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
+                     const T* __restrict__ xs, const T* __restrict__ fld, int rec, int F,
+                     T* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = W > 0 ? W : g.w;
+  int ncw = 1;
+  for (int j = 0; j < D; ++j) ncw *= w;
+  if (W > 0) ncw = 0;
+  const int bstride = 33;
+  T* cellw = reinterpret_cast<T*>(smem_raw) + warp * ncw;
+  T* buf = reinterpret_cast<T*>(smem_raw) + kGWarps * ncw + warp * 32 * bstride;
+  const BwDev& B = bwt[b];
+  const int nf0 = int(B.nf[0]), nf1 = D > 1 ? int(B.nf[1]) : 1, nf2 = D > 2 ? int(B.nf[2]) : 1;
+  const T ih0 = T(B.inv_h[0]), ih1 = T(D > 1 ? B.inv_h[1] : 1.0), ih2 = T(D > 2 ? B.inv_h[2] : 1.0);
+  const T beta = T(g.beta);
+  const T halfw = T(0.5) * T(w);
+  const int64_t ngroups = (n + 31) / 32;
+  for (int64_t grp = int64_t(blockIdx.x) * kGWarps + warp; grp < ngroups;
+       grp += int64_t(gridDim.x) * kGWarps) {
+    const int64_t s0 = grp * 32;
+    const int cnt = int(min(int64_t(32), n - s0));
+    for (int f_first = 0; f_first < F; f_first += 32) {
+      const int fcount = min(32, F - f_first);
+      for (int j = 0; j < cnt; ++j) {
+        const int64_t sj = s0 + j;
+        const SampleWin<T, D> sw = sample_window<T, D>(
+            g, w, beta, halfw, ih0, ih1, ih2, xs[sj], D > 1 ? xs[n + sj] : T(0),
+            D > 2 ? xs[2 * n + sj] : T(0), lane);
+        T acc[1];
+        gather_global<T, D, W, 1>(fld, rec, f_first, fcount, lane, sw, w, nf0, nf1, nf2, cellw, acc);
+        if (lane < fcount) buf[j * bstride + lane] = acc[0];
+        __syncwarp();
+      }
+      // transpose: lane = sample, coalesced rows of V
+      for (int f = 0; f < fcount; ++f)
+        if (lane < cnt) V[int64_t(f_first + f) * n + s0 + lane] = buf[lane * bstride + f];
+      __syncwarp();
+    }
+  }
+}
+
+// Loss scalars for bandwidth b from the forward sums:
+//   sc[0] = L_RSS = (1/N) / (1 - tr/N)^2
+//   sc[1] = L_tr * N / Np,  L_tr = 2 (RSS/N) / (N (1 - tr/N)^3)
+//   sc[2] = GCV
+__global__ void loss_scalars_kernel(const double* __restrict__ sums, int b, int nacc, int n_probes,
+                                    int64_t n, double* __restrict__ sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double* sb = sums + int64_t(b) * nacc;
+  double girard = 0.0;
+  for (int p = 0; p < n_probes; ++p) girard += sb[1 + p] / sb[1 + n_probes + p];
+  const double N = double(n);
+  const double tr = N * girard / n_probes;
+  const double rss = sb[0];
+  const double den = 1.0 - tr / N;
+  sc[0] = (1.0 / N) / (den * den);
+  sc[1] = (2.0 * (rss / N) / (N * den * den * den)) * (N / n_probes);
+  sc[2] = (rss / N) / (den * den);
+}
+
+// Per-sample adjoints.  V holds (1 + 2D) blocks of F2 fields: values, the D
+// gradient fields and the D bandwidth-derivative fields.  Writes Qbar (as
+// spreading strengths), the target-side x-gradient and the explicit y-term,
+// and per-block partial sums of the bandwidth gradient.
+template <typename T, int D>
+__global__ void __launch_bounds__(kE1Threads)
+adjoint_kernel(MonoTab mono, const BwDev* __restrict__ bwt, int b, int order, int64_t n, int F2,
+               int n_probes, const T* __restrict__ V, const T* __restrict__ str,
+               const double* __restrict__ sums, int nacc, const double* __restrict__ sc,
+               T* __restrict__ qbar, T* __restrict__ dxt, T* __restrict__ dye,
+               double* __restrict__ part) {
+  __shared__ double red[kE1Threads / 32][3];
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool valid = s < n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const BwDev& B = bwt[b];
+  const int ns = mono.n, nt = mono.nt, p = nt;
+  double dth[3] = {0, 0, 0};
+  if (valid) {
+    const double* sb = sums + int64_t(b) * nacc;
+    const double L_rss = sc[0], L_trn = sc[1];
+    // scaled normal matrix and its inverse (FP64)
+    double sv[kMaxMono];
+#pragma unroll
+    for (int k = 0; k < kMaxMono; ++k) sv[k] = k < ns ? double(V[int64_t(k) * n + s]) : 0.0;
+    double Sinv[kMaxP][kMaxP];
+    double tsc[kMaxP];
+#pragma unroll
+    for (int k = 0; k < kMaxP; ++k) tsc[k] = k < p ? 1.0 / tscale(mono, k, B.sigma) : 0.0;
+    bool ok = true;
+    if (order == 0) {
+      ok = sv[0] > 0.0;
+      Sinv[0][0] = ok ? 1.0 / sv[0] : 0.0;
+    } else {
+      // columns of the scaled inverse by elimination, then unscale
+      for (int c = 0; c < p && ok; ++c) {
+        double S[kMaxP][kMaxP], col[kMaxP];
+        for (int i = 0; i < p; ++i)
+          for (int j = 0; j < p; ++j) {
+            const int e0 = mono.e[i][0] + mono.e[j][0], e1 = mono.e[i][1] + mono.e[j][1],
+                      e2 = mono.e[i][2] + mono.e[j][2];
+            S[i][j] = sv[mono_index(mono, ns, e0, e1, e2)] * tsc[i] * tsc[j];
+          }
+        // solve S col = e_c
+        double rhs[kMaxP];
+        for (int i = 0; i < p; ++i) rhs[i] = (i == c) ? 1.0 : 0.0;
+        for (int cc = 0; cc < p && ok; ++cc) {
+          int piv = cc;
+          for (int i = cc + 1; i < p; ++i)
+            if (fabs(S[i][cc]) > fabs(S[piv][cc])) piv = i;
+          if (!(fabs(S[piv][cc]) > 0.0)) {
+            ok = false;
+            break;
+          }
+          if (piv != cc) {
+            for (int j = 0; j < p; ++j) {
+              const double t = S[cc][j];
+              S[cc][j] = S[piv][j];
+              S[piv][j] = t;
+            }
+            const double t = rhs[cc];
+            rhs[cc] = rhs[piv];
+            rhs[piv] = t;
+          }
+          for (int i = cc + 1; i < p; ++i) {
+            const double fct = S[i][cc] / S[cc][cc];
+            for (int j = cc; j < p; ++j) S[i][j] -= fct * S[cc][j];
+            rhs[i] -= fct * rhs[cc];
+          }
+        }
+        if (!ok) break;
+        for (int i = p - 1; i >= 0; --i) {
+          double v = rhs[i];
+          for (int j = i + 1; j < p; ++j) v -= S[i][j] * col[j];
+          col[i] = v / S[i][i];
+        }
+        for (int i = 0; i < p; ++i) Sinv[i][c] = col[i] * tsc[i] * tsc[c];
+      }
+    }
+    double a[kMaxP] = {0, 0, 0, 0}, bbar[kMaxP] = {0, 0, 0, 0};
+    if (ok)
+      for (int i = 0; i < p; ++i) a[i] = Sinv[i][0];
+    double dx_t[3] = {0, 0, 0};
+    const int R = 1 + n_probes;
+    const int nblk = 1 + 2 * D;
+    for (int r = 0; r < R && ok; ++r) {
+      double t[kMaxP];
+      for (int k = 0; k < p; ++k) t[k] = double(V[int64_t(ns + r * nt + k) * n + s]);
+      double mh = 0.0;
+      for (int k = 0; k < p; ++k) mh += a[k] * t[k];
+      const double c = double(str[int64_t(1 + r) * n + s]);
+      double gr;
+      if (r == 0) {
+        gr = -2.0 * L_rss * (c - mh);
+        dye[s] = T(2.0 * L_rss * (c - mh));
+      } else {
+        const int pp = r - 1;
+        gr = L_trn * c / sb[1 + n_probes + pp];
+      }
+      for (int i = 0; i < p; ++i) {
+        double beta = 0.0;
+        for (int k = 0; k < p; ++k) beta += Sinv[i][k] * t[k];
+        bbar[i] += gr * beta;
+      }
+      for (int k = 0; k < p; ++k) {
+        const int f = ns + r * nt + k;
+        const double q = gr * a[k];
+        qbar[int64_t(f) * n + s] = T(q);
+        for (int d = 0; d < D; ++d) dx_t[d] += q * double(V[(int64_t(1 + d) * F2 + f) * n + s]);
+        for (int d = 0; d < D; ++d) dth[d] += q * double(V[(int64_t(1 + D + d) * F2 + f) * n + s]);
+      }
+    }
+    // s-field adjoints: -sum_(a+b=g) a_a bbar_b over ordered pairs
+    for (int gf = 0; gf < ns; ++gf) {
+      double q = 0.0;
+      if (ok)
+        for (int i = 0; i < p; ++i)
+          for (int j = 0; j < p; ++j)
+            if (mono.e[i][0] + mono.e[j][0] == mono.e[gf][0] &&
+                mono.e[i][1] + mono.e[j][1] == mono.e[gf][1] &&
+                mono.e[i][2] + mono.e[j][2] == mono.e[gf][2])
+              q -= a[i] * bbar[j];
+      qbar[int64_t(gf) * n + s] = T(q);
+      for (int d = 0; d < D; ++d) dx_t[d] += q * double(V[(int64_t(1 + d) * F2 + gf) * n + s]);
+      for (int d = 0; d < D; ++d) dth[d] += q * double(V[(int64_t(1 + D + d) * F2 + gf) * n + s]);
+    }
+    if (!ok) {
+      for (int f = 0; f < F2; ++f) qbar[int64_t(f) * n + s] = T(0);
+      dye[s] = T(0);
+    }
+    for (int d = 0; d < D; ++d) dxt[int64_t(d) * n + s] = T(dx_t[d]);
+    (void)nblk;
+  }
+  for (int d = 0; d < 3; ++d) {
+    double v = dth[d];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][d] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int wv = 0; wv < kE1Threads / 32; ++wv) t += red[wv][threadIdx.x];
+    part[int64_t(blockIdx.x) * 3 + threadIdx.x] = t;
+  }
+}
+
+// Combine: dy_i = adjoint y-field + explicit term; dx_(i,d) = sum over
+// strength classes c of c_(c,i) * adjoint field (c, d) + target-side term.
+// Outputs in the original sample order.
+template <typename T, int D>
+__global__ void combine_kernel(int64_t n, int n_probes, const T* __restrict__ Vadj,
+                               const T* __restrict__ str, const T* __restrict__ dxt,
+                               const T* __restrict__ dye, const uint32_t* __restrict__ perm,
+                               T* __restrict__ dy, T* __restrict__ dx) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t i = perm[s];
+  if (dy) dy[i] = Vadj[s] + dye[s];
+  if (dx) {
+    const int ncls = 2 + n_probes;
+    for (int d = 0; d < D; ++d) {
+      double v = double(dxt[int64_t(d) * n + s]);
+      for (int c = 0; c < ncls; ++c) {
+        const double cc = c == 0 ? 1.0 : double(str[int64_t(c) * n + s]);
+        v += cc * double(Vadj[int64_t(1 + c * D + d) * n + s]);
+      }
+      dx[int64_t(i) * D + d] = T(v);
+    }
+  }
+}
+
+__global__ void reduce_theta(const double* __restrict__ part, int64_t nblk, int D,
+                             double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int d = blockIdx.x;
+  double t = 0.0;
+  for (int64_t k = threadIdx.x; k < nblk; k += blockDim.x) t += part[k * 3 + d];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[d] = sh[0];
+}
+
+template <typename T, int D>
+cudaError_t launch_gather_d(fkreg_plan_s* P, int b, int F, int rec, T* V, cudaStream_t st) {
+  const int w = P->geo.w;
+  int ncw = 1;
+  for (int j = 0; j < D; ++j) ncw *= w;
+  const int64_t groups = (P->n + 31) / 32;
+  const unsigned blocks = unsigned(std::max<int64_t>(1, std::min<int64_t>((groups + kGWarps - 1) / kGWarps, 152 * 16)));
+#define FK_G(WW)                                                                                  \
+  do {                                                                                            \
+    const size_t smem = sizeof(T) * (size_t(kGWarps) * ((WW) > 0 ? 0 : ncw) + kGWarps * 32 * 33); \
+    cudaError_t e = cudaFuncSetAttribute(gather_fields_kernel<T, D, WW>,                         \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
+    if (e != cudaSuccess) return e;                                                               \
+    gather_fields_kernel<T, D, WW><<<blocks, kGWarps * 32, smem, st>>>(                           \
+        P->geo, wsp<BwDev>(P, P->r_bw), b, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_t2field), rec, \
+        F, V);                                                                                    \
+  } while (0)
+  if (w == 7)
+    FK_G(7);
+  else
+    FK_G(0);
+#undef FK_G
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather(fkreg_plan_s* P, int b, int F, T* V, cudaStream_t st) {
+  if (P->n == 0) return cudaSuccess;
+  const int rec = t2_record_stride(F);
+  switch (P->d) {
+    case 1: return launch_gather_d<T, 1>(P, b, F, rec, V, st);
+    case 2: return launch_gather_d<T, 2>(P, b, F, rec, V, st);
+    default: return launch_gather_d<T, 3>(P, b, F, rec, V, st);
+  }
+}
+
+}  // namespace
+
+cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream_t st) {
+  return P->prec == FKREG_F32 ? launch_gather<float>(P, b, F, static_cast<float*>(V), st)
+                              : launch_gather<double>(P, b, F, static_cast<double*>(V), st);
+}
+
+cudaError_t run_loss_scalars(fkreg_plan_s* P, int b, int n_probes, cudaStream_t st) {
+  const int nacc = P->nrhs_real + 2 * n_probes + 1;
+  const double* sums = wsp<double>(P, P->r_part) + P->nblk_interp * int64_t(P->nbw) * P->nacc;
+  loss_scalars_kernel<<<1, 32, 0, st>>>(sums, b, nacc, n_probes, P->n, wsp<double>(P, P->r_bsc));
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t adjoint_t(fkreg_plan_s* P, int b, int n_probes, cudaStream_t st) {
+  if (P->n == 0) return cudaSuccess;
+  const int nacc = P->nrhs_real + 2 * n_probes + 1;
+  const double* sums = wsp<double>(P, P->r_part) + P->nblk_interp * int64_t(P->nbw) * P->nacc;
+  const int F2 = P->ns + (1 + n_probes) * P->nt;
+  const unsigned blocks = unsigned((P->n + kE1Threads - 1) / kE1Threads);
+  T* qbar = wsp<T>(P, P->r_str) + int64_t(P->smax) * P->n;
+  T* dxt = wsp<T>(P, P->r_bdx);
+  T* dye = dxt + int64_t(P->d) * P->n;
+#define FK_A(DD)                                                                              \
+  adjoint_kernel<T, DD><<<blocks, kE1Threads, 0, st>>>(                                       \
+      P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, F2, n_probes, wsp<T>(P, P->r_bV),  \
+      wsp<T>(P, P->r_str), sums, nacc, wsp<double>(P, P->r_bsc), qbar, dxt, dye,             \
+      wsp<double>(P, P->r_bpart))
+  if (P->d == 1)
+    FK_A(1);
+  else if (P->d == 2)
+    FK_A(2);
+  else
+    FK_A(3);
+#undef FK_A
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t run_adjoint(fkreg_plan_s* P, int b, int n_probes, cudaStream_t st) {
+  return P->prec == FKREG_F32 ? adjoint_t<float>(P, b, n_probes, st)
+                              : adjoint_t<double>(P, b, n_probes, st);
+}
+
+template <typename T>
+static cudaError_t combine_t(fkreg_plan_s* P, int n_probes, void* dy, void* dx, double* dlogh,
+                             cudaStream_t st) {
+  if (P->n > 0) {
+    const unsigned blocks = unsigned((P->n + 255) / 256);
+    const T* dxt = wsp<T>(P, P->r_bdx);
+    const T* dye = dxt + int64_t(P->d) * P->n;
+#define FK_C(DD)                                                                                 \
+  combine_kernel<T, DD><<<blocks, 256, 0, st>>>(P->n, n_probes, wsp<T>(P, P->r_bV),              \
+                                                wsp<T>(P, P->r_str), dxt, dye, perm_ptr(P),      \
+                                                static_cast<T*>(dy), static_cast<T*>(dx))
+    if (P->d == 1)
+      FK_C(1);
+    else if (P->d == 2)
+      FK_C(2);
+    else
+      FK_C(3);
+#undef FK_C
+    P->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (dlogh) {
+    const int64_t nblk = (P->n + kE1Threads - 1) / kE1Threads;
+    reduce_theta<<<P->d, 256, 0, st>>>(wsp<double>(P, P->r_bpart), nblk, P->d, dlogh);
+    P->launches += 1;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t run_combine(fkreg_plan_s* P, int n_probes, void* dy, void* dx, double* dlogh,
+                        cudaStream_t st) {
+  return P->prec == FKREG_F32 ? combine_t<float>(P, n_probes, dy, dx, dlogh, st)
+                              : combine_t<double>(P, n_probes, dy, dx, dlogh, st);
+}
+
+}  // namespace fk

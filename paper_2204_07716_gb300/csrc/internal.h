@@ -88,7 +88,10 @@ struct fkreg_plan_s {
   // workspace regions
   fk::Region r_err, r_bw, r_tab, r_xs, r_keys0, r_vals0, r_keys1, r_vals1, r_counts,
       r_binstart, r_nsub, r_substart, r_subbin, r_subfirst, r_hist, r_scan, r_str,
-      r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork;
+      r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork,
+      r_bV, r_bdx, r_bsc, r_bpart;
+  bool backward = false;        // workspace reserved for fkreg_backward
+  int f2bwd = 0;                // fields of the backward passes (one response + probes)
   size_t ws_bytes = 0;
   size_t fft_work_reserved = 0;
   char* ws = nullptr;
@@ -145,6 +148,16 @@ cudaError_t run_residual_strengths(fkreg_plan_s* P, const void* y, const void* m
 cudaError_t run_kmul_grid(fkreg_plan_s* P, int str_dens, int str_rhs, int nrhs_fields,
                           int bw_first, int bw_count, void* out_spec, cudaStream_t s);
 cudaError_t run_kmul_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
+                        cudaStream_t s);
+cudaError_t run_kmul_t2_mode(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
+                             int kind, int axis, cudaStream_t s);
+cudaError_t run_kmul_adj(fkreg_plan_s* P, int b, int sb, int n_classes, cudaStream_t s);
+
+// backward.cu
+cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream_t s);
+cudaError_t run_loss_scalars(fkreg_plan_s* P, int b, int n_probes, cudaStream_t s);
+cudaError_t run_adjoint(fkreg_plan_s* P, int b, int n_probes, cudaStream_t s);
+cudaError_t run_combine(fkreg_plan_s* P, int n_probes, void* dy, void* dx, double* dlogh,
                         cudaStream_t s);
 
 // solve.cu

@@ -304,6 +304,254 @@ cudaError_t launch_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_r
   return cudaGetLastError();
 }
 
+
+// ---- multipliers for the backward pass ----------------------------------------
+// Fourier multiplier of field f (monomial exponent e_f) at xi = k / P:
+//  kind 0: conj(w^_f(xi))             forward field T_f(q) = sum_i c_i w_f(x_i - q)
+//  kind 1: 2 pi i xi_d conj(w^_f)     its gradient in the evaluation point q_d
+//  kind 2: d conj(w^_f) / d log sigma_j   (H = diag(sigma^2))
+//  kind 3: w^_f(xi)                   adjoint field sum_m e_m w_f(q - x_m)
+//  kind 4: 2 pi i xi_d w^_f(xi)       adjoint field of the kernel derivative
+// with w^_0 = G, w^_(e_a) = -2 pi i (H xi)_a G, w^_(e_a+e_b) = (H_ab - 4 pi^2 (H xi)_a (H xi)_b) G.
+template <typename T, typename C>
+__device__ __forceinline__ C field_mult(const MonoTab& mono, int f, int kind, int axis, const T xi[3],
+                                        const ModeMul<T>& m, const BwDev& B) {
+  const T twopi = T(6.283185307179586476925286766559);
+  const T fpi2 = twopi * twopi;
+  const int deg = mono.e[f][0] + mono.e[f][1] + mono.e[f][2];
+  int a = -1, b = -1;
+  for (int j = 0; j < 3; ++j)
+    for (int r = 0; r < mono.e[f][j]; ++r) {
+      if (a < 0)
+        a = j;
+      else
+        b = j;
+    }
+  C W{T(0), T(0)};
+  if (kind == 2) {
+    const int j = axis;
+    const T s2 = T(B.H[j * 3 + j]);
+    const T dG = -T(0.5) * fpi2 * T(2) * s2 * xi[j] * xi[j] * m.G;  // -4 pi^2 sigma_j^2 xi_j^2 G
+    const T dxa = (a == j) ? T(2) * s2 * xi[j] : T(0);
+    if (deg == 0) {
+      W.x = dG;
+    } else if (deg == 1) {
+      W.y = twopi * (dxa * m.G + m.hx[a] * dG);
+    } else {
+      const T dxb = (b == j) ? T(2) * s2 * xi[j] : T(0);
+      const T dH = (a == j && b == j) ? T(2) * s2 : T(0);
+      W.x = (dH - fpi2 * (dxa * m.hx[b] + m.hx[a] * dxb)) * m.G +
+            (T(B.H[a * 3 + b]) - fpi2 * m.hx[a] * m.hx[b]) * dG;
+    }
+    return W;
+  }
+  const bool adjoint = kind >= 3;
+  if (deg == 0) {
+    W.x = m.G;
+  } else if (deg == 1) {
+    W.y = (adjoint ? -twopi : twopi) * m.hx[a] * m.G;
+  } else {
+    W.x = (T(B.H[a * 3 + b]) - fpi2 * m.hx[a] * m.hx[b]) * m.G;
+  }
+  if (kind == 1 || kind == 4) {  // times 2 pi i xi_d
+    const T s = twopi * xi[axis];
+    const C r{-W.y * s, W.x * s};
+    return r;
+  }
+  return W;
+}
+
+// Type-2 spectra of the forward fields under multiplier `kind` (0, 1, 2), for
+// one bandwidth: thread per (fine half-spectrum index, strength q).
+template <typename T, int D>
+__global__ void kmul_t2_mode_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
+                                    const double* __restrict__ tab, int64_t phi1_0, int64_t phi1_1,
+                                    int64_t phi1_2, MonoTab mono,
+                                    const typename Cx<T>::type* __restrict__ F, int64_t fine_half,
+                                    int str_dens, int str_rhs, int n_rhs_str, int kind, int axis,
+                                    int64_t t2half, typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
+  const int nq = 1 + n_rhs_str;
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= t2half * nq) return;
+  const int64_t j = gid % t2half;
+  const int q = int(gid / t2half);
+  const BwDev& B = bwt[b];
+  const bool dens = q == 0;
+  const int strength = dens ? str_dens : str_rhs + q - 1;
+  const int nfld = dens ? mono.n : mono.nt;
+  const int fbase = dens ? 0 : mono.n + (q - 1) * mono.nt;
+  int64_t kk[3] = {0, 0, 0};
+  bool inside = true;
+  {
+    int64_t rem = j;
+    for (int a = D - 1; a >= 0; --a) {
+      const int64_t nn = (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+      int64_t idx = rem % nn;
+      rem /= nn;
+      int64_t k = (a == D - 1) ? idx : (idx < (B.nf[a] + 1) / 2 ? idx : idx - B.nf[a]);
+      kk[a] = k;
+      if ((k < 0 ? -k : k) > B.K[a] / 2 - 1) inside = false;
+    }
+  }
+  C res[kMaxMono];
+  for (int f = 0; f < kMaxMono; ++f) res[f] = C{T(0), T(0)};
+  if (inside) {
+    const int64_t phi1[3] = {phi1_0, phi1_1, phi1_2};
+    T dec = T(1);
+    T xi[3] = {T(0), T(0), T(0)};
+    for (int a = 0; a < D; ++a) {
+      const int64_t ak = kk[a] < 0 ? -kk[a] : kk[a];
+      dec *= T(tab[phi1[a] + ak] * tab[B.phi2_off[a] + ak] / g.P[a]);
+      xi[a] = T(kk[a]) / T(g.P[a]);
+    }
+    const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
+    C base = fetch_F<T, C>(g, F + int64_t(strength) * fine_half, kk, D);
+    base.x *= dec;
+    base.y *= dec;
+    for (int f = 0; f < nfld; ++f) {
+      const C W = field_mult<T, C>(mono, dens ? f : f, kind, axis, xi, m, B);
+      res[f] = cmul<C, T>(W, base);
+    }
+  }
+  for (int f = 0; f < nfld; ++f) out[int64_t(fbase + f) * t2half + j] = res[f];
+}
+
+// Adjoint fields on bandwidth b's type-2 grid from the spectra E_f of the
+// adjoint strengths (strength index sb + f for field f):
+//   output 0            : sum_{f in class y} w^_f(xi) E_f                (d/dy)
+//   output 1 + c D + d  : sum_{f in class c} 2 pi i xi_d w^_f(xi) E_f     (d/dx, source side)
+// classes: c = 0 the s-fields (density), c >= 1 the t-fields of response /
+// probe c - 1.  Thread per (fine half-spectrum index, output).
+template <typename T, int D>
+__global__ void kmul_adj_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
+                                const double* __restrict__ tab, int64_t phi1_0, int64_t phi1_1,
+                                int64_t phi1_2, MonoTab mono,
+                                const typename Cx<T>::type* __restrict__ F, int64_t fine_half, int sb,
+                                int n_classes, int64_t t2half, typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
+  const int nout = 1 + n_classes * D;
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= t2half * nout) return;
+  const int64_t j = gid % t2half;
+  const int o = int(gid / t2half);
+  const BwDev& B = bwt[b];
+  int64_t kk[3] = {0, 0, 0};
+  bool inside = true;
+  {
+    int64_t rem = j;
+    for (int a = D - 1; a >= 0; --a) {
+      const int64_t nn = (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+      int64_t idx = rem % nn;
+      rem /= nn;
+      int64_t k = (a == D - 1) ? idx : (idx < (B.nf[a] + 1) / 2 ? idx : idx - B.nf[a]);
+      kk[a] = k;
+      if ((k < 0 ? -k : k) > B.K[a] / 2 - 1) inside = false;
+    }
+  }
+  C acc{T(0), T(0)};
+  if (inside) {
+    const int64_t phi1[3] = {phi1_0, phi1_1, phi1_2};
+    T dec = T(1);
+    T xi[3] = {T(0), T(0), T(0)};
+    for (int a = 0; a < D; ++a) {
+      const int64_t ak = kk[a] < 0 ? -kk[a] : kk[a];
+      dec *= T(tab[phi1[a] + ak] * tab[B.phi2_off[a] + ak] / g.P[a]);
+      xi[a] = T(kk[a]) / T(g.P[a]);
+    }
+    const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
+    int cls, kind, axis = 0;
+    if (o == 0) {
+      cls = 1;
+      kind = 3;
+    } else {
+      cls = (o - 1) / D;
+      axis = (o - 1) % D;
+      kind = 4;
+    }
+    const int f0 = cls == 0 ? 0 : mono.n + (cls - 1) * mono.nt;
+    const int nf = cls == 0 ? mono.n : mono.nt;
+    for (int q = 0; q < nf; ++q) {
+      const int f = f0 + q;
+      const int mf = cls == 0 ? q : q;  // monomial index inside the class
+      C e = fetch_F<T, C>(g, F + int64_t(sb + f) * fine_half, kk, D);
+      const C W = field_mult<T, C>(mono, mf, kind, axis, xi, m, B);
+      const C t = cmul<C, T>(W, e);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    acc.x *= dec;
+    acc.y *= dec;
+  }
+  out[int64_t(o) * t2half + j] = acc;
+}
+
+template <typename T>
+cudaError_t launch_t2_mode(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
+                           int kind, int axis, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const GeoDev& g = P->geo;
+  const int D = P->d;
+  const BwDev& B = P->bw[b];
+  int64_t t2half = 1, fhalf = 1;
+  for (int a = 0; a < D; ++a) {
+    t2half *= (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+    fhalf *= (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
+  }
+  const int64_t total = t2half * (1 + n_rhs_str);
+  const unsigned blocks = unsigned((total + 255) / 256);
+  auto* F = wsp<C>(P, P->r_spec);
+  auto* bwt = wsp<BwDev>(P, P->r_bw);
+  auto* tab = wsp<double>(P, P->r_tab);
+  C* o = wsp<C>(P, P->r_t2spec);
+#define FK_KM(DD)                                                                                    \
+  kmul_t2_mode_kernel<T, DD><<<blocks, 256, 0, st>>>(g, bwt, b, tab, P->phi1_off[0], P->phi1_off[1], \
+                                                     P->phi1_off[2], P->mono, F, fhalf, str_dens,    \
+                                                     str_rhs, n_rhs_str, kind, axis, t2half, o)
+  if (D == 1)
+    FK_KM(1);
+  else if (D == 2)
+    FK_KM(2);
+  else
+    FK_KM(3);
+#undef FK_KM
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adj(fkreg_plan_s* P, int b, int sb, int n_classes, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const GeoDev& g = P->geo;
+  const int D = P->d;
+  const BwDev& B = P->bw[b];
+  int64_t t2half = 1, fhalf = 1;
+  for (int a = 0; a < D; ++a) {
+    t2half *= (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+    fhalf *= (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
+  }
+  const int nout = 1 + n_classes * D;
+  const int64_t total = t2half * nout;
+  const unsigned blocks = unsigned((total + 255) / 256);
+  auto* F = wsp<C>(P, P->r_spec);
+  auto* bwt = wsp<BwDev>(P, P->r_bw);
+  auto* tab = wsp<double>(P, P->r_tab);
+  C* o = wsp<C>(P, P->r_t2spec);
+#define FK_KA(DD)                                                                                 \
+  kmul_adj_kernel<T, DD><<<blocks, 256, 0, st>>>(g, bwt, b, tab, P->phi1_off[0], P->phi1_off[1], \
+                                                 P->phi1_off[2], P->mono, F, fhalf, sb, n_classes, \
+                                                 t2half, o)
+  if (D == 1)
+    FK_KA(1);
+  else if (D == 2)
+    FK_KA(2);
+  else
+    FK_KA(3);
+#undef FK_KA
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t run_kmul_grid(fkreg_plan_s* P, int str_dens, int str_rhs, int nrhs_fields, int bw_first,
@@ -317,6 +565,18 @@ cudaError_t run_kmul_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n
                         cudaStream_t st) {
   return P->prec == FKREG_F32 ? launch_t2<float>(P, b, str_dens, str_rhs, n_rhs_str, st)
                               : launch_t2<double>(P, b, str_dens, str_rhs, n_rhs_str, st);
+}
+
+cudaError_t run_kmul_t2_mode(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
+                             int kind, int axis, cudaStream_t st) {
+  return P->prec == FKREG_F32
+             ? launch_t2_mode<float>(P, b, str_dens, str_rhs, n_rhs_str, kind, axis, st)
+             : launch_t2_mode<double>(P, b, str_dens, str_rhs, n_rhs_str, kind, axis, st);
+}
+
+cudaError_t run_kmul_adj(fkreg_plan_s* P, int b, int sb, int n_classes, cudaStream_t st) {
+  return P->prec == FKREG_F32 ? launch_adj<float>(P, b, sb, n_classes, st)
+                              : launch_adj<double>(P, b, sb, n_classes, st);
 }
 
 }  // namespace fk

@@ -20,15 +20,16 @@ LIB_PATH = os.path.join(HERE, "libfkreg.so")
 FKREG_F32, FKREG_F64 = 0, 1
 FKREG_SPREAD_ES, FKREG_SPREAD_GAUSS = 0, 1
 FKREG_GCV_EXACT_TRACE = 1
+FKREG_WANT_BACKWARD = 2
 STAGES = ["sort", "strengths", "spread", "fft_fwd", "kmul_grid", "fft_grid", "grid_solve",
-          "kmul_t2", "fft_t2", "interp", "finalize"]
+          "kmul_t2", "fft_t2", "interp", "finalize", "backward"]
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA", 5: "CUFFT",
           6: "TIMEOUT", 7: "DEVICE", 8: "STATE"}
 
 EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
-           "fkreg_smooth", "fkreg_df", "fkreg_variance", "fkreg_set_timing",
+           "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_variance", "fkreg_set_timing",
            "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy"]
 
@@ -93,6 +94,8 @@ def load():
     L.fkreg_smooth.argtypes = [vp, vp, ctypes.POINTER(Outputs), vp]
     L.fkreg_df.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(Outputs), vp]
     L.fkreg_variance.argtypes = [vp, vp, vp, vp, vp]
+    L.fkreg_backward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.c_int, vp, vp,
+                                 vp, vp, vp]
     L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
     L.fkreg_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]
@@ -338,6 +341,29 @@ class Plan:
                                     ctypes.byref(s), self._stream()))
         self._y_keep = (y, pr)
         return o
+
+    def backward(self, y, n_probes: int, seed: int = 0, probes=None, b: int = 0,
+                 want=("dlogh", "dy", "dx")) -> Dict[str, object]:
+        """GCV of bandwidth b and its gradient (fkreg_backward)."""
+        t = self.torch
+        y = self._y(y)
+        pr = None if probes is None else self._as_dev(probes)
+        n = max(self.n, 1)
+        out = {"gcv": t.empty(1, dtype=t.float64, device=self.device)}
+        if "dlogh" in want:
+            out["dlogh"] = t.empty(self.d, dtype=t.float64, device=self.device)
+        if "dy" in want:
+            out["dy"] = t.empty(n, dtype=self.dtype, device=self.device)
+        if "dx" in want:
+            out["dx"] = t.empty((n, self.d), dtype=self.dtype, device=self.device)
+        ptr = lambda k: ctypes.c_void_p(out[k].data_ptr()) if k in out else None
+        self._check(self.L.fkreg_backward(self.h, ctypes.c_void_p(y.data_ptr()), int(n_probes),
+                                          ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                          None if pr is None else ctypes.c_void_p(pr.data_ptr()),
+                                          int(b), ptr("gcv"), ptr("dlogh"), ptr("dy"), ptr("dx"),
+                                          self._stream()))
+        self._y_keep = (y, pr)
+        return out
 
     def variance(self, y, mhat_at_x):
         t = self.torch
