@@ -330,6 +330,42 @@ fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const double* gri
                                    const void* x_dev, uint32_t* perm_dev, uint32_t* bin_start_dev,
                                    int32_t* bad_dev, void* stream);
 
+/*
+ * Uneven batches of independent problems in one captured CUDA graph (the
+ * many-responses / many-datasets use of Sec. 4 and the EEG spectra of
+ * Sec. 4.4).  Each problem has its own options (dimension, grid, bandwidth,
+ * tile) and plan; all plans share one caller-owned workspace.
+ *   fkreg_batch_create          opts[n_problems], max_n[n_problems]; host only
+ *                               besides the cuFFT plans of each problem
+ *   fkreg_batch_workspace_bytes total bytes (256-byte aligned start)
+ *   fkreg_batch_set_workspace   hands each plan its slice (synchronises stream)
+ *   fkreg_batch_capture         records, per problem p on one of up to 16
+ *                               forked branches: fkreg_set_points(n[p], x[p]),
+ *                               fkreg_smooth(y[p], &outs[p]) and, when
+ *                               sigma2[p] is not NULL, fkreg_variance(y[p],
+ *                               outs[p].mhat_at_x, sigma2[p]); then a global
+ *                               timer stamp.  Inputs and outputs must keep
+ *                               their addresses for later launches.  The
+ *                               capture stream must not be capturing already.
+ *   fkreg_batch_launch          replays the graph on `stream`
+ *   fkreg_batch_latencies       ms[p] = completion time of problem p relative
+ *                               to the start of the last launch (synchronises)
+ *   fkreg_batch_plan            the plan of problem p (for inspection)
+ */
+typedef struct fkreg_batch_s* fkreg_batch;
+fkreg_status fkreg_batch_create(int n_problems, const fkreg_opts* opts, const int64_t* max_n,
+                                fkreg_batch* out);
+fkreg_status fkreg_batch_workspace_bytes(fkreg_batch batch, size_t* bytes);
+fkreg_status fkreg_batch_set_workspace(fkreg_batch batch, void* ws_dev, size_t bytes, void* stream);
+fkreg_status fkreg_batch_capture(fkreg_batch batch, const int64_t* n, const void* const* x_dev,
+                                 const void* const* y_dev, const fkreg_outputs* outs,
+                                 void* const* sigma2_dev, void* stream);
+fkreg_status fkreg_batch_launch(fkreg_batch batch, void* stream);
+fkreg_status fkreg_batch_latencies(fkreg_batch batch, double* ms, void* stream);
+fkreg_plan fkreg_batch_plan(fkreg_batch batch, int p);
+const char* fkreg_batch_last_error(fkreg_batch batch);
+void fkreg_batch_destroy(fkreg_batch batch);
+
 /* Synchronise the stream and report device-detected errors (then clear them). */
 fkreg_status fkreg_sync_status(fkreg_plan plan, void* stream);
 

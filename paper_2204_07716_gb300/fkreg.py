@@ -31,7 +31,10 @@ EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create"
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
            "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_variance", "fkreg_set_timing",
            "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
-           "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy"]
+           "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
+           "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
+           "fkreg_batch_capture", "fkreg_batch_launch", "fkreg_batch_latencies",
+           "fkreg_batch_plan", "fkreg_batch_last_error", "fkreg_batch_destroy"]
 
 
 class Opts(ctypes.Structure):
@@ -109,8 +112,25 @@ def load():
     L.fkreg_global_error.restype = ctypes.c_char_p
     L.fkreg_plan_destroy.argtypes = [vp]
     L.fkreg_plan_destroy.restype = None
+    L.fkreg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(i64),
+                                     ctypes.POINTER(vp)]
+    L.fkreg_batch_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.fkreg_batch_set_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.fkreg_batch_capture.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(vp),
+                                      ctypes.POINTER(vp), ctypes.POINTER(Outputs),
+                                      ctypes.POINTER(vp), vp]
+    L.fkreg_batch_launch.argtypes = [vp, vp]
+    L.fkreg_batch_latencies.argtypes = [vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.fkreg_batch_plan.argtypes = [vp, ctypes.c_int]
+    L.fkreg_batch_plan.restype = vp
+    L.fkreg_batch_last_error.argtypes = [vp]
+    L.fkreg_batch_last_error.restype = ctypes.c_char_p
+    L.fkreg_batch_destroy.argtypes = [vp]
+    L.fkreg_batch_destroy.restype = None
+    no_status = ("fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy", "fkreg_batch_plan",
+                 "fkreg_batch_last_error", "fkreg_batch_destroy")
     for name in EXPORTS:
-        if name not in ("fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy"):
+        if name not in no_status:
             getattr(L, name).restype = st
     _lib = L
     return L
@@ -375,3 +395,147 @@ class Plan:
                                           ctypes.c_void_p(out.data_ptr()), self._stream()))
         self._y_keep = (y, mh)
         return out
+
+
+class Batch:
+    """Independent problems replayed as one captured CUDA graph.
+
+    ``problems`` is a list of dicts with the keyword arguments of
+    :func:`make_opts` plus ``max_n``.  ``capture`` records, per problem, the
+    bin sort, the smoothing (grid estimate + values at the samples) and the
+    conditional-variance pass; ``launch`` replays it; ``latencies`` returns
+    each problem's completion time (ms) after the start of the last launch.
+    """
+
+    def __init__(self, problems, device=None):
+        import torch
+        self.torch = torch
+        self.L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.problems = [dict(p) for p in problems]
+        n = len(problems)
+        self._opts = (Opts * n)()
+        self._keep = []
+        maxn = (ctypes.c_int64 * n)()
+        for i, p in enumerate(problems):
+            kw = {k: v for k, v in p.items() if k != "max_n"}
+            o, keep = make_opts(**kw)
+            self._opts[i] = o
+            self._keep.append(keep)
+            maxn[i] = int(p["max_n"])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.L.fkreg_batch_create(n, self._opts, maxn, ctypes.byref(h))
+        if st != 0:
+            raise FkregError(f"{STATUS.get(st, st)}: {self.L.fkreg_global_error().decode()}")
+        self.h = h
+        nb = ctypes.c_size_t()
+        self.L.fkreg_batch_workspace_bytes(self.h, ctypes.byref(nb))
+        self._ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
+        self._ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self._check(self.L.fkreg_batch_set_workspace(
+            self.h, ctypes.c_void_p(self._ws_ptr), int(nb.value),
+            ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+
+    def _check(self, st):
+        if st != 0:
+            raise FkregError(f"{STATUS.get(st, st)}: {self.L.fkreg_batch_last_error(self.h).decode()}")
+
+    def capture(self, xs, ys, variance=True):
+        """Record the batch; xs, ys are device tensors per problem (kept alive)."""
+        t = self.torch
+        n = len(self.problems)
+        self._inputs = (list(xs), list(ys))
+        outs = []
+        arr_out = (Outputs * n)()
+        nn = (ctypes.c_int64 * n)()
+        px = (ctypes.c_void_p * n)()
+        py = (ctypes.c_void_p * n)()
+        ps2 = (ctypes.c_void_p * n)()
+        for i, p in enumerate(self.problems):
+            d = p["d"]
+            cplx = bool(p.get("y_complex", False))
+            prec = p.get("precision", "f32")
+            dt = t.float32 if prec == "f32" else t.float64
+            cdt = t.complex64 if prec == "f32" else t.complex128
+            grid = tuple(int(v) for v in p["grid_n"])
+            nbw = np.asarray(p["H"]).reshape(-1, d, d).shape[0]
+            x = xs[i]
+            ni = int(x.shape[0])
+            o = {"mhat_grid": t.empty((nbw, 1) + grid, dtype=cdt if cplx else dt, device=self.device),
+                 "mask": t.empty((nbw,) + grid, dtype=t.uint8, device=self.device),
+                 "mhat_at_x": t.empty((nbw, 1, max(ni, 1)), dtype=cdt if cplx else dt,
+                                      device=self.device)}
+            if variance:
+                o["sigma2"] = t.empty((nbw, 1) + grid, dtype=dt, device=self.device)
+            outs.append(o)
+            s = Outputs()
+            s.mhat_grid = o["mhat_grid"].data_ptr()
+            s.mask = o["mask"].data_ptr()
+            s.mhat_at_x = o["mhat_at_x"].data_ptr()
+            arr_out[i] = s
+            nn[i] = ni
+            px[i] = x.data_ptr()
+            py[i] = ys[i].data_ptr()
+            ps2[i] = o["sigma2"].data_ptr() if variance else None
+        self.outs = outs
+        self._check(self.L.fkreg_batch_capture(
+            self.h, nn, px, py, arr_out, ps2,
+            ctypes.c_void_p(t.cuda.current_stream(self.device).cuda_stream)))
+        return outs
+
+    def launch(self):
+        self._check(self.L.fkreg_batch_launch(
+            self.h, ctypes.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)))
+
+    def latencies(self) -> np.ndarray:
+        n = len(self.problems)
+        ms = (ctypes.c_double * n)()
+        self._check(self.L.fkreg_batch_latencies(
+            self.h, ms, ctypes.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)))
+        return np.array(ms[:])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.fkreg_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_tile(problem: dict, x, y, candidates=None, reps: int = 3) -> int:
+    """Pick the spreading tile for one problem by timing fkreg_set_points +
+    fkreg_smooth (grid estimate and values at the samples) for each candidate
+    tile with CUDA events; returns the fastest.  ``problem`` holds the keyword
+    arguments of :class:`Plan` (including ``max_n``)."""
+    import torch
+    d = problem["d"]
+    if candidates is None:
+        candidates = {1: (512, 1024, 2048, 4096), 2: (8, 16, 32), 3: (4, 8, 16)}[d]
+    best, best_t = None, None
+    for tile in candidates:
+        kw = dict(problem)
+        kw["tile"] = tile
+        try:
+            p = Plan(**kw)
+        except FkregError:
+            continue
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(1):
+            p.set_points(x)
+            p.smooth(y, want=("mhat_grid", "mhat_at_x"))
+        ev0.record()
+        for _ in range(reps):
+            p.set_points(x)
+            p.smooth(y, want=("mhat_grid", "mhat_at_x"))
+        ev1.record()
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        p.close()
+        if best_t is None or ms < best_t:
+            best, best_t = tile, ms
+    return int(best) if best is not None else 0
