@@ -46,6 +46,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="ll2d",
+                    choices=["ll2d", "nw1d", "nw3d_df", "ll2d_gcv", "uneven"],
+                    help="ll2d is the headline line; the others measure the remaining "
+                         "configurations (1-D NW FP64, 3-D NW + DF sweep, 2-D LL GCV "
+                         "forward + backward, 64 uneven problems in one graph)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="sample-count multiplier for the extra workloads (1 = full size)")
     return ap.parse_args()
 
 
@@ -351,11 +358,138 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
+def run_extra(args):
+    """Timed steps of the other configurations (one GPU, device events)."""
+    import numpy as np
+    import torch
+
+    from paper_2204_07716_gb300 import build as fkbuild
+    from paper_2204_07716_gb300 import fkreg, inputs
+
+    fkbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    extra = {}
+    wl = args.workload
+    sc = args.scale
+    if wl == "uneven":
+        ws = inputs.uneven(scale=sc)
+        probs = [dict(d=w.d, order=1, grid_n=w.grid_n, lo=w.lo, hi=w.hi, H=w.H, max_n=w.n,
+                      tol=w.tol, precision="f32", y_complex=True) for w in ws]
+        xs = [torch.tensor(w.x, dtype=torch.float32, device=dev) for w in ws]
+        ys = [torch.view_as_real(torch.tensor(w.y[0], dtype=torch.complex64, device=dev)).contiguous()
+              for w in ws]
+        batch = fkreg.Batch(probs, device=dev)
+        batch.capture(xs, ys, variance=True)
+        step = lambda k: batch.launch()
+        units = sum(w.n for w in ws) * 2
+        cfg = {"workload": f"uneven-{len(ws)}problems-complex-LL+variance",
+               "n_total": sum(w.n for w in ws), "problems": len(ws),
+               "dims": [w.d for w in ws].count(2), "graph": "one captured CUDA graph"}
+        dtype = "f32+f64solve"
+    else:
+        if wl == "nw1d":
+            w = inputs.nw1d(n=int(10_000 * sc))
+            np_ = 0
+        elif wl == "nw3d_df":
+            w = inputs.nw3d_df(n=int(4_000_000 * sc))
+            np_ = w.n_probes
+        else:
+            w = inputs.ll2d_gcv(n=int(2_000_000 * sc))
+            np_ = w.n_probes
+        flags = fkreg.FKREG_WANT_BACKWARD if wl == "ll2d_gcv" else 0
+        plan = fkreg.Plan(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, max_probes=np_,
+                          tol=w.tol, precision=w.precision, flags=flags, device=dev)
+        dt = torch.float32 if w.precision == "f32" else torch.float64
+        x = torch.tensor(w.x, dtype=dt, device=dev)
+        y = torch.tensor(w.y, dtype=dt, device=dev)
+        if wl == "nw1d":
+            def step(k):
+                plan.set_points(x)
+                plan.smooth(y, want=("mhat_grid", "mask"))
+            units = w.n
+        elif wl == "nw3d_df":
+            def step(k):
+                plan.set_points(x)
+                plan.df(y, np_, seed=k, want=("mhat_grid", "mask"))
+            units = w.n * (1 + np_) * w.n_bw
+        else:
+            def step(k):
+                plan.set_points(x)
+                plan.backward(y[0], np_, seed=k)
+            units = w.n * (1 + np_)
+        cfg = {"workload": {"nw1d": "nw1d-10k-256-NW-f64-tol1e-9",
+                            "nw3d_df": "nw3d-4M-64cube-NW-16bw-32probes-f32-tol1e-6",
+                            "ll2d_gcv": "ll2d-2M-512sq-LL-GCV-fwd+bwd-f32-tol1e-6"}[wl],
+               "n": w.n, "grid": list(w.grid_n), "bandwidths": w.n_bw, "probes": np_,
+               "geometry": plan.geom}
+        dtype = "f64" if w.precision == "f64" else "f32+f64solve"
+        extra["plan"] = plan
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(0)
+    clocks.start()
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step(args.warmup + k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    res = {"metric": METRIC, "value": units * args.steps / (sum(ms) / 1e3), "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sum(ms) / args.steps, "ms_step_median": float(np.median(ms)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+           "data": "synthetic", "config": cfg, "clocks": clk}
+    if wl == "uneven":
+        lat = batch.latencies()
+        res["latency_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                             "max": float(lat.max())}
+        iso = []
+        for i, p in enumerate(probs):        # isolated per-problem latency (one plan, same inputs)
+            if i % 8:
+                continue
+            pl = fkreg.Plan(**p, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            pl.set_points(xs[i])
+            o = pl.smooth(ys[i], want=("mhat_grid", "mask", "mhat_at_x"))
+            pl.variance(ys[i], o["mhat_at_x"])
+            e0.record()
+            pl.set_points(xs[i])
+            o = pl.smooth(ys[i], want=("mhat_grid", "mask", "mhat_at_x"))
+            pl.variance(ys[i], o["mhat_at_x"])
+            e1.record()
+            e1.synchronize()
+            iso.append(e0.elapsed_time(e1))
+            pl.close()
+        res["isolated_latency_ms_sampled"] = {"p50": float(np.percentile(iso, 50)),
+                                              "max": float(max(iso)), "count": len(iso)}
+    else:
+        plan = extra["plan"]
+        plan.set_timing(True)
+        step(0)
+        torch.cuda.synchronize(dev)
+        st_ms, st_calls, launches = plan.stage_times()
+        plan.set_timing(False)
+        res["stages_ms_per_step"] = {k: round(v, 4) for k, v in st_ms.items()}
+        res["gpu_launches_per_step"] = launches
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload != "ll2d":
+        if rank == 0:
+            run_extra(args)
     else:
         run_ours(args, world, rank, local)
 
