@@ -472,6 +472,7 @@ def run_extra(args):
                                               "max": float(max(iso)), "count": len(iso)}
     else:
         plan = extra["plan"]
+        plan.stage_times()          # drop the counts of the timed steps
         plan.set_timing(True)
         step(0)
         torch.cuda.synchronize(dev)

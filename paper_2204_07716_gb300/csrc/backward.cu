@@ -15,65 +15,20 @@
 //   d/dx_j (source) = sum_c c_(c,j) sum_(f in c) sum_i Qbar_(i,f) grad w_f(x_j - x_i)
 //   d/dy_j          = 2 L_RSS (y_j - mhat_y(x_j)) + sum_(f in y) sum_i Qbar_(i,f) w_f(x_j - x_i)
 // The last two are NUFFT convolutions of the adjoints spread as strengths.
+// Field values at the samples come from the interpolation kernels' gather-only
+// mode (same bin-window staging as the forward pass).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "device_common.cuh"
-#include "gather.cuh"
 #include "internal.h"
 
 namespace fk {
 
 namespace {
 
-constexpr int kGWarps = 8;
 constexpr int kE1Threads = 256;
-
-// Gather F fields (record stride rec) at every sorted sample into V[f][n].
-template <typename T, int D, int W>
-__global__ void __launch_bounds__(kGWarps * 32)
-gather_fields_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
-                     const T* __restrict__ xs, const T* __restrict__ fld, int rec, int F,
-                     T* __restrict__ V) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w = W > 0 ? W : g.w;
-  int ncw = 1;
-  for (int j = 0; j < D; ++j) ncw *= w;
-  if (W > 0) ncw = 0;
-  const int bstride = 33;
-  T* cellw = reinterpret_cast<T*>(smem_raw) + warp * ncw;
-  T* buf = reinterpret_cast<T*>(smem_raw) + kGWarps * ncw + warp * 32 * bstride;
-  const BwDev& B = bwt[b];
-  const int nf0 = int(B.nf[0]), nf1 = D > 1 ? int(B.nf[1]) : 1, nf2 = D > 2 ? int(B.nf[2]) : 1;
-  const T ih0 = T(B.inv_h[0]), ih1 = T(D > 1 ? B.inv_h[1] : 1.0), ih2 = T(D > 2 ? B.inv_h[2] : 1.0);
-  const T beta = T(g.beta);
-  const T halfw = T(0.5) * T(w);
-  const int64_t ngroups = (n + 31) / 32;
-  for (int64_t grp = int64_t(blockIdx.x) * kGWarps + warp; grp < ngroups;
-       grp += int64_t(gridDim.x) * kGWarps) {
-    const int64_t s0 = grp * 32;
-    const int cnt = int(min(int64_t(32), n - s0));
-    for (int f_first = 0; f_first < F; f_first += 32) {
-      const int fcount = min(32, F - f_first);
-      for (int j = 0; j < cnt; ++j) {
-        const int64_t sj = s0 + j;
-        const SampleWin<T, D> sw = sample_window<T, D>(
-            g, w, beta, halfw, ih0, ih1, ih2, xs[sj], D > 1 ? xs[n + sj] : T(0),
-            D > 2 ? xs[2 * n + sj] : T(0), lane);
-        T acc[1];
-        gather_global<T, D, W, 1>(fld, rec, f_first, fcount, lane, sw, w, nf0, nf1, nf2, cellw, acc);
-        if (lane < fcount) buf[j * bstride + lane] = acc[0];
-        __syncwarp();
-      }
-      // transpose: lane = sample, coalesced rows of V
-      for (int f = 0; f < fcount; ++f)
-        if (lane < cnt) V[int64_t(f_first + f) * n + s0 + lane] = buf[lane * bstride + f];
-      __syncwarp();
-    }
-  }
-}
 
 // Loss scalars for bandwidth b from the forward sums:
 //   sc[0] = L_RSS = (1/N) / (1 - tr/N)^2
@@ -280,49 +235,7 @@ __global__ void reduce_theta(const double* __restrict__ part, int64_t nblk, int 
   if (threadIdx.x == 0) out[d] = sh[0];
 }
 
-template <typename T, int D>
-cudaError_t launch_gather_d(fkreg_plan_s* P, int b, int F, int rec, T* V, cudaStream_t st) {
-  const int w = P->geo.w;
-  int ncw = 1;
-  for (int j = 0; j < D; ++j) ncw *= w;
-  const int64_t groups = (P->n + 31) / 32;
-  const unsigned blocks = unsigned(std::max<int64_t>(1, std::min<int64_t>((groups + kGWarps - 1) / kGWarps, 152 * 16)));
-#define FK_G(WW)                                                                                  \
-  do {                                                                                            \
-    const size_t smem = sizeof(T) * (size_t(kGWarps) * ((WW) > 0 ? 0 : ncw) + kGWarps * 32 * 33); \
-    cudaError_t e = cudaFuncSetAttribute(gather_fields_kernel<T, D, WW>,                         \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
-    if (e != cudaSuccess) return e;                                                               \
-    gather_fields_kernel<T, D, WW><<<blocks, kGWarps * 32, smem, st>>>(                           \
-        P->geo, wsp<BwDev>(P, P->r_bw), b, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_t2field), rec, \
-        F, V);                                                                                    \
-  } while (0)
-  if (w == 7)
-    FK_G(7);
-  else
-    FK_G(0);
-#undef FK_G
-  P->launches += 1;
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_gather(fkreg_plan_s* P, int b, int F, T* V, cudaStream_t st) {
-  if (P->n == 0) return cudaSuccess;
-  const int rec = t2_record_stride(F);
-  switch (P->d) {
-    case 1: return launch_gather_d<T, 1>(P, b, F, rec, V, st);
-    case 2: return launch_gather_d<T, 2>(P, b, F, rec, V, st);
-    default: return launch_gather_d<T, 3>(P, b, F, rec, V, st);
-  }
-}
-
 }  // namespace
-
-cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream_t st) {
-  return P->prec == FKREG_F32 ? launch_gather<float>(P, b, F, static_cast<float*>(V), st)
-                              : launch_gather<double>(P, b, F, static_cast<double*>(V), st);
-}
 
 cudaError_t run_loss_scalars(fkreg_plan_s* P, int b, int n_probes, cudaStream_t st) {
   const int nacc = P->nrhs_real + 2 * n_probes + 1;

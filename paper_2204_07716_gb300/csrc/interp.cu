@@ -240,6 +240,15 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
   }
 }
 
+// Gather-only mode: the pass's field values of this lane's sample go to
+// V[f][s] (sorted sample order; consecutive lanes write consecutive samples).
+template <typename T>
+__device__ __forceinline__ void store_fields(T* __restrict__ V, const T* my, int f_first,
+                                             int fcount, bool valid, int64_t s, int64_t n) {
+  if (!valid) return;
+  for (int f = 0; f < fcount; ++f) V[int64_t(f_first + f) * n + s] = my[f];
+}
+
 // ---- kernel 1: gathers from the global field grid ---------------------------
 template <typename T, int D, int W, int NCH>
 __global__ void __launch_bounds__(kI2Warps * 32)
@@ -247,7 +256,7 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
               const T* __restrict__ xs, const T* __restrict__ str, const uint32_t* __restrict__ perm,
               const T* __restrict__ fld, int rec, int F2, int pass_f, int n_rhs_real, int n_probes,
               int cplx, int n_rhs_out, T* __restrict__ mhat_at_x, int nacc, int nbw,
-              double* __restrict__ part) {
+              double* __restrict__ part, T* __restrict__ vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = int(blockDim.x >> 5);
@@ -285,8 +294,11 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
     T af[kMaxP] = {T(0), T(0), T(0), T(0)};
     int q_done = 0, f_first = 0;
     for (int pass = 0; f_first < F2; ++pass) {
-      const int q_in = pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt) : min(c.nq - q_done, pass_f / c.nt);
-      const int f_last = (pass == 0 ? c.ns : f_first) + q_in * c.nt;
+      const int q_in = vout ? 0
+                            : (pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt)
+                                         : min(c.nq - q_done, pass_f / c.nt));
+      const int f_last =
+          vout ? min(F2, f_first + pass_f) : (pass == 0 ? c.ns : f_first) + q_in * c.nt;
       const int fcount = f_last - f_first;
       T xn0 = xs[s0], xn1 = D > 1 ? xs[n + s0] : T(0), xn2 = D > 2 ? xs[2 * n + s0] : T(0);
       for (int j = 0; j < cnt; ++j) {
@@ -305,8 +317,11 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
           if (lane + ch * 32 < fcount) buf[j * bstride + lane + ch * 32] = acc[ch];
         __syncwarp();
       }
-      finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n, str,
-                     perm, mhat_at_x, tsc, af, red);
+      if (vout)
+        store_fields<T>(vout, buf + lane * bstride, f_first, fcount, valid, s, n);
+      else
+        finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n,
+                       str, perm, mhat_at_x, tsc, af, red);
       __syncwarp();
       q_done += q_in;
       f_first = f_last;
@@ -336,7 +351,8 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
                   T* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part,
                   const uint32_t* __restrict__ sub_bin, const uint32_t* __restrict__ sub_first,
                   const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ sub_total,
-                  int wm0, int wm1, int lo_slack, int bstride_in, int* __restrict__ errw) {
+                  int wm0, int wm1, int lo_slack, int bstride_in, int* __restrict__ errw,
+                  T* __restrict__ vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -413,9 +429,11 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
       T af[kMaxP] = {T(0), T(0), T(0), T(0)};
       int q_done = 0, f_first = 0;
       for (int pass = 0; f_first < F2; ++pass) {
-        const int q_in =
-            pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt) : min(c.nq - q_done, pass_f / c.nt);
-        const int f_last = (pass == 0 ? c.ns : f_first) + q_in * c.nt;
+        const int q_in = vout ? 0
+                              : (pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt)
+                                           : min(c.nq - q_done, pass_f / c.nt));
+        const int f_last =
+            vout ? min(F2, f_first + pass_f) : (pass == 0 ? c.ns : f_first) + q_in * c.nt;
         const int fcount = f_last - f_first;
         bool paired = false;
         if constexpr (sizeof(T) == 4) {
@@ -491,8 +509,11 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
             if (lane + ch * 32 < fcount) buf[j * bstride + lane + ch * 32] = acc[ch];
           __syncwarp();
         }
-        finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n, str,
-                       perm, mhat_at_x, tsc, af, red);
+        if (vout)
+          store_fields<T>(vout, buf + lane * bstride, f_first, fcount, valid, s, n);
+        else
+          finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n,
+                         str, perm, mhat_at_x, tsc, af, red);
         __syncwarp();
         q_done += q_in;
         f_first = f_last;
@@ -583,7 +604,7 @@ inline int record_stride(int F2) {
 
 template <typename T, int D, int W, int NCH>
 cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
-                            cudaStream_t st, int nacc, int F2) {
+                            cudaStream_t st, int nacc, int F2, T* vout) {
   constexpr int pass_f = 32 * NCH;
   const int rec = record_stride<T>(F2);
   const unsigned blocks = unsigned(P->nblk_interp);
@@ -613,7 +634,7 @@ cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
           n_probes, P->o.y_complex, P->nrhs, static_cast<T*>(mhat_at_x), nacc, P->nbw,
           wsp<double>(P, P->r_part), wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
           wsp<uint32_t>(P, P->r_binstart), wsp<uint32_t>(P, P->r_substart) + P->nbins_total, wm0,
-          wm1, slack, bstride, wsp<int>(P, P->r_err));
+          wm1, slack, bstride, wsp<int>(P, P->r_err), vout);
       P->launches += 1;
       return cudaGetLastError();
     }
@@ -633,16 +654,17 @@ cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
       P->geo, P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, wsp<T>(P, P->r_xs),
       wsp<T>(P, P->r_str), perm_ptr(P), wsp<T>(P, P->r_t2field), rec, F2, pass_f, n_rhs_real,
       n_probes, P->o.y_complex, P->nrhs, static_cast<T*>(mhat_at_x), nacc, P->nbw,
-      wsp<double>(P, P->r_part));
+      wsp<double>(P, P->r_part), vout);
   P->launches += 1;
   return cudaGetLastError();
 }
 
 template <typename T, int D, int NCH>
 cudaError_t launch_interp_d(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
-                            cudaStream_t st, int nacc, int F2) {
+                            cudaStream_t st, int nacc, int F2, T* vout = nullptr) {
   const int w = P->geo.w;
-#define FK_W(WW) return launch_interp_w<T, D, WW, NCH>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2)
+#define FK_W(WW) \
+  return launch_interp_w<T, D, WW, NCH>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, vout)
   if (w == 7) FK_W(7);
   if constexpr (sizeof(T) == 8 && D < 3) {
     if (w == 10) FK_W(10);
@@ -672,7 +694,28 @@ cudaError_t launch_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, v
   return launch_interp_d<T, 3, 1>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2);
 }
 
+// Gather-only: F fields of bandwidth b's type-2 grid at every sorted sample
+// into V[f][n], through the same kernels (and window staging) as above.
+template <typename T>
+cudaError_t launch_gather(fkreg_plan_s* P, int b, int F, T* V, cudaStream_t st) {
+  if (P->n == 0) return cudaSuccess;
+  if (P->d * P->geo.w > 64 || P->geo.w > kMaxWRun) return cudaErrorInvalidValue;
+  if (sizeof(T) == 4 && F > 32) {
+    if (P->d == 1) return launch_interp_d<T, 1, 2>(P, b, 0, 0, nullptr, st, 0, F, V);
+    if (P->d == 2) return launch_interp_d<T, 2, 2>(P, b, 0, 0, nullptr, st, 0, F, V);
+    return launch_interp_d<T, 3, 2>(P, b, 0, 0, nullptr, st, 0, F, V);
+  }
+  if (P->d == 1) return launch_interp_d<T, 1, 1>(P, b, 0, 0, nullptr, st, 0, F, V);
+  if (P->d == 2) return launch_interp_d<T, 2, 1>(P, b, 0, 0, nullptr, st, 0, F, V);
+  return launch_interp_d<T, 3, 1>(P, b, 0, 0, nullptr, st, 0, F, V);
+}
+
 }  // namespace
+
+cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream_t st) {
+  return P->prec == FKREG_F32 ? launch_gather<float>(P, b, F, static_cast<float*>(V), st)
+                              : launch_gather<double>(P, b, F, static_cast<double*>(V), st);
+}
 
 cudaError_t run_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, const void*,
                        void* mhat_at_x, cudaStream_t st) {
