@@ -147,4 +147,67 @@ __device__ __forceinline__ bool lpr_weights_fast(const MonoTab& mono, int p, con
   return lpr_weights(mono, p, s, sigma, a);
 }
 
+// ---- compensated FP32 arithmetic for the at-sample solves ------------------
+// two_sum: s + e == a + b exactly (Knuth's branch-free sum).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// a b - c d by Kahan's algorithm: the rounding error of c d is recovered
+// exactly with an FMA, so the result is within two units of rounding of the
+// exact value even under cancellation (Jeannerod, Louvet, Muller 2013).
+__device__ __forceinline__ float dop(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = fmaf(-c, d, w);
+  const float f = fmaf(a, b, -w);
+  return __fadd_rn(f, e);
+}
+
+// a = S~^-1 e_1 for p <= 3 from FP32 s-fields, S~_jk = D_j D_k s_(j+k) with
+// D = (1, dsc[1], dsc[2]) the scaling the t-fields get.  Cofactors come from
+// dop and the determinant from a compensated dot product (Ogita, Rump, Oishi
+// 2005), so the solve adds rounding errors of a few units of FP32 whatever
+// the cancellation in the cofactor expansion; the FP32 field values carry
+// the NUFFT tolerance, which dominates.
+__device__ __forceinline__ bool lpr_weights_f32(int p, const float* s, const float* dsc,
+                                                float a[kMaxP]) {
+  if (p == 1) {
+    a[0] = 1.0f / s[0];
+    return s[0] > 0.f;
+  }
+  if (p == 2) {  // 1-D local linear
+    const float h0 = dsc[1];
+    const float s01 = s[1] * h0, s11 = s[2] * (h0 * h0);
+    const float det = dop(s[0], s11, s01, s01);
+    if (!(det > 0.f)) return false;
+    const float inv = 1.0f / det;
+    a[0] = s11 * inv;
+    a[1] = -s01 * inv;
+    return isfinite(a[0]);
+  }
+  // 2-D local linear, s-fields 1, z1, z2, z1z1, z1z2, z2z2
+  const float h0 = dsc[1], h1 = dsc[2];
+  const float s00 = s[0], s01 = s[1] * h0, s02 = s[2] * h1;
+  const float s11 = s[3] * (h0 * h0), s12 = s[4] * (h0 * h1), s22 = s[5] * (h1 * h1);
+  const float c0 = dop(s11, s22, s12, s12);
+  const float c1 = dop(s12, s02, s01, s22);
+  const float c2 = dop(s01, s12, s11, s02);
+  const float p0 = __fmul_rn(s00, c0), r0 = fmaf(s00, c0, -p0);
+  const float m1 = __fmul_rn(s01, c1), r1 = fmaf(s01, c1, -m1);
+  const float m2 = __fmul_rn(s02, c2), r2 = fmaf(s02, c2, -m2);
+  float q1, q2;
+  const float p1 = two_sum(p0, m1, q1);
+  const float p2 = two_sum(p1, m2, q2);
+  const float det = __fadd_rn(p2, __fadd_rn(__fadd_rn(r0, r1), __fadd_rn(__fadd_rn(q1, r2), q2)));
+  if (!(det > 0.f)) return false;
+  const float inv = 1.0f / det;
+  a[0] = c0 * inv;
+  a[1] = c1 * inv;
+  a[2] = c2 * inv;
+  return isfinite(a[0]);
+}
+
 }  // namespace fk

@@ -180,8 +180,37 @@ struct GroupCtx {
   int ns, nt, p, nq, n_rhs_real, n_probes, cplx, n_rhs_out, nacc, order, b;
 };
 
+// Per-warp accumulators of the reductions (written by lane 0).  FP64 runs
+// accumulate in double; FP32 runs keep an unevaluated sum hi + lo of two
+// floats in the same 8 bytes (two_sum), which keeps the FP64 pipe (a small
+// fraction of the FP32 rate on this part) out of the per-sample path.
+template <typename T>
+__device__ __forceinline__ void red_add(double* red, int a, T v) {
+  if constexpr (sizeof(T) == 4) {
+    float2* r2 = reinterpret_cast<float2*>(red) + a;
+    float2 x = *r2;
+    float e;
+    x.x = two_sum(x.x, v, e);
+    x.y += e;
+    *r2 = x;
+  } else {
+    red[a] += v;
+  }
+}
+template <typename T>
+__device__ __forceinline__ double red_get(const double* red, int a) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 x = reinterpret_cast<const float2*>(red)[a];
+    return double(x.x) + double(x.y);
+  } else {
+    return red[a];
+  }
+}
+
 // Phase B of one pass: lane = sample (valid when lane < cnt).  Solves on pass 0,
-// then forms mhat for this pass's responses / probes and accumulates.
+// then forms mhat for this pass's responses / probes and accumulates.  FP32
+// runs solve p <= 3 with the compensated FP32 closed forms, everything else
+// goes through FP64.
 template <typename T>
 __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mono, const BwDev& B,
                                             const T* my, int pass, int q_done, int q_in, int lane,
@@ -189,26 +218,43 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
                                             const T* __restrict__ str,
                                             const uint32_t* __restrict__ perm,
                                             T* __restrict__ mhat_at_x, const T* tsc, T af[kMaxP],
-                                            double* red) {
+                                            double* red, T k0, const double* isg) {
   if (pass == 0) {
-    double a[kMaxP] = {0, 0, 0, 0};
     bool ok = false;
-    if (valid) {
-      double sv[kMaxMono];
+    T a0 = T(0);
+    if (sizeof(T) == 4 && c.p <= 3) {
+      float a[kMaxP] = {0.f, 0.f, 0.f, 0.f};
+      float dsc[3];
 #pragma unroll
-      for (int k = 0; k < kMaxMono; ++k) sv[k] = k < c.ns ? double(my[k]) : 0.0;
-      if (c.order == 0) {
-        ok = sv[0] > 0.0;
-        a[0] = ok ? 1.0 / sv[0] : 0.0;
-      } else {
-        const double isg[3] = {1.0 / B.sigma[0], 1.0 / B.sigma[1], 1.0 / B.sigma[2]};
-        ok = lpr_weights_fast(mono, c.p, sv, B.sigma, isg, a);
+      for (int k = 0; k < 3; ++k) dsc[k] = float(tsc[k]);
+      if (valid) {
+        float sv[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sv[k] = k < c.ns ? float(my[k]) : 0.f;
+        ok = lpr_weights_f32(c.p, sv, dsc, a);
       }
-    }
 #pragma unroll
-    for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
-    const double tv = warp_sum_t<double>((valid && ok) ? B.k0 * a[0] : 0.0);
-    if (lane == 0) red[c.nacc - 1] += tv;
+      for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
+      a0 = ok ? T(a[0]) : T(0);
+    } else {
+      double a[kMaxP] = {0, 0, 0, 0};
+      if (valid) {
+        double sv[kMaxMono];
+#pragma unroll
+        for (int k = 0; k < kMaxMono; ++k) sv[k] = k < c.ns ? double(my[k]) : 0.0;
+        if (c.order == 0) {
+          ok = sv[0] > 0.0;
+          a[0] = ok ? 1.0 / sv[0] : 0.0;
+        } else {
+          ok = lpr_weights_fast(mono, c.p, sv, B.sigma, isg, a);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
+      a0 = ok ? T(a[0]) : T(0);
+    }
+    const T tv = warp_sum_t<T>(valid ? k0 * a0 : T(0));
+    if (lane == 0) red_add<T>(red, c.nacc - 1, tv);
   }
   const int fq0 = pass == 0 ? c.ns : 0;
   const uint32_t orig = valid ? perm[s] : 0u;
@@ -222,7 +268,7 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
     if (q < c.n_rhs_real) {
       const T r = valid ? cv - mh : T(0);
       const T v = warp_sum_t<T>(r * r);
-      if (lane == 0) red[q] += double(v);
+      if (lane == 0) red_add<T>(red, q, v);
       if (valid && mhat_at_x) {
         const int mult = c.cplx ? 2 : 1;
         const int rr = q / mult, pt = q % mult;
@@ -233,8 +279,8 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
       const T v1 = warp_sum_t<T>(valid ? cv * mh : T(0));
       const T v2 = warp_sum_t<T>(valid ? cv * cv : T(0));
       if (lane == 0) {
-        red[c.n_rhs_real + pp] += double(v1);
-        red[c.n_rhs_real + c.n_probes + pp] += double(v2);
+        red_add<T>(red, c.n_rhs_real + pp, v1);
+        red_add<T>(red, c.n_rhs_real + c.n_probes + pp, v2);
       }
     }
   }
@@ -281,6 +327,8 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   T tsc[kMaxP];
 #pragma unroll
   for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
+  const T k0t = T(B.k0);
+  const double isg[3] = {1.0 / B.sigma[0], 1.0 / B.sigma[1], 1.0 / B.sigma[2]};
   // each block walks one contiguous run of sample groups (neighbouring bins)
   const int64_t ngroups = (n + 31) / 32;
   const int64_t per_block = (ngroups + gridDim.x - 1) / gridDim.x;
@@ -321,7 +369,7 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
         store_fields<T>(vout, buf + lane * bstride, f_first, fcount, valid, s, n);
       else
         finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n,
-                       str, perm, mhat_at_x, tsc, af, red);
+                       str, perm, mhat_at_x, tsc, af, red, k0t, isg);
       __syncwarp();
       q_done += q_in;
       f_first = f_last;
@@ -330,7 +378,7 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   __syncthreads();
   for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
     double t = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) t += red_all[wv * nacc + a];
+    for (int wv = 0; wv < nwarps; ++wv) t += red_get<T>(red_all, wv * nacc + a);
     part[(int64_t(blockIdx.x) * nbw + b) * nacc + a] = t;
   }
 }
@@ -381,6 +429,8 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
   T tsc[kMaxP];
 #pragma unroll
   for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
+  const T k0t = T(B.k0);
+  const double isg[3] = {1.0 / B.sigma[0], 1.0 / B.sigma[1], 1.0 / B.sigma[2]};
   uint32_t parity = 0;
   const uint32_t nsub = *sub_total;
   bool failed = false;
@@ -513,7 +563,7 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
           store_fields<T>(vout, buf + lane * bstride, f_first, fcount, valid, s, n);
         else
           finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n,
-                         str, perm, mhat_at_x, tsc, af, red);
+                         str, perm, mhat_at_x, tsc, af, red, k0t, isg);
         __syncwarp();
         q_done += q_in;
         f_first = f_last;
@@ -525,7 +575,7 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
   __syncthreads();
   for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
     double t = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) t += red_all[wv * nacc + a];
+    for (int wv = 0; wv < nwarps; ++wv) t += red_get<T>(red_all, wv * nacc + a);
     part[(int64_t(blockIdx.x) * nbw + b) * nacc + a] = t;
   }
 }
