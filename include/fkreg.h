@@ -198,11 +198,19 @@ fkreg_status fkreg_set_workspace(fkreg_plan plan, void* ws_dev, size_t bytes, vo
 
 /*
  * Bin and sort the samples x_dev [n][d] (plan precision), n <= max_n.
- * Each sample gets the bin of its fine-grid cell (floor of
- * fl(fl(x_j - lo_j) * inv_h_j), computed with round-to-nearest IEEE
- * operations and no fused multiply-add) and the samples are reordered by a
- * stable counting sort: the permutation is unique and bit-exact.  All later
- * calls share this geometry until the next fkreg_set_points.
+ * With u_j = fl(fl(x_j - lo_j) * inv_h_j) (round-to-nearest IEEE operations,
+ * no fused multiply-add) each sample gets
+ *   the bin of its fine-grid cell c_j = min(floor(u_j), nf_j - 1):
+ *     b_j = c_j / tile_j, bin = row-major index of b over nbins;
+ *   the centre cell of its spreading window, relative to the bin,
+ *     e_j = clamp(ceil(fl(u_j - w/2)) + floor(w/2) - b_j tile_j, 0, tile_j),
+ *     local = row-major index of e over (tile_j + 1) values per axis;
+ * and the key (bin << kbits) | local, kbits = bits of prod_j (tile_j + 1)
+ * (kbits = 0, i.e. bin-only keys, if the key would exceed 32 bits).  A stable
+ * counting sort orders the samples by key, then by original index: the
+ * permutation is unique and bit-exact, bins are contiguous, and samples that
+ * share a window are adjacent.  All later calls share this geometry until
+ * the next fkreg_set_points.
  */
 fkreg_status fkreg_set_points(fkreg_plan plan, int64_t n, const void* x_dev, void* stream);
 
@@ -306,8 +314,8 @@ fkreg_status fkreg_stage_times(fkreg_plan plan, double* ms, int64_t* launches,
  * fkreg_set_points + fkreg_get_sort, but keeps its scratch in a device array
  * that the library owns (about 4.3 MB, held on every GPU that loads the
  * library until the process exits) instead of a workspace.
- *   geom           geometry from fkreg_geometry_query (dim, nf, tile, nbins,
- *                  inv_h are used)
+ *   geom           geometry from fkreg_geometry_query (dim, nf, w, tile,
+ *                  nbins, inv_h are used; 2 <= w <= 32)
  *   grid_lo/hi     host [dim], the grid box of the plan options
  *   precision      FKREG_F32 or FKREG_F64: the type of x_dev
  *   n              samples, 0 <= n <= 262144 (2^18); at most 65536 bins

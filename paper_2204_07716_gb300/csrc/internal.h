@@ -38,7 +38,24 @@ struct GeoDev {
   float inv_h_f[3];
   int64_t tile[3];
   int64_t nbins[3];
+  int kbits;        // within-bin bits of the sort key (see key_local_bits)
 };
+
+// Sort keys are (bin << kbits) | local, local = row-major index of the centre
+// cell of the sample's spreading window relative to its bin's first cell,
+// tile_j + 1 values per axis.  kbits = 0 (bin-only keys) if the key would not
+// fit 32 bits.
+inline int key_local_bits(int d, const int64_t* tile, const int64_t* nbins) {
+  int64_t cells = 1, bins = 1;
+  for (int j = 0; j < d; ++j) {
+    cells *= tile[j] + 1;
+    bins *= nbins[j];
+  }
+  int lb = 0, bb = 0;
+  while ((int64_t(1) << lb) < cells) ++lb;
+  while ((int64_t(1) << bb) < bins) ++bb;
+  return bb + lb <= 32 ? lb : 0;
+}
 
 // One bandwidth, stored in the workspace (device reads it).
 struct BwDev {

@@ -383,6 +383,31 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   }
 }
 
+// Issue the bulk copies of one bin window (thread 0): rows of the window
+// [wm0][wm1][rec] (1-D: one row of wm0 cells) from the periodic field grid,
+// a row that wraps split in two, all completing on one mbarrier.
+template <typename T, int D>
+__device__ __forceinline__ void issue_window_copies(const T* __restrict__ fld, int rec, int nf0,
+                                                    int nf1, int o0, int o1, int wm0, int wm1,
+                                                    T* win, uint64_t* mbar) {
+  fence_proxy_async();  // earlier reads of the window come before the new copies
+  mbar_expect_tx(mbar, uint32_t(size_t(wm0) * wm1 * rec * sizeof(T)));
+  for (int r = 0; r < (D > 1 ? wm0 : 1); ++r) {
+    // axis of the contiguous segment: axis 1 in 2-D, axis 0 in 1-D
+    const int oseg = D > 1 ? o1 : o0;
+    const int nseg = D > 1 ? nf1 : nf0;
+    const int eseg = D > 1 ? wm1 : wm0;
+    const int64_t rowbase = D > 1 ? wrap_idx(o0 + r, nf0) * int64_t(nf1) : 0;
+    const int start = int(wrap_idx(oseg, nseg));
+    const int len = min(eseg, nseg - start);
+    T* dst = win + size_t(r) * eseg * rec;
+    bulk_g2s(dst, fld + (rowbase + start) * rec, uint32_t(size_t(len) * rec * sizeof(T)), mbar);
+    if (len < eseg)
+      bulk_g2s(dst + size_t(len) * rec, fld + rowbase * rec,
+               uint32_t(size_t(eseg - len) * rec * sizeof(T)), mbar);
+  }
+}
+
 // ---- kernel 2: bin windows staged in shared memory by bulk copies ----------
 // One block takes spreading sub-problems (samples of one bin) in turn.  The
 // bin's window of the field grid, [wm0][wm1][rec] cells x fields, is copied
@@ -442,24 +467,8 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
     const int64_t bj1 = D > 1 ? int64_t(bin) % g.nbins[1] : 0;
     const int o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - lo_slack;
     const int o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - lo_slack : 0;
-    if (threadIdx.x == 0) {
-      fence_proxy_async();  // earlier reads of the window come before the new copies
-      mbar_expect_tx(&mbar, uint32_t(size_t(wm0) * wm1 * rec * sizeof(T)));
-      for (int r = 0; r < (D > 1 ? wm0 : 1); ++r) {
-        // axis of the contiguous segment: axis 1 in 2-D, axis 0 in 1-D
-        const int oseg = D > 1 ? o1 : o0;
-        const int nseg = D > 1 ? nf1 : nf0;
-        const int eseg = D > 1 ? wm1 : wm0;
-        const int64_t rowbase = D > 1 ? wrap_idx(o0 + r, nf0) * int64_t(nf1) : 0;
-        const int start = int(wrap_idx(oseg, nseg));
-        const int len = min(eseg, nseg - start);
-        T* dst = win + size_t(r) * eseg * rec;
-        bulk_g2s(dst, fld + (rowbase + start) * rec, uint32_t(size_t(len) * rec * sizeof(T)), &mbar);
-        if (len < eseg)
-          bulk_g2s(dst + size_t(len) * rec, fld + rowbase * rec,
-                   uint32_t(size_t(eseg - len) * rec * sizeof(T)), &mbar);
-      }
-    }
+    if (threadIdx.x == 0)
+      issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, win, &mbar);
     bool ok = false;
     for (uint32_t it = 0; it < kMaxSpin && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
     if (__syncthreads_or(!ok)) {
@@ -580,6 +589,235 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
   }
 }
 
+// ---- kernel 3: one lane per sample over a staged window (FP32, fixed W) ----
+// Same sub-problem loop and window staging as kernel 2, but each lane takes
+// one sample of the group and walks the window cells and the float4 quads
+// of the fields itself: every shared load is 16 bytes, every lane does useful
+// multiply-adds, and because sorted samples that share a window are adjacent
+// most loads of a warp are broadcasts of a few addresses.  The lane's field
+// values go to its own row of the staging buffer (or straight to V in the
+// gather-only mode) and phase B follows as in the other kernels.
+template <int D, int W, int NQ>
+__device__ __forceinline__ void lane_gather_smem(const float* base, int rec, int e1, int nq,
+                                                 int skind, float beta, float off0,
+                                                 const float (&pl)[W], float4 (&acc)[NQ]) {
+  if (D == 1) {
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const float wgt = pl[t];
+      const float* cell = base + t * rec;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (q < nq) {
+          const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
+          acc[q].x += wgt * v.x;
+          acc[q].y += wgt * v.y;
+          acc[q].z += wgt * v.z;
+          acc[q].w += wgt * v.w;
+        }
+    }
+  } else {
+#pragma unroll 1
+    for (int t0 = 0; t0 < W; ++t0) {
+      const float w0 = phi<float>(skind, W, beta, off0 + float(t0));
+      const float* row = base + t0 * e1 * rec;
+#pragma unroll
+      for (int t1 = 0; t1 < W; ++t1) {
+        const float wgt = w0 * pl[t1];
+        const float* cell = row + t1 * rec;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          if (q < nq) {
+            const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
+            acc[q].x += wgt * v.x;
+            acc[q].y += wgt * v.y;
+            acc[q].z += wgt * v.z;
+            acc[q].w += wgt * v.w;
+          }
+      }
+    }
+  }
+}
+
+// The same from the global field grid (periodic wrap), for the rare sample
+// whose window leaves the staged one.
+template <int D, int W, int NQ>
+__device__ __forceinline__ void lane_gather_global(const float* __restrict__ fld, int rec, int qa,
+                                                int nq, int i0, int i1, int nf0, int nf1,
+                                                int skind, float beta, float off0,
+                                                const float (&pl)[W], float4 (&acc)[NQ]) {
+#pragma unroll 1
+  for (int t0 = 0; t0 < (D == 1 ? 1 : W); ++t0) {
+    const float w0 = D == 1 ? 1.f : phi<float>(skind, W, beta, off0 + float(t0));
+    const int64_t r = D == 1 ? 0 : wrap_idx(i0 + t0, nf0) * int64_t(nf1);
+#pragma unroll
+    for (int t1 = 0; t1 < W; ++t1) {
+      const int64_t c = D == 1 ? wrap_idx(i0 + t1, nf0) : r + wrap_idx(i1 + t1, nf1);
+      const float wgt = w0 * pl[t1];
+      const float* cell = fld + c * rec + 4 * qa;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (q < nq) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(cell + 4 * q));
+          acc[q].x += wgt * v.x;
+          acc[q].y += wgt * v.y;
+          acc[q].z += wgt * v.z;
+          acc[q].w += wgt * v.w;
+        }
+    }
+  }
+}
+
+__device__ __forceinline__ float quad_comp(const float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+template <int D, int W, int NQ>
+__global__ void __launch_bounds__(kTWarps * 32)
+interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int order,
+                   int64_t n, const float* __restrict__ xs, const float* __restrict__ str,
+                   const uint32_t* __restrict__ perm, const float* __restrict__ fld, int rec,
+                   int F2, int pass_f, int n_rhs_real, int n_probes, int cplx, int n_rhs_out,
+                   float* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part,
+                   const uint32_t* __restrict__ sub_bin, const uint32_t* __restrict__ sub_first,
+                   const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ sub_total,
+                   int wm0, int wm1, int lo_slack, int bstride, int* __restrict__ errw,
+                   float* __restrict__ vout) {
+  using T = float;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = int(blockDim.x >> 5);
+  const size_t win_bytes = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
+  T* win = reinterpret_cast<T*>(smem_raw);
+  double* red_all = reinterpret_cast<double*>(smem_raw + win_bytes);
+  double* red = red_all + warp * nacc;
+  T* my = reinterpret_cast<T*>(red_all + nwarps * nacc) + (warp * 32 + lane) * bstride;
+  for (int a = lane; a < nacc; a += 32) red[a] = 0.0;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const BwDev& B = bwt[b];
+  const int nf0 = int(B.nf[0]), nf1 = D > 1 ? int(B.nf[1]) : 1;
+  const T ih0 = T(B.inv_h[0]), ih1 = T(D > 1 ? B.inv_h[1] : 1.0);
+  const double r0 = double(B.nf[0]) / double(g.nf[0]);
+  const double r1 = D > 1 ? double(B.nf[1]) / double(g.nf[1]) : 1.0;
+  const T beta = T(g.beta);
+  const T halfw = T(0.5) * T(W);
+  const int skind = g.skind;
+  const int e1 = D > 1 ? wm1 : 1;
+  GroupCtx c{mono.n, mono.nt, mono.nt, n_rhs_real + n_probes, n_rhs_real, n_probes, cplx,
+             n_rhs_out, nacc, order, b};
+  T tsc[kMaxP];
+#pragma unroll
+  for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
+  const T k0t = T(B.k0);
+  const double isg[3] = {1.0 / B.sigma[0], 1.0 / B.sigma[1], 1.0 / B.sigma[2]};
+  uint32_t parity = 0;
+  const uint32_t nsub = *sub_total;
+  bool failed = false;
+  for (uint32_t k = blockIdx.x; k < nsub; k += gridDim.x) {
+    const uint32_t bin = sub_bin[k];
+    const uint32_t first = sub_first[k];
+    const uint32_t last = min(first + uint32_t(kSubMax), bin_start[bin + 1]);
+    const int64_t bj0 = D > 1 ? int64_t(bin) / g.nbins[1] : int64_t(bin);
+    const int64_t bj1 = D > 1 ? int64_t(bin) % g.nbins[1] : 0;
+    const int o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - lo_slack;
+    const int o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - lo_slack : 0;
+    if (threadIdx.x == 0)
+      issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, win, &mbar);
+    bool ok = false;
+    for (uint32_t it = 0; it < kMaxSpin && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(errw, 2);
+      bool late = false;
+      for (uint32_t it = 0; it < kMaxSpin && !late; ++it) late = mbar_try_wait(&mbar, parity);
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    const int ngr = int((last - first + 31) / 32);
+    for (int gi = warp; gi < ngr; gi += nwarps) {
+      const int64_t s0 = int64_t(first) + int64_t(gi) * 32;
+      const int cnt = int(min(int64_t(32), int64_t(last) - s0));
+      const int64_t s = s0 + lane;
+      const bool valid = lane < cnt;
+      const int64_t sl = valid ? s : s0;
+      // window of this lane's sample (same rounding as the bin rule)
+      const T u0 = __fmul_rn(xs[sl], ih0);
+      const T fo0 = ceilf(__fsub_rn(u0, halfw));
+      const int i0 = int(fo0);
+      const T off0 = fo0 - u0;
+      int i1 = 0;
+      T off1 = T(0);
+      if (D > 1) {
+        const T u1 = __fmul_rn(xs[n + sl], ih1);
+        const T fo1 = ceilf(__fsub_rn(u1, halfw));
+        i1 = int(fo1);
+        off1 = fo1 - u1;
+      }
+      const int l0 = i0 - o0, l1 = D > 1 ? i1 - o1 : 0;
+      const bool inside = l0 >= 0 && l0 + W <= wm0 && (D == 1 || (l1 >= 0 && l1 + W <= wm1));
+      T pl[W];  // kernel values along the last axis
+#pragma unroll
+      for (int t = 0; t < W; ++t) pl[t] = phi<T>(skind, W, beta, (D > 1 ? off1 : off0) + T(t));
+      T af[kMaxP] = {T(0), T(0), T(0), T(0)};
+      int q_done = 0, f_first = 0;
+      for (int pass = 0; f_first < F2; ++pass) {
+        const int q_in = vout ? 0
+                              : (pass == 0 ? min(c.nq, (pass_f - c.ns) / c.nt)
+                                           : min(c.nq - q_done, pass_f / c.nt));
+        const int f_last =
+            vout ? min(F2, f_first + pass_f) : (pass == 0 ? c.ns : f_first) + q_in * c.nt;
+        const int qa = f_first >> 2, nq = ((f_last + 3) >> 2) - qa;
+        float4 acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (inside)
+          lane_gather_smem<D, W, NQ>(win + (size_t(l0) * e1 + l1) * rec + 4 * qa, rec, e1, nq,
+                                     skind, beta, off0, pl, acc);
+        if (__any_sync(0xffffffffu, valid && !inside)) {
+          if (valid && !inside)
+            lane_gather_global<D, W, NQ>(fld, rec, qa, nq, i0, i1, nf0, nf1, skind, beta, off0, pl,
+                                         acc);
+        }
+        if (vout) {
+          if (valid)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc) {
+                const int f = 4 * (qa + q) + cc;
+                if (q < nq && f >= f_first && f < f_last) vout[int64_t(f) * n + s] = quad_comp(acc[q], cc);
+              }
+        } else {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              const int f = 4 * (qa + q) + cc;
+              if (q < nq && f >= f_first && f < f_last) my[f - f_first] = quad_comp(acc[q], cc);
+            }
+          finish_pass<T>(c, mono, B, my, pass, q_done, q_in, lane, valid, s, n, str, perm,
+                         mhat_at_x, tsc, af, red, k0t, isg);
+        }
+        q_done += q_in;
+        f_first = f_last;
+      }
+    }
+    __syncthreads();  // every read of this window is done before the next copies
+  }
+  if (failed) return;
+  __syncthreads();
+  for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
+    double t = 0.0;
+    for (int wv = 0; wv < nwarps; ++wv) t += red_get<T>(red_all, wv * nacc + a);
+    part[(int64_t(blockIdx.x) * nbw + b) * nacc + a] = t;
+  }
+}
+
 // sum block partials in a fixed order: sums[b][a]; one block per output
 __global__ void reduce_partials(const double* __restrict__ part, int64_t nblk, int nbw, int nacc,
                                 double* __restrict__ sums) {
@@ -652,12 +890,62 @@ inline int record_stride(int F2) {
   return (F2 + 3) / 4 * 4;
 }
 
+template <int D, int NQ>
+cudaError_t launch_lane(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
+                        cudaStream_t st, int nacc, int F2, float* vout, int rec, int pass_f,
+                        int bstride, int wm0, int wm1, int slack, int nw, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(interp_lane_kernel<D, 7, NQ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  interp_lane_kernel<D, 7, NQ><<<unsigned(P->nblk_interp), nw * 32, smem, st>>>(
+      P->geo, P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, wsp<float>(P, P->r_xs),
+      wsp<float>(P, P->r_str), perm_ptr(P), wsp<float>(P, P->r_t2field), rec, F2, pass_f,
+      n_rhs_real, n_probes, P->o.y_complex, P->nrhs, static_cast<float*>(mhat_at_x), nacc, P->nbw,
+      wsp<double>(P, P->r_part), wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
+      wsp<uint32_t>(P, P->r_binstart), wsp<uint32_t>(P, P->r_substart) + P->nbins_total, wm0, wm1,
+      slack, bstride, wsp<int>(P, P->r_err), vout);
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
 template <typename T, int D, int W, int NCH>
 cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
                             cudaStream_t st, int nacc, int F2, T* vout) {
   constexpr int pass_f = 32 * NCH;
   const int rec = record_stride<T>(F2);
   const unsigned blocks = unsigned(P->nblk_interp);
+  if constexpr (sizeof(T) == 4 && W == 7 && D <= 2) {
+    // lane-per-sample kernel: every field in one pass up to 64 fields, else
+    // passes of 60 (any 60 consecutive fields span at most 16 quads)
+    const BwDev& B = P->bw[b];
+    const int wm0 = tma_window(P->geo, B, 0);
+    const int wm1 = D > 1 ? tma_window(P->geo, B, 1) : 1;
+    const size_t win = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
+    const int slack = std::max(tma_slack(P->geo, B, 0), D > 1 ? tma_slack(P->geo, B, 1) : 0);
+    const int pf = F2 <= 64 ? F2 : 60;
+    const int bstride = pf | 1;
+    const size_t per_warp = sizeof(T) * 32 * bstride + sizeof(double) * nacc;
+    const size_t budget = 220 * 1024;
+    const int nw = win < budget ? int(std::min<size_t>(kTWarps, (budget - win) / per_warp)) : 0;
+    const size_t smem = win + per_warp * size_t(nw);
+    const bool fits = wm0 <= B.nf[0] && (D == 1 || wm1 <= B.nf[1]) && nw >= 4;
+    if (fits) {
+      const int nqn = F2 <= 64 ? rec / 4 : 16;
+      float* vo = reinterpret_cast<float*>(vout);
+#define FK_L(Q) \
+  return launch_lane<D, Q>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, vo, rec, pf, bstride, wm0, wm1, slack, nw, smem)
+      if (nqn <= 1) FK_L(1);
+      if (nqn <= 2) FK_L(2);
+      if (nqn <= 3) FK_L(3);
+      if (nqn <= 4) FK_L(4);
+      if (nqn <= 6) FK_L(6);
+      if (nqn <= 8) FK_L(8);
+      if (nqn <= 10) FK_L(10);
+      if (nqn <= 12) FK_L(12);
+      FK_L(16);
+#undef FK_L
+    }
+  }
   const size_t buf_warp = sizeof(T) * 32 * (pass_f + 1) + sizeof(double) * nacc;
   if constexpr (D <= 2 && W > 0) {
     const BwDev& B = P->bw[b];

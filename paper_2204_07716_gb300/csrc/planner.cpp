@@ -374,6 +374,7 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
       geo->tile[j] = g->tile[j];
       geo->nbins[j] = g->nbins[j];
     }
+    geo->kbits = key_local_bits(d, geo->tile, geo->nbins);
   }
   return FKREG_OK;
 }

@@ -4,11 +4,17 @@
 //   u_j   = fl(fl(x_j - lo_j) * inv_h_j)      (round-to-nearest, no FMA)
 //   c_j   = min(floor(u_j), nf_j - 1)
 //   bin   = row-major index of (c_j / tile_j)
-// The samples are then ordered by bin with a least-significant-digit radix
-// sort (8-bit digits).  Each pass is a stable counting sort: per-tile digit
+// and, inside the bin, the centre cell of its spreading window
+//   o_j   = ceil(fl(u_j - w/2)),   e_j = o_j + floor(w/2)   (c_j or c_j + 1)
+//   local = row-major index of clamp(e_j - b_j tile_j, 0, tile_j) over
+//           (tile_j + 1) values per axis
+// The key (bin << kbits) | local orders the samples by bin and, inside a bin,
+// by the window they touch, so consecutive sorted samples share windows.
+// The samples are ordered by key with a least-significant-digit radix sort
+// (8-bit digits).  Each pass is a stable counting sort: per-tile digit
 // histograms, one exclusive scan over (digit, tile), and a scatter that ranks
 // equal digits inside a tile in index order with warp match masks.  The
-// resulting permutation is therefore unique: bin first, original index second.
+// resulting permutation is therefore unique: key first, original index second.
 // The paper bins the samples onto the grid too (Sec. 1.1, O(N) gridding); the
 // counting sort is this implementation's own device-side organisation of it.
 #include <cuda_runtime.h>
@@ -46,8 +52,9 @@ __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
   // counts == nullptr: the caller counts with bin_count_shared
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t key = 0;
+  uint32_t bin = 0, local = 0;
   bool bad = false;
+  const T halfw = T(0.5) * T(g.w);
   for (int j = 0; j < g.d; ++j) {
     T xv = x[i * g.d + j];
     const T lo = T(g.lo[j]), hi = T(g.hi[j]);
@@ -59,24 +66,28 @@ __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
     int64_t c = int64_t(floor(u));
     if (c < 0) c = 0;
     if (c > g.nf[j] - 1) c = g.nf[j] - 1;
-    key = key * uint32_t(g.nbins[j]) + uint32_t(c / g.tile[j]);
+    const int64_t b = c / g.tile[j];
+    int64_t e = int64_t(ceil(sub_rn(u, halfw))) + g.w / 2 - b * g.tile[j];
+    e = e < 0 ? 0 : (e > g.tile[j] ? g.tile[j] : e);
+    bin = bin * uint32_t(g.nbins[j]) + uint32_t(b);
+    local = local * uint32_t(g.tile[j] + 1) + uint32_t(e);
   }
   if (bad) atomicOr(errw, 1);
-  keys[i] = key;
+  keys[i] = g.kbits ? (bin << g.kbits) | local : bin;
   vals[i] = uint32_t(i);
-  if (counts) atomicAdd(&counts[key], 1u);
+  if (counts) atomicAdd(&counts[bin], 1u);
 }
 
 // Bin counts through a per-block shared-memory histogram (few bins: the
 // global counters would otherwise see heavy contention).
 __global__ void bin_count_shared(const uint32_t* __restrict__ keys, int64_t n, int64_t nbins,
-                                 uint32_t* __restrict__ counts) {
+                                 int kbits, uint32_t* __restrict__ counts) {
   extern __shared__ uint32_t h[];
   for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
   __syncthreads();
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += int64_t(gridDim.x) * blockDim.x)
-    atomicAdd(&h[keys[i]], 1u);
+    atomicAdd(&h[keys[i] >> kbits], 1u);
   __syncthreads();
   for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x)
     if (h[b]) atomicAdd(&counts[b], h[b]);
@@ -297,14 +308,14 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
     P->launches += 1;
     if (shared_hist) {
       const unsigned hb = unsigned(std::min<int64_t>((n + 4095) / 4096, 152 * 4));
-      bin_count_shared<<<hb, 512, sizeof(uint32_t) * nbins, s>>>(keys0, n, nbins, counts);
+      bin_count_shared<<<hb, 512, sizeof(uint32_t) * nbins, s>>>(keys0, n, nbins, g.kbits, counts);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       P->launches += 1;
     }
   }
-  // radix passes over the significant bits of the bin index
-  int bits = 0;
-  while ((int64_t(1) << bits) < nbins) ++bits;
+  // radix passes over the significant bits of the key
+  int bits = g.kbits;
+  while ((int64_t(1) << (bits - g.kbits)) < nbins) ++bits;
   const int passes = (bits + kRadixBits - 1) / kRadixBits;
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   uint32_t* hist = wsp<uint32_t>(P, P->r_hist);
@@ -394,6 +405,7 @@ extern "C" fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const 
   if (d < 1 || d > 3) return FKREG_ERR_INVALID_ARG;
   if (precision != FKREG_F32 && precision != FKREG_F64) return FKREG_ERR_INVALID_ARG;
   if (n < 0 || n > kStaticMaxN) return FKREG_ERR_INVALID_ARG;
+  if (geom->w < 2 || geom->w > 32) return FKREG_ERR_INVALID_ARG;
   if ((n > 0 && !x_dev) || !perm_dev || !bin_start_dev) return FKREG_ERR_INVALID_ARG;
   int64_t nbins = 1;
   for (int j = 0; j < d; ++j) {
@@ -429,6 +441,8 @@ extern "C" fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const 
     g.inv_h[j] = j < d ? geom->inv_h[j] : 1.0;
     g.inv_h_f[j] = float(g.inv_h[j]);
   }
+  g.w = geom->w;
+  g.kbits = key_local_bits(d, g.tile, g.nbins);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t* keys0 = base + kOffKeys0;
   uint32_t* vals0 = base + kOffVals0;
@@ -452,8 +466,8 @@ extern "C" fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const 
                                                      vals0, counts, errw);
     if (cudaGetLastError() != cudaSuccess) return FKREG_ERR_CUDA;
   }
-  int bits = 0;
-  while ((int64_t(1) << bits) < nbins) ++bits;
+  int bits = g.kbits;
+  while ((int64_t(1) << (bits - g.kbits)) < nbins) ++bits;
   const int passes = (bits + kRadixBits - 1) / kRadixBits;
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   uint32_t *kin = keys0, *vin = vals0, *kout = keys1, *vout = vals1;

@@ -22,6 +22,7 @@ namespace {
 constexpr int kSpreadThreads = 256;
 constexpr int kMaxChunk = 8;
 constexpr int kMaxWRun = 24;
+constexpr int kMaxChunk2 = 16;  // strengths per launch of the run kernel
 
 // Shared-memory accumulator of the tile.  FP32 plans accumulate in 32-bit
 // fixed point (native integer shared-memory atomics); the scale of each
@@ -204,6 +205,170 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
   }
 }
 
+// Run-aggregated spreading (1-D and 2-D, fixed width).  Same sub-problem,
+// tile and flush as spread_kernel, but warps take groups of 32 consecutive
+// sorted samples: each lane stages one sample of the group (window origin in
+// the tile, the 1-D kernel values, the scaled strengths) in shared memory,
+// then the warp walks the group's samples in order with its lanes over the
+// window cells.  A lane keeps the running sums of its cells for the current
+// window in registers and adds them to the tile only when the window changes;
+// the sort puts samples that share a window next to each other, so the
+// shared-memory atomics drop from one per sample, cell and strength to one
+// per run of samples, cell and strength.
+template <typename T, int D, int W, int CN>
+__global__ void __launch_bounds__(kSpreadThreads)
+spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict__ str,
+                  int s0, const uint32_t* __restrict__ sub_bin,
+                  const uint32_t* __restrict__ sub_first, const uint32_t* __restrict__ bin_start,
+                  const uint32_t* __restrict__ sub_total, T* __restrict__ fine) {
+  static_assert(D <= 2 && W > 0, "run spreading serves 1-D and 2-D with a fixed width");
+  constexpr int NC = D == 1 ? W : W * W;      // window cells
+  constexpr int CS = (NC + 31) / 32;          // cell slots per lane
+  constexpr int PS = D * W + 1;               // staged kernel values per sample (odd stride)
+  constexpr int NWARP = kSpreadThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using A = typename TileAcc<T>::type;
+  __shared__ T s_scale[kMaxChunk2], s_inv[kMaxChunk2];
+  __shared__ T s_red[NWARP][kMaxChunk2];
+  __shared__ __align__(16) T s_str[NWARP][32][CN];
+  __shared__ T s_phi[NWARP][32][PS];
+  __shared__ int s_org[NWARP][32];
+  A* sm = reinterpret_cast<A*>(smem_raw);
+  const uint32_t k = blockIdx.x;
+  if (k >= *sub_total) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t b = sub_bin[k];
+  const uint32_t first = sub_first[k];
+  const uint32_t last = min(first + uint32_t(kSubMax), bin_start[b + 1]);
+  int64_t bj[2] = {0, 0};
+  {
+    int64_t rem = b;
+    for (int j = D - 1; j >= 0; --j) {
+      bj[j] = rem % g.nbins[j];
+      rem /= g.nbins[j];
+    }
+  }
+  int64_t o[2] = {0, 0};
+  int W3[2] = {1, 1};
+  for (int j = 0; j < D; ++j) {
+    o[j] = bj[j] * g.tile[j] - g.pad;
+    W3[j] = int(g.tile[j]) + 2 * g.pad;
+  }
+  const int cells = W3[0] * W3[1];
+  const T beta = T(g.beta);
+  const T halfw = T(0.5) * T(W);
+  const int64_t fine_cells = g.nf[0] * g.nf[1] * g.nf[2];
+  for (int idx = threadIdx.x; idx < CN * cells; idx += blockDim.x) sm[idx] = A(0);
+  if (sizeof(A) == 4) {
+    // fixed-point scale per strength: 2^30 / sum |c| over this sub-problem
+    T part[CN];
+#pragma unroll
+    for (int c = 0; c < CN; ++c) part[c] = T(0);
+    for (uint32_t p = first + threadIdx.x; p < last; p += blockDim.x)
+#pragma unroll
+      for (int c = 0; c < CN; ++c) part[c] += fabs(str[int64_t(s0 + c) * n + p]);
+#pragma unroll
+    for (int c = 0; c < CN; ++c) {
+      const T v = warp_sum_t<T>(part[c]);
+      if (lane == 0) s_red[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < CN) {
+      T tot = T(0);
+      for (int wv = 0; wv < NWARP; ++wv) tot += s_red[wv][threadIdx.x];
+      s_scale[threadIdx.x] = tot > T(0) ? T(1073741824.0) / tot : T(0);
+      s_inv[threadIdx.x] = tot > T(0) ? tot / T(1073741824.0) : T(0);
+    }
+  } else if (threadIdx.x < CN) {
+    s_scale[threadIdx.x] = T(1);
+    s_inv[threadIdx.x] = T(1);
+  }
+  __syncthreads();
+  // this lane's window cells: tile offset relative to the window origin
+  int rel[CS];
+  bool act[CS];
+#pragma unroll
+  for (int a = 0; a < CS; ++a) {
+    const int ci = lane + 32 * a;
+    act[a] = ci < NC;
+    const int t0 = D == 2 ? ci / W : ci, t1 = D == 2 ? ci % W : 0;
+    rel[a] = D == 2 ? t0 * W3[1] + t1 : t0;
+  }
+  const int ngr = int((last - first + 31) / 32);
+  for (int gi = warp; gi < ngr; gi += NWARP) {
+    const int64_t g0 = int64_t(first) + int64_t(gi) * 32;
+    const int cnt = int(min(int64_t(32), int64_t(last) - g0));
+    if (lane < cnt) {
+      const int64_t p = g0 + lane;
+      int org = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const T u = mul_rn(xs[int64_t(j) * n + p], inv_h_of<T>(g, j));
+        const T f0 = ceil(u - halfw);
+        const int l = int(int64_t(f0) - o[j]);
+        org = j == 0 ? l : org * W3[1] + l;
+        const T off = f0 - u;
+#pragma unroll
+        for (int t = 0; t < W; ++t) s_phi[warp][lane][j * W + t] = phi<T>(g.skind, W, beta, off + T(t));
+      }
+      s_org[warp][lane] = org;
+#pragma unroll
+      for (int c = 0; c < CN; ++c) s_str[warp][lane][c] = str[int64_t(s0 + c) * n + p] * s_scale[c];
+    }
+    __syncwarp();
+    T acc[CS][CN];
+#pragma unroll
+    for (int a = 0; a < CS; ++a)
+#pragma unroll
+      for (int c = 0; c < CN; ++c) acc[a][c] = T(0);
+    int cur = s_org[warp][0];
+    for (int j = 0; j < cnt; ++j) {
+      const int org = s_org[warp][j];
+      if (org != cur) {
+#pragma unroll
+        for (int a = 0; a < CS; ++a)
+          if (act[a])
+#pragma unroll
+            for (int c = 0; c < CN; ++c) {
+              TileAcc<T>::add(&sm[c * cells + cur + rel[a]], acc[a][c]);
+              acc[a][c] = T(0);
+            }
+        cur = org;
+      }
+      const T* ph = s_phi[warp][j];
+      T cv[CN];
+#pragma unroll
+      for (int c = 0; c < CN; ++c) cv[c] = s_str[warp][j][c];
+#pragma unroll
+      for (int a = 0; a < CS; ++a) {
+        const int ci = lane + 32 * a;
+        const int t0 = D == 2 ? ci / W : ci, t1 = D == 2 ? ci % W : 0;
+        T wa = T(0);
+        if (act[a]) wa = D == 2 ? ph[t0] * ph[W + t1] : ph[t0];
+#pragma unroll
+        for (int c = 0; c < CN; ++c) acc[a][c] += wa * cv[c];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < CS; ++a)
+      if (act[a])
+#pragma unroll
+        for (int c = 0; c < CN; ++c) TileAcc<T>::add(&sm[c * cells + cur + rel[a]], acc[a][c]);
+    __syncwarp();  // staging rows are rewritten by the next group
+  }
+  __syncthreads();
+  // flush the tile (periodic wrap) into the fine grid
+  for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+    const int l0 = D == 2 ? idx / W3[1] : idx, l1 = D == 2 ? idx % W3[1] : 0;
+    int64_t gidx = wrap_idx(o[0] + l0, g.nf[0]);
+    if (D == 2) gidx = gidx * g.nf[1] + wrap_idx(o[1] + l1, g.nf[1]);
+    for (int c = 0; c < CN; ++c) {
+      const A av = sm[c * cells + idx];
+      if (av != A(0)) atomicAdd(&fine[int64_t(s0 + c) * fine_cells + gidx], T(av) * s_inv[c]);
+    }
+  }
+}
+
 template <typename T, int D, int W, int CN>
 cudaError_t launch_spread_cn(fkreg_plan_s* P, int s0, cudaStream_t st) {
   const GeoDev& g = P->geo;
@@ -224,11 +389,63 @@ cudaError_t launch_spread_cn(fkreg_plan_s* P, int s0, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int D, int CN>
+cudaError_t launch_spread_run(fkreg_plan_s* P, int s0, cudaStream_t st) {
+  const GeoDev& g = P->geo;
+  int cells = 1;
+  for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
+  const size_t smem = size_t(cells) * sizeof(int) * CN;
+  if (smem > 160 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(spread_run_kernel<float, D, 7, CN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned(P->nsub_max);
+  const uint32_t* sub_total = wsp<uint32_t>(P, P->r_substart) + P->nbins_total;
+  spread_run_kernel<float, D, 7, CN><<<grid, kSpreadThreads, smem, st>>>(
+      g, P->n, wsp<float>(P, P->r_xs), wsp<float>(P, P->r_str), s0, wsp<uint32_t>(P, P->r_subbin),
+      wsp<uint32_t>(P, P->r_subfirst), wsp<uint32_t>(P, P->r_binstart), sub_total,
+      wsp<float>(P, P->r_fine));
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
 // Strengths go in launches of 8, 4, 2 or 1 (compile-time chunk sizes, as
-// many as the shared-memory budget allows per launch).
+// many as the shared-memory budget allows per launch); FP32 1-D / 2-D plans
+// of width 7 use the run kernel in launches of up to 16.
 template <typename T, int D, int W>
 cudaError_t launch_spread_w(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
   const GeoDev& g = P->geo;
+  if constexpr (sizeof(T) == 4 && W == 7 && D <= 2) {
+    int cells = 1;
+    for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
+    if (size_t(cells) * sizeof(int) * 16 <= 160 * 1024) {
+      int done = 0;
+      while (done < scount) {
+        const int rem = scount - done;
+        cudaError_t e;
+        int used;
+        if (rem >= 16) {
+          e = launch_spread_run<D, 16>(P, s0 + done, st);
+          used = 16;
+        } else if (rem >= 8) {
+          e = launch_spread_run<D, 8>(P, s0 + done, st);
+          used = 8;
+        } else if (rem >= 4) {
+          e = launch_spread_run<D, 4>(P, s0 + done, st);
+          used = 4;
+        } else if (rem >= 2) {
+          e = launch_spread_run<D, 2>(P, s0 + done, st);
+          used = 2;
+        } else {
+          e = launch_spread_run<D, 1>(P, s0 + done, st);
+          used = 1;
+        }
+        if (e != cudaSuccess) return e;
+        done += used;
+      }
+      return cudaSuccess;
+    }
+  }
   int cells = 1;
   for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
   const size_t per = size_t(cells) * sizeof(typename TileAcc<T>::type);

@@ -80,16 +80,31 @@ def check_grid(w, out, b=0, idx=None, bar=None):
 
 # ---------------------------------------------------------------- sorting ----
 def cpu_keys(x, geom, precision):
+    """Sort keys of the bin rule (bin, then window centre inside the bin)."""
     ft = np.float32 if precision == "f32" else np.float64
     d = x.shape[1]
-    key = np.zeros(x.shape[0], dtype=np.int64)
+    w = geom["w"]
+    tile, nbins = geom["tile"], geom["nbins"]
+    bins = np.zeros(x.shape[0], dtype=np.int64)
+    local = np.zeros(x.shape[0], dtype=np.int64)
+    cells, nb = 1, 1
     for j in range(d):
         xp = (x[:, j].astype(ft) - ft(0.0)).astype(ft)
         u = (xp * ft(geom["inv_h"][j])).astype(ft)
         c = np.floor(u).astype(np.int64)
         c = np.clip(c, 0, geom["nf"][j] - 1)
-        key = key * geom["nbins"][j] + c // geom["tile"][j]
-    return key
+        b = c // tile[j]
+        e = np.ceil((u - ft(0.5 * w)).astype(ft)).astype(np.int64) + w // 2 - b * tile[j]
+        e = np.clip(e, 0, tile[j])
+        bins = bins * nbins[j] + b
+        local = local * (tile[j] + 1) + e
+        cells *= tile[j] + 1
+        nb *= nbins[j]
+    kb = int(np.ceil(np.log2(cells))) if cells > 1 else 0
+    bb = int(np.ceil(np.log2(nb))) if nb > 1 else 0
+    if bb + kb > 32:
+        return bins, bins
+    return (bins << kb) | local, bins
 
 
 @pytest.mark.parametrize("case", ["d1", "d2clip", "d3", "dups", "one"])
@@ -110,11 +125,11 @@ def test_sort_is_bit_exact(case):
     p.set_points(torch.tensor(w.x))
     perm, bstart = p.get_sort()
     p.sync()
-    key = cpu_keys(w.x, p.geom, w.precision)
+    key, bins = cpu_keys(w.x, p.geom, w.precision)
     ref = np.argsort(key, kind="stable")
     assert np.array_equal(perm.cpu().numpy().astype(np.int64), ref)
     nb = int(np.prod(p.geom["nbins"]))
-    counts = np.bincount(key, minlength=nb)
+    counts = np.bincount(bins, minlength=nb)
     ref_start = np.concatenate([[0], np.cumsum(counts)])
     assert np.array_equal(bstart.cpu().numpy().astype(np.int64), ref_start)
     assert bstart.cpu().numpy()[-1] == w.n
