@@ -70,6 +70,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(m))
       : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -214,11 +218,10 @@ __device__ __forceinline__ double red_get(const double* red, int a) {
 template <typename T>
 __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mono, const BwDev& B,
                                             const T* my, int pass, int q_done, int q_in, int lane,
-                                            bool valid, int64_t s, int64_t n,
-                                            const T* __restrict__ str,
-                                            const uint32_t* __restrict__ perm,
-                                            T* __restrict__ mhat_at_x, const T* tsc, T af[kMaxP],
-                                            double* red, T k0, const double* isg) {
+                                            bool valid, int64_t n, const T* cvp, int64_t cstride,
+                                            uint32_t orig, T* __restrict__ mhat_at_x,
+                                            const T* tsc, T af[kMaxP], double* red, T k0,
+                                            const double* isg) {
   if (pass == 0) {
     bool ok = false;
     T a0 = T(0);
@@ -257,14 +260,13 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
     if (lane == 0) red_add<T>(red, c.nacc - 1, tv);
   }
   const int fq0 = pass == 0 ? c.ns : 0;
-  const uint32_t orig = valid ? perm[s] : 0u;
   for (int qq = 0; qq < q_in; ++qq) {
     const int q = q_done + qq;
     T mh = T(0);
 #pragma unroll
     for (int k = 0; k < kMaxP; ++k)
       if (k < c.p) mh += af[k] * my[fq0 + qq * c.nt + k];
-    const T cv = valid ? str[int64_t(1 + q) * n + s] : T(0);
+    const T cv = valid ? cvp[int64_t(q) * cstride] : T(0);
     if (q < c.n_rhs_real) {
       const T r = valid ? cv - mh : T(0);
       const T v = warp_sum_t<T>(r * r);
@@ -368,8 +370,8 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
       if (vout)
         store_fields<T>(vout, buf + lane * bstride, f_first, fcount, valid, s, n);
       else
-        finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n,
-                       str, perm, mhat_at_x, tsc, af, red, k0t, isg);
+        finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, n,
+                       str + n + s, n, valid ? perm[s] : 0u, mhat_at_x, tsc, af, red, k0t, isg);
       __syncwarp();
       q_done += q_in;
       f_first = f_last;
@@ -571,8 +573,8 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
         if (vout)
           store_fields<T>(vout, buf + lane * bstride, f_first, fcount, valid, s, n);
         else
-          finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, s, n,
-                         str, perm, mhat_at_x, tsc, af, red, k0t, isg);
+          finish_pass<T>(c, mono, B, buf + lane * bstride, pass, q_done, q_in, lane, valid, n,
+                         str + n + s, n, valid ? perm[s] : 0u, mhat_at_x, tsc, af, red, k0t, isg);
         __syncwarp();
         q_done += q_in;
         f_first = f_last;
@@ -681,8 +683,8 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
                    float* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part,
                    const uint32_t* __restrict__ sub_bin, const uint32_t* __restrict__ sub_first,
                    const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ sub_total,
-                   int wm0, int wm1, int lo_slack, int bstride, int* __restrict__ errw,
-                   float* __restrict__ vout) {
+                   int wm0, int wm1, int lo_slack, int bstride, int cst,
+                   int* __restrict__ errw, float* __restrict__ vout) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
@@ -693,6 +695,9 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
   double* red_all = reinterpret_cast<double*>(smem_raw + win_bytes);
   double* red = red_all + warp * nacc;
   T* my = reinterpret_cast<T*>(red_all + nwarps * nacc) + (warp * 32 + lane) * bstride;
+  // this lane's strengths (responses, probes) of its sample, copied ahead
+  T* cvs = reinterpret_cast<T*>(red_all + nwarps * nacc) + nwarps * 32 * bstride +
+           (warp * 32 + lane) * cst;
   for (int a = lane; a < nacc; a += 32) red[a] = 0.0;
   if (threadIdx.x == 0) {
     mbar_init(&mbar, 1);
@@ -739,21 +744,39 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
     }
     parity ^= 1u;
     const int ngr = int((last - first + 31) / 32);
+    // coordinates of this lane's sample, one group ahead
+    T xn0 = T(0), xn1 = T(0);
+    if (warp < ngr) {
+      const int64_t sn = min(int64_t(first) + int64_t(warp) * 32 + lane, int64_t(last) - 1);
+      xn0 = xs[sn];
+      if (D > 1) xn1 = xs[n + sn];
+    }
     for (int gi = warp; gi < ngr; gi += nwarps) {
       const int64_t s0 = int64_t(first) + int64_t(gi) * 32;
       const int cnt = int(min(int64_t(32), int64_t(last) - s0));
       const int64_t s = s0 + lane;
       const bool valid = lane < cnt;
-      const int64_t sl = valid ? s : s0;
+      const T x0 = xn0, x1 = xn1;
+      if (gi + nwarps < ngr) {
+        const int64_t sn =
+            min(int64_t(first) + int64_t(gi + nwarps) * 32 + lane, int64_t(last) - 1);
+        xn0 = xs[sn];
+        if (D > 1) xn1 = xs[n + sn];
+      }
+      uint32_t orig = 0u;
+      if (!vout && valid) {
+        orig = perm[s];
+        for (int q = 0; q < c.nq; ++q) cp_async4(cvs + q, str + int64_t(1 + q) * n + s);
+      }
       // window of this lane's sample (same rounding as the bin rule)
-      const T u0 = __fmul_rn(xs[sl], ih0);
+      const T u0 = __fmul_rn(x0, ih0);
       const T fo0 = ceilf(__fsub_rn(u0, halfw));
       const int i0 = int(fo0);
       const T off0 = fo0 - u0;
       int i1 = 0;
       T off1 = T(0);
       if (D > 1) {
-        const T u1 = __fmul_rn(xs[n + sl], ih1);
+        const T u1 = __fmul_rn(x1, ih1);
         const T fo1 = ceilf(__fsub_rn(u1, halfw));
         i1 = int(fo1);
         off1 = fo1 - u1;
@@ -800,8 +823,9 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
               const int f = 4 * (qa + q) + cc;
               if (q < nq && f >= f_first && f < f_last) my[f - f_first] = quad_comp(acc[q], cc);
             }
-          finish_pass<T>(c, mono, B, my, pass, q_done, q_in, lane, valid, s, n, str, perm,
-                         mhat_at_x, tsc, af, red, k0t, isg);
+          if (pass == 0) cp_async_wait_all();
+          finish_pass<T>(c, mono, B, my, pass, q_done, q_in, lane, valid, n, cvs + q_done, 1,
+                         orig, mhat_at_x, tsc, af, red, k0t, isg);
         }
         q_done += q_in;
         f_first = f_last;
@@ -893,7 +917,7 @@ inline int record_stride(int F2) {
 template <int D, int NQ>
 cudaError_t launch_lane(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
                         cudaStream_t st, int nacc, int F2, float* vout, int rec, int pass_f,
-                        int bstride, int wm0, int wm1, int slack, int nw, size_t smem) {
+                        int bstride, int cst, int wm0, int wm1, int slack, int nw, size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(interp_lane_kernel<D, 7, NQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
@@ -903,7 +927,7 @@ cudaError_t launch_lane(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, vo
       n_rhs_real, n_probes, P->o.y_complex, P->nrhs, static_cast<float*>(mhat_at_x), nacc, P->nbw,
       wsp<double>(P, P->r_part), wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
       wsp<uint32_t>(P, P->r_binstart), wsp<uint32_t>(P, P->r_substart) + P->nbins_total, wm0, wm1,
-      slack, bstride, wsp<int>(P, P->r_err), vout);
+      slack, bstride, cst, wsp<int>(P, P->r_err), vout);
   P->launches += 1;
   return cudaGetLastError();
 }
@@ -924,7 +948,8 @@ cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
     const int slack = std::max(tma_slack(P->geo, B, 0), D > 1 ? tma_slack(P->geo, B, 1) : 0);
     const int pf = F2 <= 64 ? F2 : 60;
     const int bstride = pf | 1;
-    const size_t per_warp = sizeof(T) * 32 * bstride + sizeof(double) * nacc;
+    const int cst = (n_rhs_real + n_probes) | 1;
+    const size_t per_warp = sizeof(T) * 32 * (bstride + cst) + sizeof(double) * nacc;
     const size_t budget = 220 * 1024;
     const int nw = win < budget ? int(std::min<size_t>(kTWarps, (budget - win) / per_warp)) : 0;
     const size_t smem = win + per_warp * size_t(nw);
@@ -933,7 +958,7 @@ cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
       const int nqn = F2 <= 64 ? rec / 4 : 16;
       float* vo = reinterpret_cast<float*>(vout);
 #define FK_L(Q) \
-  return launch_lane<D, Q>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, vo, rec, pf, bstride, wm0, wm1, slack, nw, smem)
+  return launch_lane<D, Q>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, vo, rec, pf, bstride, cst, wm0, wm1, slack, nw, smem)
       if (nqn <= 1) FK_L(1);
       if (nqn <= 2) FK_L(2);
       if (nqn <= 3) FK_L(3);
