@@ -172,6 +172,12 @@ cudaError_t run_kmul_adj(fkreg_plan_s* P, int b, int sb, int n_classes, cudaStre
 
 // backward.cu
 cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream_t s);
+// Persistent interpolation kernel (FP32, width 7, 1-D / 2-D, F2 <= 64):
+// launched only when it applies (*launched); vout != NULL selects the
+// gather-only form (F2 fields into vout[f][n]).
+cudaError_t run_interp_direct(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes,
+                              void* mhat_at_x, cudaStream_t st, int nacc, int F2, void* vout,
+                              bool* launched);
 cudaError_t run_loss_scalars(fkreg_plan_s* P, int b, int n_probes, cudaStream_t s);
 cudaError_t run_adjoint(fkreg_plan_s* P, int b, int n_probes, cudaStream_t s);
 cudaError_t run_combine(fkreg_plan_s* P, int n_probes, void* dy, void* dx, double* dlogh,

@@ -30,6 +30,7 @@
 
 #include "device_common.cuh"
 #include "gather.cuh"
+#include "interp_common.cuh"
 #include "internal.h"
 
 namespace fk {
@@ -40,46 +41,6 @@ constexpr int kI2Warps = 16;   // global kernel: warps per block (upper bound)
 constexpr int kTWarps = 16;    // TMA kernel: warps per block (upper bound)
 constexpr int kMaxAcc = 512;
 constexpr int kMaxWRun = 32;   // runtime-width fallback
-constexpr uint32_t kMaxSpin = 1u << 22;  // bounded mbarrier wait
-
-// ---- bulk-copy / mbarrier primitives (inline PTX) --------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return uint32_t(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(m)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(m))
-      : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
 
 // Gather from a window staged in shared memory: win[(l0 * e1 + l1) * rec + f],
 // (l0, l1) = (i0 - o0, i1 - o1) already checked to lie inside the window.
@@ -183,33 +144,6 @@ __device__ __forceinline__ void gather_smem_pair(const float* win, int rec, int 
 struct GroupCtx {
   int ns, nt, p, nq, n_rhs_real, n_probes, cplx, n_rhs_out, nacc, order, b;
 };
-
-// Per-warp accumulators of the reductions (written by lane 0).  FP64 runs
-// accumulate in double; FP32 runs keep an unevaluated sum hi + lo of two
-// floats in the same 8 bytes (two_sum), which keeps the FP64 pipe (a small
-// fraction of the FP32 rate on this part) out of the per-sample path.
-template <typename T>
-__device__ __forceinline__ void red_add(double* red, int a, T v) {
-  if constexpr (sizeof(T) == 4) {
-    float2* r2 = reinterpret_cast<float2*>(red) + a;
-    float2 x = *r2;
-    float e;
-    x.x = two_sum(x.x, v, e);
-    x.y += e;
-    *r2 = x;
-  } else {
-    red[a] += v;
-  }
-}
-template <typename T>
-__device__ __forceinline__ double red_get(const double* red, int a) {
-  if constexpr (sizeof(T) == 4) {
-    const float2 x = reinterpret_cast<const float2*>(red)[a];
-    return double(x.x) + double(x.y);
-  } else {
-    return red[a];
-  }
-}
 
 // Phase B of one pass: lane = sample (valid when lane < cnt).  Solves on pass 0,
 // then forms mhat for this pass's responses / probes and accumulates.  FP32
@@ -385,31 +319,6 @@ interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int 
   }
 }
 
-// Issue the bulk copies of one bin window (thread 0): rows of the window
-// [wm0][wm1][rec] (1-D: one row of wm0 cells) from the periodic field grid,
-// a row that wraps split in two, all completing on one mbarrier.
-template <typename T, int D>
-__device__ __forceinline__ void issue_window_copies(const T* __restrict__ fld, int rec, int nf0,
-                                                    int nf1, int o0, int o1, int wm0, int wm1,
-                                                    T* win, uint64_t* mbar) {
-  fence_proxy_async();  // earlier reads of the window come before the new copies
-  mbar_expect_tx(mbar, uint32_t(size_t(wm0) * wm1 * rec * sizeof(T)));
-  for (int r = 0; r < (D > 1 ? wm0 : 1); ++r) {
-    // axis of the contiguous segment: axis 1 in 2-D, axis 0 in 1-D
-    const int oseg = D > 1 ? o1 : o0;
-    const int nseg = D > 1 ? nf1 : nf0;
-    const int eseg = D > 1 ? wm1 : wm0;
-    const int64_t rowbase = D > 1 ? wrap_idx(o0 + r, nf0) * int64_t(nf1) : 0;
-    const int start = int(wrap_idx(oseg, nseg));
-    const int len = min(eseg, nseg - start);
-    T* dst = win + size_t(r) * eseg * rec;
-    bulk_g2s(dst, fld + (rowbase + start) * rec, uint32_t(size_t(len) * rec * sizeof(T)), mbar);
-    if (len < eseg)
-      bulk_g2s(dst + size_t(len) * rec, fld + rowbase * rec,
-               uint32_t(size_t(eseg - len) * rec * sizeof(T)), mbar);
-  }
-}
-
 // ---- kernel 2: bin windows staged in shared memory by bulk copies ----------
 // One block takes spreading sub-problems (samples of one bin) in turn.  The
 // bin's window of the field grid, [wm0][wm1][rec] cells x fields, is copied
@@ -470,7 +379,7 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
     const int o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - lo_slack;
     const int o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - lo_slack : 0;
     if (threadIdx.x == 0)
-      issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, win, &mbar);
+      issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, wm1 * rec, win, &mbar);
     bool ok = false;
     for (uint32_t it = 0; it < kMaxSpin && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
     if (__syncthreads_or(!ok)) {
@@ -600,82 +509,7 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
 // values go to its own row of the staging buffer (or straight to V in the
 // gather-only mode) and phase B follows as in the other kernels.
 template <int D, int W, int NQ>
-__device__ __forceinline__ void lane_gather_smem(const float* base, int rec, int e1, int nq,
-                                                 int skind, float beta, float off0,
-                                                 const float (&pl)[W], float4 (&acc)[NQ]) {
-  if (D == 1) {
-#pragma unroll
-    for (int t = 0; t < W; ++t) {
-      const float wgt = pl[t];
-      const float* cell = base + t * rec;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q)
-        if (q < nq) {
-          const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
-          acc[q].x += wgt * v.x;
-          acc[q].y += wgt * v.y;
-          acc[q].z += wgt * v.z;
-          acc[q].w += wgt * v.w;
-        }
-    }
-  } else {
-#pragma unroll 1
-    for (int t0 = 0; t0 < W; ++t0) {
-      const float w0 = phi<float>(skind, W, beta, off0 + float(t0));
-      const float* row = base + t0 * e1 * rec;
-#pragma unroll
-      for (int t1 = 0; t1 < W; ++t1) {
-        const float wgt = w0 * pl[t1];
-        const float* cell = row + t1 * rec;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-          if (q < nq) {
-            const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
-            acc[q].x += wgt * v.x;
-            acc[q].y += wgt * v.y;
-            acc[q].z += wgt * v.z;
-            acc[q].w += wgt * v.w;
-          }
-      }
-    }
-  }
-}
-
-// The same from the global field grid (periodic wrap), for the rare sample
-// whose window leaves the staged one.
-template <int D, int W, int NQ>
-__device__ __forceinline__ void lane_gather_global(const float* __restrict__ fld, int rec, int qa,
-                                                int nq, int i0, int i1, int nf0, int nf1,
-                                                int skind, float beta, float off0,
-                                                const float (&pl)[W], float4 (&acc)[NQ]) {
-#pragma unroll 1
-  for (int t0 = 0; t0 < (D == 1 ? 1 : W); ++t0) {
-    const float w0 = D == 1 ? 1.f : phi<float>(skind, W, beta, off0 + float(t0));
-    const int64_t r = D == 1 ? 0 : wrap_idx(i0 + t0, nf0) * int64_t(nf1);
-#pragma unroll
-    for (int t1 = 0; t1 < W; ++t1) {
-      const int64_t c = D == 1 ? wrap_idx(i0 + t1, nf0) : r + wrap_idx(i1 + t1, nf1);
-      const float wgt = w0 * pl[t1];
-      const float* cell = fld + c * rec + 4 * qa;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q)
-        if (q < nq) {
-          const float4 v = __ldg(reinterpret_cast<const float4*>(cell + 4 * q));
-          acc[q].x += wgt * v.x;
-          acc[q].y += wgt * v.y;
-          acc[q].z += wgt * v.z;
-          acc[q].w += wgt * v.w;
-        }
-    }
-  }
-}
-
-__device__ __forceinline__ float quad_comp(const float4& v, int c) {
-  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
-}
-
-template <int D, int W, int NQ>
-__global__ void __launch_bounds__(kTWarps * 32)
+__global__ void __launch_bounds__(kLWarps * 32)
 interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int order,
                    int64_t n, const float* __restrict__ xs, const float* __restrict__ str,
                    const uint32_t* __restrict__ perm, const float* __restrict__ fld, int rec,
@@ -683,14 +517,14 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
                    float* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part,
                    const uint32_t* __restrict__ sub_bin, const uint32_t* __restrict__ sub_first,
                    const uint32_t* __restrict__ bin_start, const uint32_t* __restrict__ sub_total,
-                   int wm0, int wm1, int lo_slack, int bstride, int cst,
+                   int wm0, int wm1, int pitch, int lo_slack, int bstride, int cst,
                    int* __restrict__ errw, float* __restrict__ vout) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = int(blockDim.x >> 5);
-  const size_t win_bytes = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
+  const size_t win_bytes = (size_t(D > 1 ? wm0 : 1) * pitch * sizeof(T) + 127) / 128 * 128;
   T* win = reinterpret_cast<T*>(smem_raw);
   double* red_all = reinterpret_cast<double*>(smem_raw + win_bytes);
   double* red = red_all + warp * nacc;
@@ -712,7 +546,6 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
   const T beta = T(g.beta);
   const T halfw = T(0.5) * T(W);
   const int skind = g.skind;
-  const int e1 = D > 1 ? wm1 : 1;
   GroupCtx c{mono.n, mono.nt, mono.nt, n_rhs_real + n_probes, n_rhs_real, n_probes, cplx,
              n_rhs_out, nacc, order, b};
   T tsc[kMaxP];
@@ -732,7 +565,7 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
     const int o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - lo_slack;
     const int o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - lo_slack : 0;
     if (threadIdx.x == 0)
-      issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, win, &mbar);
+      issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, pitch, win, &mbar);
     bool ok = false;
     for (uint32_t it = 0; it < kMaxSpin && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
     if (__syncthreads_or(!ok)) {
@@ -799,8 +632,8 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (inside)
-          lane_gather_smem<D, W, NQ>(win + (size_t(l0) * e1 + l1) * rec + 4 * qa, rec, e1, nq,
-                                     skind, beta, off0, pl, acc);
+          lane_gather_smem<D, W, NQ>(win + size_t(l0) * (D > 1 ? pitch : rec) + l1 * rec + 4 * qa,
+                                     rec, pitch, nq, skind, beta, off0, pl, acc);
         if (__any_sync(0xffffffffu, valid && !inside)) {
           if (valid && !inside)
             lane_gather_global<D, W, NQ>(fld, rec, qa, nq, i0, i1, nf0, nf1, skind, beta, off0, pl,
@@ -897,27 +730,16 @@ __global__ void finalize_kernel(const double* __restrict__ sums, int nbw, int na
   }
 }
 
-// Window extent of a bin on bandwidth b's fine grid (cells, per axis): covers
-// every window of a sample in the bin with one cell of slack on each side.
-// On the spreading grid itself (r = 1) the window is exact: origin
-// b T - pad, extent T + w + 1.  Other grids get one more cell of slack on each
-// side for the rounding of the rescaled coordinates (a sample whose window
-// still falls outside is gathered from global memory).
-inline int tma_slack(const GeoDev& g, const BwDev& B, int j) { return B.nf[j] == g.nf[j] ? 0 : 1; }
-inline int tma_window(const GeoDev& g, const BwDev& B, int j) {
-  const double r = double(B.nf[j]) / double(g.nf[j]);
-  return int(std::ceil(double(g.tile[j]) * r)) + g.w + 1 + 2 * tma_slack(g, B, j);
-}
-
 template <typename T>
 inline int record_stride(int F2) {
-  return (F2 + 3) / 4 * 4;
+  return t2_record_stride(F2);
 }
 
 template <int D, int NQ>
 cudaError_t launch_lane(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, void* mhat_at_x,
                         cudaStream_t st, int nacc, int F2, float* vout, int rec, int pass_f,
-                        int bstride, int cst, int wm0, int wm1, int slack, int nw, size_t smem) {
+                        int bstride, int cst, int wm0, int wm1, int pitch, int slack, int nw,
+                        size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(interp_lane_kernel<D, 7, NQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
@@ -927,7 +749,7 @@ cudaError_t launch_lane(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes, vo
       n_rhs_real, n_probes, P->o.y_complex, P->nrhs, static_cast<float*>(mhat_at_x), nacc, P->nbw,
       wsp<double>(P, P->r_part), wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
       wsp<uint32_t>(P, P->r_binstart), wsp<uint32_t>(P, P->r_substart) + P->nbins_total, wm0, wm1,
-      slack, bstride, cst, wsp<int>(P, P->r_err), vout);
+      pitch, slack, bstride, cst, wsp<int>(P, P->r_err), vout);
   P->launches += 1;
   return cudaGetLastError();
 }
@@ -944,7 +766,9 @@ cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
     const BwDev& B = P->bw[b];
     const int wm0 = tma_window(P->geo, B, 0);
     const int wm1 = D > 1 ? tma_window(P->geo, B, 1) : 1;
-    const size_t win = (size_t(wm0) * wm1 * rec * sizeof(T) + 127) / 128 * 128;
+    // window rows one quad apart in bank space (2-D)
+    const int pitch = D > 1 ? wm1 * rec + 4 : wm0 * rec;
+    const size_t win = (size_t(D > 1 ? wm0 : 1) * pitch * sizeof(T) + 127) / 128 * 128;
     const int slack = std::max(tma_slack(P->geo, B, 0), D > 1 ? tma_slack(P->geo, B, 1) : 0);
     const int pf = F2 <= 64 ? F2 : 60;
     const int bstride = pf | 1;
@@ -955,10 +779,10 @@ cudaError_t launch_interp_w(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
     const size_t smem = win + per_warp * size_t(nw);
     const bool fits = wm0 <= B.nf[0] && (D == 1 || wm1 <= B.nf[1]) && nw >= 4;
     if (fits) {
-      const int nqn = F2 <= 64 ? rec / 4 : 16;
+      const int nqn = F2 <= 64 ? (F2 + 3) / 4 : 16;
       float* vo = reinterpret_cast<float*>(vout);
 #define FK_L(Q) \
-  return launch_lane<D, Q>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, vo, rec, pf, bstride, cst, wm0, wm1, slack, nw, smem)
+  return launch_lane<D, Q>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, vo, rec, pf, bstride, cst, wm0, wm1, pitch, slack, nw, smem)
       if (nqn <= 1) FK_L(1);
       if (nqn <= 2) FK_L(2);
       if (nqn <= 3) FK_L(3);
@@ -1045,6 +869,12 @@ cudaError_t launch_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, v
   if (nacc > kMaxAcc) return cudaErrorInvalidValue;
   const int F2 = P->ns + (n_rhs_real + n_probes) * P->nt;
   if (P->d * P->geo.w > 64 || P->geo.w > kMaxWRun) return cudaErrorInvalidValue;
+  if (sizeof(T) == 4) {
+    bool used = false;
+    const cudaError_t e =
+        run_interp_direct(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, nullptr, &used);
+    if (used || e != cudaSuccess) return e;
+  }
   // fields per pass: 64 (float) or 32 (double)
   const bool two = sizeof(T) == 4 && F2 > 32;
   if (two) {
@@ -1063,6 +893,11 @@ template <typename T>
 cudaError_t launch_gather(fkreg_plan_s* P, int b, int F, T* V, cudaStream_t st) {
   if (P->n == 0) return cudaSuccess;
   if (P->d * P->geo.w > 64 || P->geo.w > kMaxWRun) return cudaErrorInvalidValue;
+  if (sizeof(T) == 4) {
+    bool used = false;
+    const cudaError_t e = run_interp_direct(P, b, 0, 0, nullptr, st, 0, F, V, &used);
+    if (used || e != cudaSuccess) return e;
+  }
   if (sizeof(T) == 4 && F > 32) {
     if (P->d == 1) return launch_interp_d<T, 1, 2>(P, b, 0, 0, nullptr, st, 0, F, V);
     if (P->d == 2) return launch_interp_d<T, 2, 2>(P, b, 0, 0, nullptr, st, 0, F, V);
@@ -1103,8 +938,13 @@ cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out
   return cudaGetLastError();
 }
 
-// Field record stride of the type-2 grids for F2 fields (multiple of 4 so
-// every cell record starts on a 16-byte boundary for the bulk copies).
-int t2_record_stride(int F2) { return (F2 + 3) / 4 * 4; }
+// Field record stride of the type-2 grids for F2 fields: a multiple of 4 so
+// every cell record starts on a 16-byte boundary for the bulk copies, with an
+// odd number of 16-byte quads so neighbouring cells start on different
+// shared-memory banks.
+int t2_record_stride(int F2) {
+  const int r = (F2 + 3) / 4 * 4;
+  return (r / 4) % 2 == 0 ? r + 4 : r;
+}
 
 }  // namespace fk

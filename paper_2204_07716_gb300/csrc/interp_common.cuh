@@ -1,0 +1,204 @@
+// Device helpers shared by the interpolation kernels (interp.cu and
+// interp_direct.cu): bulk-copy / mbarrier / cp.async primitives, the bin
+// window staging, the lane-per-sample gathers and the per-warp reduction
+// accumulators.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace fk {
+
+namespace {
+
+constexpr uint32_t kMaxSpin = 1u << 22;  // bounded mbarrier wait
+constexpr int kLWarps = 16;              // lane-per-sample kernels: warps per block (upper bound)
+
+// ---- bulk-copy / mbarrier primitives (inline PTX) --------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return uint32_t(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(m))
+      : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Per-warp accumulators of the reductions (written by lane 0).  FP64 runs
+// accumulate in double; FP32 runs keep an unevaluated sum hi + lo of two
+// floats in the same 8 bytes (two_sum), which keeps the FP64 pipe (a small
+// fraction of the FP32 rate on this part) out of the per-sample path.
+template <typename T>
+__device__ __forceinline__ void red_add(double* red, int a, T v) {
+  if constexpr (sizeof(T) == 4) {
+    float2* r2 = reinterpret_cast<float2*>(red) + a;
+    float2 x = *r2;
+    float e;
+    x.x = two_sum(x.x, v, e);
+    x.y += e;
+    *r2 = x;
+  } else {
+    red[a] += v;
+  }
+}
+template <typename T>
+__device__ __forceinline__ double red_get(const double* red, int a) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 x = reinterpret_cast<const float2*>(red)[a];
+    return double(x.x) + double(x.y);
+  } else {
+    return red[a];
+  }
+}
+
+// Issue the bulk copies of one bin window (thread 0): rows of the window
+// [wm0][wm1][rec] (1-D: one row of wm0 cells) from the periodic field grid,
+// row r landing at win + r * pitch, a row that wraps split in two, all
+// completing on one mbarrier.
+template <typename T, int D>
+__device__ __forceinline__ void issue_window_copies(const T* __restrict__ fld, int rec, int nf0,
+                                                    int nf1, int o0, int o1, int wm0, int wm1,
+                                                    int pitch, T* win, uint64_t* mbar) {
+  fence_proxy_async();  // earlier reads of the window come before the new copies
+  mbar_expect_tx(mbar, uint32_t(size_t(wm0) * wm1 * rec * sizeof(T)));
+  for (int r = 0; r < (D > 1 ? wm0 : 1); ++r) {
+    // axis of the contiguous segment: axis 1 in 2-D, axis 0 in 1-D
+    const int oseg = D > 1 ? o1 : o0;
+    const int nseg = D > 1 ? nf1 : nf0;
+    const int eseg = D > 1 ? wm1 : wm0;
+    const int64_t rowbase = D > 1 ? wrap_idx(o0 + r, nf0) * int64_t(nf1) : 0;
+    const int start = int(wrap_idx(oseg, nseg));
+    const int len = min(eseg, nseg - start);
+    T* dst = win + size_t(r) * pitch;
+    bulk_g2s(dst, fld + (rowbase + start) * rec, uint32_t(size_t(len) * rec * sizeof(T)), mbar);
+    if (len < eseg)
+      bulk_g2s(dst + size_t(len) * rec, fld + rowbase * rec,
+               uint32_t(size_t(eseg - len) * rec * sizeof(T)), mbar);
+  }
+}
+
+// ---- lane-per-sample gathers (FP32, fixed width) ----------------------------
+template <int D, int W, int NQ>
+__device__ __forceinline__ void lane_gather_smem(const float* base, int rec, int pitch, int nq,
+                                                 int skind, float beta, float off0,
+                                                 const float (&pl)[W], float4 (&acc)[NQ]) {
+  if (D == 1) {
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const float wgt = pl[t];
+      const float* cell = base + t * rec;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (q < nq) {
+          const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
+          acc[q].x += wgt * v.x;
+          acc[q].y += wgt * v.y;
+          acc[q].z += wgt * v.z;
+          acc[q].w += wgt * v.w;
+        }
+    }
+  } else {
+#pragma unroll 1
+    for (int t0 = 0; t0 < W; ++t0) {
+      const float w0 = phi<float>(skind, W, beta, off0 + float(t0));
+      const float* row = base + t0 * pitch;
+#pragma unroll
+      for (int t1 = 0; t1 < W; ++t1) {
+        const float wgt = w0 * pl[t1];
+        const float* cell = row + t1 * rec;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          if (q < nq) {
+            const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
+            acc[q].x += wgt * v.x;
+            acc[q].y += wgt * v.y;
+            acc[q].z += wgt * v.z;
+            acc[q].w += wgt * v.w;
+          }
+      }
+    }
+  }
+}
+
+// The same from the global field grid (periodic wrap), for the rare sample
+// whose window leaves the staged one.
+template <int D, int W, int NQ>
+__device__ __forceinline__ void lane_gather_global(const float* __restrict__ fld, int rec, int qa,
+                                                int nq, int i0, int i1, int nf0, int nf1,
+                                                int skind, float beta, float off0,
+                                                const float (&pl)[W], float4 (&acc)[NQ]) {
+#pragma unroll 1
+  for (int t0 = 0; t0 < (D == 1 ? 1 : W); ++t0) {
+    const float w0 = D == 1 ? 1.f : phi<float>(skind, W, beta, off0 + float(t0));
+    const int64_t r = D == 1 ? 0 : wrap_idx(i0 + t0, nf0) * int64_t(nf1);
+#pragma unroll
+    for (int t1 = 0; t1 < W; ++t1) {
+      const int64_t c = D == 1 ? wrap_idx(i0 + t1, nf0) : r + wrap_idx(i1 + t1, nf1);
+      const float wgt = w0 * pl[t1];
+      const float* cell = fld + c * rec + 4 * qa;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (q < nq) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(cell + 4 * q));
+          acc[q].x += wgt * v.x;
+          acc[q].y += wgt * v.y;
+          acc[q].z += wgt * v.z;
+          acc[q].w += wgt * v.w;
+        }
+    }
+  }
+}
+
+__device__ __forceinline__ float quad_comp(const float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// Window extent of a bin on bandwidth b's fine grid (cells, per axis): covers
+// every window of a sample in the bin with one cell of slack on each side.
+// On the spreading grid itself (r = 1) the window is exact: origin
+// b T - pad, extent T + w + 1.  Other grids get one more cell of slack on each
+// side for the rounding of the rescaled coordinates (a sample whose window
+// still falls outside is gathered from global memory).
+inline int tma_slack(const GeoDev& g, const BwDev& B, int j) { return B.nf[j] == g.nf[j] ? 0 : 1; }
+inline int tma_window(const GeoDev& g, const BwDev& B, int j) {
+  const double r = double(B.nf[j]) / double(g.nf[j]);
+  return int(std::ceil(double(g.tile[j]) * r)) + g.w + 1 + 2 * tma_slack(g, B, j);
+}
+
+}  // namespace
+
+}  // namespace fk

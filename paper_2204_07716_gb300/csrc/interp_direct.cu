@@ -1,0 +1,320 @@
+// Type-2 interpolation, persistent form (FP32, width 7, 1-D / 2-D, every
+// field in one pass): see interp.cu for the method.  For every field in one
+// pass (F2 <= 64) and a compile-time system (order, dimension) the
+// lane-per-sample gather leaves a sample's fields in registers and phase B
+// reads them there, so no staging rows are needed and two bin windows fit
+// shared memory.  One block per SM walks its sub-problems in turn; while it
+// gathers from one window the bulk copies fill the other.  The gather-only
+// form (GONLY) writes V[f][s] for the backward instead of phase B.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "interp_common.cuh"
+#include "internal.h"
+
+namespace fk {
+
+namespace {
+
+template <int D, int W, int NQ, int ORD, bool GONLY>
+__global__ void __launch_bounds__(kLWarps * 32, 1)
+interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
+                     const float* __restrict__ xs, const float* __restrict__ str,
+                     const uint32_t* __restrict__ perm, const float* __restrict__ fld, int rec,
+                     int F2, int n_rhs_real, int n_probes, int cplx, int n_rhs_out,
+                     float* __restrict__ mhat_at_x, int nacc, int nbw, int64_t nblk_rows,
+                     double* __restrict__ part, const uint32_t* __restrict__ sub_bin,
+                     const uint32_t* __restrict__ sub_first, const uint32_t* __restrict__ bin_start,
+                     const uint32_t* __restrict__ sub_total, int wm0, int wm1, int pitch,
+                     int lo_slack, int win_floats, int* __restrict__ errw,
+                     float* __restrict__ vout) {
+  using T = float;
+  constexpr int NS = ORD == 0 ? 1 : (D == 1 ? 3 : 6);   // s-fields
+  constexpr int NT = ORD == 0 ? 1 : D + 1;              // t-fields per response (= p)
+  constexpr int QMAX = GONLY ? 0 : (4 * NQ - NS) / NT;  // responses + probes held
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = int(blockDim.x >> 5);
+  T* wins = reinterpret_cast<T*>(smem_raw);
+  double* red_all = reinterpret_cast<double*>(wins + 2 * size_t(win_floats));
+  double* red = red_all + warp * nacc;
+  for (int a = lane; a < nacc; a += 32) red[a] = 0.0;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const BwDev& B = bwt[b];
+  const int nf0 = int(B.nf[0]), nf1 = D > 1 ? int(B.nf[1]) : 1;
+  const T ih0 = T(B.inv_h[0]), ih1 = T(D > 1 ? B.inv_h[1] : 1.0);
+  const double r0 = double(B.nf[0]) / double(g.nf[0]);
+  const double r1 = D > 1 ? double(B.nf[1]) / double(g.nf[1]) : 1.0;
+  const T beta = T(g.beta);
+  const T halfw = T(0.5) * T(W);
+  const int skind = g.skind;
+  const int nq = n_rhs_real + n_probes;
+  // scaling of the t-fields: 1, 1/sigma_j
+  T dsc[3] = {T(1), T(1.0 / B.sigma[0]), T(D > 1 ? 1.0 / B.sigma[1] : 1.0)};
+  const T k0t = T(B.k0);
+  const uint32_t nsub = *sub_total;
+  auto window_of = [&](uint32_t k, int& o0, int& o1) {
+    const uint32_t bin = sub_bin[k];
+    const int64_t bj0 = D > 1 ? int64_t(bin) / g.nbins[1] : int64_t(bin);
+    const int64_t bj1 = D > 1 ? int64_t(bin) % g.nbins[1] : 0;
+    o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - lo_slack;
+    o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - lo_slack : 0;
+  };
+  if (threadIdx.x == 0 && blockIdx.x < nsub) {
+    int a0, a1;
+    window_of(blockIdx.x, a0, a1);
+    issue_window_copies<T, D>(fld, rec, nf0, nf1, a0, a1, wm0, wm1, pitch, wins, &mbar[0]);
+  }
+  bool failed = false;
+  int it = 0;
+  for (uint32_t k = blockIdx.x; k < nsub; k += gridDim.x, ++it) {
+    const int cur = it & 1;
+    const uint32_t parity = uint32_t(it >> 1) & 1u;
+    const T* win = wins + size_t(cur) * win_floats;
+    int o0, o1;
+    window_of(k, o0, o1);
+    const uint32_t first = sub_first[k];
+    const uint32_t last = min(first + uint32_t(kSubMax), bin_start[sub_bin[k] + 1]);
+    // the other buffer's readers finished at the barrier that ended the last
+    // sub-problem: fill it with the next window now
+    const bool more = k + gridDim.x < nsub;
+    if (threadIdx.x == 0 && more) {
+      int a0, a1;
+      window_of(k + gridDim.x, a0, a1);
+      issue_window_copies<T, D>(fld, rec, nf0, nf1, a0, a1, wm0, wm1, pitch,
+                                wins + size_t(cur ^ 1) * win_floats, &mbar[cur ^ 1]);
+    }
+    bool ok = false;
+    for (uint32_t i = 0; i < kMaxSpin && !ok; ++i) ok = mbar_try_wait(&mbar[cur], parity);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(errw, 2);
+      // wait (bounded) for the copies still in flight before leaving
+      bool late = ok;
+      for (uint32_t i = 0; i < kMaxSpin && !late; ++i) late = mbar_try_wait(&mbar[cur], parity);
+      if (more) {
+        const uint32_t pn = uint32_t((it + 1) >> 1) & 1u;
+        bool late2 = false;
+        for (uint32_t i = 0; i < kMaxSpin && !late2; ++i) late2 = mbar_try_wait(&mbar[cur ^ 1], pn);
+      }
+      failed = true;
+      break;
+    }
+    const int ngr = int((last - first + 31) / 32);
+    T xn0 = T(0), xn1 = T(0);
+    if (warp < ngr) {
+      const int64_t sn = min(int64_t(first) + int64_t(warp) * 32 + lane, int64_t(last) - 1);
+      xn0 = xs[sn];
+      if (D > 1) xn1 = xs[n + sn];
+    }
+    for (int gi = warp; gi < ngr; gi += nwarps) {
+      const int64_t s0 = int64_t(first) + int64_t(gi) * 32;
+      const int cnt = int(min(int64_t(32), int64_t(last) - s0));
+      const int64_t s = s0 + lane;
+      const bool valid = lane < cnt;
+      const T x0 = xn0, x1 = xn1;
+      if (gi + nwarps < ngr) {
+        const int64_t sn =
+            min(int64_t(first) + int64_t(gi + nwarps) * 32 + lane, int64_t(last) - 1);
+        xn0 = xs[sn];
+        if (D > 1) xn1 = xs[n + sn];
+      }
+      // strengths and original index, loaded ahead of the gather
+      uint32_t orig = 0u;
+      T cv[QMAX > 0 ? QMAX : 1];
+      if (!GONLY) {
+        orig = valid ? perm[s] : 0u;
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) cv[q] = (valid && q < nq) ? str[int64_t(1 + q) * n + s] : T(0);
+      }
+      const T u0 = __fmul_rn(x0, ih0);
+      const T fo0 = ceilf(__fsub_rn(u0, halfw));
+      const int i0 = int(fo0);
+      const T off0 = fo0 - u0;
+      int i1 = 0;
+      T off1 = T(0);
+      if (D > 1) {
+        const T u1 = __fmul_rn(x1, ih1);
+        const T fo1 = ceilf(__fsub_rn(u1, halfw));
+        i1 = int(fo1);
+        off1 = fo1 - u1;
+      }
+      const int l0 = i0 - o0, l1 = D > 1 ? i1 - o1 : 0;
+      const bool inside = l0 >= 0 && l0 + W <= wm0 && (D == 1 || (l1 >= 0 && l1 + W <= wm1));
+      T pl[W];
+#pragma unroll
+      for (int t = 0; t < W; ++t) pl[t] = phi<T>(skind, W, beta, (D > 1 ? off1 : off0) + T(t));
+      const int nqd = (F2 + 3) >> 2;
+      float4 acc[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (inside)
+        lane_gather_smem<D, W, NQ>(win + size_t(l0) * (D > 1 ? pitch : rec) + l1 * rec, rec, pitch,
+                                   nqd, skind, beta, off0, pl, acc);
+      if (__any_sync(0xffffffffu, valid && !inside)) {
+        if (valid && !inside)
+          lane_gather_global<D, W, NQ>(fld, rec, 0, nqd, i0, i1, nf0, nf1, skind, beta, off0, pl,
+                                       acc);
+      }
+      if (GONLY) {
+        if (valid)
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              const int f = 4 * q + cc;
+              if (f < F2) vout[int64_t(f) * n + s] = quad_comp(acc[q], cc);
+            }
+        continue;
+      }
+      // phase B: the system of eq. 3 at x_i from the s-fields in registers
+      float a[kMaxP] = {0.f, 0.f, 0.f, 0.f};
+      bool okv = false;
+      if (valid) {
+        float sv[6];
+#pragma unroll
+        for (int k2 = 0; k2 < 6; ++k2) sv[k2] = k2 < NS ? quad_comp(acc[k2 >> 2], k2 & 3) : 0.f;
+        okv = lpr_weights_f32(NT, sv, dsc, a);
+      }
+      T af[NT];
+#pragma unroll
+      for (int k2 = 0; k2 < NT; ++k2) af[k2] = okv ? a[k2] * dsc[k2 < 3 ? k2 : 0] : T(0);
+      {
+        const T tv = warp_sum_t<T>(okv ? k0t * a[0] : T(0));
+        if (lane == 0) red_add<T>(red, nacc - 1, tv);
+      }
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) {
+        if (q >= nq) break;
+        T mh = T(0);
+#pragma unroll
+        for (int k2 = 0; k2 < NT; ++k2) {
+          const int f = NS + q * NT + k2;
+          mh += af[k2] * quad_comp(acc[f >> 2], f & 3);
+        }
+        if (q < n_rhs_real) {
+          const T r = valid ? cv[q] - mh : T(0);
+          const T v = warp_sum_t<T>(r * r);
+          if (lane == 0) red_add<T>(red, q, v);
+          if (valid && mhat_at_x) {
+            const int mult = cplx ? 2 : 1;
+            const int rr = q / mult, pt = q % mult;
+            mhat_at_x[((int64_t(b) * n_rhs_out + rr) * n + orig) * mult + pt] = mh;
+          }
+        } else {
+          const int pp = q - n_rhs_real;
+          const T v1 = warp_sum_t<T>(valid ? cv[q] * mh : T(0));
+          const T v2 = warp_sum_t<T>(valid ? cv[q] * cv[q] : T(0));
+          if (lane == 0) {
+            red_add<T>(red, n_rhs_real + pp, v1);
+            red_add<T>(red, n_rhs_real + n_probes + pp, v2);
+          }
+        }
+      }
+    }
+    __syncthreads();  // every read of this window is done before it is refilled
+  }
+  if (failed) return;
+  __syncthreads();
+  for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
+    double t = 0.0;
+    for (int wv = 0; wv < nwarps; ++wv) t += red_get<T>(red_all, wv * nacc + a);
+    part[(int64_t(blockIdx.x) * nbw + b) * nacc + a] = t;
+    // partial rows of the block indices this persistent grid does not launch
+    for (int64_t r = int64_t(blockIdx.x) + gridDim.x; r < nblk_rows; r += gridDim.x)
+      part[(r * nbw + b) * nacc + a] = 0.0;
+  }
+}
+
+
+template <int D, int NQ, int ORD, bool GONLY>
+cudaError_t launch_direct_k(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes,
+                            void* mhat_at_x, cudaStream_t st, int nacc, int F2, float* vout,
+                            int rec, int wm0, int wm1, int pitch, int slack, int win_floats,
+                            int nw, size_t smem, unsigned grid) {
+  auto kern = interp_direct_kernel<D, 7, NQ, ORD, GONLY>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, nw * 32, smem, st>>>(
+      P->geo, wsp<BwDev>(P, P->r_bw), b, P->n, wsp<float>(P, P->r_xs), wsp<float>(P, P->r_str),
+      perm_ptr(P), wsp<float>(P, P->r_t2field), rec, F2, n_rhs_real, n_probes, P->o.y_complex,
+      P->nrhs, static_cast<float*>(mhat_at_x), nacc, P->nbw, P->nblk_interp,
+      wsp<double>(P, P->r_part), wsp<uint32_t>(P, P->r_subbin), wsp<uint32_t>(P, P->r_subfirst),
+      wsp<uint32_t>(P, P->r_binstart), wsp<uint32_t>(P, P->r_substart) + P->nbins_total, wm0, wm1,
+      pitch, slack, win_floats, wsp<int>(P, P->r_err), vout);
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+template <int D, int ORD, bool GONLY>
+cudaError_t launch_direct_q(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes,
+                            void* mhat_at_x, cudaStream_t st, int nacc, int F2, float* vout,
+                            int rec, int wm0, int wm1, int pitch, int slack, int win_floats,
+                            int nw, size_t smem, unsigned grid) {
+  const int nqn = (F2 + 3) / 4;
+#define FK_Q(Q)                                                                                  \
+  return launch_direct_k<D, Q, ORD, GONLY>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, \
+                                           vout, rec, wm0, wm1, pitch, slack, win_floats, nw,     \
+                                           smem, grid)
+  if (nqn <= 2) FK_Q(2);
+  if (nqn <= 4) FK_Q(4);
+  if (nqn <= 6) FK_Q(6);
+  if (nqn <= 8) FK_Q(8);
+  if (nqn <= 10) FK_Q(10);
+  if (nqn <= 12) FK_Q(12);
+  FK_Q(16);
+#undef FK_Q
+}
+
+}  // namespace
+
+// Launch the persistent kernel if it applies (FP32, width 7, 1-D / 2-D,
+// F2 <= 64, two windows fit shared memory); *launched says whether it ran.
+cudaError_t run_interp_direct(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes,
+                              void* mhat_at_x, cudaStream_t st, int nacc, int F2, void* vout,
+                              bool* launched) {
+  *launched = false;
+  const int D = P->d;
+  if (P->prec != FKREG_F32 || P->geo.w != 7 || D > 2 || F2 > 64 || P->n == 0) return cudaSuccess;
+  if (!vout && P->order > 1) return cudaSuccess;
+  const BwDev& B = P->bw[b];
+  const int rec = t2_record_stride(F2);
+  const int wm0 = tma_window(P->geo, B, 0);
+  const int wm1 = D > 1 ? tma_window(P->geo, B, 1) : 1;
+  if (wm0 > B.nf[0] || (D > 1 && wm1 > B.nf[1])) return cudaSuccess;
+  const int pitch = D > 1 ? wm1 * rec + 4 : wm0 * rec;
+  const int win_floats = ((D > 1 ? wm0 : 1) * pitch + 31) / 32 * 32;
+  const int slack = std::max(tma_slack(P->geo, B, 0), D > 1 ? tma_slack(P->geo, B, 1) : 0);
+  const size_t budget = 225 * 1024;
+  const size_t wins = 2 * sizeof(float) * size_t(win_floats);
+  const size_t per_warp = sizeof(double) * nacc;
+  if (wins + per_warp * 8 > budget) return cudaSuccess;
+  const int nw = int(std::min<size_t>(kLWarps, (budget - wins) / std::max<size_t>(per_warp, 1)));
+  const size_t smem = wins + per_warp * size_t(nw);
+  const unsigned grid = unsigned(std::min<int64_t>(152, std::max<int64_t>(1, P->nsub_max)));
+  float* vo = static_cast<float*>(vout);
+  *launched = true;
+#define FK_A(DD, OO, GG)                                                                        \
+  return launch_direct_q<DD, OO, GG>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, vo,  \
+                                     rec, wm0, wm1, pitch, slack, win_floats, nw, smem, grid)
+  if (vout) {
+    if (D == 1) FK_A(1, 0, true);
+    FK_A(2, 0, true);
+  }
+  if (D == 1) {
+    if (P->order == 0) FK_A(1, 0, false);
+    FK_A(1, 1, false);
+  }
+  if (P->order == 0) FK_A(2, 0, false);
+  FK_A(2, 1, false);
+#undef FK_A
+}
+
+}  // namespace fk
