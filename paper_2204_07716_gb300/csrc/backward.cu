@@ -195,6 +195,175 @@ adjoint_kernel(MonoTab mono, const BwDev* __restrict__ bwt, int b, int order, in
   }
 }
 
+// Index of the s-field of the monomial product z^(e_i + e_j) for the
+// local-linear unknowns i, j (0 = intercept, k >= 1 = z_(k-1)) in the graded
+// order of the s-fields (1, z_1..z_D, then z_u z_v, u <= v, lexicographic).
+template <int D>
+__host__ __device__ constexpr int sidx(int i, int j) {
+  return i == 0 ? j
+                : (j == 0 ? i
+                          : 1 + D + (i <= j ? (i - 1) * D - (i - 1) * (i - 2) / 2 + (j - i)
+                                            : (j - 1) * D - (j - 1) * (j - 2) / 2 + (i - j)));
+}
+
+// Inverse of the scaled normal matrix (p <= 3) in FP32: cofactors by Kahan's
+// difference of products, the determinant by a compensated dot product
+// (the same arithmetic as the at-sample solve).  Returns false if singular.
+template <int P>
+__device__ __forceinline__ bool sym_inverse_f32(const float (&m)[P][P], float (&inv)[P][P]) {
+  if (P == 1) {
+    inv[0][0] = 1.0f / m[0][0];
+    return m[0][0] > 0.f;
+  } else if (P == 2) {
+    const float det = dop(m[0][0], m[1][1], m[0][1], m[0][1]);
+    if (!(det > 0.f)) return false;
+    const float r = 1.0f / det;
+    inv[0][0] = m[1][1] * r;
+    inv[1][1] = m[0][0] * r;
+    inv[0][1] = inv[1][0] = -m[0][1] * r;
+    return isfinite(inv[0][0]);
+  } else {
+    const float c00 = dop(m[1][1], m[2][2], m[1][2], m[1][2]);
+    const float c01 = dop(m[1][2], m[0][2], m[0][1], m[2][2]);
+    const float c02 = dop(m[0][1], m[1][2], m[1][1], m[0][2]);
+    const float c11 = dop(m[0][0], m[2][2], m[0][2], m[0][2]);
+    const float c12 = dop(m[0][1], m[0][2], m[0][0], m[1][2]);
+    const float c22 = dop(m[0][0], m[1][1], m[0][1], m[0][1]);
+    const float p0 = __fmul_rn(m[0][0], c00), r0 = fmaf(m[0][0], c00, -p0);
+    const float m1 = __fmul_rn(m[0][1], c01), r1 = fmaf(m[0][1], c01, -m1);
+    const float m2 = __fmul_rn(m[0][2], c02), r2 = fmaf(m[0][2], c02, -m2);
+    float q1, q2;
+    const float p1 = two_sum(p0, m1, q1);
+    const float p2 = two_sum(p1, m2, q2);
+    const float det = __fadd_rn(p2, __fadd_rn(__fadd_rn(r0, r1), __fadd_rn(__fadd_rn(q1, r2), q2)));
+    if (!(det > 0.f)) return false;
+    const float r = 1.0f / det;
+    inv[0][0] = c00 * r;
+    inv[1][1] = c11 * r;
+    inv[2][2] = c22 * r;
+    inv[0][1] = inv[1][0] = c01 * r;
+    inv[0][2] = inv[2][0] = c02 * r;
+    inv[1][2] = inv[2][1] = c12 * r;
+    return isfinite(inv[0][0]);
+  }
+}
+
+// FP32 form of adjoint_kernel for 1-D / 2-D systems known at compile time
+// (NW: p = 1; local linear: p = D + 1).  Same quantities; FP32 per sample
+// (the FP64 pipe is a small fraction of the FP32 rate on this part), FP64
+// for the block sums of the bandwidth gradient.
+template <int D, int ORD>
+__global__ void __launch_bounds__(kE1Threads)
+adjoint_f32_kernel(const BwDev* __restrict__ bwt, int b, int64_t n, int F2, int n_probes,
+                   const float* __restrict__ V, const float* __restrict__ str,
+                   const double* __restrict__ sums, int nacc, const double* __restrict__ sc,
+                   float* __restrict__ qbar, float* __restrict__ dxt, float* __restrict__ dye,
+                   double* __restrict__ part) {
+  constexpr int P = ORD == 0 ? 1 : D + 1;
+  constexpr int NS = ORD == 0 ? 1 : (D + 1) * (D + 2) / 2;
+  __shared__ double red[kE1Threads / 32][3];
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool valid = s < n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const BwDev& B = bwt[b];
+  float dth[3] = {0.f, 0.f, 0.f};
+  if (valid) {
+    const double* sb = sums + int64_t(b) * nacc;
+    const float L_rss = float(sc[0]), L_trn = float(sc[1]);
+    float dsc[P];
+    dsc[0] = 1.f;
+#pragma unroll
+    for (int k = 1; k < P; ++k) dsc[k] = float(1.0 / B.sigma[k - 1]);
+    float sv[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) sv[k] = V[int64_t(k) * n + s];
+    float m[P][P], mi[P][P];
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+      for (int j = 0; j < P; ++j) m[i][j] = sv[sidx<D>(i, j)] * (dsc[i] * dsc[j]);
+    const bool ok = sym_inverse_f32<P>(m, mi);
+    float Sinv[P][P];
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+      for (int j = 0; j < P; ++j) Sinv[i][j] = ok ? mi[i][j] * (dsc[i] * dsc[j]) : 0.f;
+    float a[P], bbar[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      a[i] = Sinv[i][0];
+      bbar[i] = 0.f;
+    }
+    float dx_t[3] = {0.f, 0.f, 0.f};
+    const int R = 1 + n_probes;
+    for (int r = 0; r < R; ++r) {
+      float t[P];
+#pragma unroll
+      for (int k = 0; k < P; ++k) t[k] = V[int64_t(NS + r * P + k) * n + s];
+      float mh = 0.f;
+#pragma unroll
+      for (int k = 0; k < P; ++k) mh += a[k] * t[k];
+      const float c = str[int64_t(1 + r) * n + s];
+      float gr;
+      if (r == 0) {
+        gr = -2.f * L_rss * (c - mh);
+        dye[s] = ok ? 2.f * L_rss * (c - mh) : 0.f;
+      } else {
+        gr = L_trn * c / float(sb[1 + n_probes + (r - 1)]);
+      }
+      if (!ok) gr = 0.f;
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        float beta = 0.f;
+#pragma unroll
+        for (int k = 0; k < P; ++k) beta += Sinv[i][k] * t[k];
+        bbar[i] += gr * beta;
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int f = NS + r * P + k;
+        const float q = gr * a[k];
+        qbar[int64_t(f) * n + s] = q;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          dx_t[d] += q * V[(int64_t(1 + d) * F2 + f) * n + s];
+          dth[d] += q * V[(int64_t(1 + D + d) * F2 + f) * n + s];
+        }
+      }
+    }
+    // s-field adjoints: -sum_(a+b=g) a_a bbar_b over ordered pairs
+    float qs[NS];
+#pragma unroll
+    for (int g = 0; g < NS; ++g) qs[g] = 0.f;
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+      for (int j = 0; j < P; ++j) qs[sidx<D>(i, j)] -= a[i] * bbar[j];
+#pragma unroll
+    for (int g = 0; g < NS; ++g) {
+      qbar[int64_t(g) * n + s] = qs[g];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        dx_t[d] += qs[g] * V[(int64_t(1 + d) * F2 + g) * n + s];
+        dth[d] += qs[g] * V[(int64_t(1 + D + d) * F2 + g) * n + s];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) dxt[int64_t(d) * n + s] = dx_t[d];
+  }
+  for (int d = 0; d < 3; ++d) {
+    double v = double(dth[d]);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][d] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int wv = 0; wv < kE1Threads / 32; ++wv) t += red[wv][threadIdx.x];
+    part[int64_t(blockIdx.x) * 3 + threadIdx.x] = t;
+  }
+}
+
 // Combine: dy_i = adjoint y-field + explicit term; dx_(i,d) = sum over
 // strength classes c of c_(c,i) * adjoint field (c, d) + target-side term.
 // Outputs in the original sample order.
@@ -255,6 +424,26 @@ static cudaError_t adjoint_t(fkreg_plan_s* P, int b, int n_probes, cudaStream_t 
   T* qbar = wsp<T>(P, P->r_str) + int64_t(P->smax) * P->n;
   T* dxt = wsp<T>(P, P->r_bdx);
   T* dye = dxt + int64_t(P->d) * P->n;
+  if constexpr (sizeof(T) == 4) {
+    if (P->d <= 2 || P->order == 0) {
+#define FK_F(DD, OO)                                                                            \
+  adjoint_f32_kernel<DD, OO><<<blocks, kE1Threads, 0, st>>>(                                    \
+      wsp<BwDev>(P, P->r_bw), b, P->n, F2, n_probes, wsp<float>(P, P->r_bV),                   \
+      wsp<float>(P, P->r_str), sums, nacc, wsp<double>(P, P->r_bsc), qbar, dxt, dye,           \
+      wsp<double>(P, P->r_bpart))
+      if (P->order == 0) {
+        if (P->d == 1) FK_F(1, 0);
+        else if (P->d == 2) FK_F(2, 0);
+        else FK_F(3, 0);
+      } else {
+        if (P->d == 1) FK_F(1, 1);
+        else FK_F(2, 1);
+      }
+#undef FK_F
+      P->launches += 1;
+      return cudaGetLastError();
+    }
+  }
 #define FK_A(DD)                                                                              \
   adjoint_kernel<T, DD><<<blocks, kE1Threads, 0, st>>>(                                       \
       P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, F2, n_probes, wsp<T>(P, P->r_bV),  \
