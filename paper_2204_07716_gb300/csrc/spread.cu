@@ -411,7 +411,7 @@ cudaError_t launch_spread_run(fkreg_plan_s* P, int s0, cudaStream_t st) {
 
 // Strengths go in launches of 8, 4, 2 or 1 (compile-time chunk sizes, as
 // many as the shared-memory budget allows per launch); FP32 1-D / 2-D plans
-// of width 7 use the run kernel in launches of up to 16.
+// of width 7 use the run kernel in launches of 16, 12, 8, 4, 2 or 1.
 template <typename T, int D, int W>
 cudaError_t launch_spread_w(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
   const GeoDev& g = P->geo;
@@ -427,6 +427,9 @@ cudaError_t launch_spread_w(fkreg_plan_s* P, int s0, int scount, cudaStream_t st
         if (rem >= 16) {
           e = launch_spread_run<D, 16>(P, s0 + done, st);
           used = 16;
+        } else if (rem >= 12) {
+          e = launch_spread_run<D, 12>(P, s0 + done, st);
+          used = 12;
         } else if (rem >= 8) {
           e = launch_spread_run<D, 8>(P, s0 + done, st);
           used = 8;
