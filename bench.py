@@ -47,10 +47,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="ll2d",
-                    choices=["ll2d", "nw1d", "nw3d_df", "ll2d_gcv", "uneven"],
+                    choices=["ll2d", "nw1d", "nw3d_df", "ll2d_gcv", "uneven",
+                             "ll2d_plain64", "ll2d_plain32"],
                     help="ll2d is the headline line; the others measure the remaining "
                          "configurations (1-D NW FP64, 3-D NW + DF sweep, 2-D LL GCV "
-                         "forward + backward, 64 uneven problems in one graph)")
+                         "forward + backward, 64 uneven problems in one graph) and the "
+                         "plain single-response form of the ll2d step (FP64 or FP32: "
+                         "one smooth call per response / probe, no stacking)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="sample-count multiplier for the extra workloads (1 = full size)")
     return ap.parse_args()
@@ -408,6 +411,30 @@ def run_extra(args):
                "n_total": sum(w.n for w in ws), "problems": len(ws),
                "dims": [w.d for w in ws].count(2), "graph": "one captured CUDA graph"}
         dtype = "f32+f64solve"
+    elif wl in ("ll2d_plain64", "ll2d_plain32"):
+        # the ll2d step without stacking: y and each of the 10 probes is its
+        # own smooth call (one response per launch chain), then the variance
+        prec = "f64" if wl == "ll2d_plain64" else "f32"
+        w = inputs.ll2d(n=int(1_000_000 * sc))
+        np_ = 10
+        dt = torch.float32 if prec == "f32" else torch.float64
+        plan = fkreg.Plan(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, n_rhs=1,
+                          tol=w.tol, precision=prec, device=dev)
+        x = torch.tensor(w.x, dtype=dt, device=dev)
+        ys = [torch.tensor(w.y[0], dtype=dt, device=dev)] + \
+             [torch.tensor(z, dtype=dt, device=dev)
+              for z in inputs.gaussian_probes(np_, w.n, inputs.SEED_BASE + 99)]
+
+        def step(k):
+            plan.set_points(x)
+            outs = [plan.smooth(yr, want=("mhat_grid", "mask", "mhat_at_x")) for yr in ys]
+            plan.variance(ys[0], outs[0]["mhat_at_x"])
+        units = w.n * (1 + np_ + 1)
+        cfg = {"workload": f"ll2d-1M-256sq-LL-plain-{prec}-1rhs-per-call-tol1e-6",
+               "n": w.n, "grid": list(w.grid_n), "responses_per_call": 1,
+               "calls_per_step": 1 + np_, "geometry": plan.geom}
+        dtype = "f64" if prec == "f64" else "f32+f64solve"
+        extra["plan"] = plan
     else:
         if wl == "nw1d":
             w = inputs.nw1d(n=int(10_000 * sc))

@@ -2,12 +2,16 @@
 //
 // fine_s[m] = sum_i c_{s,i} prod_j phi(m_j - u_ij),  u_ij = (x_ij - lo_j) nf_j / P_j,
 // periodic in m_j (mod nf_j).  One CTA owns one sub-problem: up to kSubMax
-// sorted samples of one bin.  Each thread takes one sample at a time and adds
-// its w^d window into a shared-memory copy of the bin's tile plus a halo of
-// ceil(w/2) cells per side (shared-memory atomics); the CTA then adds the tile
-// to the fine grid in global memory with one atomic per non-zero cell.
-// Strengths go in chunks that fit the shared-memory budget.  W > 0 fixes the
-// width at compile time (unrolled window, weights in registers).
+// sorted samples of one bin, accumulated into a shared-memory copy of the
+// bin's tile plus a halo of ceil(w/2) cells per side; the CTA then adds the
+// tile to the fine grid in global memory with one atomic per non-zero cell.
+// Two kernels fill the tile.  1-D and 2-D plans of a compile-time width use
+// spread_run_kernel: the lanes of a warp cover the window cells and sum runs
+// of consecutive samples that share a window (the sort puts them together)
+// in registers before one shared-memory atomic per cell and strength.  3-D
+// and runtime widths use spread_kernel: each thread adds one sample's w^d
+// window at a time.  Strengths go in chunks that fit the shared-memory
+// budget.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -230,9 +234,6 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
   using A = typename TileAcc<T>::type;
   __shared__ T s_scale[kMaxChunk2], s_inv[kMaxChunk2];
   __shared__ T s_red[NWARP][kMaxChunk2];
-  __shared__ __align__(16) T s_str[NWARP][32][CN];
-  __shared__ T s_phi[NWARP][32][PS];
-  __shared__ int s_org[NWARP][32];
   A* sm = reinterpret_cast<A*>(smem_raw);
   const uint32_t k = blockIdx.x;
   if (k >= *sub_total) return;
@@ -255,6 +256,13 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
     W3[j] = int(g.tile[j]) + 2 * g.pad;
   }
   const int cells = W3[0] * W3[1];
+  // per-warp staging rows after the tile: strengths [32][CN], kernel values
+  // [32][PS], window origins [32]
+  const size_t tile_bytes = (size_t(CN) * cells * sizeof(A) + 15) / 16 * 16;
+  T* str_rows = reinterpret_cast<T*>(smem_raw + tile_bytes) + warp * 32 * CN;
+  T* phi_rows = reinterpret_cast<T*>(smem_raw + tile_bytes) + NWARP * 32 * CN + warp * 32 * PS;
+  int* org_row = reinterpret_cast<int*>(reinterpret_cast<T*>(smem_raw + tile_bytes) +
+                                        NWARP * 32 * (CN + PS)) + warp * 32;
   const T beta = T(g.beta);
   const T halfw = T(0.5) * T(W);
   const int64_t fine_cells = g.nf[0] * g.nf[1] * g.nf[2];
@@ -309,11 +317,11 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
         org = j == 0 ? l : org * W3[1] + l;
         const T off = f0 - u;
 #pragma unroll
-        for (int t = 0; t < W; ++t) s_phi[warp][lane][j * W + t] = phi<T>(g.skind, W, beta, off + T(t));
+        for (int t = 0; t < W; ++t) phi_rows[lane * PS + j * W + t] = phi<T>(g.skind, W, beta, off + T(t));
       }
-      s_org[warp][lane] = org;
+      org_row[lane] = org;
 #pragma unroll
-      for (int c = 0; c < CN; ++c) s_str[warp][lane][c] = str[int64_t(s0 + c) * n + p] * s_scale[c];
+      for (int c = 0; c < CN; ++c) str_rows[lane * CN + c] = str[int64_t(s0 + c) * n + p] * s_scale[c];
     }
     __syncwarp();
     T acc[CS][CN];
@@ -321,9 +329,9 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
     for (int a = 0; a < CS; ++a)
 #pragma unroll
       for (int c = 0; c < CN; ++c) acc[a][c] = T(0);
-    int cur = s_org[warp][0];
+    int cur = org_row[0];
     for (int j = 0; j < cnt; ++j) {
-      const int org = s_org[warp][j];
+      const int org = org_row[j];
       if (org != cur) {
 #pragma unroll
         for (int a = 0; a < CS; ++a)
@@ -335,10 +343,10 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
             }
         cur = org;
       }
-      const T* ph = s_phi[warp][j];
+      const T* ph = phi_rows + j * PS;
       T cv[CN];
 #pragma unroll
-      for (int c = 0; c < CN; ++c) cv[c] = s_str[warp][j][c];
+      for (int c = 0; c < CN; ++c) cv[c] = str_rows[j * CN + c];
 #pragma unroll
       for (int a = 0; a < CS; ++a) {
         const int ci = lane + 32 * a;
@@ -389,65 +397,83 @@ cudaError_t launch_spread_cn(fkreg_plan_s* P, int s0, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int D, int CN>
-cudaError_t launch_spread_run(fkreg_plan_s* P, int s0, cudaStream_t st) {
-  const GeoDev& g = P->geo;
+// Shared memory of one run-kernel block: the tile for CN strengths plus the
+// per-warp staging rows.
+template <typename T, int D, int W, int CN>
+size_t spread_run_smem(const GeoDev& g) {
+  using A = typename TileAcc<T>::type;
   int cells = 1;
   for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
-  const size_t smem = size_t(cells) * sizeof(int) * CN;
-  if (smem > 160 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(spread_run_kernel<float, D, 7, CN>,
+  const size_t tile_bytes = (size_t(CN) * cells * sizeof(A) + 15) / 16 * 16;
+  return tile_bytes + size_t(kSpreadThreads) * (CN + D * W + 1) * sizeof(T) +
+         size_t(kSpreadThreads) * sizeof(int);
+}
+
+template <typename T, int D, int W, int CN>
+cudaError_t launch_spread_run(fkreg_plan_s* P, int s0, cudaStream_t st) {
+  const GeoDev& g = P->geo;
+  const size_t smem = spread_run_smem<T, D, W, CN>(g);
+  if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(spread_run_kernel<T, D, W, CN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const unsigned grid = unsigned(P->nsub_max);
   const uint32_t* sub_total = wsp<uint32_t>(P, P->r_substart) + P->nbins_total;
-  spread_run_kernel<float, D, 7, CN><<<grid, kSpreadThreads, smem, st>>>(
-      g, P->n, wsp<float>(P, P->r_xs), wsp<float>(P, P->r_str), s0, wsp<uint32_t>(P, P->r_subbin),
+  spread_run_kernel<T, D, W, CN><<<grid, kSpreadThreads, smem, st>>>(
+      g, P->n, wsp<T>(P, P->r_xs), wsp<T>(P, P->r_str), s0, wsp<uint32_t>(P, P->r_subbin),
       wsp<uint32_t>(P, P->r_subfirst), wsp<uint32_t>(P, P->r_binstart), sub_total,
-      wsp<float>(P, P->r_fine));
+      wsp<T>(P, P->r_fine));
   P->launches += 1;
   return cudaGetLastError();
 }
 
+// All strengths through the run kernel in launches of the largest chunk
+// sizes that fit shared memory (FP32: 16, 12, 8, 4, 2, 1; FP64: 4, 2, 1).
+template <typename T, int D, int W>
+cudaError_t launch_spread_runs(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
+  int done = 0;
+  while (done < scount) {
+    const int rem = scount - done;
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    int used = 0;
+    if constexpr (sizeof(T) == 4) {
+      if (rem >= 16 && spread_run_smem<T, D, W, 16>(P->geo) <= 220 * 1024) {
+        e = launch_spread_run<T, D, W, 16>(P, s0 + done, st);
+        used = 16;
+      } else if (rem >= 12 && spread_run_smem<T, D, W, 12>(P->geo) <= 220 * 1024) {
+        e = launch_spread_run<T, D, W, 12>(P, s0 + done, st);
+        used = 12;
+      } else if (rem >= 8 && spread_run_smem<T, D, W, 8>(P->geo) <= 220 * 1024) {
+        e = launch_spread_run<T, D, W, 8>(P, s0 + done, st);
+        used = 8;
+      }
+    }
+    if (!used) {
+      if (rem >= 4 && spread_run_smem<T, D, W, 4>(P->geo) <= 220 * 1024) {
+        e = launch_spread_run<T, D, W, 4>(P, s0 + done, st);
+        used = 4;
+      } else if (rem >= 2 && spread_run_smem<T, D, W, 2>(P->geo) <= 220 * 1024) {
+        e = launch_spread_run<T, D, W, 2>(P, s0 + done, st);
+        used = 2;
+      } else {
+        e = launch_spread_run<T, D, W, 1>(P, s0 + done, st);
+        used = 1;
+      }
+    }
+    if (e != cudaSuccess) return e;
+    done += used;
+  }
+  return cudaSuccess;
+}
+
 // Strengths go in launches of 8, 4, 2 or 1 (compile-time chunk sizes, as
-// many as the shared-memory budget allows per launch); FP32 1-D / 2-D plans
-// of width 7 use the run kernel in launches of 16, 12, 8, 4, 2 or 1.
+// many as the shared-memory budget allows per launch); 1-D / 2-D plans of a
+// compile-time width use the run kernel instead (launch_spread_runs).
 template <typename T, int D, int W>
 cudaError_t launch_spread_w(fkreg_plan_s* P, int s0, int scount, cudaStream_t st) {
   const GeoDev& g = P->geo;
-  if constexpr (sizeof(T) == 4 && W == 7 && D <= 2) {
-    int cells = 1;
-    for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
-    if (size_t(cells) * sizeof(int) * 16 <= 160 * 1024) {
-      int done = 0;
-      while (done < scount) {
-        const int rem = scount - done;
-        cudaError_t e;
-        int used;
-        if (rem >= 16) {
-          e = launch_spread_run<D, 16>(P, s0 + done, st);
-          used = 16;
-        } else if (rem >= 12) {
-          e = launch_spread_run<D, 12>(P, s0 + done, st);
-          used = 12;
-        } else if (rem >= 8) {
-          e = launch_spread_run<D, 8>(P, s0 + done, st);
-          used = 8;
-        } else if (rem >= 4) {
-          e = launch_spread_run<D, 4>(P, s0 + done, st);
-          used = 4;
-        } else if (rem >= 2) {
-          e = launch_spread_run<D, 2>(P, s0 + done, st);
-          used = 2;
-        } else {
-          e = launch_spread_run<D, 1>(P, s0 + done, st);
-          used = 1;
-        }
-        if (e != cudaSuccess) return e;
-        done += used;
-      }
-      return cudaSuccess;
-    }
+  if constexpr (W > 0 && D <= 2) {
+    if (spread_run_smem<T, D, W, 1>(g) <= 220 * 1024) return launch_spread_runs<T, D, W>(P, s0, scount, st);
   }
   int cells = 1;
   for (int j = 0; j < D; ++j) cells *= int(g.tile[j]) + 2 * g.pad;
