@@ -178,6 +178,11 @@ cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream
 cudaError_t run_interp_direct(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes,
                               void* mhat_at_x, cudaStream_t st, int nacc, int F2, void* vout,
                               bool* launched);
+// Lane-per-sample kernel over the global field grid (FP32, width 7, 3-D
+// Nadaraya-Watson or gather-only, F2 <= 64), launched only when it applies.
+cudaError_t run_interp_global_lane(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes,
+                                   void* mhat_at_x, cudaStream_t st, int nacc, int F2,
+                                   void* vout, bool* launched);
 cudaError_t run_loss_scalars(fkreg_plan_s* P, int b, int n_probes, cudaStream_t s);
 cudaError_t run_adjoint(fkreg_plan_s* P, int b, int n_probes, cudaStream_t s);
 cudaError_t run_combine(fkreg_plan_s* P, int n_probes, void* dy, void* dx, double* dlogh,

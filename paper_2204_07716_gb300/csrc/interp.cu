@@ -871,8 +871,10 @@ cudaError_t launch_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, v
   if (P->d * P->geo.w > 64 || P->geo.w > kMaxWRun) return cudaErrorInvalidValue;
   if (sizeof(T) == 4) {
     bool used = false;
-    const cudaError_t e =
+    cudaError_t e =
         run_interp_direct(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, nullptr, &used);
+    if (used || e != cudaSuccess) return e;
+    e = run_interp_global_lane(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, nullptr, &used);
     if (used || e != cudaSuccess) return e;
   }
   // fields per pass: 64 (float) or 32 (double)
@@ -895,7 +897,9 @@ cudaError_t launch_gather(fkreg_plan_s* P, int b, int F, T* V, cudaStream_t st) 
   if (P->d * P->geo.w > 64 || P->geo.w > kMaxWRun) return cudaErrorInvalidValue;
   if (sizeof(T) == 4) {
     bool used = false;
-    const cudaError_t e = run_interp_direct(P, b, 0, 0, nullptr, st, 0, F, V, &used);
+    cudaError_t e = run_interp_direct(P, b, 0, 0, nullptr, st, 0, F, V, &used);
+    if (used || e != cudaSuccess) return e;
+    e = run_interp_global_lane(P, b, 0, 0, nullptr, st, 0, F, V, &used);
     if (used || e != cudaSuccess) return e;
   }
   if (sizeof(T) == 4 && F > 32) {
