@@ -95,7 +95,8 @@ int64_t full_cells(const int64_t* n, int d) {
 
 namespace fk {
 
-// kind 0: forward R2C, kind 1: inverse C2R, kind 2: inverse C2R with outputs interleaved
+// kind 0: forward R2C, kind 1: inverse C2R, kind 2: inverse C2R in place whose
+// outputs exec_fft then interleaves into cell records
 fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, cufftHandle* h) {
   auto key = std::make_tuple(kind, dims[0], P->d > 1 ? dims[1] : 1, P->d > 2 ? dims[2] : 1, batch);
   auto it = P->ffts.find(key);
@@ -115,15 +116,16 @@ fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, 
   size_t work = 0;
   cufftResult r;
   if (kind == 2) {
-    // inverse transform whose outputs are interleaved per cell: element
-    // (field b, cell m) lands at m * batch + b
+    // in-place inverse transform (padded real rows of 2 (n_last/2 + 1));
+    // run_t2_interleave then builds the cell records
     long long inembed[3] = {n[0], n[1], n[2]};
     inembed[P->d - 1] = n[P->d - 1] / 2 + 1;
     long long onembed[3] = {n[0], n[1], n[2]};
+    onembed[P->d - 1] = 2 * (n[P->d - 1] / 2 + 1);
     long long idist = 1;
     for (int a = 0; a < P->d; ++a) idist *= inembed[a];
-    const long long rec = fk::t2_record_stride(batch);
-    r = cufftMakePlanMany64(hd, P->d, n, inembed, 1, idist, onembed, rec, 1, type, batch, &work);
+    r = cufftMakePlanMany64(hd, P->d, n, inembed, 1, idist, onembed, 1, 2 * idist, type, batch,
+                            &work);
   } else {
     r = cufftMakePlanMany64(hd, P->d, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &work);
   }
@@ -408,14 +410,19 @@ fkreg_status exec_fft(fkreg_plan_s* P, int kind, const int64_t* dims, int batch,
   if (st != FKREG_OK) return st;
   if (cufftSetStream(h, s) != CUFFT_SUCCESS) return plan_err(P, FKREG_ERR_CUFFT, "cufftSetStream failed");
   cufftResult r;
+  void* dst = kind == 2 ? in : out;  // kind 2 runs in place, then interleaves into out
   if (P->prec == FKREG_F32) {
-    r = kind == 0 ? cufftExecR2C(h, static_cast<cufftReal*>(in), static_cast<cufftComplex*>(out))
-                  : cufftExecC2R(h, static_cast<cufftComplex*>(in), static_cast<cufftReal*>(out));
+    r = kind == 0 ? cufftExecR2C(h, static_cast<cufftReal*>(in), static_cast<cufftComplex*>(dst))
+                  : cufftExecC2R(h, static_cast<cufftComplex*>(in), static_cast<cufftReal*>(dst));
   } else {
-    r = kind == 0 ? cufftExecD2Z(h, static_cast<cufftDoubleReal*>(in), static_cast<cufftDoubleComplex*>(out))
-                  : cufftExecZ2D(h, static_cast<cufftDoubleComplex*>(in), static_cast<cufftDoubleReal*>(out));
+    r = kind == 0 ? cufftExecD2Z(h, static_cast<cufftDoubleReal*>(in), static_cast<cufftDoubleComplex*>(dst))
+                  : cufftExecZ2D(h, static_cast<cufftDoubleComplex*>(in), static_cast<cufftDoubleReal*>(dst));
   }
   if (r != CUFFT_SUCCESS) return plan_err(P, FKREG_ERR_CUFFT, "cuFFT exec failed (" + std::to_string(int(r)) + ")");
+  if (kind == 2) {
+    const cudaError_t e = fk::run_t2_interleave(P, dims, batch, in, out, s);
+    if (e != cudaSuccess) return cuda_err(P, e, "interleave type-2 fields");
+  }
   return FKREG_OK;
 }
 

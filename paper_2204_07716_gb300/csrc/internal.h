@@ -199,6 +199,10 @@ cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out
 
 const uint32_t* perm_ptr(fkreg_plan_s* P);
 int t2_record_stride(int F2);
+// Interleave F in-place C2R outputs (padded real rows) at src into cell records
+// [cell][t2_record_stride(F)] at dst.
+cudaError_t run_t2_interleave(fkreg_plan_s* P, const int64_t* dims, int F, const void* src,
+                              void* dst, cudaStream_t st);
 
 // fft helpers (api.cu)
 fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, cufftHandle* h);

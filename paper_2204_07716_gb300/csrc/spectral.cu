@@ -186,7 +186,40 @@ __global__ void kmul_grid_kernel(GeoDev g, const BwDev* __restrict__ bwt,
   for (int f = 0; f < nfld; ++f) out[(int64_t(bb) * fgrid + fbase + f) * lhalf + j] = acc[f];
 }
 
-// Type-2 stage for one bandwidth: thread per (fine half-spectrum index, strength q).
+// base * W_f for monomial f (one field of acc_fields)
+template <typename T, typename C>
+__device__ __forceinline__ C mult_field(C base, const ModeMul<T>& m, const BwDev& B,
+                                        const MonoTab& mono, int f) {
+  const T twopi = T(6.283185307179586476925286766559);
+  const int deg = mono.e[f][0] + mono.e[f][1] + mono.e[f][2];
+  C r;
+  if (deg == 0) {
+    r = base;
+  } else if (deg == 1) {
+    const int a = mono.e[f][0] ? 0 : (mono.e[f][1] ? 1 : 2);
+    const T sc = twopi * m.hx[a];  // multiply by i * sc
+    r.x = -base.y * sc;
+    r.y = base.x * sc;
+  } else {
+    int a = -1, c = -1;
+    for (int j = 0; j < 3; ++j)
+      for (int q = 0; q < mono.e[f][j]; ++q) {
+        if (a < 0)
+          a = j;
+        else
+          c = j;
+      }
+    const T sc = T(B.H[a * 3 + c]) - twopi * twopi * m.hx[a] * m.hx[c];
+    r.x = base.x * sc;
+    r.y = base.y * sc;
+  }
+  return r;
+}
+
+// Type-2 stage for one bandwidth: thread per fine half-spectrum index; the
+// mode's multiplier and deconvolution are formed once and applied to every
+// strength (density and responses / probes).  Modes outside the kept box
+// are written as zeros.
 template <typename T, int D>
 __global__ void kmul_t2_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
                                const double* __restrict__ tab, int64_t phi1_0, int64_t phi1_1,
@@ -194,46 +227,58 @@ __global__ void kmul_t2_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
                                int64_t fine_half, int str_dens, int str_rhs, int n_rhs_str,
                                int64_t t2half, typename Cx<T>::type* __restrict__ out) {
   using C = typename Cx<T>::type;
-  const int nq = 1 + n_rhs_str;
-  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gid >= t2half * nq) return;
-  const int64_t j = gid % t2half;
-  const int q = int(gid / t2half);
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= t2half) return;
   const BwDev& B = bwt[b];
-  const bool dens = q == 0;
-  const int strength = dens ? str_dens : str_rhs + q - 1;
-  const int nfld = dens ? mono.n : mono.nt;
-  const int fbase = dens ? 0 : mono.n + (q - 1) * mono.nt;
+  const int nfields = mono.n + n_rhs_str * mono.nt;
   int64_t kk[3] = {0, 0, 0};
   bool inside = true;
   {
     int64_t rem = j;
     for (int a = D - 1; a >= 0; --a) {
       const int64_t n = (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
-      int64_t idx = rem % n;
+      const int64_t idx = rem % n;
       rem /= n;
-      int64_t k = (a == D - 1) ? idx : (idx < (B.nf[a] + 1) / 2 ? idx : idx - B.nf[a]);
+      const int64_t k = (a == D - 1) ? idx : (idx < (B.nf[a] + 1) / 2 ? idx : idx - B.nf[a]);
       kk[a] = k;
       if ((k < 0 ? -k : k) > B.K[a] / 2 - 1) inside = false;
     }
   }
-  C acc[kMaxMono];
-  for (int f = 0; f < kMaxMono; ++f) acc[f] = C{T(0), T(0)};
-  if (inside) {
-    const int64_t phi1[3] = {phi1_0, phi1_1, phi1_2};
-    T dec = T(1);
-    for (int a = 0; a < D; ++a) {
-      const int64_t ak = kk[a] < 0 ? -kk[a] : kk[a];
-      dec *= T(tab[phi1[a] + ak] * tab[B.phi2_off[a] + ak] / g.P[a]);
-    }
-    const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
-    C base = fetch_F<T, C>(g, F + int64_t(strength) * fine_half, kk, D);
-    const T s = dec * m.G;
-    base.x *= s;
-    base.y *= s;
-    acc_fields<T, C>(acc, base, m, B, mono, nfld);
+  if (!inside) {
+    for (int f = 0; f < nfields; ++f) out[int64_t(f) * t2half + j] = C{T(0), T(0)};
+    return;
   }
-  for (int f = 0; f < nfld; ++f) out[int64_t(fbase + f) * t2half + j] = acc[f];
+  const int64_t phi1[3] = {phi1_0, phi1_1, phi1_2};
+  T dec = T(1);
+  for (int a = 0; a < D; ++a) {
+    const int64_t ak = kk[a] < 0 ? -kk[a] : kk[a];
+    dec *= T(tab[phi1[a] + ak] * tab[B.phi2_off[a] + ak] / g.P[a]);
+  }
+  const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
+  const T sc = dec * m.G;
+  // index of the mode in the type-1 half spectrum (conjugate for k_last < 0)
+  const bool neg = kk[D - 1] < 0;
+  int64_t fidx = 0;
+  for (int a = 0; a < D; ++a) {
+    int64_t k = neg ? -kk[a] : kk[a];
+    const int64_t n = (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
+    if (a < D - 1) {
+      k %= g.nf[a];
+      if (k < 0) k += g.nf[a];
+    }
+    fidx = fidx * n + k;
+  }
+  for (int q = 0; q <= n_rhs_str; ++q) {
+    const int strength = q == 0 ? str_dens : str_rhs + q - 1;
+    const int nfld = q == 0 ? mono.n : mono.nt;
+    const int fbase = q == 0 ? 0 : mono.n + (q - 1) * mono.nt;
+    C base = F[int64_t(strength) * fine_half + fidx];
+    if (neg) base.y = -base.y;
+    base.x *= sc;
+    base.y *= sc;
+    for (int f = 0; f < nfld; ++f)
+      out[int64_t(fbase + f) * t2half + j] = mult_field<T, C>(base, m, B, mono, f);
+  }
 }
 
 template <typename T>
@@ -283,8 +328,7 @@ cudaError_t launch_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_r
     t2half *= (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
     fhalf *= (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
   }
-  const int64_t total = t2half * (1 + n_rhs_str);
-  const unsigned blocks = unsigned((total + 255) / 256);
+  const unsigned blocks = unsigned((t2half + 255) / 256);
   auto* F = wsp<C>(P, P->r_spec);
   auto* bwt = wsp<BwDev>(P, P->r_bw);
   auto* tab = wsp<double>(P, P->r_tab);
@@ -577,6 +621,74 @@ cudaError_t run_kmul_t2_mode(fkreg_plan_s* P, int b, int str_dens, int str_rhs, 
 cudaError_t run_kmul_adj(fkreg_plan_s* P, int b, int sb, int n_classes, cudaStream_t st) {
   return P->prec == FKREG_F32 ? launch_adj<float>(P, b, sb, n_classes, st)
                               : launch_adj<double>(P, b, sb, n_classes, st);
+}
+
+}  // namespace fk
+
+// ---- interleave the type-2 fields into cell records ----------------------------
+// The inverse FFT of the type-2 spectra runs in place (cuFFT's padded real
+// layout: field f, row r, column i at f * 2 t2half + r * 2 (n_last/2 + 1) + i),
+// which is over twice as fast on large 3-D grids as writing strided records
+// directly.  This kernel then gathers the fields of 32 cells at a time through
+// shared memory into the record layout [cell][rec] that the interpolation
+// reads (coalesced reads along cells, coalesced writes along records).
+namespace fk {
+namespace {
+
+template <typename T>
+__global__ void t2_interleave_kernel(const T* __restrict__ src, int64_t cells, int64_t nlast,
+                                     int64_t row_pitch, int64_t fdist, int F, int rec,
+                                     T* __restrict__ dst) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);  // [F][33]
+  const int64_t c0 = int64_t(blockIdx.x) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int nty = blockDim.x >> 5;
+  const int64_t c = c0 + tx;
+  if (c < cells) {
+    const int64_t off = (c / nlast) * row_pitch + c % nlast;
+    for (int f = ty; f < F; f += nty) tile[f * 33 + tx] = src[int64_t(f) * fdist + off];
+  }
+  __syncthreads();
+  const int ncell = int(min(int64_t(32), cells - c0));
+  for (int idx = threadIdx.x; idx < ncell * F; idx += blockDim.x) {
+    const int i = idx / F, f = idx - i * F;
+    dst[(c0 + i) * rec + f] = tile[f * 33 + i];
+  }
+}
+
+}  // namespace
+
+cudaError_t run_t2_interleave(fkreg_plan_s* P, const int64_t* dims, int F, const void* src,
+                              void* dst, cudaStream_t st) {
+  const int D = P->d;
+  int64_t cells = 1, rows = 1;
+  for (int a = 0; a < D; ++a) cells *= dims[a];
+  for (int a = 0; a < D - 1; ++a) rows *= dims[a];
+  const int64_t nlast = dims[D - 1];
+  const int64_t row_pitch = 2 * (nlast / 2 + 1);
+  const int64_t fdist = rows * row_pitch;
+  const int rec = t2_record_stride(F);
+  if (cells == 0 || F == 0) return cudaSuccess;
+  const unsigned blocks = unsigned((cells + 31) / 32);
+  const size_t smem = size_t(F) * 33 * P->tsize;
+  if (P->prec == FKREG_F32) {
+    cudaError_t e = cudaFuncSetAttribute(t2_interleave_kernel<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    t2_interleave_kernel<float><<<blocks, 256, smem, st>>>(static_cast<const float*>(src), cells,
+                                                           nlast, row_pitch, fdist, F, rec,
+                                                           static_cast<float*>(dst));
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(t2_interleave_kernel<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    t2_interleave_kernel<double><<<blocks, 256, smem, st>>>(static_cast<const double*>(src), cells,
+                                                            nlast, row_pitch, fdist, F, rec,
+                                                            static_cast<double*>(dst));
+  }
+  P->launches += 1;
+  return cudaGetLastError();
 }
 
 }  // namespace fk
