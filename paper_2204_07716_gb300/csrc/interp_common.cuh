@@ -112,6 +112,15 @@ __device__ __forceinline__ void issue_window_copies(const T* __restrict__ fld, i
 }
 
 // ---- lane-per-sample gathers (FP32, fixed width) ----------------------------
+// acc += w * v on four fields with two packed FP32 FMAs (one issue slot per
+// pair of fields; per-component results equal fmaf).
+__device__ __forceinline__ void quad_fma(float4& acc, float w, const float4& v) {
+  const float2 w2 = make_float2(w, w);
+  const float2 lo = __ffma2_rn(w2, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+  const float2 hi = __ffma2_rn(w2, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
+  acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 template <int D, int W, int NQ>
 __device__ __forceinline__ void lane_gather_smem(const float* base, int rec, int pitch, int nq,
                                                  int skind, float beta, float off0,
@@ -125,10 +134,7 @@ __device__ __forceinline__ void lane_gather_smem(const float* base, int rec, int
       for (int q = 0; q < NQ; ++q)
         if (q < nq) {
           const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
-          acc[q].x += wgt * v.x;
-          acc[q].y += wgt * v.y;
-          acc[q].z += wgt * v.z;
-          acc[q].w += wgt * v.w;
+          quad_fma(acc[q], wgt, v);
         }
     }
   } else {
@@ -144,10 +150,7 @@ __device__ __forceinline__ void lane_gather_smem(const float* base, int rec, int
         for (int q = 0; q < NQ; ++q)
           if (q < nq) {
             const float4 v = *reinterpret_cast<const float4*>(cell + 4 * q);
-            acc[q].x += wgt * v.x;
-            acc[q].y += wgt * v.y;
-            acc[q].z += wgt * v.z;
-            acc[q].w += wgt * v.w;
+            quad_fma(acc[q], wgt, v);
           }
       }
     }
@@ -174,10 +177,7 @@ __device__ __forceinline__ void lane_gather_global(const float* __restrict__ fld
       for (int q = 0; q < NQ; ++q)
         if (q < nq) {
           const float4 v = __ldg(reinterpret_cast<const float4*>(cell + 4 * q));
-          acc[q].x += wgt * v.x;
-          acc[q].y += wgt * v.y;
-          acc[q].z += wgt * v.z;
-          acc[q].w += wgt * v.w;
+          quad_fma(acc[q], wgt, v);
         }
     }
   }

@@ -99,10 +99,7 @@ interp_global_lane_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_
           for (int q = 0; q < NQ; ++q)
             if (q < nqd) {
               const float4 v = __ldg(reinterpret_cast<const float4*>(cell + 4 * q));
-              acc[q].x += wgt * v.x;
-              acc[q].y += wgt * v.y;
-              acc[q].z += wgt * v.z;
-              acc[q].w += wgt * v.w;
+              quad_fma(acc[q], wgt, v);
             }
         }
       }

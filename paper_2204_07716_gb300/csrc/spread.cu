@@ -353,8 +353,20 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
         const int t0 = D == 2 ? ci / W : ci, t1 = D == 2 ? ci % W : 0;
         T wa = T(0);
         if (act[a]) wa = D == 2 ? ph[t0] * ph[W + t1] : ph[t0];
+        if constexpr (sizeof(T) == 4 && CN % 2 == 0) {
+          // two strengths per packed FP32 FMA
+          const float2 w2 = make_float2(wa, wa);
 #pragma unroll
-        for (int c = 0; c < CN; ++c) acc[a][c] += wa * cv[c];
+          for (int c = 0; c < CN; c += 2) {
+            const float2 r = __ffma2_rn(w2, make_float2(cv[c], cv[c + 1]),
+                                        make_float2(acc[a][c], acc[a][c + 1]));
+            acc[a][c] = r.x;
+            acc[a][c + 1] = r.y;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < CN; ++c) acc[a][c] += wa * cv[c];
+        }
       }
     }
 #pragma unroll
