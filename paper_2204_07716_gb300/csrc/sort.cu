@@ -49,7 +49,6 @@ template <typename T>
 __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                 uint32_t* __restrict__ counts, int* __restrict__ errw) {
-  // counts == nullptr: the caller counts with bin_count_shared
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t bin = 0, local = 0;
@@ -78,16 +77,43 @@ __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
   if (counts) atomicAdd(&counts[bin], 1u);
 }
 
-// Bin counts through a per-block shared-memory histogram (few bins: the
-// global counters would otherwise see heavy contention).
-__global__ void bin_count_shared(const uint32_t* __restrict__ keys, int64_t n, int64_t nbins,
-                                 int kbits, uint32_t* __restrict__ counts) {
+// Keys and bin counts in one pass for plans with few bins: grid-stride
+// blocks count into a shared-memory histogram and add it to the global
+// counters once per block (few global atomics, no contention).
+template <typename T>
+__global__ void bin_keys_hist_kernel(GeoDev g, int64_t n, int64_t nbins, const T* __restrict__ x,
+                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                     uint32_t* __restrict__ counts, int* __restrict__ errw) {
   extern __shared__ uint32_t h[];
   for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
   __syncthreads();
+  const T halfw = T(0.5) * T(g.w);
+  bool bad = false;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += int64_t(gridDim.x) * blockDim.x)
-    atomicAdd(&h[keys[i] >> kbits], 1u);
+       i += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t bin = 0, local = 0;
+    for (int j = 0; j < g.d; ++j) {
+      T xv = x[i * g.d + j];
+      const T lo = T(g.lo[j]), hi = T(g.hi[j]);
+      if (!(xv >= lo && xv <= hi)) {
+        bad = true;
+        xv = lo;
+      }
+      const T u = mul_rn(sub_rn(xv, lo), inv_h_of<T>(g, j));
+      int64_t c = int64_t(floor(u));
+      if (c < 0) c = 0;
+      if (c > g.nf[j] - 1) c = g.nf[j] - 1;
+      const int64_t b = c / g.tile[j];
+      int64_t e = int64_t(ceil(sub_rn(u, halfw))) + g.w / 2 - b * g.tile[j];
+      e = e < 0 ? 0 : (e > g.tile[j] ? g.tile[j] : e);
+      bin = bin * uint32_t(g.nbins[j]) + uint32_t(b);
+      local = local * uint32_t(g.tile[j] + 1) + uint32_t(e);
+    }
+    keys[i] = g.kbits ? (bin << g.kbits) | local : bin;
+    vals[i] = uint32_t(i);
+    atomicAdd(&h[bin], 1u);
+  }
+  if (bad) atomicOr(errw, 1);
   __syncthreads();
   for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x)
     if (h[b]) atomicAdd(&counts[b], h[b]);
@@ -267,10 +293,52 @@ __global__ void fill_sub_kernel(const uint32_t* __restrict__ bin_start, int64_t 
   }
 }
 
+// Exclusive scan by one block of 1024 threads (short arrays such as the bin
+// counts, at most 4 elements per thread): each thread sums a contiguous chunk, the
+// block scans the chunk sums, and each thread writes its chunk's prefixes.
+// in may alias out.
+__global__ void __launch_bounds__(1024) scan_one_block(const uint32_t* in, int64_t n,
+                                                       uint32_t* out) {
+  __shared__ uint32_t wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t chunk = (n + 1023) / 1024;
+  const int64_t b0 = min(n, int64_t(tid) * chunk), b1 = min(n, b0 + chunk);
+  uint32_t t = 0;
+  for (int64_t i = b0; i < b1; ++i) t += in[i];
+  uint32_t inc = t;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    wsum[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = (warp > 0 ? wsum[warp - 1] : 0u) + inc - t;
+  for (int64_t i = b0; i < b1; ++i) {
+    const uint32_t v = in[i];
+    out[i] = run;
+    run += v;
+  }
+  if (tid == 1023) out[n] = wsum[31];
+}
+
 // exclusive scan of in[0..n) into out[0..n], out[n] = total
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* scratch,
                            cudaStream_t s, int64_t* launches) {
   if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+  if (n <= 4096) {
+    *launches += 1;
+    scan_one_block<<<1, 1024, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+  }
   *launches += 3;
   const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
   scan_block_sums<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, scratch);
@@ -297,21 +365,24 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
   if (n > 0) {
     const unsigned blocks = unsigned((n + 255) / 256);
     const bool shared_hist = nbins <= 8192;
-    uint32_t* gcounts = shared_hist ? nullptr : counts;
-    if (P->prec == FKREG_F32)
+    if (shared_hist) {
+      const unsigned hb = unsigned(std::min<int64_t>((n + 2047) / 2048, 152 * 4));
+      const size_t hs = sizeof(uint32_t) * nbins;
+      if (P->prec == FKREG_F32)
+        bin_keys_hist_kernel<float><<<hb, 512, hs, s>>>(g, n, nbins, static_cast<const float*>(x),
+                                                        keys0, vals0, counts, errw);
+      else
+        bin_keys_hist_kernel<double><<<hb, 512, hs, s>>>(g, n, nbins, static_cast<const double*>(x),
+                                                         keys0, vals0, counts, errw);
+    } else if (P->prec == FKREG_F32) {
       bin_keys_kernel<float><<<blocks, 256, 0, s>>>(g, n, static_cast<const float*>(x), keys0, vals0,
-                                                    gcounts, errw);
-    else
+                                                    counts, errw);
+    } else {
       bin_keys_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), keys0,
-                                                     vals0, gcounts, errw);
+                                                     vals0, counts, errw);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     P->launches += 1;
-    if (shared_hist) {
-      const unsigned hb = unsigned(std::min<int64_t>((n + 4095) / 4096, 152 * 4));
-      bin_count_shared<<<hb, 512, sizeof(uint32_t) * nbins, s>>>(keys0, n, nbins, g.kbits, counts);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      P->launches += 1;
-    }
   }
   // radix passes over the significant bits of the key
   int bits = g.kbits;
