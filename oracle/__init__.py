@@ -241,6 +241,26 @@ def variance_pass(x: np.ndarray, y: np.ndarray, mhat_at_x: np.ndarray,
     return smooth_at(x, r, H, order, q, nthreads)["mhat"]
 
 
+def log_variance(x: np.ndarray, y: np.ndarray, mhat_at_x: np.ndarray, H: np.ndarray,
+                 q: np.ndarray, order: int = 1, nthreads: int = 0) -> dict:
+    """Log-variance estimator of Sec. 3 (eqs. 24-26), real responses.
+
+    r_i = (y_i - mhat(x_i))^2; v is the local-polynomial smooth of
+    log(r_i + 1/N) (eq. 25), evaluated at the query points q and at the
+    samples; kappa = [mean_i r_i exp(-v(x_i))]^-1; sigma^2(q) = exp(v(q)) /
+    kappa (eq. 26).  Returns v_grid [nq, nrhs], v_at_x [n, nrhs], kappa [nrhs]
+    and sigma2 [nq, nrhs].
+    """
+    x = _c64(x)
+    n = x.shape[0]
+    r = (np.atleast_2d(y) - np.atleast_2d(mhat_at_x)) ** 2
+    ell = np.log(r + 1.0 / n)
+    v_grid = smooth_at(x, ell, H, order, q, nthreads)["mhat"]
+    v_x = smooth_at(x, ell, H, order, x, nthreads)["mhat"]
+    kappa = 1.0 / np.mean(r.T * np.exp(-v_x), axis=0)
+    return {"v_grid": v_grid, "v_at_x": v_x, "kappa": kappa, "sigma2": np.exp(v_grid) / kappa}
+
+
 def get_hlist(n: int, lo: float, hi: float, spacing: str = "log") -> np.ndarray:
     """Bandwidth candidates of Sec. 4 (get_hList): n values from lo to hi.
 

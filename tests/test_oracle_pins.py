@@ -251,6 +251,35 @@ def test_variance_pass_reproduces_constant_and_linear_residuals():
     np.testing.assert_allclose(v[:, 0], 0.5 + q[:, 0] - 0.25 * q[:, 1], rtol=1e-10)
 
 
+def test_log_variance_closed_forms():
+    # eqs. 24-26 on residuals with known structure
+    rng = np.random.default_rng(6)
+    n = 80
+    x = rng.random((n, 2))
+    q = rng.random((12, 2))
+    H = np.diag([0.1 ** 2, 0.12 ** 2])
+    y = rng.standard_normal(n)
+    # constant squared residual c: v = log(c + 1/N), kappa = (c + 1/N) / c,
+    # sigma^2 = c exactly
+    c = 0.09
+    m = y - 0.3 * np.sign(rng.standard_normal(n))
+    out = oracle.log_variance(x, y[None], m[None], H, q)
+    np.testing.assert_allclose(out["v_grid"][:, 0], np.log(c + 1.0 / n), rtol=1e-12)
+    assert out["kappa"][0] == pytest.approx((c + 1.0 / n) / c, rel=1e-12)
+    np.testing.assert_allclose(out["sigma2"][:, 0], c, rtol=1e-12)
+    # log(r + 1/N) linear in x: local linear reproduces v at q and at the
+    # samples, so kappa = 1 / (1 - mean(exp(-v_i)) / N)
+    def v_true(p):
+        return -1.0 + 0.8 * p[:, 0] - 0.5 * p[:, 1]
+    r = np.exp(v_true(x)) - 1.0 / n
+    out = oracle.log_variance(x, np.sqrt(r)[None], np.zeros((1, n)), H, q)
+    np.testing.assert_allclose(out["v_grid"][:, 0], v_true(q), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(out["v_at_x"][:, 0], v_true(x), rtol=1e-10, atol=1e-12)
+    kappa = 1.0 / (1.0 - np.mean(np.exp(-v_true(x))) / n)
+    assert out["kappa"][0] == pytest.approx(kappa, rel=1e-12)
+    np.testing.assert_allclose(out["sigma2"][:, 0], np.exp(v_true(q)) / kappa, rtol=1e-10)
+
+
 def test_kde_integrates_to_one():
     # eq. 8: s_0 / N is a density (Gaussian K has unit mass)
     rng = np.random.default_rng(3)
