@@ -255,6 +255,29 @@ fkreg_status fkreg_variance(fkreg_plan plan, const void* y_dev, const void* mhat
                             void* sigma2_grid_dev, void* stream);
 
 /*
+ * Log-variance estimator of Sec. 3 (eqs. 24-26), for real responses:
+ *   l_i      = log(r_i + 1/N),  r_i = (y_i - mhat(x_i))^2         (eq. 25)
+ *   v(q)     = the plan's local-polynomial smooth of l at q        (eq. 25)
+ *   kappa    = [ (1/N) sum_i r_i exp(-v(x_i)) ]^-1
+ *   sigma2(q)= exp(v(q)) / kappa > 0                               (eq. 26)
+ * with bandwidth b's residuals smoothed with bandwidth b and the s-field
+ * spectrum of the last fkreg_smooth / fkreg_df on these points reused.
+ *   y_dev           [n_rhs][n] responses (plan precision, original order)
+ *   mhat_at_x_dev   [n_bw][n_rhs][n] that call's mhat_at_x output
+ *   v_grid_dev      out [n_bw][n_rhs][M]: v on the grid (NaN where masked)
+ *   v_at_x_dev      out [n_bw][n_rhs][n]: v at the samples (original order)
+ *   kappa_dev       out [n_bw][n_rhs] FP64
+ *   sigma2_grid_dev out [n_bw][n_rhs][M] or NULL
+ * All pointers but sigma2_grid_dev are required; n >= 1.  Complex
+ * responses return FKREG_ERR_UNSUPPORTED.  The call overwrites the plan's
+ * internal strength, field and partial-sum buffers (not the caller's
+ * outputs of earlier calls).
+ */
+fkreg_status fkreg_log_variance(fkreg_plan plan, const void* y_dev, const void* mhat_at_x_dev,
+                                void* v_grid_dev, void* v_at_x_dev, double* kappa_dev,
+                                void* sigma2_grid_dev, void* stream);
+
+/*
  * Gradient of GCV (eq. 22) for bandwidth b, with the Monte-Carlo trace of
  * Sec. 2.1 over n_probes fixed probes (given, or drawn as in fkreg_df from
  * seed), with respect to the log bandwidths, the responses and the samples.

@@ -624,6 +624,69 @@ fkreg_status fkreg_variance(fkreg_plan P, const void* y, const void* mhat_at_x, 
   return FKREG_OK;
 }
 
+fkreg_status fkreg_log_variance(fkreg_plan P, const void* y, const void* mhat_at_x, void* v_grid,
+                                void* v_at_x, double* kappa, void* sigma2, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (!P->dens_valid)
+    return plan_err(P, FKREG_ERR_STATE, "fkreg_log_variance must follow fkreg_smooth/fkreg_df on the same points");
+  if (P->o.y_complex)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_log_variance takes real responses");
+  if (P->n < 1) return plan_err(P, FKREG_ERR_INVALID_ARG, "fkreg_log_variance needs at least one sample");
+  if (!y || !mhat_at_x || !v_grid || !v_at_x || !kappa)
+    return plan_err(P, FKREG_ERR_INVALID_ARG, "y, mhat_at_x, v_grid, v_at_x and kappa are required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d = P->d;
+  const int64_t nf_cells = full_cells(P->g.nf, d), nf_half = half_cells(P->g.nf, d);
+  const int R = P->nrhs;
+  const int f2 = P->ns + R * P->nt;
+  for (int b = 0; b < P->nbw; ++b) {
+    {
+      FK_STAGE(FKREG_STAGE_STRENGTHS);
+      FK_CHECK(fk::run_logres_strengths(P, y, mhat_at_x, b, 1, s), "log residuals");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_SPREAD);
+      FK_CHECK(fk::run_spread(P, 1, R, s), "spread");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_FFT_FWD);
+      FK_STATUS(exec_fft(P, 0, P->g.nf, R, P->ws + P->r_fine.off + P->tsize * nf_cells,
+                         P->ws + P->r_spec.off + 2 * P->tsize * nf_half, s));
+    }
+    {
+      FK_STAGE(FKREG_STAGE_KMUL_GRID);
+      FK_CHECK(fk::run_kmul_grid(P, 0, 1, R, b, 1, P->ws + P->r_gspec.off, s), "kmul grid");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_FFT_GRID);
+      FK_STATUS(exec_fft(P, 1, P->g.ldft, P->ns + R * P->nt, P->ws + P->r_gspec.off,
+                         P->ws + P->r_gfield.off, s));
+    }
+    {
+      FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+      FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, v_grid, s), "grid solve");
+    }
+    // v at the samples: type-2 of the same fields
+    {
+      FK_STAGE(FKREG_STAGE_KMUL_T2);
+      FK_CHECK(fk::run_kmul_t2(P, b, 0, 1, R, s), "kmul type-2");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_FFT_T2);
+      FK_STATUS(exec_fft(P, 2, P->bw[b].nf, f2, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
+    }
+    {
+      FK_STAGE(FKREG_STAGE_INTERP);
+      FK_CHECK(fk::run_interp(P, b, R, 0, y, v_at_x, s), "interpolation");
+    }
+    {
+      FK_STAGE(FKREG_STAGE_FINALIZE);
+      FK_CHECK(fk::run_kappa_sigma2(P, b, y, mhat_at_x, v_at_x, v_grid, kappa, sigma2, s), "kappa");
+    }
+  }
+  return FKREG_OK;
+}
+
 fkreg_status fkreg_set_timing(fkreg_plan P, int enable) {
   if (!P) return FKREG_ERR_INVALID_ARG;
   P->timing = enable != 0;

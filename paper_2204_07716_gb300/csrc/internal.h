@@ -160,6 +160,8 @@ cudaError_t run_gather_strengths(fkreg_plan_s* P, const void* y, int first_str, 
                                  cudaStream_t s);
 cudaError_t run_residual_strengths(fkreg_plan_s* P, const void* y, const void* mhat_at_x,
                                    int b, int first_str, cudaStream_t s);
+cudaError_t run_logres_strengths(fkreg_plan_s* P, const void* y, const void* mhat_at_x, int b,
+                                 int first_str, cudaStream_t s);
 
 // spectral.cu
 cudaError_t run_kmul_grid(fkreg_plan_s* P, int str_dens, int str_rhs, int nrhs_fields,
@@ -196,6 +198,11 @@ cudaError_t run_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, cons
                        void* mhat_at_x, cudaStream_t s);
 cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out,
                          cudaStream_t s);
+// kappa (eq. 26 normaliser) of bandwidth b for every response, and
+// sigma2(g) = exp(v(g)) / kappa when sigma2 != NULL.
+cudaError_t run_kappa_sigma2(fkreg_plan_s* P, int b, const void* y, const void* mhat_at_x,
+                             const void* v_at_x, const void* v_grid, double* kappa, void* sigma2,
+                             cudaStream_t s);
 
 const uint32_t* perm_ptr(fkreg_plan_s* P);
 int t2_record_stride(int F2);

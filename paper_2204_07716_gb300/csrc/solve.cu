@@ -175,3 +175,101 @@ cudaError_t run_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int nrhs
 }
 
 }  // namespace fk
+
+// ---- log-variance estimator (Sec. 3, eqs. 24-26) ------------------------------
+// kappa_r = [ (1/N) sum_i r_i exp(-v_r(x_i)) ]^-1 with r_i = (y_ri - mhat_r(x_i))^2,
+// then sigma2_r(g) = exp(v_r(g)) / kappa_r on the grid.  Block partial sums in
+// FP64, summed in a fixed order (deterministic).
+namespace fk {
+namespace {
+
+template <typename T>
+__global__ void kappa_partial_kernel(int64_t n, int n_rhs, int b, const T* __restrict__ y,
+                                     const T* __restrict__ mh, const T* __restrict__ v,
+                                     double* __restrict__ part) {
+  __shared__ double red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < n_rhs; ++r) {
+    double t = 0.0;
+    const T* yr = y + int64_t(r) * n;
+    const T* mr = mh + (int64_t(b) * n_rhs + r) * n;
+    const T* vr = v + (int64_t(b) * n_rhs + r) * n;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+      const T d = yr[i] - mr[i];
+      t += double(d * d * exp(-vr[i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
+      part[int64_t(blockIdx.x) * n_rhs + r] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void kappa_finish_kernel(const double* __restrict__ part, int nblk, int n_rhs, int b,
+                                    int64_t n, double* __restrict__ kappa) {
+  __shared__ double sh[256];
+  const int r = blockIdx.x;
+  double t = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) t += part[int64_t(k) * n_rhs + r];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) kappa[int64_t(b) * n_rhs + r] = double(n) / sh[0];
+}
+
+template <typename T>
+__global__ void sigma2_from_v_kernel(int64_t Mtot, int n_rhs, int b, const T* __restrict__ v,
+                                     const double* __restrict__ kappa, T* __restrict__ sigma2) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= Mtot * n_rhs) return;
+  const int r = int(gid / Mtot);
+  const int64_t o = int64_t(b) * n_rhs * Mtot + gid;
+  sigma2[o] = T(double(exp(v[o])) / kappa[int64_t(b) * n_rhs + r]);
+}
+
+}  // namespace
+
+cudaError_t run_kappa_sigma2(fkreg_plan_s* P, int b, const void* y, const void* mhat_at_x,
+                             const void* v_at_x, const void* v_grid, double* kappa, void* sigma2,
+                             cudaStream_t st) {
+  const int R = P->nrhs;
+  const int nblk = 512;
+  double* part = wsp<double>(P, P->r_part);
+  int64_t Mtot = 1;
+  for (int a = 0; a < 3; ++a) Mtot *= P->geo.M[a];
+  const unsigned gb = unsigned((Mtot * R + 255) / 256);
+  if (P->prec == FKREG_F32) {
+    kappa_partial_kernel<float><<<nblk, 256, 0, st>>>(P->n, R, b, static_cast<const float*>(y),
+                                                      static_cast<const float*>(mhat_at_x),
+                                                      static_cast<const float*>(v_at_x), part);
+  } else {
+    kappa_partial_kernel<double><<<nblk, 256, 0, st>>>(P->n, R, b, static_cast<const double*>(y),
+                                                       static_cast<const double*>(mhat_at_x),
+                                                       static_cast<const double*>(v_at_x), part);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  kappa_finish_kernel<<<R, 256, 0, st>>>(part, nblk, R, b, P->n, kappa);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (sigma2) {
+    if (P->prec == FKREG_F32)
+      sigma2_from_v_kernel<float><<<gb, 256, 0, st>>>(Mtot, R, b, static_cast<const float*>(v_grid),
+                                                      kappa, static_cast<float*>(sigma2));
+    else
+      sigma2_from_v_kernel<double><<<gb, 256, 0, st>>>(Mtot, R, b, static_cast<const double*>(v_grid),
+                                                       kappa, static_cast<double*>(sigma2));
+  }
+  P->launches += sigma2 ? 3 : 2;
+  return cudaGetLastError();
+}
+
+}  // namespace fk

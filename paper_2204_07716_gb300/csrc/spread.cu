@@ -617,6 +617,22 @@ __global__ void residual_strengths_kernel(int64_t n, const uint32_t* __restrict_
   }
 }
 
+// l_i = log(|y_i - mhat_b(x_i)|^2 + 1/N) for every real response (eq. 25),
+// sorted order.
+template <typename T>
+__global__ void logres_strengths_kernel(int64_t n, const uint32_t* __restrict__ perm,
+                                        const T* __restrict__ y, const T* __restrict__ mh,
+                                        int n_rhs, int b, T* __restrict__ str, int first) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t i = perm[s];
+  const T inv_n = T(1) / T(n);
+  for (int r = 0; r < n_rhs; ++r) {
+    const T dr = y[int64_t(r) * n + i] - mh[(int64_t(b) * n_rhs + r) * n + i];
+    str[int64_t(first + r) * n + s] = log(dr * dr + inv_n);
+  }
+}
+
 }  // namespace
 
 const uint32_t* perm_ptr(fkreg_plan_s* P) {
@@ -663,6 +679,27 @@ cudaError_t run_residual_strengths(fkreg_plan_s* P, const void* y, const void* m
     residual_strengths_kernel<double><<<blocks, 256, 0, st>>>(
         P->n, perm, static_cast<const double*>(y), static_cast<const double*>(mhat_at_x), P->nrhs,
         P->o.y_complex, b, wsp<double>(P, P->r_str), first_str);
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace fk
+
+namespace fk {
+
+cudaError_t run_logres_strengths(fkreg_plan_s* P, const void* y, const void* mhat_at_x, int b,
+                                 int first_str, cudaStream_t st) {
+  if (P->n == 0) return cudaSuccess;
+  const unsigned blocks = unsigned((P->n + 255) / 256);
+  const uint32_t* perm = perm_ptr(P);
+  if (P->prec == FKREG_F32)
+    logres_strengths_kernel<float><<<blocks, 256, 0, st>>>(
+        P->n, perm, static_cast<const float*>(y), static_cast<const float*>(mhat_at_x), P->nrhs,
+        b, wsp<float>(P, P->r_str), first_str);
+  else
+    logres_strengths_kernel<double><<<blocks, 256, 0, st>>>(
+        P->n, perm, static_cast<const double*>(y), static_cast<const double*>(mhat_at_x), P->nrhs,
+        b, wsp<double>(P, P->r_str), first_str);
   P->launches += 1;
   return cudaGetLastError();
 }

@@ -29,7 +29,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA"
 
 EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
-           "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_variance", "fkreg_set_timing",
+           "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_variance",
+           "fkreg_log_variance", "fkreg_set_timing",
            "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
            "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
@@ -97,6 +98,7 @@ def load():
     L.fkreg_smooth.argtypes = [vp, vp, ctypes.POINTER(Outputs), vp]
     L.fkreg_df.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(Outputs), vp]
     L.fkreg_variance.argtypes = [vp, vp, vp, vp, vp]
+    L.fkreg_log_variance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.fkreg_backward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.c_int, vp, vp,
                                  vp, vp, vp]
     L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
@@ -394,6 +396,28 @@ class Plan:
                                           ctypes.c_void_p(mh.data_ptr()),
                                           ctypes.c_void_p(out.data_ptr()), self._stream()))
         self._y_keep = (y, mh)
+        return out
+
+    def log_variance(self, y, mhat_at_x, want_sigma2=True):
+        """Log-variance estimator (eqs. 24-26): v on the grid and at the samples,
+        kappa per bandwidth and response, and sigma^2 = exp(v) / kappa on the grid."""
+        t = self.torch
+        y = self._y(y)
+        mh = self._as_dev(mhat_at_x)
+        v_grid = t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
+        v_x = t.empty((self.n_bw, self.n_rhs, self.n), dtype=self.dtype, device=self.device)
+        kappa = t.empty((self.n_bw, self.n_rhs), dtype=t.float64, device=self.device)
+        s2 = (t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
+              if want_sigma2 else None)
+        self._check(self.L.fkreg_log_variance(
+            self.h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(mh.data_ptr()),
+            ctypes.c_void_p(v_grid.data_ptr()), ctypes.c_void_p(v_x.data_ptr()),
+            ctypes.c_void_p(kappa.data_ptr()),
+            ctypes.c_void_p(s2.data_ptr() if s2 is not None else 0), self._stream()))
+        self._y_keep = (y, mh)
+        out = {"v_grid": v_grid, "v_at_x": v_x, "kappa": kappa}
+        if s2 is not None:
+            out["sigma2"] = s2
         return out
 
 

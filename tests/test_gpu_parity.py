@@ -317,6 +317,43 @@ def test_variance_pass():
     assert mhat_error(s2[0, 0].cpu().numpy(), ro[:, 0], s0, ar, valid) < 1e-10
 
 
+@pytest.mark.parametrize("d,order,prec,tol,bar", [(1, 1, "f64", 1e-12, 1e-10),
+                                                  (2, 1, "f64", 1e-12, 1e-10),
+                                                  (2, 0, "f64", 1e-12, 1e-10),
+                                                  (2, 1, "f32", 1e-6, 1e-5)])
+def test_log_variance(d, order, prec, tol, bar):
+    # eqs. 24-26 against the oracle, with the device's mhat(x_i) as the
+    # common input so the comparison isolates the log-variance step
+    grid = {1: 100, 2: 24}[d]
+    w = inputs.random_small(71 + d + 3 * order, d, 3000, grid, order, [0.05], precision=prec,
+                            tol=tol)
+    p = plan_for(w)
+    p.set_points(torch.tensor(w.x))
+    out = p.smooth(torch.tensor(w.y), want=("mhat_at_x",))
+    lv = p.log_variance(torch.tensor(w.y), out["mhat_at_x"])
+    p.sync()
+    x, y = as_seen(w)
+    mh = out["mhat_at_x"][0, 0].cpu().numpy().astype(np.float64)
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    ro = oracle.log_variance(x, y, mh[None], w.H[0], gp, order=order)
+    ell = np.log((y[0] - mh) ** 2 + 1.0 / w.n)
+    s0 = oracle.moment_sums(x, np.ones((1, w.n)), w.H[0], 0, gp)[:, 0, 0]
+    al = oracle.scale_field(x, ell[None], w.H[0], gp)[:, 0]
+    valid = s0 >= 2e-3 * s0.max()
+    vg = lv["v_grid"][0, 0].cpu().numpy().reshape(-1)
+    assert mhat_error(vg, ro["v_grid"][:, 0], s0, al, valid) < bar
+    sx = oracle.moment_sums(x, np.ones((1, w.n)), w.H[0], 0, x)[:, 0, 0]
+    alx = oracle.scale_field(x, ell[None], w.H[0], x)[:, 0]
+    vx = lv["v_at_x"][0, 0].cpu().numpy()
+    assert mhat_error(vx, ro["v_at_x"][:, 0], sx, alx) < bar
+    kappa = lv["kappa"][0, 0].item()
+    assert kappa == pytest.approx(ro["kappa"][0], rel=10 * bar)
+    s2 = lv["sigma2"][0, 0].cpu().numpy().reshape(-1)
+    ok = valid & np.isfinite(s2)
+    np.testing.assert_allclose(s2[ok], np.exp(vg[ok]) / kappa, rtol=1e-5 if prec == "f32" else 1e-12)
+    assert np.all(s2[ok] > 0)
+
+
 # ------------------------------------------------------------ edge cases ----
 def test_empty_and_single_sample():
     w = inputs.random_small(80, 2, 1, 20, 0, [0.1], precision="f64", tol=1e-12)
