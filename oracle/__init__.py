@@ -261,6 +261,20 @@ def log_variance(x: np.ndarray, y: np.ndarray, mhat_at_x: np.ndarray, H: np.ndar
     return {"v_grid": v_grid, "v_at_x": v_x, "kappa": kappa, "sigma2": np.exp(v_grid) / kappa}
 
 
+def interval(mhat: np.ndarray, var: np.ndarray, alpha: float = 0.05):
+    """Pointwise interval of eq. 28: mhat -/+ z_(1 - alpha/2) sqrt(var).
+
+    z is the standard normal quantile (scipy's ppf); var is the variance
+    estimate the caller supplies (NaN where it is negative or not finite).
+    """
+    from scipy.stats import norm
+    z = norm.ppf(1.0 - 0.5 * alpha)
+    v = np.asarray(var, dtype=np.float64)
+    sd = np.where(v >= 0, np.sqrt(np.where(v >= 0, v, 0.0)), np.nan)
+    m = np.asarray(mhat, dtype=np.float64)
+    return m - z * sd, m + z * sd
+
+
 def get_hlist(n: int, lo: float, hi: float, spacing: str = "log") -> np.ndarray:
     """Bandwidth candidates of Sec. 4 (get_hList): n values from lo to hi.
 

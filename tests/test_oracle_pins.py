@@ -280,6 +280,19 @@ def test_log_variance_closed_forms():
     np.testing.assert_allclose(out["sigma2"][:, 0], np.exp(v_true(q)) / kappa, rtol=1e-10)
 
 
+def test_interval_eq28():
+    # 95 % two-sided normal quantile is the textbook 1.959963984540054; a
+    # 68.27 % interval is one standard deviation wide on each side
+    lo, hi = oracle.interval(np.array([1.0, -2.0]), np.array([4.0, 0.25]), 0.05)
+    np.testing.assert_allclose(hi - np.array([1.0, -2.0]), 1.959963984540054 * np.array([2.0, 0.5]),
+                               rtol=1e-14)
+    np.testing.assert_allclose(lo + hi, 2 * np.array([1.0, -2.0]), rtol=1e-15)
+    lo, hi = oracle.interval(np.zeros(1), np.ones(1), 1 - 0.6826894921370859)
+    assert hi[0] == pytest.approx(1.0, rel=1e-12)
+    lo, hi = oracle.interval(np.zeros(1), -np.ones(1), 0.05)
+    assert np.isnan(lo[0]) and np.isnan(hi[0])
+
+
 def test_kde_integrates_to_one():
     # eq. 8: s_0 / N is a density (Gaussian K has unit mass)
     rng = np.random.default_rng(3)
