@@ -278,6 +278,19 @@ fkreg_status fkreg_log_variance(fkreg_plan plan, const void* y_dev, const void* 
                                 void* sigma2_grid_dev, void* stream);
 
 /*
+ * Pointwise 100(1 - alpha) % interval of eq. 28: lower/upper =
+ * mhat -/+ z_(1 - alpha/2) sqrt(var), z the standard normal quantile, for
+ * count elements (any layout; typically a grid estimate and the variance
+ * estimate of fkreg_variance or fkreg_log_variance, or a scalar variance
+ * broadcast by the caller).  A negative or NaN variance gives NaN bounds.
+ * precision FKREG_F32 / FKREG_F64 is the element type of all four arrays.
+ * 0 < alpha < 1, else FKREG_ERR_INVALID_ARG.  No plan is needed.
+ */
+fkreg_status fkreg_interval(int precision, int64_t count, const void* mhat_dev,
+                            const void* var_dev, double alpha, void* lower_dev, void* upper_dev,
+                            void* stream);
+
+/*
  * Gradient of GCV (eq. 22) for bandwidth b, with the Monte-Carlo trace of
  * Sec. 2.1 over n_probes fixed probes (given, or drawn as in fkreg_df from
  * seed), with respect to the log bandwidths, the responses and the samples.

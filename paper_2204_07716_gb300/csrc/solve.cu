@@ -273,3 +273,45 @@ cudaError_t run_kappa_sigma2(fkreg_plan_s* P, int b, const void* y, const void* 
 }
 
 }  // namespace fk
+
+// ---- pointwise interval (Sec. 4.2, eq. 28) -------------------------------------
+namespace fk {
+namespace {
+
+template <typename T>
+__global__ void interval_kernel(int64_t count, const T* __restrict__ mhat, const T* __restrict__ var,
+                                double alpha, T* __restrict__ lower, T* __restrict__ upper) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const T z = T(normcdfinv(1.0 - 0.5 * alpha));  // z_(1 - alpha/2)
+  const T v = var[i];
+  const T sd = v >= T(0) ? sqrt(v) : T(__longlong_as_double(0x7ff8000000000000LL));
+  lower[i] = mhat[i] - z * sd;
+  upper[i] = mhat[i] + z * sd;
+}
+
+}  // namespace
+}  // namespace fk
+
+extern "C" fkreg_status fkreg_interval(int precision, int64_t count, const void* mhat_dev,
+                                       const void* var_dev, double alpha, void* lower_dev,
+                                       void* upper_dev, void* stream) {
+  using namespace fk;
+  if (precision != FKREG_F32 && precision != FKREG_F64) return FKREG_ERR_INVALID_ARG;
+  if (count < 0 || !(alpha > 0.0 && alpha < 1.0)) return FKREG_ERR_INVALID_ARG;
+  if (count == 0) return FKREG_OK;
+  if (!mhat_dev || !var_dev || !lower_dev || !upper_dev) return FKREG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned blocks = unsigned((count + 255) / 256);
+  if (precision == FKREG_F32)
+    interval_kernel<float><<<blocks, 256, 0, s>>>(count, static_cast<const float*>(mhat_dev),
+                                                  static_cast<const float*>(var_dev), alpha,
+                                                  static_cast<float*>(lower_dev),
+                                                  static_cast<float*>(upper_dev));
+  else
+    interval_kernel<double><<<blocks, 256, 0, s>>>(count, static_cast<const double*>(mhat_dev),
+                                                   static_cast<const double*>(var_dev), alpha,
+                                                   static_cast<double*>(lower_dev),
+                                                   static_cast<double*>(upper_dev));
+  return cudaGetLastError() == cudaSuccess ? FKREG_OK : FKREG_ERR_CUDA;
+}

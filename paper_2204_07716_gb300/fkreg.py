@@ -30,7 +30,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA"
 EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
            "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_variance",
-           "fkreg_log_variance", "fkreg_set_timing",
+           "fkreg_log_variance", "fkreg_interval", "fkreg_set_timing",
            "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
            "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
@@ -99,6 +99,7 @@ def load():
     L.fkreg_df.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(Outputs), vp]
     L.fkreg_variance.argtypes = [vp, vp, vp, vp, vp]
     L.fkreg_log_variance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fkreg_interval.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_double, vp, vp, vp]
     L.fkreg_backward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.c_int, vp, vp,
                                  vp, vp, vp]
     L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
@@ -419,6 +420,26 @@ class Plan:
         if s2 is not None:
             out["sigma2"] = s2
         return out
+
+
+def interval(mhat, var, alpha: float = 0.05):
+    """Pointwise interval of eq. 28 on device tensors of one dtype (float32 or
+    float64): returns (lower, upper) = mhat -/+ z_(1-alpha/2) sqrt(var)."""
+    import torch
+    L = load()
+    m = mhat.contiguous()
+    v = var.to(m.dtype).contiguous()
+    if v.shape != m.shape:
+        v = v.expand(m.shape).contiguous()
+    lo, hi = torch.empty_like(m), torch.empty_like(m)
+    prec = FKREG_F32 if m.dtype == torch.float32 else FKREG_F64
+    st = L.fkreg_interval(prec, m.numel(), ctypes.c_void_p(m.data_ptr()),
+                          ctypes.c_void_p(v.data_ptr()), float(alpha),
+                          ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(hi.data_ptr()),
+                          ctypes.c_void_p(torch.cuda.current_stream(m.device).cuda_stream))
+    if st != 0:
+        raise FkregError(f"fkreg_interval: {STATUS.get(st, st)}")
+    return lo, hi
 
 
 class Batch:

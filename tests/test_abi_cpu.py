@@ -73,6 +73,10 @@ def test_invalid_arguments_are_reported(lib):
         fkreg.geometry(**opts(grid_n=(1, 256)))
     with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
         fkreg.geometry(**opts(tol=0.5))
+    # the interval refuses alpha outside (0, 1) and bad precisions before any launch
+    L = fkreg.load()
+    for prec, alpha in ((0, 0.0), (0, 1.0), (1, -0.1), (7, 0.05)):
+        assert L.fkreg_interval(prec, 4, None, None, alpha, None, None, None) == 1
 
 
 @pytest.mark.parametrize("kind", ["es", "gauss"])

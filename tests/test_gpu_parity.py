@@ -354,6 +354,30 @@ def test_log_variance(d, order, prec, tol, bar):
     assert np.all(s2[ok] > 0)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_interval_eq28(prec):
+    # eq. 28 on the grid estimate and the log-variance sigma^2 of one smooth
+    w = inputs.random_small(77, 2, 3000, 20, 1, [0.06], precision=prec,
+                            tol=1e-12 if prec == "f64" else 1e-6)
+    p = plan_for(w)
+    p.set_points(torch.tensor(w.x))
+    out = p.smooth(torch.tensor(w.y), want=("mhat_grid", "mhat_at_x"))
+    s2 = p.log_variance(torch.tensor(w.y), out["mhat_at_x"])["sigma2"]
+    from paper_2204_07716_gb300.fkreg import interval
+    for alpha in (0.05, 0.2):
+        lo, hi = interval(out["mhat_grid"], s2, alpha)
+        p.sync()
+        lo_o, hi_o = oracle.interval(out["mhat_grid"].cpu().numpy(), s2.cpu().numpy(), alpha)
+        rt = 1e-13 if prec == "f64" else 2e-6
+        np.testing.assert_allclose(lo.cpu().numpy(), lo_o, rtol=rt, atol=rt, equal_nan=True)
+        np.testing.assert_allclose(hi.cpu().numpy(), hi_o, rtol=rt, atol=rt, equal_nan=True)
+    # a scalar variance (homoscedastic model) broadcast over the grid
+    lo, hi = interval(out["mhat_grid"], torch.tensor(0.04, dtype=out["mhat_grid"].dtype,
+                                                     device=out["mhat_grid"].device), 0.05)
+    np.testing.assert_allclose((hi - lo).cpu().numpy(), 2 * 1.959963984540054 * 0.2,
+                               rtol=1e-6 if prec == "f32" else 1e-14)
+
+
 # ------------------------------------------------------------ edge cases ----
 def test_empty_and_single_sample():
     w = inputs.random_small(80, 2, 1, 20, 0, [0.1], precision="f64", tol=1e-12)
