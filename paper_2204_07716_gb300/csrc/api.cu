@@ -533,6 +533,8 @@ fkreg_status fkreg_backward(fkreg_plan P, const void* y, int n_probes, uint64_t 
     return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward supports one real response");
   if (P->o.flags & FKREG_GCV_EXACT_TRACE)
     return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward differentiates the Monte-Carlo trace");
+  if (P->order > 1)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward supports orders 0 and 1");
   if (n_probes < 1 || n_probes > P->max_probes)
     return plan_err(P, FKREG_ERR_INVALID_ARG, "n_probes must lie in [1, max_probes]");
   if (b < 0 || b >= P->nbw) return plan_err(P, FKREG_ERR_INVALID_ARG, "bandwidth index out of range");

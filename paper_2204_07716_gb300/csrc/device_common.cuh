@@ -112,7 +112,9 @@ __device__ __forceinline__ bool lpr_weights(const MonoTab& mono, int p, const do
   return solve_e1(p, S, a);
 }
 
-// Same result with closed forms for p <= 3 (one division); isg = 1 / sigma.
+// Same result with closed forms for Nadaraya-Watson and local linear in 1-D
+// and 2-D (one division); isg = 1 / sigma.  Other systems (local linear in
+// 3-D, local quadratic) go through elimination.
 __device__ __forceinline__ bool lpr_weights_fast(const MonoTab& mono, int p, const double* s,
                                                  const double* sigma, const double* isg,
                                                  double a[kMaxP]) {
@@ -120,7 +122,7 @@ __device__ __forceinline__ bool lpr_weights_fast(const MonoTab& mono, int p, con
     a[0] = 1.0 / s[0];
     return s[0] > 0.0;
   }
-  if (p == 2) {  // 1-D local linear
+  if (p == 2 && mono.n == 3) {  // 1-D local linear
     const double s01 = s[1] * isg[0], s11 = s[2] * (isg[0] * isg[0]);
     const double det = s[0] * s11 - s01 * s01;
     if (!(det > 0.0)) return false;
@@ -129,7 +131,7 @@ __device__ __forceinline__ bool lpr_weights_fast(const MonoTab& mono, int p, con
     a[1] = -s01 * inv;
     return isfinite(a[0]);
   }
-  if (p == 3) {  // 2-D local linear, s-fields 1, z1, z2, z1z1, z1z2, z2z2
+  if (p == 3 && mono.n == 6) {  // 2-D local linear, s-fields 1, z1, z2, z1z1, z1z2, z2z2
     const double h0 = isg[0], h1 = isg[1];
     const double s00 = s[0], s01 = s[1] * h0, s02 = s[2] * h1;
     const double s11 = s[3] * (h0 * h0), s12 = s[4] * (h0 * h1), s22 = s[5] * (h1 * h1);

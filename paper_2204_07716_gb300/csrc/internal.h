@@ -15,8 +15,8 @@
 namespace fk {
 
 constexpr int kMaxD = 3;
-constexpr int kMaxMono = 10;     // monomials of degree <= 2 in 3-D
-constexpr int kMaxP = 4;         // unknowns of the local-linear system in 3-D
+constexpr int kMaxMono = 35;     // monomials of degree <= 4 in 3-D (s-fields of local quadratic)
+constexpr int kMaxP = 10;        // unknowns of the local-quadratic system in 3-D
 constexpr int kSubMax = 1024;    // samples per spreading sub-problem
 constexpr int kRadixBits = 8;
 

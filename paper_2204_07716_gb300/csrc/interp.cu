@@ -159,7 +159,7 @@ __device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mo
   if (pass == 0) {
     bool ok = false;
     T a0 = T(0);
-    if (sizeof(T) == 4 && c.p <= 3) {
+    if (sizeof(T) == 4 && c.p <= 3 && c.order <= 1) {
       float a[kMaxP] = {0.f, 0.f, 0.f, 0.f};
       float dsc[3];
 #pragma unroll

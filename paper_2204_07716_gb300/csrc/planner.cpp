@@ -184,8 +184,9 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
   if (!o || !g) return fail(err, FKREG_ERR_INVALID_ARG, "opts and output must be non-NULL");
   const int d = o->dim;
   if (d < 1 || d > 3) return fail(err, FKREG_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
-  if (o->order == 2) return fail(err, FKREG_ERR_UNSUPPORTED, "order 2 (local quadratic) is not supported");
-  if (o->order < 0 || o->order > 1) return fail(err, FKREG_ERR_INVALID_ARG, "order must be 0 or 1");
+  if (o->order < 0 || o->order > 2) return fail(err, FKREG_ERR_INVALID_ARG, "order must be 0, 1 or 2");
+  if (o->order == 2 && o->dim > 2)
+    return fail(err, FKREG_ERR_UNSUPPORTED, "order 2 (local quadratic) is supported in 1-D and 2-D");
   if (o->kernel != FKREG_KERNEL_GAUSSIAN)
     return fail(err, FKREG_ERR_UNSUPPORTED, "only the Gaussian regression kernel is supported");
   if (o->spread_kernel != FKREG_SPREAD_ES && o->spread_kernel != FKREG_SPREAD_GAUSS)

@@ -89,6 +89,50 @@ __device__ __forceinline__ ModeMul<T> mode_mul(const GeoDev& g, const BwDev& B, 
   return m;
 }
 
+// Transform of z^g K_H for |g| <= 4: W_g = (2 pi i)^-|g| d^g G / dxi^g, and
+// the derivatives of a Gaussian sum over the ways to split the index list of
+// g into pairs (each -4 pi^2 H_ab) and singletons (each u_a = -4 pi^2 (H xi)_a)
+// (Isserlis' rule).  Returns c with W_g = c G (real, |g| even) or
+// W_g = i c G (|g| odd, *imag = true).
+template <typename T>
+__device__ __forceinline__ T moment_factor(const MonoTab& mono, int f, const ModeMul<T>& m,
+                                           const BwDev& B, bool* imag) {
+  const T twopi = T(6.283185307179586476925286766559);
+  const T fpi2 = twopi * twopi;  // 4 pi^2
+  int id[4] = {0, 0, 0, 0}, k = 0;
+  for (int j = 0; j < 3; ++j)
+    for (int r = 0; r < mono.e[f][j]; ++r) id[k++] = j;
+  T u[4], P[4][4];
+  for (int x = 0; x < k; ++x) {
+    u[x] = -fpi2 * m.hx[id[x]];
+    for (int y = 0; y < k; ++y) P[x][y] = -fpi2 * T(B.H[id[x] * 3 + id[y]]);
+  }
+  T poly;
+  if (k == 0) {
+    poly = T(1);
+  } else if (k == 1) {
+    poly = u[0];
+  } else if (k == 2) {
+    poly = u[0] * u[1] + P[0][1];
+  } else if (k == 3) {
+    poly = u[0] * u[1] * u[2] + P[0][1] * u[2] + P[0][2] * u[1] + P[1][2] * u[0];
+  } else {
+    poly = u[0] * u[1] * u[2] * u[3] + P[0][1] * u[2] * u[3] + P[0][2] * u[1] * u[3] +
+           P[0][3] * u[1] * u[2] + P[1][2] * u[0] * u[3] + P[1][3] * u[0] * u[2] +
+           P[2][3] * u[0] * u[1] + P[0][1] * P[2][3] + P[0][2] * P[1][3] + P[0][3] * P[1][2];
+  }
+  // (2 pi i)^-k: k = 1: -i/(2 pi); 2: -1/(4 pi^2); 3: i/(8 pi^3); 4: 1/(16 pi^4)
+  const T ip = T(1) / twopi;
+  *imag = (k & 1) != 0;
+  switch (k) {
+    case 0: return poly;
+    case 1: return -ip * poly;
+    case 2: return -ip * ip * poly;
+    case 3: return ip * ip * ip * poly;
+    default: return ip * ip * ip * ip * poly;
+  }
+}
+
 // accumulate base * W_g for the first nf monomials
 template <typename T, typename C>
 __device__ __forceinline__ void acc_fields(C* acc, C base, const ModeMul<T>& m, const BwDev& B,
@@ -104,7 +148,7 @@ __device__ __forceinline__ void acc_fields(C* acc, C base, const ModeMul<T>& m, 
       const T s = twopi * m.hx[a];  // multiply by i * s
       acc[f].x += -base.y * s;
       acc[f].y += base.x * s;
-    } else {
+    } else if (deg == 2) {
       int a = -1, c = -1;
       for (int j = 0; j < 3; ++j)
         for (int r = 0; r < mono.e[f][j]; ++r) {
@@ -116,6 +160,16 @@ __device__ __forceinline__ void acc_fields(C* acc, C base, const ModeMul<T>& m, 
       const T s = T(B.H[a * 3 + c]) - twopi * twopi * m.hx[a] * m.hx[c];
       acc[f].x += base.x * s;
       acc[f].y += base.y * s;
+    } else {
+      bool imag;
+      const T s = moment_factor<T>(mono, f, m, B, &imag);
+      if (imag) {
+        acc[f].x += -base.y * s;
+        acc[f].y += base.x * s;
+      } else {
+        acc[f].x += base.x * s;
+        acc[f].y += base.y * s;
+      }
     }
   }
 }
@@ -200,7 +254,7 @@ __device__ __forceinline__ C mult_field(C base, const ModeMul<T>& m, const BwDev
     const T sc = twopi * m.hx[a];  // multiply by i * sc
     r.x = -base.y * sc;
     r.y = base.x * sc;
-  } else {
+  } else if (deg == 2) {
     int a = -1, c = -1;
     for (int j = 0; j < 3; ++j)
       for (int q = 0; q < mono.e[f][j]; ++q) {
@@ -212,6 +266,11 @@ __device__ __forceinline__ C mult_field(C base, const ModeMul<T>& m, const BwDev
     const T sc = T(B.H[a * 3 + c]) - twopi * twopi * m.hx[a] * m.hx[c];
     r.x = base.x * sc;
     r.y = base.y * sc;
+  } else {
+    bool imag;
+    const T sc = moment_factor<T>(mono, f, m, B, &imag);
+    r.x = imag ? -base.y * sc : base.x * sc;
+    r.y = imag ? base.x * sc : base.y * sc;
   }
   return r;
 }

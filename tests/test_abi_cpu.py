@@ -67,8 +67,8 @@ def test_width_follows_tolerance(lib):
 def test_invalid_arguments_are_reported(lib):
     with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
         fkreg.geometry(**opts(H=np.array([[1.0, 2.0], [2.0, 1.0]]) * 1e-4))   # not SPD
-    with pytest.raises(fkreg.FkregError, match="UNSUPPORTED"):
-        fkreg.geometry(**opts(order=2))
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
+        fkreg.geometry(**opts(order=3))
     with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
         fkreg.geometry(**opts(grid_n=(1, 256)))
     with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):

@@ -158,7 +158,8 @@ def test_nw1d_fp64_tol12():
 
 
 @pytest.mark.parametrize("d,order,grid,sig", [(1, 1, 200, 0.01), (2, 0, 40, 0.03), (2, 1, 40, 0.03),
-                                              (3, 0, 12, 0.06), (3, 1, 12, 0.07)])
+                                              (3, 0, 12, 0.06), (3, 1, 12, 0.07), (1, 2, 200, 0.01),
+                                              (2, 2, 40, 0.03)])
 def test_fp64_tol12_all_dims(d, order, grid, sig):
     w = inputs.random_small(10 + d + order, d, 3000, grid, order, [sig], precision="f64", tol=1e-12)
     _, out = smooth(w)
@@ -166,15 +167,16 @@ def test_fp64_tol12_all_dims(d, order, grid, sig):
 
 
 @pytest.mark.parametrize("d,order,grid,sig", [(1, 0, 300, 0.01), (2, 1, 64, 0.02), (3, 0, 16, 0.05),
-                                              (3, 1, 16, 0.06)])
+                                              (3, 1, 16, 0.06), (2, 2, 64, 0.03)])
 def test_fp32_tol6_all_dims(d, order, grid, sig):
     w = inputs.random_small(20 + d + order, d, 20_000, grid, order, [sig], precision="f32", tol=1e-6)
     _, out = smooth(w)
     check_grid(w, out)
 
 
-def test_full_bandwidth_matrix():
-    w = inputs.random_small(31, 2, 4000, 40, 1, [0.04], precision="f64", tol=1e-12, full_h=True)
+@pytest.mark.parametrize("order", [1, 2])
+def test_full_bandwidth_matrix(order):
+    w = inputs.random_small(31, 2, 4000, 40, order, [0.04], precision="f64", tol=1e-12, full_h=True)
     _, out = smooth(w)
     check_grid(w, out)
 
@@ -235,7 +237,7 @@ def test_at_samples_rss_and_exact_trace():
     assert out["trace"][0, 2].item() == pytest.approx(tr_o, rel=1e-9)
 
 
-@pytest.mark.parametrize("d,order", [(1, 0), (2, 1), (3, 0)])
+@pytest.mark.parametrize("d,order", [(1, 0), (2, 1), (3, 0), (1, 2), (2, 2)])
 def test_df_and_gcv_with_given_probes(d, order):
     grid = {1: 64, 2: 24, 3: 10}[d]
     w = inputs.random_small(50 + d, d, 2500, grid, order, [0.04, 0.08], precision="f64", tol=1e-12)

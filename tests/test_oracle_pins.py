@@ -119,6 +119,24 @@ def test_local_linear_reproduces_linear_m(d):
     assert np.max(np.abs(r0["mhat"][:, 0] - (a + q @ b))) > 1e-3
 
 
+@pytest.mark.parametrize("d", [1, 2])
+def test_local_quadratic_reproduces_quadratic_m(d):
+    # order 2 (the paper's LQ): exact for any quadratic m, where LL is not
+    rng = np.random.default_rng(35 + d)
+    x = rng.random((90, d))
+    H = rand_spd(rng, d, 0.2)
+    a, b = 0.4, rng.standard_normal(d)
+    C = rng.standard_normal((d, d))
+    C = C + C.T
+    y = a + x @ b + np.einsum("ni,ij,nj->n", x, C, x)
+    q = rng.random((25, d))
+    r = oracle.smooth_at(x, y[None], H, 2, q)
+    np.testing.assert_allclose(r["mhat"][:, 0], a + q @ b + np.einsum("ni,ij,nj->n", q, C, q),
+                               rtol=1e-9, atol=1e-10)
+    r1 = oracle.smooth_at(x, y[None], H, 1, q)
+    assert np.max(np.abs(r1["mhat"][:, 0] - r["mhat"][:, 0])) > 1e-3
+
+
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_local_linear_equals_weighted_least_squares(d):
     # eq. 2 minimised directly with numpy's least-squares routine
