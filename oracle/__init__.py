@@ -25,6 +25,7 @@ built on top of those sums, each written from its definition in the paper:
 from __future__ import annotations
 
 import ctypes
+import itertools
 import math
 import os
 import subprocess
@@ -273,6 +274,80 @@ def interval(mhat: np.ndarray, var: np.ndarray, alpha: float = 0.05):
     sd = np.where(v >= 0, np.sqrt(np.where(v >= 0, v, 0.0)), np.nan)
     m = np.asarray(mhat, dtype=np.float64)
     return m - z * sd, m + z * sd
+
+
+def _keys_weights(t: float, a: float = -0.5):
+    """Cubic-convolution weights (Keys 1981) of the taps -1, 0, 1, 2 at offset t in [0, 1]."""
+    def w(s):
+        s = abs(s)
+        if s <= 1:
+            return (a + 2) * s ** 3 - (a + 3) * s ** 2 + 1
+        if s < 2:
+            return a * s ** 3 - 5 * a * s ** 2 + 8 * a * s - 4 * a
+        return 0.0
+    return [w(t + 1), w(t), w(1 - t), w(2 - t)]
+
+
+def predict(grid_vals: np.ndarray, grid_n: Sequence[int], lo: Sequence[float],
+            hi: Sequence[float], xq: np.ndarray, method: str = "linear") -> np.ndarray:
+    """Values of a grid estimate at new points (the griddedInterpolant step of Sec. 1.1).
+
+    grid_vals [count, M] on the eq. 6 lattice (last axis fastest); xq [nq, d].
+    ``linear``: multilinear inside the box, extended linearly from the
+    boundary cell outside.  ``cubic``: separable cubic convolution (Keys 1981,
+    a = -1/2) with Keys' boundary rows f[-1] = 3f[0] - 3f[1] + f[2] (and the
+    mirror at the top); NaN outside the box.  Returns [count, nq].
+    Pure-Python loops: small cases only.
+    """
+    g = np.asarray(grid_vals, dtype=np.float64).reshape((-1,) + tuple(grid_n))
+    xq = np.atleast_2d(np.asarray(xq, dtype=np.float64))
+    d = xq.shape[1]
+    out = np.empty((g.shape[0], xq.shape[0]))
+    for qi, x in enumerate(xq):
+        taps = []
+        bad = False
+        for j in range(d):
+            M = grid_n[j]
+            delta = (hi[j] - lo[j]) / (M - 1)
+            u = (x[j] - lo[j]) / delta
+            i = int(min(max(math.floor(u), 0), M - 2))
+            t = u - i
+            if method == "linear":
+                taps.append([(i, 1 - t), (i + 1, t)])
+            else:
+                if u < 0 or u > M - 1:
+                    bad = True
+                ws = _keys_weights(min(max(t, 0.0), 1.0))
+                taps.append([(i - 1 + k, ws[k]) for k in range(4)])
+        if bad:
+            out[:, qi] = np.nan
+            continue
+        val = np.zeros(g.shape[0])
+        for combo in itertools.product(*taps):
+            wgt = 1.0
+            idx = []
+            for j, (ii, wj) in enumerate(combo):
+                wgt *= wj
+                idx.append(ii)
+            val += wgt * _grid_at(g, idx, grid_n)
+        out[:, qi] = val
+    return out
+
+
+def _grid_at(g: np.ndarray, idx, grid_n) -> np.ndarray:
+    """Grid values at a multi-index, with Keys' boundary rows at -1 and M."""
+    for j, ii in enumerate(idx):
+        M = grid_n[j]
+        if ii == -1 or ii == M:
+            sgn = 1 if ii == -1 else -1
+            base = 0 if ii == -1 else M - 1
+            parts = []
+            for c, off in ((3, 0), (-3, 1), (1, 2)):
+                jj = list(idx)
+                jj[j] = base + sgn * off
+                parts.append(c * _grid_at(g, jj, grid_n))
+            return parts[0] + parts[1] + parts[2]
+    return g[(slice(None),) + tuple(idx)]
 
 
 def get_hlist(n: int, lo: float, hi: float, spacing: str = "log") -> np.ndarray:

@@ -311,6 +311,42 @@ def test_interval_eq28():
     assert np.isnan(lo[0]) and np.isnan(hi[0])
 
 
+@pytest.mark.parametrize("d", [1, 2])
+def test_predict_reproduces_polynomials(d):
+    # multilinear interpolation is exact for affine functions (also when it
+    # extends past the box); cubic convolution with Keys' boundary rows is
+    # exact for quadratics anywhere in the box and returns node values at nodes
+    rng = np.random.default_rng(60 + d)
+    grid_n = (9, 7)[:d]
+    lo, hi = (0.0, -1.0)[:d], (2.0, 1.0)[:d]
+    gp = oracle.grid_points(grid_n, lo, hi)
+    b = rng.standard_normal(d)
+    C = rng.standard_normal((d, d))
+    C = C + C.T
+    aff = 0.3 + gp @ b
+    quad = 0.3 + gp @ b + np.einsum("ni,ij,nj->n", gp, C, gp)
+    xin = np.asarray(lo) + rng.random((40, d)) * (np.asarray(hi) - np.asarray(lo))
+    xin[:4] = np.asarray(lo)            # on the lower edge
+    xin[4:8] = np.asarray(hi)           # on the upper edge
+    xout = np.asarray(lo) - 0.3 + rng.random((10, d)) * (np.asarray(hi) - np.asarray(lo) + 0.6)
+    lin = oracle.predict(aff[None], grid_n, lo, hi, np.vstack([xin, xout]), "linear")
+    np.testing.assert_allclose(lin[0], 0.3 + np.vstack([xin, xout]) @ b, rtol=1e-12, atol=1e-12)
+    cub = oracle.predict(quad[None], grid_n, lo, hi, xin, "cubic")
+    np.testing.assert_allclose(cub[0], 0.3 + xin @ b + np.einsum("ni,ij,nj->n", xin, C, xin),
+                               rtol=1e-11, atol=1e-11)
+    node = oracle.predict(np.sin(3 * gp.sum(axis=1))[None], grid_n, lo, hi, gp[::5], "cubic")
+    np.testing.assert_allclose(node[0], np.sin(3 * gp[::5].sum(axis=1)), rtol=1e-13, atol=1e-14)
+    assert np.all(np.isnan(oracle.predict(quad[None], grid_n, lo, hi, np.asarray(lo)[None] - 0.1,
+                                          "cubic")))
+    # multilinear against scipy's regular-grid interpolator
+    from scipy.interpolate import RegularGridInterpolator
+    axes = [np.linspace(lo[j], hi[j], grid_n[j]) for j in range(d)]
+    f = np.cos(gp.sum(axis=1))
+    ref = RegularGridInterpolator(axes, f.reshape(grid_n))(xin)
+    np.testing.assert_allclose(oracle.predict(f[None], grid_n, lo, hi, xin, "linear")[0], ref,
+                               rtol=1e-12, atol=1e-13)
+
+
 def test_kde_integrates_to_one():
     # eq. 8: s_0 / N is a density (Gaussian K has unit mass)
     rng = np.random.default_rng(3)
