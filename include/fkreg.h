@@ -291,6 +291,25 @@ fkreg_status fkreg_interval(int precision, int64_t count, const void* mhat_dev,
                             void* stream);
 
 /*
+ * Values of grid estimates at new points (the grid-to-point interpolation
+ * the paper applies to its grid estimates, Sec. 1.1).
+ *   precision        FKREG_F32 / FKREG_F64: element type of grid, xq and out
+ *   dim, grid_n/lo/hi the lattice of eq. 6 (host arrays of dim entries)
+ *   grid_dev         [count][M_1..M_dim] device, last axis fastest (e.g. the
+ *                    mhat_grid output: count = n_bw * n_rhs)
+ *   xq_dev           [nq][dim] device query points
+ *   method           0: multilinear, extended linearly from the boundary
+ *                    cell outside the box; 1: cubic convolution (Keys 1981,
+ *                    a = -1/2) with Keys' boundary rows, NaN outside the box
+ *   out_dev          [count][nq] device
+ * Needs grid_n[j] >= 2 (linear) or >= 4 (cubic).  NaN grid values (masked
+ * points) propagate to the queries that use them.  No plan is needed.
+ */
+fkreg_status fkreg_predict(int precision, int dim, const int64_t* grid_n, const double* grid_lo,
+                           const double* grid_hi, int count, const void* grid_dev, int64_t nq,
+                           const void* xq_dev, int method, void* out_dev, void* stream);
+
+/*
  * Gradient of GCV (eq. 22) for bandwidth b, with the Monte-Carlo trace of
  * Sec. 2.1 over n_probes fixed probes (given, or drawn as in fkreg_df from
  * seed), with respect to the log bandwidths, the responses and the samples.

@@ -30,7 +30,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA"
 EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
            "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_variance",
-           "fkreg_log_variance", "fkreg_interval", "fkreg_set_timing",
+           "fkreg_log_variance", "fkreg_interval", "fkreg_predict", "fkreg_set_timing",
            "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
            "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
@@ -100,6 +100,8 @@ def load():
     L.fkreg_variance.argtypes = [vp, vp, vp, vp, vp]
     L.fkreg_log_variance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.fkreg_interval.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_double, vp, vp, vp]
+    L.fkreg_predict.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int, vp,
+                                ctypes.c_int64, vp, ctypes.c_int, vp, vp]
     L.fkreg_backward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.c_int, vp, vp,
                                  vp, vp, vp]
     L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
@@ -440,6 +442,32 @@ def interval(mhat, var, alpha: float = 0.05):
     if st != 0:
         raise FkregError(f"fkreg_interval: {STATUS.get(st, st)}")
     return lo, hi
+
+
+def predict(grid, grid_n, lo, hi, xq, method: str = "linear"):
+    """Values of grid estimates at new points (device tensors).
+
+    grid: [..., M_1..M_d] (leading dims flattened into count); xq: [nq, d] of
+    the same dtype.  method "linear" or "cubic".  Returns [..., nq].
+    """
+    import torch
+    L = load()
+    d = len(grid_n)
+    lead = grid.shape[: grid.dim() - d]
+    g = grid.reshape(-1, *grid_n).contiguous()
+    x = xq.to(g.dtype).reshape(-1, d).contiguous()
+    out = torch.empty((g.shape[0], x.shape[0]), dtype=g.dtype, device=g.device)
+    gn = (ctypes.c_int64 * d)(*[int(v) for v in grid_n])
+    glo = (ctypes.c_double * d)(*[float(v) for v in lo])
+    ghi = (ctypes.c_double * d)(*[float(v) for v in hi])
+    prec = FKREG_F32 if g.dtype == torch.float32 else FKREG_F64
+    st = L.fkreg_predict(prec, d, gn, glo, ghi, g.shape[0], ctypes.c_void_p(g.data_ptr()),
+                         x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                         0 if method == "linear" else 1, ctypes.c_void_p(out.data_ptr()),
+                         ctypes.c_void_p(torch.cuda.current_stream(g.device).cuda_stream))
+    if st != 0:
+        raise FkregError(f"fkreg_predict: {STATUS.get(st, st)}")
+    return out.reshape(*lead, x.shape[0])
 
 
 class Batch:

@@ -1,5 +1,6 @@
 """CPU-side checks of the C-ABI library: it loads, exports every declared
 symbol, validates arguments, and its host planner is right.  No GPU needed."""
+import ctypes
 import math
 import os
 import re
@@ -77,6 +78,13 @@ def test_invalid_arguments_are_reported(lib):
     L = fkreg.load()
     for prec, alpha in ((0, 0.0), (0, 1.0), (1, -0.1), (7, 0.05)):
         assert L.fkreg_interval(prec, 4, None, None, alpha, None, None, None) == 1
+    # prediction: bad method, dimension or grid sizes are refused before any launch
+    gn = (ctypes.c_int64 * 2)(3, 3)
+    lo2, hi2 = (ctypes.c_double * 2)(0, 0), (ctypes.c_double * 2)(1, 1)
+    assert L.fkreg_predict(0, 2, gn, lo2, hi2, 1, None, 5, None, 2, None, None) == 1   # method
+    assert L.fkreg_predict(0, 4, gn, lo2, hi2, 1, None, 5, None, 0, None, None) == 1   # dim
+    assert L.fkreg_predict(0, 2, gn, lo2, hi2, 1, None, 5, None, 1, None, None) == 1   # cubic, M < 4
+    assert L.fkreg_predict(0, 2, gn, lo2, hi2, 1, None, 0, None, 0, None, None) == 0   # nothing to do
 
 
 @pytest.mark.parametrize("kind", ["es", "gauss"])

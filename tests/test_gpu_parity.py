@@ -380,6 +380,36 @@ def test_interval_eq28(prec):
                                rtol=1e-6 if prec == "f32" else 1e-14)
 
 
+@pytest.mark.parametrize("d,prec", [(1, "f64"), (2, "f64"), (2, "f32"), (3, "f64")])
+def test_predict_at_new_points(d, prec):
+    # the grid estimate carried to new points, linear and cubic, against the
+    # oracle's interpolation of the same grid values
+    grid = {1: 60, 2: 20, 3: 8}[d]
+    w = inputs.random_small(90 + d, d, 3000, grid, 1, [0.08], precision=prec,
+                            tol=1e-12 if prec == "f64" else 1e-6)
+    p = plan_for(w)
+    p.set_points(torch.tensor(w.x))
+    out = p.smooth(torch.tensor(w.y), want=("mhat_grid",))
+    rng = np.random.default_rng(5 + d)
+    xq = rng.random((500, d)) * 1.2 - 0.1          # some queries outside the box
+    xq[:3] = 0.0
+    xq[3:6] = 1.0
+    from paper_2204_07716_gb300.fkreg import predict
+    dt = torch.float32 if prec == "f32" else torch.float64
+    g = out["mhat_grid"]
+    gh = g.reshape(1, -1).cpu().numpy().astype(np.float64)
+    for method in ("linear", "cubic"):
+        v = predict(g, w.grid_n, w.lo, w.hi, torch.tensor(xq, dtype=dt, device=g.device), method)
+        p.sync()
+        xr = xq.astype(np.float32).astype(np.float64) if prec == "f32" else xq
+        ref = oracle.predict(gh, w.grid_n, w.lo, w.hi, xr, method)[0]
+        got = v.reshape(-1).cpu().numpy()
+        ok = np.isfinite(ref)
+        assert np.array_equal(np.isfinite(got), ok)
+        rt = 1e-12 if prec == "f64" else 1e-5
+        np.testing.assert_allclose(got[ok], ref[ok], rtol=rt, atol=rt * np.max(np.abs(gh[np.isfinite(gh)])))
+
+
 # ------------------------------------------------------------ edge cases ----
 def test_empty_and_single_sample():
     w = inputs.random_small(80, 2, 1, 20, 0, [0.1], precision="f64", tol=1e-12)
