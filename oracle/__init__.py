@@ -140,6 +140,72 @@ def moment_sums(x: np.ndarray, c: np.ndarray, H: np.ndarray, deg: int,
     return out
 
 
+# ---- compact regression kernels (Table 1; Sec. 1 lists uniform, bi-weight,
+# tri-weight, Epanechnikov) -------------------------------------------------
+# Radial on the unit ball of u = H^(-1/2) z: K(u) = c_d k(|u|^2) for |u| <= 1,
+# with c_d making K a density in d dimensions (V_d = unit-ball volume):
+#   uniform      k = 1                 c_d = 1 / V_d
+#   epanechnikov k = 1 - r^2           c_d = (d + 2) / (2 V_d)
+#   triangle     k = 1 - r             c_d = (d + 1) / V_d
+#   biweight     k = (1 - r^2)^2       c_d = (d + 2)(d + 4) / (8 V_d)
+#   triweight    k = (1 - r^2)^3       c_d = (d + 2)(d + 4)(d + 6) / (48 V_d)
+# and K_H(z) = |H|^(-1/2) K(H^(-1/2) z).
+COMPACT_KERNELS = ("uniform", "epanechnikov", "triangle", "biweight", "triweight")
+
+
+def compact_profile(name: str, d: int, r2: np.ndarray) -> np.ndarray:
+    """c_d k(r^2) on |u| <= 1, 0 outside."""
+    vd = {1: 2.0, 2: math.pi, 3: 4.0 * math.pi / 3.0}[d]
+    r2 = np.asarray(r2, dtype=np.float64)
+    inside = r2 <= 1.0
+    if name == "uniform":
+        k, c = np.ones_like(r2), 1.0 / vd
+    elif name == "epanechnikov":
+        k, c = 1.0 - r2, (d + 2) / (2.0 * vd)
+    elif name == "triangle":
+        k, c = 1.0 - np.sqrt(np.clip(r2, 0.0, None)), (d + 1) / vd
+    elif name == "biweight":
+        k, c = (1.0 - r2) ** 2, (d + 2) * (d + 4) / (8.0 * vd)
+    elif name == "triweight":
+        k, c = (1.0 - r2) ** 3, (d + 2) * (d + 4) * (d + 6) / (48.0 * vd)
+    else:
+        raise ValueError(name)
+    return np.where(inside, c * k, 0.0)
+
+
+def moment_sums_compact(x: np.ndarray, c: np.ndarray, H: np.ndarray, deg: int,
+                        q: np.ndarray, kernel: str) -> np.ndarray:
+    """Eq. 9 sums with a compact kernel, [nq, nstr, nmono(d, deg)] (direct, loops over q)."""
+    x = _c64(x)
+    n, d = x.shape
+    c = _c64(np.atleast_2d(c))
+    q = _c64(np.atleast_2d(q))
+    H = _c64(H).reshape(d, d)
+    Hinv = np.linalg.inv(H)
+    scale = 1.0 / math.sqrt(np.linalg.det(H))
+    ex = monomials(d, deg)
+    out = np.zeros((q.shape[0], c.shape[0], ex.shape[0]))
+    for k, qq in enumerate(q):
+        z = x - qq
+        r2 = np.einsum("ni,ij,nj->n", z, Hinv, z)
+        wgt = scale * compact_profile(kernel, d, r2)
+        mono = np.prod(z[:, None, :] ** ex[None, :, :], axis=2)      # [n, nm]
+        out[k] = (c * wgt[None, :]) @ mono
+    return out
+
+
+def smooth_at_compact(x: np.ndarray, y: np.ndarray, H: np.ndarray, order: int,
+                      q: np.ndarray, kernel: str) -> dict:
+    """Local-polynomial estimate with a compact kernel (eqs. 3, 9), same outputs as smooth_at."""
+    x = _c64(x)
+    y = _c64(np.atleast_2d(y))
+    d = x.shape[1]
+    s = moment_sums_compact(x, np.ones((1, x.shape[0])), H, 2 * order, q, kernel)[:, 0, :]
+    t = moment_sums_compact(x, y, H, order, q, kernel)
+    mh, si = lpr_solve(d, order, s, t)
+    return {"mhat": mh, "s": s, "t": t, "sinv11": si}
+
+
 def lpr_solve(d: int, order: int, s: np.ndarray, t: np.ndarray):
     """mhat = e_1^T S^-1 t and [S^-1]_11 from moment sums (eqs. 3, 11).
 

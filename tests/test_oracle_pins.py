@@ -347,6 +347,44 @@ def test_predict_reproduces_polynomials(d):
                                rtol=1e-12, atol=1e-13)
 
 
+@pytest.mark.parametrize("name", oracle.COMPACT_KERNELS)
+def test_compact_kernels_are_densities(name):
+    from scipy import integrate
+    v1 = integrate.quad(lambda u: float(oracle.compact_profile(name, 1, u * u)), -1, 1,
+                        points=[0.0], epsabs=1e-13)[0]
+    assert v1 == pytest.approx(1.0, rel=1e-9)
+    v2 = integrate.dblquad(lambda b, a: float(oracle.compact_profile(name, 2, a * a + b * b)),
+                           -1, 1, lambda a: -math.sqrt(1 - a * a), lambda a: math.sqrt(1 - a * a),
+                           epsabs=1e-11, epsrel=1e-10)[0]
+    assert v2 == pytest.approx(1.0, rel=1e-7)
+    assert float(oracle.compact_profile(name, 2, 1.0001)) == 0.0
+
+
+@pytest.mark.parametrize("name", oracle.COMPACT_KERNELS)
+def test_compact_kernel_smoothing(name):
+    rng = np.random.default_rng(70)
+    x = rng.random((400, 2))
+    H = np.diag([0.2 ** 2, 0.25 ** 2])
+    q = 0.2 + 0.6 * rng.random((12, 2))
+    # a constant is returned, local linear reproduces a line
+    r = oracle.smooth_at_compact(x, np.full((1, 400), 1.5), H, 0, q, name)
+    np.testing.assert_allclose(r["mhat"][:, 0], 1.5, rtol=1e-12)
+    b = np.array([0.7, -0.4])
+    r = oracle.smooth_at_compact(x, (0.2 + x @ b)[None], H, 1, q, name)
+    np.testing.assert_allclose(r["mhat"][:, 0], 0.2 + q @ b, rtol=1e-10, atol=1e-12)
+    # the density sum counts exactly the samples inside the ellipse, weighted
+    z = x - q[0]
+    u2 = z[:, 0] ** 2 / 0.04 + z[:, 1] ** 2 / 0.0625
+    s0 = oracle.moment_sums_compact(x, np.ones((1, 400)), H, 0, q[:1], name)[0, 0, 0]
+    ref = np.sum(oracle.compact_profile(name, 2, u2[u2 <= 1])) / (0.2 * 0.25)
+    assert s0 == pytest.approx(ref, rel=1e-12)
+    if name == "uniform":
+        # NW with the uniform kernel is the plain mean of y over the ellipse
+        y = rng.standard_normal(400)
+        r = oracle.smooth_at_compact(x, y[None], H, 0, q[:1], name)
+        assert r["mhat"][0, 0] == pytest.approx(np.mean(y[u2 <= 1]), rel=1e-12)
+
+
 def test_kde_integrates_to_one():
     # eq. 8: s_0 / N is a density (Gaussian K has unit mass)
     rng = np.random.default_rng(3)
