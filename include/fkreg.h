@@ -65,7 +65,15 @@ typedef enum {
 
 enum { FKREG_F32 = 0, FKREG_F64 = 1 };
 enum { FKREG_SPREAD_ES = 0, FKREG_SPREAD_GAUSS = 1 };
-enum { FKREG_KERNEL_GAUSSIAN = 0 };
+enum {
+  FKREG_KERNEL_GAUSSIAN = 0,
+  /* compact radial kernels on the unit ball of u = H^(-1/2) z (Table 1; Sec. 1) */
+  FKREG_KERNEL_UNIFORM = 1,       /* k = 1                                     */
+  FKREG_KERNEL_EPANECHNIKOV = 2,  /* k = 1 - |u|^2                             */
+  FKREG_KERNEL_TRIANGLE = 3,      /* k = 1 - |u|                               */
+  FKREG_KERNEL_BIWEIGHT = 4,      /* k = (1 - |u|^2)^2                         */
+  FKREG_KERNEL_TRIWEIGHT = 5      /* k = (1 - |u|^2)^3                         */
+};
 
 /* fkreg_opts.flags */
 enum {
@@ -78,8 +86,14 @@ enum {
  * Problem description (the arguments of cv_fkreg in Sec. 4 and Table 1).
  *   dim            d, 1..3
  *   order          l: 0 = Nadaraya-Watson (eq. 7), 1 = local linear (eq. 3)
- *   kernel         FKREG_KERNEL_GAUSSIAN (the only kernel whose transform the
- *                  tolerance controls; Table 1's compact kernels -> UNSUPPORTED)
+ *   kernel         FKREG_KERNEL_GAUSSIAN: the NUFFT path (the transform of the
+ *                  Gaussian moment kernels decays fast enough for tol to
+ *                  control the truncation).  The compact kernels
+ *                  (FKREG_KERNEL_UNIFORM ... TRIWEIGHT, normalised to unit
+ *                  mass in d dimensions, K_H(z) = |H|^(-1/2) K(H^(-1/2) z))
+ *                  use exact direct sums over the binned samples inside each
+ *                  point's support instead (tol and spread_kernel unused);
+ *                  fkreg_backward and FKREG_WANT_BACKWARD are refused for them.
  *   spread_kernel  NUFFT spreading kernel: exponential of semicircle (default)
  *                  or the Gaussian of Sec. 1.2 eq. 17 (about twice as wide)
  *   precision      FKREG_F32 (spreading, FFT, interpolation in float, FP64

@@ -203,6 +203,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   P->fgrid = P->ns + P->nrhs_real * P->nt;
   P->nacc = P->nrhs_real + 2 * P->max_probes + 1;
   P->backward = (opts->flags & FKREG_WANT_BACKWARD) != 0;
+  P->direct = opts->kernel != FKREG_KERNEL_GAUSSIAN;
   P->f2bwd = P->ns + (1 + P->max_probes) * P->nt;
   const int nout_bwd = 1 + (2 + P->max_probes) * opts->dim;
   const int strengths_total = P->smax + (P->backward ? P->f2bwd : 0);
@@ -210,6 +211,11 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   if (P->nacc > 512) {
     delete P;
     return set_global_error(FKREG_ERR_UNSUPPORTED, "n_rhs (real parts) + 2 max_probes must be <= 511");
+  }
+  if (P->direct && P->f2max > 64) {
+    delete P;
+    return set_global_error(FKREG_ERR_UNSUPPORTED,
+                            "compact kernels: s-fields + (responses + probes) t-fields must be <= 64");
   }
   if (P->nt * (P->nrhs_real + P->max_probes) + P->ns > 4096) {
     delete P;
@@ -261,12 +267,15 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   L.take(P->r_hist, 4 * (256 * ntiles + 1));
   L.take(P->r_scan, 4 * (scan_len / 1024 + 2));
   L.take(P->r_str, T * strengths_total * std::max<int64_t>(1, max_n));
-  L.take(P->r_fine, T * strengths_total * nf_cells);
-  L.take(P->r_spec, 2 * T * strengths_total * nf_half);
-  L.take(P->r_gspec, 2 * T * size_t(P->nbw) * P->fgrid * l_half);
+  // the direct path (compact kernels) needs only the grid fields
+  const int64_t fft_scale = P->direct ? 0 : 1;
+  L.take(P->r_fine, std::max<int64_t>(256, fft_scale * T * strengths_total * nf_cells));
+  L.take(P->r_spec, std::max<int64_t>(256, fft_scale * 2 * T * strengths_total * nf_half));
+  L.take(P->r_gspec, std::max<int64_t>(256, fft_scale * 2 * T * int64_t(P->nbw) * P->fgrid * l_half));
   L.take(P->r_gfield, T * size_t(P->nbw) * P->fgrid * l_cells);
-  L.take(P->r_t2spec, 2 * T * size_t(t2_fields) * t2_half);
-  L.take(P->r_t2field, T * size_t(fk::t2_record_stride(t2_fields)) * t2_cells);
+  L.take(P->r_t2spec, std::max<int64_t>(256, fft_scale * 2 * T * int64_t(t2_fields) * t2_half));
+  L.take(P->r_t2field,
+         std::max<int64_t>(256, fft_scale * T * int64_t(fk::t2_record_stride(t2_fields)) * t2_cells));
   L.take(P->r_part, sizeof(double) * size_t(P->nblk_interp + 1) * P->nbw * P->nacc);
   L.take(P->r_smax, 8 * size_t(P->nbw));
   if (P->backward) {
@@ -277,7 +286,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
     L.take(P->r_bpart, 8 * 3 * size_t((nn + 255) / 256 + 1));
   }
   // cuFFT plans for the standard passes (work sizes decide the reserved area)
-  {
+  if (!P->direct) {
     int64_t dims[3];
     cufftHandle h;
     std::vector<int> fwd_batches = {1 + P->nrhs_real, P->nrhs};
@@ -455,6 +464,31 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
     FK_STAGE(FKREG_STAGE_STRENGTHS);
     FK_CHECK(fk::run_gather_strengths(P, y, 0, n_probes, seed, probes, 1, s), "strengths");
   }
+  if (P->direct) {
+    // compact kernels: direct sums for the grid and at the samples
+    if (out && (out->mhat_grid || out->mask || out->moments)) {
+      {
+        FK_STAGE(FKREG_STAGE_KMUL_GRID);
+        FK_CHECK(fk::run_direct_grid(P, 1, P->nrhs_real, 0, P->nbw, s), "direct grid sums");
+      }
+      {
+        FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+        FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, nullptr, out, nullptr, s), "grid solve");
+      }
+    }
+    if (want_df || n_probes > 0 || (out && (out->mhat_at_x || out->rss))) {
+      for (int b = 0; b < P->nbw; ++b) {
+        FK_STAGE(FKREG_STAGE_INTERP);
+        FK_CHECK(fk::run_interp(P, b, P->nrhs_real, n_probes, y, out ? out->mhat_at_x : nullptr, s),
+                 "direct sums at the samples");
+      }
+      FK_STAGE(FKREG_STAGE_FINALIZE);
+      FK_CHECK(fk::run_finalize(P, n_probes, out, s), "finalize");
+    }
+    (void)T;
+    P->dens_valid = true;
+    return FKREG_OK;
+  }
   {
     FK_STAGE(FKREG_STAGE_SPREAD);
     FK_CHECK(fk::run_spread(P, 0, S, s), "spread");
@@ -600,6 +634,15 @@ fkreg_status fkreg_variance(fkreg_plan P, const void* y, const void* mhat_at_x, 
       FK_STAGE(FKREG_STAGE_STRENGTHS);
       FK_CHECK(fk::run_residual_strengths(P, y, mhat_at_x, b, 1, s), "residuals");
     }
+    if (P->direct) {
+      {
+        FK_STAGE(FKREG_STAGE_KMUL_GRID);
+        FK_CHECK(fk::run_direct_grid(P, 1, R, b, 1, s), "direct grid sums");
+      }
+      FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+      FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, sigma2, s), "grid solve");
+      continue;
+    }
     {
       FK_STAGE(FKREG_STAGE_SPREAD);
       FK_CHECK(fk::run_spread(P, 1, R, s), "spread");
@@ -645,6 +688,23 @@ fkreg_status fkreg_log_variance(fkreg_plan P, const void* y, const void* mhat_at
     {
       FK_STAGE(FKREG_STAGE_STRENGTHS);
       FK_CHECK(fk::run_logres_strengths(P, y, mhat_at_x, b, 1, s), "log residuals");
+    }
+    if (P->direct) {
+      {
+        FK_STAGE(FKREG_STAGE_KMUL_GRID);
+        FK_CHECK(fk::run_direct_grid(P, 1, R, b, 1, s), "direct grid sums");
+      }
+      {
+        FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+        FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, v_grid, s), "grid solve");
+      }
+      {
+        FK_STAGE(FKREG_STAGE_INTERP);
+        FK_CHECK(fk::run_interp(P, b, R, 0, y, v_at_x, s), "direct sums at the samples");
+      }
+      FK_STAGE(FKREG_STAGE_FINALIZE);
+      FK_CHECK(fk::run_kappa_sigma2(P, b, y, mhat_at_x, v_at_x, v_grid, kappa, sigma2, s), "kappa");
+      continue;
     }
     {
       FK_STAGE(FKREG_STAGE_SPREAD);

@@ -30,6 +30,74 @@ __device__ __forceinline__ T phi(int kind, int w, T beta, T z) {
   return (fabs(z) <= T(0.5) * T(w)) ? exp(-beta * z * z) : T(0);
 }
 
+// Compact radial profile k(|u|^2) of the regression kernels (unit ball;
+// normalisation in BwDev::kscale): uniform, Epanechnikov, triangle,
+// biweight, triweight.
+template <typename T>
+__device__ __forceinline__ T compact_k(int kern, T u2) {
+  if (!(u2 <= T(1))) return T(0);
+  const T e = T(1) - u2;
+  switch (kern) {
+    case FKREG_KERNEL_UNIFORM: return T(1);
+    case FKREG_KERNEL_EPANECHNIKOV: return e;
+    case FKREG_KERNEL_TRIANGLE: return T(1) - sqrt(u2);
+    case FKREG_KERNEL_BIWEIGHT: return e * e;
+    default: return e * e * e;
+  }
+}
+
+// Direct moment sums of one evaluation point q (coordinates relative to lo)
+// over the binned samples inside its kernel support: acc[0..ns) the s-fields,
+// acc[ns + r nt + k] the t-fields of strengths str_first + r (sorted order).
+template <typename T>
+__device__ __forceinline__ void direct_sums(const GeoDev& g, const MonoTab& mono, const BwDev& B,
+                                            int64_t n, const T* __restrict__ xs,
+                                            const T* __restrict__ str, int str_first, int nstr,
+                                            const uint32_t* __restrict__ bin_start,
+                                            const double* q, double* acc) {
+  const int D = g.d, ns = mono.n, nt = mono.nt;
+  int64_t blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+  for (int j = 0; j < D; ++j) {
+    const double hw = B.sigma[j];
+    int64_t c0 = int64_t(floor((q[j] - hw) * g.inv_h[j]));
+    int64_t c1 = int64_t(floor((q[j] + hw) * g.inv_h[j]));
+    c0 = c0 < 0 ? 0 : (c0 > g.nf[j] - 1 ? g.nf[j] - 1 : c0);
+    c1 = c1 < 0 ? 0 : (c1 > g.nf[j] - 1 ? g.nf[j] - 1 : c1);
+    blo[j] = c0 / g.tile[j];
+    bhi[j] = c1 / g.tile[j];
+  }
+  for (int f = 0; f < ns + nstr * nt; ++f) acc[f] = 0.0;
+  for (int64_t b0 = blo[0]; b0 <= bhi[0]; ++b0)
+    for (int64_t b1 = blo[1]; b1 <= (D > 1 ? bhi[1] : 0); ++b1)
+      for (int64_t b2 = blo[2]; b2 <= (D > 2 ? bhi[2] : 0); ++b2) {
+        int64_t bin = b0;
+        if (D > 1) bin = bin * g.nbins[1] + b1;
+        if (D > 2) bin = bin * g.nbins[2] + b2;
+        const uint32_t i0 = bin_start[bin], i1 = bin_start[bin + 1];
+        for (uint32_t i = i0; i < i1; ++i) {
+          double z[3] = {0.0, 0.0, 0.0};
+          for (int j = 0; j < D; ++j) z[j] = double(xs[int64_t(j) * n + i]) - q[j];
+          double u2 = 0.0;
+          for (int a = 0; a < D; ++a)
+            for (int c = 0; c < D; ++c) u2 += z[a] * B.Hinv[a * 3 + c] * z[c];
+          if (!(u2 <= 1.0)) continue;
+          const double wgt = B.kscale * compact_k<double>(g.kern, u2);
+          double zp[3][5];
+          for (int j = 0; j < 3; ++j) {
+            zp[j][0] = 1.0;
+            for (int e = 1; e < 5; ++e) zp[j][e] = zp[j][e - 1] * z[j];
+          }
+          for (int f = 0; f < ns; ++f)
+            acc[f] += wgt * zp[0][mono.e[f][0]] * zp[1][mono.e[f][1]] * zp[2][mono.e[f][2]];
+          for (int r = 0; r < nstr; ++r) {
+            const double cw = wgt * double(str[int64_t(str_first + r) * n + i]);
+            for (int k = 0; k < nt; ++k)
+              acc[ns + r * nt + k] += cw * zp[0][mono.e[k][0]] * zp[1][mono.e[k][1]] * zp[2][mono.e[k][2]];
+          }
+        }
+      }
+}
+
 template <typename T>
 __device__ __forceinline__ T sel3(int ax, T a, T b, T c) {
   return ax == 0 ? a : (ax == 1 ? b : c);

@@ -39,6 +39,7 @@ struct GeoDev {
   int64_t tile[3];
   int64_t nbins[3];
   int kbits;        // within-bin bits of the sort key (see key_local_bits)
+  int kern;         // regression kernel: FKREG_KERNEL_GAUSSIAN (NUFFT) or a compact one (direct)
 };
 
 // Sort keys are (bin << kbits) | local, local = row-major index of the centre
@@ -66,6 +67,8 @@ struct BwDev {
   int64_t nf[3];       // type-2 fine grid for this bandwidth
   double inv_h[3];     // nf_b / P
   int64_t phi2_off[3]; // offset (doubles) of 1/phihat tables (k >= 0) for type-2
+  double Hinv[9];      // H^-1 (compact kernels)
+  double kscale;       // c_d / sqrt(det H): K_H(z) = kscale k(|H^(-1/2) z|^2) (compact kernels)
 };
 
 // Monomial exponents (degree <= 2) for device code.
@@ -108,6 +111,7 @@ struct fkreg_plan_s {
       r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork,
       r_bV, r_bdx, r_bsc, r_bpart;
   bool backward = false;        // workspace reserved for fkreg_backward
+  bool direct = false;          // compact kernel: direct sums instead of the NUFFT
   int f2bwd = 0;                // fields of the backward passes (one response + probes)
   size_t ws_bytes = 0;
   size_t fft_work_reserved = 0;
@@ -196,6 +200,12 @@ cudaError_t run_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int nrhs
                            void* sigma2, cudaStream_t s);
 cudaError_t run_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, const void* y,
                        void* mhat_at_x, cudaStream_t s);
+// direct path (compact kernels): grid fields of strengths [str_first, str_first + nstr)
+// plus the s-fields, bandwidths [bw_first, bw_first + bw_count), into r_gfield
+cudaError_t run_direct_grid(fkreg_plan_s* P, int str_first, int nstr, int bw_first,
+                            int bw_count, cudaStream_t s);
+cudaError_t run_direct_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes,
+                              void* mhat_at_x, cudaStream_t s);
 cudaError_t run_finalize(fkreg_plan_s* P, int n_probes, const fkreg_outputs* out,
                          cudaStream_t s);
 // kappa (eq. 26 normaliser) of bandwidth b for every response, and

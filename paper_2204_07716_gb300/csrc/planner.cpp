@@ -178,6 +178,112 @@ static fkreg_status fail(std::string* err, fkreg_status st, const char* msg) {
   return st;
 }
 
+// Unit-mass constant c_d of the compact radial profile k on the unit ball in
+// d dimensions (V_d = unit-ball volume): uniform 1/V_d, Epanechnikov
+// (d+2)/(2 V_d), triangle (d+1)/V_d, biweight (d+2)(d+4)/(8 V_d), triweight
+// (d+2)(d+4)(d+6)/(48 V_d).
+static double compact_constant(int kernel, int d) {
+  const double vd = d == 1 ? 2.0 : (d == 2 ? M_PI : 4.0 * M_PI / 3.0);
+  switch (kernel) {
+    case FKREG_KERNEL_UNIFORM: return 1.0 / vd;
+    case FKREG_KERNEL_EPANECHNIKOV: return (d + 2) / (2.0 * vd);
+    case FKREG_KERNEL_TRIANGLE: return (d + 1) / vd;
+    case FKREG_KERNEL_BIWEIGHT: return (d + 2) * (d + 4) / (8.0 * vd);
+    default: return (d + 2) * (d + 4) * (d + 6) / (48.0 * vd);
+  }
+}
+
+// Geometry of the direct-sum path (compact kernels): samples are binned on
+// the output lattice itself (cell j = floor((x - lo) / delta)), bins of T
+// cells with T about half the widest support half-width, so a point's
+// support spans a few bins per axis.  No FFT grids.
+static fkreg_status compute_geometry_direct(const fkreg_opts* o, fkreg_geometry* g,
+                                            std::string* err, std::vector<BwDev>* bwv,
+                                            std::vector<double>* tab, int64_t phi1_off[3],
+                                            GeoDev* geo, const std::vector<double>& Hinv,
+                                            const std::vector<double>& det) {
+  const int d = o->dim, nbw = o->n_bw, order = o->order;
+  std::memset(g, 0, sizeof(*g));
+  g->dim = d;
+  g->w = 2;
+  g->beta = 0.0;
+  std::vector<BwDev> bws(nbw);
+  const double cd = compact_constant(o->kernel, d);
+  for (int b = 0; b < nbw; ++b) {
+    BwDev& B = bws[b];
+    std::memset(&B, 0, sizeof(B));
+    const double* Hb = o->H + size_t(b) * d * d;
+    for (int a = 0; a < d; ++a)
+      for (int c = 0; c < d; ++c) {
+        B.H[a * 3 + c] = Hb[a * d + c];
+        B.Hinv[a * 3 + c] = Hinv[size_t(b) * d * d + a * d + c];
+      }
+    B.kscale = cd / std::sqrt(det[b]);
+    B.k0 = B.kscale;
+    for (int j = 0; j < 3; ++j) {
+      B.sigma[j] = j < d ? std::sqrt(Hb[j * d + j]) : 1.0;
+      B.K[j] = 1;
+      B.nf[j] = j < d ? o->grid_n[j] : 1;
+    }
+  }
+  for (int j = 0; j < 3; ++j) {
+    if (j >= d) {
+      g->ldft[j] = g->modes[j] = g->nf[j] = g->tile[j] = g->nbins[j] = 1;
+      g->period[j] = g->delta[j] = g->inv_h[j] = 1;
+      continue;
+    }
+    const int64_t M = o->grid_n[j];
+    const double delta = (o->grid_hi[j] - o->grid_lo[j]) / double(M - 1);
+    g->delta[j] = delta;
+    g->ldft[j] = M;
+    g->modes[j] = 1;
+    g->nf[j] = M;
+    g->period[j] = delta * double(M);
+    g->inv_h[j] = double(M - 1) / (o->grid_hi[j] - o->grid_lo[j]);
+    if (o->precision == FKREG_F32) g->inv_h[j] = double(float(g->inv_h[j]));
+    double rmax = 0;
+    for (int b = 0; b < nbw; ++b) rmax = std::max(rmax, bws[b].sigma[j] / delta);
+    int64_t t = o->tile > 0 ? o->tile : std::max<int64_t>(1, std::min<int64_t>(64, int64_t(std::ceil(0.5 * rmax))));
+    t = std::min<int64_t>(t, M);
+    g->tile[j] = t;
+    g->nbins[j] = (M + t - 1) / t;
+    for (auto& B : bws) B.inv_h[j] = g->inv_h[j];
+  }
+  g->ns = nmono(d, 2 * order);
+  g->nt = nmono(d, order);
+  double nb = 1;
+  for (int j = 0; j < d; ++j) nb *= double(g->nbins[j]);
+  if (nb > 4.0e9) return fail(err, FKREG_ERR_UNSUPPORTED, "too many bins (raise tile)");
+  if (tab) tab->clear();
+  if (phi1_off)
+    for (int j = 0; j < 3; ++j) phi1_off[j] = 0;
+  if (bwv) *bwv = bws;
+  if (geo) {
+    std::memset(geo, 0, sizeof(*geo));
+    geo->d = d;
+    geo->w = g->w;
+    geo->pad = (g->w + 1) / 2;
+    geo->skind = o->spread_kernel;
+    geo->beta = 0.0;
+    geo->kern = o->kernel;
+    for (int j = 0; j < 3; ++j) {
+      geo->nf[j] = g->nf[j];
+      geo->L[j] = g->ldft[j];
+      geo->M[j] = (j < d) ? o->grid_n[j] : 1;
+      geo->K[j] = 1;
+      geo->P[j] = g->period[j];
+      geo->lo[j] = (j < d) ? o->grid_lo[j] : 0;
+      geo->hi[j] = (j < d) ? o->grid_hi[j] : 0;
+      geo->inv_h[j] = g->inv_h[j];
+      geo->inv_h_f[j] = float(g->inv_h[j]);
+      geo->tile[j] = g->tile[j];
+      geo->nbins[j] = g->nbins[j];
+    }
+    geo->kbits = key_local_bits(d, geo->tile, geo->nbins);
+  }
+  return FKREG_OK;
+}
+
 fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::string* err,
                               std::vector<BwDev>* bwv, std::vector<double>* tab,
                               int64_t phi1_off[3], GeoDev* geo) {
@@ -187,8 +293,10 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
   if (o->order < 0 || o->order > 2) return fail(err, FKREG_ERR_INVALID_ARG, "order must be 0, 1 or 2");
   if (o->order == 2 && o->dim > 2)
     return fail(err, FKREG_ERR_UNSUPPORTED, "order 2 (local quadratic) is supported in 1-D and 2-D");
-  if (o->kernel != FKREG_KERNEL_GAUSSIAN)
-    return fail(err, FKREG_ERR_UNSUPPORTED, "only the Gaussian regression kernel is supported");
+  if (o->kernel < FKREG_KERNEL_GAUSSIAN || o->kernel > FKREG_KERNEL_TRIWEIGHT)
+    return fail(err, FKREG_ERR_INVALID_ARG, "unknown regression kernel");
+  if (o->kernel != FKREG_KERNEL_GAUSSIAN && (o->flags & FKREG_WANT_BACKWARD))
+    return fail(err, FKREG_ERR_UNSUPPORTED, "the backward needs the Gaussian kernel");
   if (o->spread_kernel != FKREG_SPREAD_ES && o->spread_kernel != FKREG_SPREAD_GAUSS)
     return fail(err, FKREG_ERR_INVALID_ARG, "spread_kernel must be FKREG_SPREAD_ES or FKREG_SPREAD_GAUSS");
   if (o->precision != FKREG_F32 && o->precision != FKREG_F64)
@@ -212,6 +320,9 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
   for (int b = 0; b < nbw; ++b)
     if (!spd_inverse(d, o->H + size_t(b) * d * d, &Hinv[size_t(b) * d * d], &det[b]))
       return fail(err, FKREG_ERR_INVALID_ARG, "every bandwidth matrix H must be symmetric positive definite");
+
+  if (o->kernel != FKREG_KERNEL_GAUSSIAN)
+    return compute_geometry_direct(o, g, err, bwv, tab, phi1_off, geo, Hinv, det);
 
   std::memset(g, 0, sizeof(*g));
   g->dim = d;
@@ -376,6 +487,7 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
       geo->nbins[j] = g->nbins[j];
     }
     geo->kbits = key_local_bits(d, geo->tile, geo->nbins);
+    geo->kern = FKREG_KERNEL_GAUSSIAN;
   }
   return FKREG_OK;
 }

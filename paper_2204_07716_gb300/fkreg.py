@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "libfkreg.so")
 
 FKREG_F32, FKREG_F64 = 0, 1
 FKREG_SPREAD_ES, FKREG_SPREAD_GAUSS = 0, 1
+KERNELS = {"gaussian": 0, "uniform": 1, "epanechnikov": 2, "triangle": 3, "biweight": 4,
+           "triweight": 5}
 FKREG_GCV_EXACT_TRACE = 1
 FKREG_WANT_BACKWARD = 2
 STAGES = ["sort", "strengths", "spread", "fft_fwd", "kmul_grid", "fft_grid", "grid_solve",
@@ -145,11 +147,11 @@ def make_opts(d: int, order: int, grid_n: Sequence[int], lo: Sequence[float],
               hi: Sequence[float], H: np.ndarray, n_rhs: int = 1, max_probes: int = 0,
               tol: float = 1e-6, precision: str = "f32", y_complex: bool = False,
               spread_kernel: str = "es", mask_rho: float = 0.0, tile: int = 0,
-              flags: int = 0):
+              flags: int = 0, kernel: str = "gaussian"):
     """Build an Opts struct; returns (opts, keepalive) -- keep both alive."""
     H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1, d, d))
     o = Opts()
-    o.dim, o.order, o.kernel = d, order, 0
+    o.dim, o.order, o.kernel = d, order, KERNELS[kernel]
     o.spread_kernel = FKREG_SPREAD_ES if spread_kernel == "es" else FKREG_SPREAD_GAUSS
     o.precision = FKREG_F32 if precision == "f32" else FKREG_F64
     o.y_complex = int(bool(y_complex))
@@ -199,7 +201,7 @@ class Plan:
     def __init__(self, d: int, order: int, grid_n, lo, hi, H, max_n: int, n_rhs: int = 1,
                  max_probes: int = 0, tol: float = 1e-6, precision: str = "f32",
                  y_complex: bool = False, spread_kernel: str = "es", mask_rho: float = 0.0,
-                 tile: int = 0, flags: int = 0, device=None):
+                 tile: int = 0, flags: int = 0, device=None, kernel: str = "gaussian"):
         import torch
         self.torch = torch
         self.L = load()
@@ -214,7 +216,7 @@ class Plan:
         self.cdtype = torch.complex64 if precision == "f32" else torch.complex128
         self._opts, self._keep = make_opts(d, order, grid_n, lo, hi, H, n_rhs, max_probes, tol,
                                            precision, y_complex, spread_kernel, mask_rho, tile,
-                                           flags)
+                                           flags, kernel)
         self.n_bw = self._opts.n_bw
         g = Geometry()
         self._check_global(self.L.fkreg_geometry_query(ctypes.byref(self._opts), ctypes.byref(g)))

@@ -410,6 +410,52 @@ def test_predict_at_new_points(d, prec):
         np.testing.assert_allclose(got[ok], ref[ok], rtol=rt, atol=rt * np.max(np.abs(gh[np.isfinite(gh)])))
 
 
+@pytest.mark.parametrize("kernel,d,order,prec", [("epanechnikov", 1, 1, "f64"),
+                                                  ("uniform", 2, 0, "f64"),
+                                                  ("triangle", 2, 1, "f64"),
+                                                  ("biweight", 2, 2, "f64"),
+                                                  ("triweight", 3, 1, "f64"),
+                                                  ("epanechnikov", 2, 1, "f32")])
+def test_compact_kernel_direct_path(kernel, d, order, prec):
+    # compact kernels: exact direct sums on the grid and at the samples
+    grid = {1: 80, 2: 30, 3: 12}[d]
+    sig = {1: 0.05, 2: 0.09, 3: 0.2}[d]
+    w = inputs.random_small(120 + d + order, d, 3000, grid, order, [sig], precision=prec,
+                            tol=1e-12 if prec == "f64" else 1e-6)
+    p = plan_for(w, n_probes=1, kernel=kernel)
+    p.set_points(torch.tensor(w.x))
+    z = oracle.probes(9, 1, w.n)
+    out = p.df(torch.tensor(w.y), 1, probes=torch.tensor(z),
+               want=("mhat_grid", "mask", "moments", "mhat_at_x"))
+    p.sync()
+    bar = BAR[(w.precision, w.tol)]
+    x, y = as_seen(w)
+    H = w.H[0]
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    r = oracle.smooth_at_compact(x, y, H, order, gp, kernel)
+    a1 = oracle.moment_sums_compact(x, np.ones((1, w.n)), H, 0, gp, kernel)[:, 0, 0]
+    ay = oracle.moment_sums_compact(x, np.abs(y), H, 0, gp, kernel)[:, 0, 0]
+    mask = out["mask"][0].reshape(-1).cpu().numpy().astype(bool)
+    mg = out["mhat_grid"][0, 0].reshape(-1).cpu().numpy()
+    assert mhat_error(mg, r["mhat"][:, 0], r["s"][:, 0], ay, mask) < bar
+    mom = out["moments"][0].reshape(out["moments"].shape[1], -1).cpu().numpy()
+    ex = oracle.monomials(w.d, 2 * order)
+    for f in range(r["s"].shape[1]):
+        assert field_error(mom[f], r["s"][:, f], a1, field_scale_sigma(H, ex[f])) < bar
+    # at the samples: mhat, RSS, the exact trace and the Monte-Carlo trace
+    rx = oracle.smooth_at_compact(x, y, H, order, x, kernel)
+    ayx = oracle.moment_sums_compact(x, np.abs(y), H, 0, x, kernel)[:, 0, 0]
+    mh = out["mhat_at_x"][0, 0].cpu().numpy()
+    assert mhat_error(mh, rx["mhat"][:, 0], rx["s"][:, 0], ayx) < bar
+    k0 = float(oracle.compact_profile(kernel, d, 0.0)) / math.sqrt(np.linalg.det(H))
+    tr_exact = k0 * np.nansum(rx["sinv11"])
+    rel = 1e-9 if prec == "f64" else 1e-4
+    assert out["trace"][0, 2].item() == pytest.approx(tr_exact, rel=rel)
+    sz = oracle.smooth_at_compact(x, z, H, order, x, kernel)["mhat"][:, 0]
+    girard = w.n * float(z[0] @ sz) / float(z[0] @ z[0])
+    assert out["trace"][0, 0].item() == pytest.approx(girard, rel=rel)
+
+
 # ------------------------------------------------------------ edge cases ----
 def test_empty_and_single_sample():
     w = inputs.random_small(80, 2, 1, 20, 0, [0.1], precision="f64", tol=1e-12)
