@@ -48,13 +48,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="ll2d",
                     choices=["ll2d", "nw1d", "nw3d_df", "ll2d_gcv", "uneven",
-                             "ll2d_plain64", "ll2d_plain32", "ll2d_logvar"],
+                             "ll2d_plain64", "ll2d_plain32", "ll2d_logvar", "ll2d_epan"],
                     help="ll2d is the headline line; the others measure the remaining "
                          "configurations (1-D NW FP64, 3-D NW + DF sweep, 2-D LL GCV "
                          "forward + backward, 64 uneven problems in one graph) and the "
                          "plain single-response form of the ll2d step (FP64 or FP32: "
                          "one smooth call per response / probe, no stacking), and the "
-                         "ll2d smooth followed by the log-variance estimator (eqs. 24-26)")
+                         "ll2d smooth followed by the log-variance estimator (eqs. 24-26), "
+                         "and the ll2d step with the Epanechnikov kernel (direct sums)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="sample-count multiplier for the extra workloads (1 = full size)")
     return ap.parse_args()
@@ -412,6 +413,26 @@ def run_extra(args):
                "n_total": sum(w.n for w in ws), "problems": len(ws),
                "dims": [w.d for w in ws].count(2), "graph": "one captured CUDA graph"}
         dtype = "f32+f64solve"
+    elif wl == "ll2d_epan":
+        # the headline step (df with y + 10 probes, then the variance pass)
+        # with the compact Epanechnikov kernel: direct sums, no NUFFT
+        w = inputs.ll2d(n=int(1_000_000 * sc))
+        np_ = 10
+        plan = fkreg.Plan(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, n_rhs=1,
+                          max_probes=np_, tol=w.tol, precision="f32", device=dev,
+                          kernel="epanechnikov")
+        x = torch.tensor(w.x, dtype=torch.float32, device=dev)
+        y = torch.tensor(w.y[0], dtype=torch.float32, device=dev)
+
+        def step(k):
+            plan.set_points(x)
+            o = plan.df(y, np_, seed=k, want=("mhat_grid", "mask", "mhat_at_x"))
+            plan.variance(y, o["mhat_at_x"])
+        units = w.n * (1 + np_ + 1)
+        cfg = {"workload": "ll2d-1M-256sq-LL-epanechnikov-direct-f32", "n": w.n,
+               "grid": list(w.grid_n), "probes": np_, "geometry": plan.geom}
+        dtype = "f32+f64solve"
+        extra["plan"] = plan
     elif wl == "ll2d_logvar":
         # smooth y, then the log-variance estimator on its residuals
         w = inputs.ll2d(n=int(1_000_000 * sc))

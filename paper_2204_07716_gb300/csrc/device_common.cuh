@@ -46,17 +46,101 @@ __device__ __forceinline__ T compact_k(int kern, T u2) {
   }
 }
 
-// Direct moment sums of one evaluation point q (coordinates relative to lo)
-// over the binned samples inside its kernel support: acc[0..ns) the s-fields,
-// acc[ns + r nt + k] the t-fields of strengths str_first + r (sorted order).
-template <typename T>
-__device__ __forceinline__ void direct_sums(const GeoDev& g, const MonoTab& mono, const BwDev& B,
-                                            int64_t n, const T* __restrict__ xs,
-                                            const T* __restrict__ str, int str_first, int nstr,
-                                            const uint32_t* __restrict__ bin_start,
-                                            const double* q, double* acc) {
-  const int D = g.d, ns = mono.n, nt = mono.nt;
+// Compile-time chain of the monomials of degree <= DEG in d = D variables, in
+// the graded order the plan's monomial table uses (degree by degree, index
+// multisets in lexicographic order): monomial f > 0 is monomial parent[f]
+// times coordinate axis[f].  The monomials of degree <= l are a prefix.
+struct MonoChain {
+  int n;
+  int parent[kMaxMono];
+  int axis[kMaxMono];
+};
+
+__host__ __device__ constexpr MonoChain make_mono_chain(int D, int DEG) {
+  MonoChain c{0, {}, {}};
+  int e[kMaxMono][3] = {};
+  for (int k = 0; k <= DEG; ++k) {
+    int idx[4] = {0, 0, 0, 0};
+    for (;;) {
+      const int m = c.n;
+      for (int j = 0; j < 3; ++j) e[m][j] = 0;
+      for (int j = 0; j < k; ++j) e[m][idx[j]] += 1;
+      c.parent[m] = 0;
+      c.axis[m] = 0;
+      if (k > 0) {
+        const int ax = idx[k - 1];
+        c.axis[m] = ax;
+        for (int r = 0; r < m; ++r) {
+          bool same = true;
+          for (int j = 0; j < 3; ++j)
+            if (e[r][j] != e[m][j] - (j == ax ? 1 : 0)) same = false;
+          if (same) {
+            c.parent[m] = r;
+            break;
+          }
+        }
+      }
+      c.n = m + 1;
+      int p = k - 1;
+      while (p >= 0 && idx[p] == D - 1) --p;
+      if (p < 0) break;
+      idx[p] += 1;
+      for (int j = p + 1; j < k; ++j) idx[j] = idx[p];
+    }
+  }
+  return c;
+}
+
+__host__ __device__ constexpr int mono_count(int D, int DEG) { return make_mono_chain(D, DEG).n; }
+
+template <typename T, int D, int DEG, int F = 0>
+__device__ __forceinline__ void mono_build(T* mo, const T* z) {
+  if constexpr (F < mono_count(D, DEG)) {
+    if constexpr (F == 0) {
+      mo[0] = T(1);
+    } else {
+      constexpr int pf = make_mono_chain(D, DEG).parent[F];
+      constexpr int af = make_mono_chain(D, DEG).axis[F];
+      mo[F] = mo[pf] * z[af];
+    }
+    mono_build<T, D, DEG, F + 1>(mo, z);
+  }
+}
+
+// Shared memory of one warp's candidate queue in direct_warp_sums: 64
+// entries of (z[0..D), weight) in T, then 64 sample indices.
+template <typename T, int D>
+__host__ __device__ constexpr int direct_queue_bytes() {
+  return 64 * (D + 1) * int(sizeof(T)) + 64 * 4;
+}
+
+// Warp-cooperative moment sums of one evaluation point q (coordinates
+// relative to lo) over the binned samples inside its kernel support: the
+// lanes stride over the sample ranges of the support's bins (bins adjacent
+// along the last axis are one contiguous range of the sort) and test each
+// candidate; the ones inside the support are compacted into a per-warp queue
+// in shared memory (qmem, direct_queue_bytes), and each time 32 are queued
+// every lane adds one of them to all fields in registers, so that the
+// monomial and strength work runs on full warps.  The fields are reduced
+// across the warp at the end: field f is returned to lane f mod 32 (out0 for
+// f < 32, out1 above): [0, NS) the s-fields, NS + r NT + k the t-fields of
+// strength str_first + r.  NS and NT are the monomial counts of degrees 2*ORD
+// and ORD; FMAX >= NS + nstr NT bounds the fields.  Sums are in the plan
+// precision T.
+template <typename T, int D, int ORD, int FMAX>
+__device__ __forceinline__ void direct_warp_sums(const GeoDev& g, const BwDev& B, int64_t n,
+                                                 const T* __restrict__ xs,
+                                                 const T* __restrict__ str, int str_first,
+                                                 int nstr, const uint32_t* __restrict__ bin_start,
+                                                 const double* q, int lane, unsigned char* qmem,
+                                                 T& out0, T& out1) {
+  constexpr int NS = mono_count(D, 2 * ORD), NT = mono_count(D, ORD);
+  constexpr int QMAX = (FMAX - NS) / NT;
+  static_assert(QMAX >= 1 && FMAX <= 64, "field bucket");
+  T* qv = reinterpret_cast<T*>(qmem);                                   // [D + 1][64]
+  uint32_t* qi = reinterpret_cast<uint32_t*>(qmem + 64 * (D + 1) * sizeof(T));  // [64]
   int64_t blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+#pragma unroll
   for (int j = 0; j < D; ++j) {
     const double hw = B.sigma[j];
     int64_t c0 = int64_t(floor((q[j] - hw) * g.inv_h[j]));
@@ -66,36 +150,119 @@ __device__ __forceinline__ void direct_sums(const GeoDev& g, const MonoTab& mono
     blo[j] = c0 / g.tile[j];
     bhi[j] = c1 / g.tile[j];
   }
-  for (int f = 0; f < ns + nstr * nt; ++f) acc[f] = 0.0;
-  for (int64_t b0 = blo[0]; b0 <= bhi[0]; ++b0)
-    for (int64_t b1 = blo[1]; b1 <= (D > 1 ? bhi[1] : 0); ++b1)
-      for (int64_t b2 = blo[2]; b2 <= (D > 2 ? bhi[2] : 0); ++b2) {
-        int64_t bin = b0;
-        if (D > 1) bin = bin * g.nbins[1] + b1;
-        if (D > 2) bin = bin * g.nbins[2] + b2;
-        const uint32_t i0 = bin_start[bin], i1 = bin_start[bin + 1];
-        for (uint32_t i = i0; i < i1; ++i) {
-          double z[3] = {0.0, 0.0, 0.0};
-          for (int j = 0; j < D; ++j) z[j] = double(xs[int64_t(j) * n + i]) - q[j];
-          double u2 = 0.0;
-          for (int a = 0; a < D; ++a)
-            for (int c = 0; c < D; ++c) u2 += z[a] * B.Hinv[a * 3 + c] * z[c];
-          if (!(u2 <= 1.0)) continue;
-          const double wgt = B.kscale * compact_k<double>(g.kern, u2);
-          double zp[3][5];
-          for (int j = 0; j < 3; ++j) {
-            zp[j][0] = 1.0;
-            for (int e = 1; e < 5; ++e) zp[j][e] = zp[j][e - 1] * z[j];
+  T qt[D], hi[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    qt[a] = T(q[a]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) hi[a][c] = T(B.Hinv[a * 3 + c]);
+  }
+  const T ks = T(B.kscale);
+  const int kern = g.kern;
+  T acc[FMAX];
+#pragma unroll
+  for (int f = 0; f < FMAX; ++f) acc[f] = T(0);
+  // one queued candidate per lane (lane < cnt) into every field
+  auto consume = [&](int cnt) {
+    if (lane < cnt) {
+      T z[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) z[j] = qv[j * 64 + lane];
+      const T wgt = qv[D * 64 + lane];
+      const int64_t i = qi[lane];
+      T mo[NS];
+      mono_build<T, D, 2 * ORD>(mo, z);
+#pragma unroll
+      for (int f = 0; f < NS; ++f) acc[f] += wgt * mo[f];
+#pragma unroll
+      for (int r = 0; r < QMAX; ++r)
+        if (r < nstr) {
+          const T cw = wgt * str[int64_t(str_first + r) * n + i];
+#pragma unroll
+          for (int k = 0; k < NT; ++k) acc[NS + r * NT + k] += cw * mo[k];
+        }
+    }
+  };
+  int qn = 0;  // queued candidates (warp-uniform)
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t o0 = D > 1 ? bhi[0] - blo[0] + 1 : 1;
+  const int64_t o1 = D > 2 ? bhi[1] - blo[1] + 1 : 1;
+  for (int64_t r0 = 0; r0 < o0; ++r0)
+    for (int64_t r1 = 0; r1 < o1; ++r1) {
+      int64_t first, last;  // bins [first, last] are adjacent in sorted order
+      if (D == 1) {
+        first = blo[0];
+        last = bhi[0];
+      } else if (D == 2) {
+        first = (blo[0] + r0) * g.nbins[1] + blo[1];
+        last = first + (bhi[1] - blo[1]);
+      } else {
+        first = ((blo[0] + r0) * g.nbins[1] + blo[1] + r1) * g.nbins[2] + blo[2];
+        last = first + (bhi[2] - blo[2]);
+      }
+      const uint32_t i1 = bin_start[last + 1];
+      for (uint32_t base = bin_start[first]; base < i1; base += 32) {
+        const uint32_t i = base + uint32_t(lane);
+        T z[D];
+        bool in = false;
+        T wgt = T(0);
+        if (i < i1) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) z[j] = xs[int64_t(j) * n + i] - qt[j];
+          T u2 = T(0);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            T ra = T(0);
+#pragma unroll
+            for (int c = 0; c < D; ++c) ra += hi[a][c] * z[c];
+            u2 += z[a] * ra;
           }
-          for (int f = 0; f < ns; ++f)
-            acc[f] += wgt * zp[0][mono.e[f][0]] * zp[1][mono.e[f][1]] * zp[2][mono.e[f][2]];
-          for (int r = 0; r < nstr; ++r) {
-            const double cw = wgt * double(str[int64_t(str_first + r) * n + i]);
-            for (int k = 0; k < nt; ++k)
-              acc[ns + r * nt + k] += cw * zp[0][mono.e[k][0]] * zp[1][mono.e[k][1]] * zp[2][mono.e[k][2]];
+          in = u2 <= T(1);
+          if (in) wgt = ks * compact_k<T>(kern, u2);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const int slot = qn + __popc(m & below);
+#pragma unroll
+          for (int j = 0; j < D; ++j) qv[j * 64 + slot] = z[j];
+          qv[D * 64 + slot] = wgt;
+          qi[slot] = i;
+        }
+        qn += __popc(m);
+        if (qn >= 32) {
+          __syncwarp();
+          consume(32);
+          __syncwarp();
+          if (lane < qn - 32) {  // move the overflow to the front of the queue
+#pragma unroll
+            for (int j = 0; j <= D; ++j) qv[j * 64 + lane] = qv[j * 64 + 32 + lane];
+            qi[lane] = qi[32 + lane];
           }
+          qn -= 32;
+          __syncwarp();
         }
       }
+    }
+  __syncwarp();
+  consume(qn);
+  __syncwarp();
+  out0 = T(0);
+  out1 = T(0);
+  const int nf = NS + nstr * NT;
+#pragma unroll
+  for (int f = 0; f < FMAX; ++f) {
+    if (f < nf) {
+      T v = acc[f];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == (f & 31)) {
+        if (f < 32)
+          out0 = v;
+        else
+          out1 = v;
+      }
+    }
+  }
 }
 
 template <typename T>

@@ -39,7 +39,6 @@ namespace {
 
 constexpr int kI2Warps = 16;   // global kernel: warps per block (upper bound)
 constexpr int kTWarps = 16;    // TMA kernel: warps per block (upper bound)
-constexpr int kMaxAcc = 512;
 constexpr int kMaxWRun = 32;   // runtime-width fallback
 
 // Gather from a window staged in shared memory: win[(l0 * e1 + l1) * rec + f],
@@ -136,88 +135,6 @@ __device__ __forceinline__ void gather_smem_pair(const float* win, int rec, int 
       acca.y += ra2.y * wa[0][t0];
       accb.x += rb2.x * wb[0][t0];
       accb.y += rb2.y * wb[0][t0];
-    }
-  }
-}
-
-// Per-group epilogue state shared by both kernels.
-struct GroupCtx {
-  int ns, nt, p, nq, n_rhs_real, n_probes, cplx, n_rhs_out, nacc, order, b;
-};
-
-// Phase B of one pass: lane = sample (valid when lane < cnt).  Solves on pass 0,
-// then forms mhat for this pass's responses / probes and accumulates.  FP32
-// runs solve p <= 3 with the compensated FP32 closed forms, everything else
-// goes through FP64.
-template <typename T>
-__device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mono, const BwDev& B,
-                                            const T* my, int pass, int q_done, int q_in, int lane,
-                                            bool valid, int64_t n, const T* cvp, int64_t cstride,
-                                            uint32_t orig, T* __restrict__ mhat_at_x,
-                                            const T* tsc, T af[kMaxP], double* red, T k0,
-                                            const double* isg) {
-  if (pass == 0) {
-    bool ok = false;
-    T a0 = T(0);
-    if (sizeof(T) == 4 && c.p <= 3 && c.order <= 1) {
-      float a[kMaxP] = {0.f, 0.f, 0.f, 0.f};
-      float dsc[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) dsc[k] = float(tsc[k]);
-      if (valid) {
-        float sv[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) sv[k] = k < c.ns ? float(my[k]) : 0.f;
-        ok = lpr_weights_f32(c.p, sv, dsc, a);
-      }
-#pragma unroll
-      for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
-      a0 = ok ? T(a[0]) : T(0);
-    } else {
-      double a[kMaxP] = {0, 0, 0, 0};
-      if (valid) {
-        double sv[kMaxMono];
-#pragma unroll
-        for (int k = 0; k < kMaxMono; ++k) sv[k] = k < c.ns ? double(my[k]) : 0.0;
-        if (c.order == 0) {
-          ok = sv[0] > 0.0;
-          a[0] = ok ? 1.0 / sv[0] : 0.0;
-        } else {
-          ok = lpr_weights_fast(mono, c.p, sv, B.sigma, isg, a);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
-      a0 = ok ? T(a[0]) : T(0);
-    }
-    const T tv = warp_sum_t<T>(valid ? k0 * a0 : T(0));
-    if (lane == 0) red_add<T>(red, c.nacc - 1, tv);
-  }
-  const int fq0 = pass == 0 ? c.ns : 0;
-  for (int qq = 0; qq < q_in; ++qq) {
-    const int q = q_done + qq;
-    T mh = T(0);
-#pragma unroll
-    for (int k = 0; k < kMaxP; ++k)
-      if (k < c.p) mh += af[k] * my[fq0 + qq * c.nt + k];
-    const T cv = valid ? cvp[int64_t(q) * cstride] : T(0);
-    if (q < c.n_rhs_real) {
-      const T r = valid ? cv - mh : T(0);
-      const T v = warp_sum_t<T>(r * r);
-      if (lane == 0) red_add<T>(red, q, v);
-      if (valid && mhat_at_x) {
-        const int mult = c.cplx ? 2 : 1;
-        const int rr = q / mult, pt = q % mult;
-        mhat_at_x[((int64_t(c.b) * c.n_rhs_out + rr) * n + orig) * mult + pt] = mh;
-      }
-    } else {
-      const int pp = q - c.n_rhs_real;
-      const T v1 = warp_sum_t<T>(valid ? cv * mh : T(0));
-      const T v2 = warp_sum_t<T>(valid ? cv * cv : T(0));
-      if (lane == 0) {
-        red_add<T>(red, c.n_rhs_real + pp, v1);
-        red_add<T>(red, c.n_rhs_real + c.n_probes + pp, v2);
-      }
     }
   }
 }
@@ -675,57 +592,6 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
   }
 }
 
-// ---- at-sample pass of the direct path (compact kernels) --------------------
-// Lane per sorted sample: the sample's moment sums over its support come
-// from direct_sums (no field grid), land in the lane's staging row, and phase
-// B follows as in the other kernels (one pass, F2 <= 64).
-template <typename T>
-__global__ void __launch_bounds__(256)
-direct_interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, int order,
-                     int64_t n, const T* __restrict__ xs, const T* __restrict__ str,
-                     const uint32_t* __restrict__ perm, const uint32_t* __restrict__ bin_start,
-                     int F2, int n_rhs_real, int n_probes, int cplx, int n_rhs_out,
-                     T* __restrict__ mhat_at_x, int nacc, int nbw, double* __restrict__ part,
-                     int bstride) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = int(blockDim.x >> 5);
-  double* red_all = reinterpret_cast<double*>(smem_raw);
-  double* red = red_all + warp * nacc;
-  T* my = reinterpret_cast<T*>(red_all + nwarps * nacc) + (warp * 32 + lane) * bstride;
-  for (int a = lane; a < nacc; a += 32) red[a] = 0.0;
-  __syncwarp();
-  const BwDev& B = bwt[b];
-  GroupCtx c{mono.n, mono.nt, mono.nt, n_rhs_real + n_probes, n_rhs_real, n_probes, cplx,
-             n_rhs_out, nacc, order, b};
-  T tsc[kMaxP];
-#pragma unroll
-  for (int k = 0; k < kMaxP; ++k) tsc[k] = (k < c.p) ? T(1.0 / tscale(mono, k, B.sigma)) : T(0);
-  const T k0t = T(B.k0);
-  const double isg[3] = {1.0 / B.sigma[0], 1.0 / B.sigma[1], 1.0 / B.sigma[2]};
-  const int64_t ngroups = (n + 31) / 32;
-  for (int64_t grp = int64_t(blockIdx.x) * nwarps + warp; grp < ngroups;
-       grp += int64_t(gridDim.x) * nwarps) {
-    const int64_t s = grp * 32 + lane;
-    const bool valid = s < n;
-    const int64_t sl = valid ? s : grp * 32;
-    double q[3] = {0.0, 0.0, 0.0};
-    for (int j = 0; j < g.d; ++j) q[j] = double(xs[int64_t(j) * n + sl]);
-    double acc[64];
-    direct_sums<T>(g, mono, B, n, xs, str, 1, c.nq, bin_start, q, acc);
-    for (int f = 0; f < F2; ++f) my[f] = T(acc[f]);
-    T af[kMaxP] = {T(0), T(0), T(0), T(0)};
-    finish_pass<T>(c, mono, B, my, 0, 0, c.nq, lane, valid, n, str + n + sl, n,
-                   valid ? perm[s] : 0u, mhat_at_x, tsc, af, red, k0t, isg);
-  }
-  __syncthreads();
-  for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
-    double t = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) t += red_get<T>(red_all, wv * nacc + a);
-    part[(int64_t(blockIdx.x) * nbw + b) * nacc + a] = t;
-  }
-}
-
 // sum block partials in a fixed order: sums[b][a]; one block per output
 __global__ void reduce_partials(const double* __restrict__ part, int64_t nblk, int nbw, int nacc,
                                 double* __restrict__ sums) {
@@ -968,35 +834,6 @@ cudaError_t launch_gather(fkreg_plan_s* P, int b, int F, T* V, cudaStream_t st) 
 cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream_t st) {
   return P->prec == FKREG_F32 ? launch_gather<float>(P, b, F, static_cast<float*>(V), st)
                               : launch_gather<double>(P, b, F, static_cast<double*>(V), st);
-}
-
-cudaError_t run_direct_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes,
-                              void* mhat_at_x, cudaStream_t st) {
-  if (P->n == 0) return cudaSuccess;
-  const int nacc = n_rhs_str + 2 * n_probes + 1;
-  const int F2 = P->ns + (n_rhs_str + n_probes) * P->nt;
-  if (F2 > 64 || nacc > kMaxAcc) return cudaErrorInvalidValue;
-  const int bstride = F2 | 1;
-  const size_t smem = sizeof(double) * 8 * nacc + P->tsize * 8 * 32 * bstride;
-  const unsigned blocks = unsigned(P->nblk_interp);
-#define FK_DI(TT)                                                                                 \
-  do {                                                                                            \
-    cudaError_t e = cudaFuncSetAttribute(direct_interp_kernel<TT>,                               \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
-    if (e != cudaSuccess) return e;                                                               \
-    direct_interp_kernel<TT><<<blocks, 256, smem, st>>>(                                          \
-        P->geo, P->mono, wsp<BwDev>(P, P->r_bw), b, P->order, P->n, wsp<TT>(P, P->r_xs),          \
-        wsp<TT>(P, P->r_str), perm_ptr(P), wsp<uint32_t>(P, P->r_binstart), F2, n_rhs_str,        \
-        n_probes, P->o.y_complex, P->nrhs, static_cast<TT*>(mhat_at_x), nacc, P->nbw,             \
-        wsp<double>(P, P->r_part), bstride);                                                      \
-  } while (0)
-  if (P->prec == FKREG_F32)
-    FK_DI(float);
-  else
-    FK_DI(double);
-#undef FK_DI
-  P->launches += 1;
-  return cudaGetLastError();
 }
 
 cudaError_t run_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, const void*,

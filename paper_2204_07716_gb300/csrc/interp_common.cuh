@@ -16,6 +16,8 @@ namespace fk {
 
 namespace {
 
+constexpr int kMaxAcc = 512;  // bound on the reduced sums of one at-sample launch
+
 constexpr uint32_t kMaxSpin = 1u << 22;  // bounded mbarrier wait
 constexpr int kLWarps = 16;              // lane-per-sample kernels: warps per block (upper bound)
 
@@ -197,6 +199,88 @@ inline int tma_slack(const GeoDev& g, const BwDev& B, int j) { return B.nf[j] ==
 inline int tma_window(const GeoDev& g, const BwDev& B, int j) {
   const double r = double(B.nf[j]) / double(g.nf[j]);
   return int(std::ceil(double(g.tile[j]) * r)) + g.w + 1 + 2 * tma_slack(g, B, j);
+}
+
+// Per-group epilogue state shared by the at-sample kernels.
+struct GroupCtx {
+  int ns, nt, p, nq, n_rhs_real, n_probes, cplx, n_rhs_out, nacc, order, b;
+};
+
+// Phase B of one pass: lane = sample (valid when lane < cnt).  Solves on pass 0,
+// then forms mhat for this pass's responses / probes and accumulates.  FP32
+// runs solve p <= 3 with the compensated FP32 closed forms, everything else
+// goes through FP64.
+template <typename T>
+__device__ __forceinline__ void finish_pass(const GroupCtx& c, const MonoTab& mono, const BwDev& B,
+                                            const T* my, int pass, int q_done, int q_in, int lane,
+                                            bool valid, int64_t n, const T* cvp, int64_t cstride,
+                                            uint32_t orig, T* __restrict__ mhat_at_x,
+                                            const T* tsc, T af[kMaxP], double* red, T k0,
+                                            const double* isg) {
+  if (pass == 0) {
+    bool ok = false;
+    T a0 = T(0);
+    if (sizeof(T) == 4 && c.p <= 3 && c.order <= 1) {
+      float a[kMaxP] = {0.f, 0.f, 0.f, 0.f};
+      float dsc[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dsc[k] = float(tsc[k]);
+      if (valid) {
+        float sv[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sv[k] = k < c.ns ? float(my[k]) : 0.f;
+        ok = lpr_weights_f32(c.p, sv, dsc, a);
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
+      a0 = ok ? T(a[0]) : T(0);
+    } else {
+      double a[kMaxP] = {0, 0, 0, 0};
+      if (valid) {
+        double sv[kMaxMono];
+#pragma unroll
+        for (int k = 0; k < kMaxMono; ++k) sv[k] = k < c.ns ? double(my[k]) : 0.0;
+        if (c.order == 0) {
+          ok = sv[0] > 0.0;
+          a[0] = ok ? 1.0 / sv[0] : 0.0;
+        } else {
+          ok = lpr_weights_fast(mono, c.p, sv, B.sigma, isg, a);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxP; ++k) af[k] = (ok && k < c.p) ? T(a[k]) * tsc[k] : T(0);
+      a0 = ok ? T(a[0]) : T(0);
+    }
+    const T tv = warp_sum_t<T>(valid ? k0 * a0 : T(0));
+    if (lane == 0) red_add<T>(red, c.nacc - 1, tv);
+  }
+  const int fq0 = pass == 0 ? c.ns : 0;
+  for (int qq = 0; qq < q_in; ++qq) {
+    const int q = q_done + qq;
+    T mh = T(0);
+#pragma unroll
+    for (int k = 0; k < kMaxP; ++k)
+      if (k < c.p) mh += af[k] * my[fq0 + qq * c.nt + k];
+    const T cv = valid ? cvp[int64_t(q) * cstride] : T(0);
+    if (q < c.n_rhs_real) {
+      const T r = valid ? cv - mh : T(0);
+      const T v = warp_sum_t<T>(r * r);
+      if (lane == 0) red_add<T>(red, q, v);
+      if (valid && mhat_at_x) {
+        const int mult = c.cplx ? 2 : 1;
+        const int rr = q / mult, pt = q % mult;
+        mhat_at_x[((int64_t(c.b) * c.n_rhs_out + rr) * n + orig) * mult + pt] = mh;
+      }
+    } else {
+      const int pp = q - c.n_rhs_real;
+      const T v1 = warp_sum_t<T>(valid ? cv * mh : T(0));
+      const T v2 = warp_sum_t<T>(valid ? cv * cv : T(0));
+      if (lane == 0) {
+        red_add<T>(red, c.n_rhs_real + pp, v1);
+        red_add<T>(red, c.n_rhs_real + c.n_probes + pp, v2);
+      }
+    }
+  }
 }
 
 }  // namespace
