@@ -107,6 +107,90 @@ __device__ __forceinline__ void mono_build(T* mo, const T* z) {
   }
 }
 
+// Candidate bins of a support query for points whose coordinates (relative
+// to lo) span [mn_j, mx_j] on each axis.  box(): the bins of the leading axes
+// and the full range of the last axis; row(): one row of leading-axis bins,
+// i.e. a run of bins adjacent along the last axis (one contiguous range of
+// the sort).  With a diagonal H the row's last-axis range is cut to the
+// section of the support ellipsoid nearest to the points: a sample whose
+// leading coordinates lie at distances dx_j from [mn_j, mx_j] can be inside
+// the support only within sigma_d sqrt(1 - sum (dx_j / sigma_j)^2) of
+// [mn_d, mx_d].  The bin arithmetic is FP32 (floor(floor(u) / t) =
+// floor(u / t) for the tile t); every range is widened by 1e-3 sigma and by
+// a rounding margin in bins, so that no sample inside a support is dropped.
+template <int D>
+struct DirectRows {
+  int blo[3], bhi[3];
+  float mn[3], mx[3], sg[3], isg[3], ibw[3], wb[3], mb[3];
+  bool diag;
+
+  __device__ __forceinline__ void box(const GeoDev& g, const BwDev& B) {
+    diag = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (a != c && B.Hinv[a * 3 + c] != 0.0) diag = false;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      blo[j] = 0;
+      bhi[j] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      sg[j] = float(B.sigma[j]);
+      isg[j] = float(1.0 / B.sigma[j]);
+      ibw[j] = float(g.inv_h[j] / double(g.tile[j]));
+      wb[j] = float(double(g.tile[j]) / g.inv_h[j]);
+      mb[j] = 1e-3f + 2e-7f * float(g.nbins[j]);
+      const float hw = sg[j] * 1.001f;
+      const int nb = int(g.nbins[j]);
+      int b0 = int(floorf((mn[j] - hw) * ibw[j] - mb[j]));
+      int b1 = int(floorf((mx[j] + hw) * ibw[j] + mb[j]));
+      blo[j] = b0 < 0 ? 0 : (b0 > nb - 1 ? nb - 1 : b0);
+      bhi[j] = b1 < 0 ? 0 : (b1 > nb - 1 ? nb - 1 : b1);
+    }
+  }
+  __device__ __forceinline__ int rows0() const { return D > 1 ? bhi[0] - blo[0] + 1 : 1; }
+  __device__ __forceinline__ int rows1() const { return D > 2 ? bhi[1] - blo[1] + 1 : 1; }
+
+  // bins [first, last] of row (r0, r1); false when the row is empty
+  __device__ __forceinline__ bool row(const GeoDev& g, int r0, int r1, int64_t& first,
+                                      int64_t& last) const {
+    int lo = blo[D - 1], hi = bhi[D - 1];
+    if (D > 1 && diag) {
+      const int b[2] = {blo[0] + r0, blo[1] + r1};
+      float rem = 1.f;
+#pragma unroll
+      for (int j = 0; j < D - 1; ++j) {
+        const float a = float(b[j]) * wb[j], e = a + wb[j];
+        float dx = fmaxf(a - mx[j], mn[j] - e) - 1e-3f * sg[j];
+        dx = dx > 0.f ? dx : 0.f;
+        const float t = dx * isg[j];
+        rem -= t * t;
+      }
+      if (rem < 0.f) return false;
+      const float hw = sg[D - 1] * (sqrtf(rem) + 1e-3f);
+      const int c0 = int(floorf((mn[D - 1] - hw) * ibw[D - 1] - mb[D - 1]));
+      const int c1 = int(floorf((mx[D - 1] + hw) * ibw[D - 1] + mb[D - 1]));
+      lo = c0 > lo ? c0 : lo;
+      hi = c1 < hi ? c1 : hi;
+      if (lo > hi) return false;
+    }
+    if (D == 1) {
+      first = lo;
+      last = hi;
+    } else if (D == 2) {
+      first = int64_t(blo[0] + r0) * g.nbins[1] + lo;
+      last = first + (hi - lo);
+    } else {
+      first = (int64_t(blo[0] + r0) * g.nbins[1] + blo[1] + r1) * g.nbins[2] + lo;
+      last = first + (hi - lo);
+    }
+    return true;
+  }
+};
+
 // Shared memory of one warp's candidate queue in direct_warp_sums: 64
 // entries of (z[0..D), weight) in T, then 64 sample indices.
 template <typename T, int D>
@@ -139,17 +223,10 @@ __device__ __forceinline__ void direct_warp_sums(const GeoDev& g, const BwDev& B
   static_assert(QMAX >= 1 && FMAX <= 64, "field bucket");
   T* qv = reinterpret_cast<T*>(qmem);                                   // [D + 1][64]
   uint32_t* qi = reinterpret_cast<uint32_t*>(qmem + 64 * (D + 1) * sizeof(T));  // [64]
-  int64_t blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+  DirectRows<D> rows;
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    const double hw = B.sigma[j];
-    int64_t c0 = int64_t(floor((q[j] - hw) * g.inv_h[j]));
-    int64_t c1 = int64_t(floor((q[j] + hw) * g.inv_h[j]));
-    c0 = c0 < 0 ? 0 : (c0 > g.nf[j] - 1 ? g.nf[j] - 1 : c0);
-    c1 = c1 < 0 ? 0 : (c1 > g.nf[j] - 1 ? g.nf[j] - 1 : c1);
-    blo[j] = c0 / g.tile[j];
-    bhi[j] = c1 / g.tile[j];
-  }
+  for (int j = 0; j < D; ++j) rows.mn[j] = rows.mx[j] = float(q[j]);
+  rows.box(g, B);
   T qt[D], hi[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -185,21 +262,11 @@ __device__ __forceinline__ void direct_warp_sums(const GeoDev& g, const BwDev& B
   };
   int qn = 0;  // queued candidates (warp-uniform)
   const unsigned below = (1u << lane) - 1u;
-  const int64_t o0 = D > 1 ? bhi[0] - blo[0] + 1 : 1;
-  const int64_t o1 = D > 2 ? bhi[1] - blo[1] + 1 : 1;
-  for (int64_t r0 = 0; r0 < o0; ++r0)
-    for (int64_t r1 = 0; r1 < o1; ++r1) {
+  const int o0 = rows.rows0(), o1 = rows.rows1();
+  for (int r0 = 0; r0 < o0; ++r0)
+    for (int r1 = 0; r1 < o1; ++r1) {
       int64_t first, last;  // bins [first, last] are adjacent in sorted order
-      if (D == 1) {
-        first = blo[0];
-        last = bhi[0];
-      } else if (D == 2) {
-        first = (blo[0] + r0) * g.nbins[1] + blo[1];
-        last = first + (bhi[1] - blo[1]);
-      } else {
-        first = ((blo[0] + r0) * g.nbins[1] + blo[1] + r1) * g.nbins[2] + blo[2];
-        last = first + (bhi[2] - blo[2]);
-      }
+      if (!rows.row(g, r0, r1, first, last)) continue;
       const uint32_t i1 = bin_start[last + 1];
       for (uint32_t base = bin_start[first]; base < i1; base += 32) {
         const uint32_t i = base + uint32_t(lane);

@@ -243,7 +243,7 @@ static fkreg_status compute_geometry_direct(const fkreg_opts* o, fkreg_geometry*
     if (o->precision == FKREG_F32) g->inv_h[j] = double(float(g->inv_h[j]));
     double rmax = 0;
     for (int b = 0; b < nbw; ++b) rmax = std::max(rmax, bws[b].sigma[j] / delta);
-    int64_t t = o->tile > 0 ? o->tile : std::max<int64_t>(1, std::min<int64_t>(64, int64_t(std::ceil(0.5 * rmax))));
+    int64_t t = o->tile > 0 ? o->tile : std::max<int64_t>(1, std::min<int64_t>(64, int64_t(std::ceil(0.25 * rmax))));
     t = std::min<int64_t>(t, M);
     g->tile[j] = t;
     g->nbins[j] = (M + t - 1) / t;

@@ -456,6 +456,48 @@ def test_compact_kernel_direct_path(kernel, d, order, prec):
     assert out["trace"][0, 0].item() == pytest.approx(girard, rel=rel)
 
 
+@pytest.mark.parametrize("kernel,full_h,prec", [("epanechnikov", True, "f64"),
+                                                 ("biweight", False, "f64"),
+                                                 ("triangle", True, "f32")])
+def test_compact_probes_and_variance(kernel, full_h, prec):
+    # several probes (strengths in more than one chunk of four), a correlated
+    # H (no row cut) or a diagonal one (rows cut to the ellipse), a sample
+    # cluster denser than one warp per bin, and the variance pass of eq. 23
+    n_pr = 6
+    w = inputs.random_small(131 + int(full_h), 2, 4000, 26, 1, [0.08], precision=prec,
+                            tol=1e-12 if prec == "f64" else 1e-6, full_h=full_h)
+    g = np.random.Generator(np.random.PCG64(77))
+    w.x[:600] = 0.5 + 0.01 * g.standard_normal((600, 2))
+    p = plan_for(w, n_probes=n_pr, kernel=kernel)
+    p.set_points(torch.tensor(w.x))
+    z = oracle.probes(13, n_pr, w.n)
+    out = p.df(torch.tensor(w.y), n_pr, probes=torch.tensor(z), want=("mhat_at_x",))
+    s2 = p.variance(torch.tensor(w.y), out["mhat_at_x"])
+    p.sync()
+    bar = BAR[(w.precision, w.tol)]
+    x, y = as_seen(w)
+    H = w.H[0]
+    rx = oracle.smooth_at_compact(x, y, H, 1, x, kernel)
+    ayx = oracle.moment_sums_compact(x, np.abs(y), H, 0, x, kernel)[:, 0, 0]
+    mh = out["mhat_at_x"][0, 0].cpu().numpy()
+    assert mhat_error(mh, rx["mhat"][:, 0], rx["s"][:, 0], ayx) < bar
+    sz = oracle.smooth_at_compact(x, z, H, 1, x, kernel)["mhat"]
+    girard = w.n * np.mean([float(z[k] @ sz[:, k]) / float(z[k] @ z[k]) for k in range(n_pr)])
+    rel = 1e-9 if prec == "f64" else 1e-4
+    assert out["trace"][0, 0].item() == pytest.approx(girard, rel=rel)
+    # variance: the same smoother applied to r_i = (y_i - mhat(x_i))^2 on the grid,
+    # with the device's mhat(x_i) as the common input
+    r = (y[0] - mh.astype(np.float64)) ** 2
+    if prec == "f32":
+        r = ((w.y[0].astype(np.float32) - mh) ** 2).astype(np.float64)
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    ro = oracle.smooth_at_compact(x, r, H, 1, gp, kernel)
+    ar = oracle.moment_sums_compact(x, np.abs(r), H, 0, gp, kernel)[:, 0, 0]
+    s0 = ro["s"][:, 0]
+    valid = s0 >= 2e-3 * s0.max()
+    assert mhat_error(s2[0, 0].reshape(-1).cpu().numpy(), ro["mhat"][:, 0], s0, ar, valid) < bar
+
+
 # ------------------------------------------------------------ edge cases ----
 def test_empty_and_single_sample():
     w = inputs.random_small(80, 2, 1, 20, 0, [0.1], precision="f64", tol=1e-12)
