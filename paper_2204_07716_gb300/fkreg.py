@@ -275,7 +275,19 @@ class Plan:
 
     # -- calls -------------------------------------------------------------
     def set_points(self, x):
-        x = self._as_dev(x)
+        """Sample locations [n, d].  A complex vector z on a 2-D plan is the
+        set of points (Re z, Im z): the complex-location regression of
+        Sec. 4.4 smooths over the complex plane as over R^2."""
+        t = self.torch
+        cplx = x.is_complex() if isinstance(x, t.Tensor) else np.iscomplexobj(x)
+        if cplx:
+            if self.d != 2:
+                raise FkregError("complex locations need a 2-D plan")
+            x = self._as_dev(x, complex_ok=True)
+            if x.dim() != 2 or x.shape[1] != 2:
+                raise FkregError("complex locations are a vector of n points")
+        else:
+            x = self._as_dev(x)
         n = int(x.shape[0])
         self._x = x
         self._check(self.L.fkreg_set_points(self.h, n, ctypes.c_void_p(x.data_ptr()), self._stream()))
@@ -455,6 +467,10 @@ def predict(grid, grid_n, lo, hi, xq, method: str = "linear"):
     import torch
     L = load()
     d = len(grid_n)
+    if xq.is_complex():  # complex new points on a 2-D grid: (Re z, Im z)
+        if d != 2:
+            raise FkregError("complex points need a 2-D grid")
+        xq = torch.view_as_real(xq.reshape(-1))
     lead = grid.shape[: grid.dim() - d]
     g = grid.reshape(-1, *grid_n).contiguous()
     x = xq.to(g.dtype).reshape(-1, d).contiguous()

@@ -176,6 +176,21 @@ def uneven(n_problems: int = 64, nmin: float = 1e3, nmax: float = 1e6,
     return out
 
 
+def complex_log2d(n: int = 2500, grid: int = 24, sigma: float = 0.2) -> Workload:
+    """Complex-location regression of Sec. 4.4: points z = x1 + i x2 with
+    x1 ~ U[0.1, 2.1], x2 ~ U[-2, 2], complex responses log z plus noise of
+    a tenth of the real and imaginary parts' spreads.  x holds (Re z, Im z);
+    y[0] is the complex response."""
+    g = _rng(6)
+    x = np.column_stack([2.0 * g.random(n) + 0.1, 4.0 * g.random(n) - 2.0])
+    z = x[:, 0] + 1j * x[:, 1]
+    y = np.log(z)
+    y = (y + 0.1 * np.std(y.real) * g.standard_normal(n)
+         + 0.1j * np.std(y.imag) * g.standard_normal(n))
+    return Workload("complex_log2d", 2, x, y[None], (grid, grid), (0.1, -2.0), (2.1, 2.0),
+                    iso_bandwidths([sigma], 2), 1, 1e-12, "f64", 0)
+
+
 def random_small(seed: int, d: int, n: int, grid, order: int, sigmas,
                  precision: str = "f64", tol: float = 1e-12, n_rhs: int = 1,
                  n_probes: int = 0, full_h: bool = False) -> Workload:

@@ -211,6 +211,38 @@ def test_stacked_and_complex_responses():
         check_grid(wr, o2)
 
 
+def test_complex_locations():
+    # Sec. 4.4: complex points z smoothed over the plane as (Re z, Im z), with
+    # complex responses; grid, at-sample values and prediction at complex points
+    from paper_2204_07716_gb300.fkreg import Plan, predict
+    wc = inputs.complex_log2d()
+    z = wc.x[:, 0] + 1j * wc.x[:, 1]
+    p = Plan(2, 1, wc.grid_n, wc.lo, wc.hi, wc.H, max_n=wc.n, n_rhs=1, tol=1e-12,
+             precision="f64", y_complex=True)
+    p.set_points(torch.tensor(z))
+    out = p.smooth(torch.tensor(wc.y[0]), want=("mhat_grid", "mask", "mhat_at_x"))
+    p.sync()
+    mg = out["mhat_grid"][0, 0].reshape(-1).cpu().numpy()
+    for part in ("re", "im"):
+        yy = wc.y[0].real if part == "re" else wc.y[0].imag
+        wr = inputs.Workload("c", 2, wc.x, yy[None], wc.grid_n, wc.lo, wc.hi, wc.H, 1, 1e-12, "f64")
+        o2 = {"mhat_grid": torch.tensor((mg.real if part == "re" else mg.imag).reshape((1, 1) + wc.grid_n)),
+              "mask": out["mask"]}
+        check_grid(wr, o2)
+    ro = oracle.smooth_at(wc.x, np.stack([wc.y[0].real, wc.y[0].imag]), wc.H[0], 1, wc.x)
+    ay = oracle.scale_field(wc.x, np.stack([wc.y[0].real, wc.y[0].imag]), wc.H[0], wc.x)
+    mh = out["mhat_at_x"][0, 0].cpu().numpy()
+    assert mhat_error(mh.real, ro["mhat"][:, 0], ro["s"][:, 0], ay[:, 0]) < 1e-10
+    assert mhat_error(mh.imag, ro["mhat"][:, 1], ro["s"][:, 0], ay[:, 1]) < 1e-10
+    # prediction at complex points equals prediction at their (re, im) pairs
+    g = torch.nan_to_num(out["mhat_grid"][0, 0].real.contiguous())
+    zq = torch.tensor(z[:50])
+    a = predict(g, wc.grid_n, wc.lo, wc.hi, zq, "linear")
+    b = predict(g, wc.grid_n, wc.lo, wc.hi, torch.tensor(wc.x[:50]), "linear")
+    p.sync()
+    assert torch.equal(a, b)
+
+
 def test_ll2d_full_size_sampled():
     # 2-D local linear, N = 10^6, 256^2 grid, FP32, tol 1e-6 (sampled grid points)
     w = inputs.ll2d()
