@@ -488,6 +488,35 @@ def predict(grid, grid_n, lo, hi, xq, method: str = "linear"):
     return out.reshape(*lead, x.shape[0])
 
 
+class StepGraph:
+    """A sequence of plan calls captured once as a CUDA graph.
+
+    ``fn()`` issues the calls on the current stream and returns their
+    outputs.  It runs ``warmup`` times on a side stream, then once under
+    capture; ``replay()`` re-issues every kernel, copy and FFT of the
+    sequence with one launch, reading the same input buffers (copy new data
+    into them before a replay) and writing the tensors ``fn`` returned at
+    capture (``outputs``).  Stage timing must be off during capture.  Seeds
+    given to the captured calls are fixed at capture.
+    """
+
+    def __init__(self, fn, warmup: int = 2):
+        import torch
+        self.torch = torch
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.outputs = fn()
+
+    def replay(self):
+        self.graph.replay()
+
+
 class Batch:
     """Independent problems replayed as one captured CUDA graph.
 

@@ -1,6 +1,7 @@
 """Uneven batch of independent problems in one captured CUDA graph: results
 equal the standalone plans', one problem checked against the FP64 oracle,
-per-problem latencies from the device timer, and the tile autotuner."""
+per-problem latencies from the device timer, the tile autotuner, and one
+plan's whole step captured as a graph (StepGraph)."""
 import numpy as np
 import pytest
 
@@ -77,3 +78,42 @@ def test_autotuner_picks_a_candidate():
     y = torch.tensor(w.y, dtype=torch.float32, device="cuda")
     t = autotune_tile(kw, x, y, candidates=(8, 16, 32))
     assert t in (8, 16, 32)
+
+
+def test_step_graph_replays_the_eager_step():
+    # set_points + df (device probes) + variance captured as one CUDA graph:
+    # a replay after new data is copied into the input buffers gives the eager
+    # step's results on that data (FP64; the spreading's atomic order may
+    # differ between runs, so the comparison allows rounding)
+    from paper_2204_07716_gb300.fkreg import Plan, StepGraph
+    w = inputs.random_small(150, 2, 3000, 28, 1, [0.06], precision="f64", tol=1e-12)
+    p = Plan(2, 1, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, n_rhs=1, max_probes=4, tol=1e-12,
+             precision="f64")
+    x = torch.tensor(w.x, device="cuda")
+    y = torch.tensor(w.y, device="cuda")
+
+    def step():
+        p.set_points(x)
+        o = p.df(y, 4, seed=5, want=("mhat_grid", "mask", "mhat_at_x"))
+        return o, p.variance(y, o["mhat_at_x"])
+
+    g = StepGraph(step)
+    g2 = inputs.random_small(151, 2, 3000, 28, 1, [0.06], precision="f64", tol=1e-12)
+    x.copy_(torch.tensor(g2.x))
+    y.copy_(torch.tensor(g2.y))
+    g.replay()
+    go, gs2 = g.outputs
+    eo, es2 = step()
+    torch.cuda.synchronize()
+    p.sync()
+    for a, b in ((go["mhat_grid"], eo["mhat_grid"]), (go["mhat_at_x"], eo["mhat_at_x"]),
+                 (gs2, es2), (go["gcv"], eo["gcv"]), (go["trace"], eo["trace"])):
+        a, b = torch.nan_to_num(a), torch.nan_to_num(b)
+        assert torch.allclose(a, b, rtol=1e-11, atol=1e-12 * float(b.abs().max()))
+    assert torch.equal(go["mask"], eo["mask"])
+    # and it differs from the first data set's result (the buffers were read)
+    y.copy_(torch.tensor(w.y))
+    x.copy_(torch.tensor(w.x))
+    g.replay()
+    torch.cuda.synchronize()
+    assert not torch.allclose(torch.nan_to_num(go["mhat_grid"]), torch.nan_to_num(eo["mhat_grid"]))
