@@ -249,7 +249,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
     t2_cells = std::max(t2_cells, full_cells(B.nf, d));
     t2_half = std::max(t2_half, half_cells(B.nf, d));
   }
-  const int64_t ntiles = (max_n + 4095) / 4096;
+  const int64_t ntiles = (max_n + fk::kSortTileKeys - 1) / fk::kSortTileKeys;
   const int64_t scan_len = std::max<int64_t>(256 * ntiles, nb + 1);
   Layout L;
   L.take(P->r_err, 256);

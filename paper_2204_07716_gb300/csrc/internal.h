@@ -19,6 +19,7 @@ constexpr int kMaxMono = 35;     // monomials of degree <= 4 in 3-D (s-fields of
 constexpr int kMaxP = 10;        // unknowns of the local-quadratic system in 3-D
 constexpr int kSubMax = 1024;    // samples per spreading sub-problem
 constexpr int kRadixBits = 8;
+constexpr int kSortTileKeys = 4096;  // keys per radix-sort tile (one block)
 
 // Geometry of the whole plan, passed to kernels by value.
 struct GeoDev {

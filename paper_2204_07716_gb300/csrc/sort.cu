@@ -28,8 +28,8 @@ namespace fk {
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;                      // keys per thread per tile
-constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per tile
+constexpr int kSortTile = kSortTileKeys;               // keys per tile
+constexpr int kSortRounds = kSortTile / kSortThreads;  // keys per thread per tile
 constexpr int kScanThreads = 256;
 constexpr int kScanChunk = 1024;                     // elements per scan block
 
@@ -100,14 +100,16 @@ __global__ void bin_keys_hist_kernel(GeoDev g, int64_t n, int64_t nbins, const T
         xv = lo;
       }
       const T u = mul_rn(sub_rn(xv, lo), inv_h_of<T>(g, j));
-      int64_t c = int64_t(floor(u));
+      // 32-bit integer arithmetic: cells, tiles and bins are below 2^31
+      const int nfj = int(g.nf[j]), tj = int(g.tile[j]);
+      int c = int(floor(u));
       if (c < 0) c = 0;
-      if (c > g.nf[j] - 1) c = g.nf[j] - 1;
-      const int64_t b = c / g.tile[j];
-      int64_t e = int64_t(ceil(sub_rn(u, halfw))) + g.w / 2 - b * g.tile[j];
-      e = e < 0 ? 0 : (e > g.tile[j] ? g.tile[j] : e);
+      if (c > nfj - 1) c = nfj - 1;
+      const int b = c / tj;
+      int e = int(ceil(sub_rn(u, halfw))) + g.w / 2 - b * tj;
+      e = e < 0 ? 0 : (e > tj ? tj : e);
       bin = bin * uint32_t(g.nbins[j]) + uint32_t(b);
-      local = local * uint32_t(g.tile[j] + 1) + uint32_t(e);
+      local = local * uint32_t(tj + 1) + uint32_t(e);
     }
     keys[i] = g.kbits ? (bin << g.kbits) | local : bin;
     vals[i] = uint32_t(i);
@@ -198,65 +200,134 @@ __global__ void scan_apply(const uint32_t* in, int64_t n, const uint32_t* __rest
 }
 
 // ---- radix sort passes ---------------------------------------------------
-__global__ void radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                              int64_t ntiles, uint32_t* __restrict__ hist) {
+// A tile of kSortTile keys is split into one contiguous chunk per warp.  Both
+// kernels group equal digits of a 32-key round with match_digit, so one
+// lane per group updates a counter: the upsweep adds to the tile histogram
+// (shared atomics, warps run concurrently); the downsweep first counts per
+// warp, turns the counts into per-warp offsets (warps in chunk order after
+// the tile's scanned global base), then re-walks its keys from registers and
+// writes each key at offset + rank among the equal digits of lower lanes.
+// Order is preserved within a round, across rounds, across warps and across
+// tiles, so every pass is stable.
+// Lanes of the warp holding the same 9-bit value (a digit, or 256 for "no
+// key"): one ballot per bit, AND of the agreeing masks.
+__device__ __forceinline__ uint32_t match_digit(uint32_t dig) {
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const uint32_t bit = (dig >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
+              uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  uint32_t dg[kSortRounds];  // every load of the tile in flight before the first use
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    int64_t i = base + int64_t(r) * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    const int64_t i = base + int64_t(r) * kSortThreads + threadIdx.x;
+    dg[r] = i < n ? (keys[i] >> shift) & 255u : 256u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const uint32_t dig = dg[r];
+    const uint32_t peers = match_digit(dig);
+    if (dig < 256u && (__ffs(peers) - 1) == lane) atomicAdd(&h[dig], uint32_t(__popc(peers)));
   }
   __syncthreads();
   hist[int64_t(threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void radix_downsweep(const uint32_t* __restrict__ keys_in,
-                                const uint32_t* __restrict__ vals_in, int64_t n, int shift,
-                                int64_t ntiles, const uint32_t* __restrict__ hist_scanned,
-                                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t wcnt[kSortThreads / 32][257];
-  __shared__ uint32_t base_off[256];
-  __shared__ uint32_t running[256];
+__global__ void __launch_bounds__(kSortThreads, 2)
+radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                int64_t n, int shift, int64_t ntiles, const uint32_t* __restrict__ hist_scanned,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+  constexpr int NW = kSortThreads / 32;
+  constexpr int RW = kSortTile / NW / 32;  // rounds of 32 keys per warp
+  static_assert(kSortThreads == 256 && RW * NW * 32 == kSortTile, "one thread per digit");
+  __shared__ uint32_t wh[NW][256];        // per-warp digit counts, then offsets in the tile
+  __shared__ uint32_t dstart[256];        // first tile position of each digit
+  __shared__ uint32_t gbase[256];         // first output position of each digit
+  __shared__ uint32_t wsum[NW];
+  __shared__ uint32_t skey[kSortTile], sval[kSortTile];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  running[tid] = hist_scanned[int64_t(tid) * ntiles + blockIdx.x];
+  for (int w = 0; w < NW; ++w) wh[w][tid] = 0;
+  __syncthreads();
   const int64_t tbase = int64_t(blockIdx.x) * kSortTile;
+  const int64_t wbase = tbase + int64_t(warp) * (RW * 32);
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int r = 0; r < kSortRounds; ++r) {
-    for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][tid] = 0;
-    if (tid == 0)
-      for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][256] = 0;
-    __syncthreads();
-    const int64_t i = tbase + int64_t(r) * kSortThreads + tid;
-    const bool valid = i < n;
-    uint32_t key = 0, val = 0, dig = 256;
-    if (valid) {
-      key = keys_in[i];
-      val = vals_in[i];
-      dig = (key >> shift) & 255u;
+  uint32_t key[RW], val[RW];
+#pragma unroll
+  for (int r = 0; r < RW; ++r) {  // every load of the chunk in flight first
+    const int64_t i = wbase + r * 32 + lane;
+    key[r] = i < n ? keys_in[i] : 0u;
+    val[r] = i < n ? vals_in[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < RW; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const uint32_t dig = i < n ? (key[r] >> shift) & 255u : 256u;
+    const uint32_t peers = match_digit(dig);
+    if (dig < 256u && (peers & lt_mask) == 0) wh[warp][dig] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread tid = digit: per-warp offsets inside the digit's run, the digit's
+  // total, then an exclusive scan of the totals over the 256 digits
+  uint32_t tot = 0;
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t t = wh[w][tid];
+    wh[w][tid] = tot;
+    tot += t;
+  }
+  uint32_t inc = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  gbase[tid] = hist_scanned[int64_t(tid) * ntiles + blockIdx.x];
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  dstart[tid] = before + inc - tot;
+  __syncthreads();
+  // tile-local scatter into shared memory (sorted by digit, stable)
+#pragma unroll
+  for (int r = 0; r < RW; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const uint32_t dig = i < n ? (key[r] >> shift) & 255u : 256u;
+    const uint32_t peers = match_digit(dig);
+    uint32_t off = 0;
+    if (dig < 256u) {
+      off = wh[warp][dig];
+      const uint32_t lp = dstart[dig] + off + __popc(peers & lt_mask);
+      skey[lp] = key[r];
+      sval[lp] = val[r];
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, dig);
-    const uint32_t rank = __popc(peers & lt_mask);
-    if ((peers & lt_mask) == 0) wcnt[warp][dig] = __popc(peers);  // lowest lane of the group
-    __syncthreads();
-    {
-      uint32_t run = 0;
-      for (int w = 0; w < kSortThreads / 32; ++w) {
-        uint32_t t = wcnt[w][tid];
-        wcnt[w][tid] = run;
-        run += t;
-      }
-      base_off[tid] = running[tid];
-      running[tid] += run;
-    }
-    __syncthreads();
-    if (valid) {
-      const uint32_t pos = base_off[dig] + wcnt[warp][dig] + rank;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
-    }
-    __syncthreads();
+    __syncwarp();  // every lane has read its group's offset
+    if (dig < 256u && (peers & lt_mask) == 0) wh[warp][dig] = off + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // write out in tile order: consecutive threads write consecutive positions
+  // of one digit's run
+  const int cnt = int(n - tbase < kSortTile ? n - tbase : kSortTile);
+  for (int t = tid; t < cnt; t += kSortThreads) {
+    const uint32_t k = skey[t];
+    const uint32_t dig = (k >> shift) & 255u;
+    const uint32_t pos = gbase[dig] + uint32_t(t) - dstart[dig];
+    keys_out[pos] = k;
+    vals_out[pos] = sval[t];
   }
 }
 
