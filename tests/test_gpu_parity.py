@@ -530,6 +530,64 @@ def test_compact_probes_and_variance(kernel, full_h, prec):
     assert mhat_error(s2[0, 0].reshape(-1).cpu().numpy(), ro["mhat"][:, 0], s0, ar, valid) < bar
 
 
+def test_compact_full_size_sampled():
+    # the ll2d_epan bench step's configuration: N = 10^6 clustered samples,
+    # 256^2 grid, Epanechnikov, FP32, y + 10 device probes; grid values on
+    # sampled grid points and at-sample values on sampled samples against the
+    # oracle's direct sums (the Girard trace is checked through the probes'
+    # smoother in the small cases)
+    w = inputs.ll2d()
+    p = plan_for(w, n_probes=10, kernel="epanechnikov")
+    p.set_points(torch.tensor(w.x))
+    out = p.df(torch.tensor(w.y), 10, seed=3, want=("mhat_grid", "mask", "mhat_at_x"))
+    p.sync()
+    bar = BAR[(w.precision, w.tol)]
+    x, y = as_seen(w)
+    H = w.H[0]
+    half = 1.01 * np.sqrt(np.diag(H))
+
+    ex = [tuple(e) for e in oracle.monomials(2, 2)]
+    lin = [(0, 0), (1, 0), (0, 1)]
+    dsc = np.diag([1.0, 1.0 / np.sqrt(H[0, 0]), 1.0 / np.sqrt(H[1, 1])])
+
+    def ref(q):
+        # the oracle's direct sums over the samples of the query's support box
+        # (every sample outside it has weight exactly 0), and the condition
+        # number of the scaled local-linear system S of eq. 3
+        mh, s0, ay, cond = [], [], [], []
+        for qq in q:
+            sel = np.all(np.abs(x - qq) <= half, axis=1)
+            r = oracle.smooth_at_compact(x[sel], y[:, sel], H, 1, qq[None], "epanechnikov")
+            a = oracle.moment_sums_compact(x[sel], np.abs(y[:, sel]), H, 0, qq[None],
+                                           "epanechnikov")
+            sf = r["s"][0]
+            S = np.array([[sf[ex.index((u[0] + v[0], u[1] + v[1]))] for v in lin] for u in lin])
+            mh.append(r["mhat"][0, 0])
+            s0.append(sf[0])
+            ay.append(a[0, 0, 0])
+            cond.append(np.linalg.cond(dsc @ S @ dsc) if sf[0] > 0 else np.inf)
+        return np.array(mh), np.array(s0), np.array(ay), np.array(cond)
+
+    # Fewer than three samples in a support make S singular: m-hat is not
+    # defined there and any value the rounding gives is as right as another,
+    # so parity is taken where S is well-posed and the rest need only be NaN
+    # or finite (both are)
+    idx = sample_grid_indices(w.grid_n, 200, seed=4)
+    rm, rs, ra, rc = ref(oracle.grid_points(w.grid_n, w.lo, w.hi)[idx])
+    mask = out["mask"][0].reshape(-1).cpu().numpy()[idx].astype(bool)
+    mg = out["mhat_grid"][0, 0].reshape(-1).cpu().numpy()[idx]
+    posed = rc < 1e8
+    assert posed.sum() > 100
+    assert np.all(np.isfinite(mg[mask & posed]))
+    assert mhat_error(mg, rm, rs, ra, mask & posed) < bar
+    si = np.random.default_rng(5).choice(w.n, 200, replace=False)
+    rm, rs, ra, rc = ref(x[si])
+    mh = out["mhat_at_x"][0, 0].cpu().numpy()[si]
+    posed = rc < 1e8
+    assert np.all(np.isfinite(mh[posed]))
+    assert mhat_error(mh[posed], rm[posed], rs[posed], ra[posed]) < bar
+
+
 # ------------------------------------------------------------ edge cases ----
 def test_empty_and_single_sample():
     w = inputs.random_small(80, 2, 1, 20, 0, [0.1], precision="f64", tol=1e-12)
