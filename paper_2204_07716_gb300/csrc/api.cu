@@ -67,6 +67,36 @@ struct StageScope {
   }
 };
 
+// Joins a forked branch back into the caller's stream when it leaves scope
+// (also on early error returns, so no work of the branch is left unordered).
+struct Join {
+  fkreg_plan_s* P = nullptr;
+  cudaStream_t branch = nullptr, caller = nullptr;
+  bool joined = false;
+  bool ok = true;
+  bool done() {
+    if (P && !joined) {
+      joined = true;
+      ok = cudaEventRecord(P->ev_join, branch) == cudaSuccess &&
+           cudaStreamWaitEvent(caller, P->ev_join, 0) == cudaSuccess;
+    }
+    return ok;
+  }
+  Join() = default;
+  Join(fkreg_plan_s* p, cudaStream_t b, cudaStream_t c) : P(p), branch(b), caller(c) {}
+  Join& operator=(Join&& o) noexcept {
+    P = o.P;
+    branch = o.branch;
+    caller = o.caller;
+    joined = o.joined;
+    ok = o.ok;
+    o.P = nullptr;
+    return *this;
+  }
+  Join(const Join&) = delete;
+  ~Join() { done(); }
+};
+
 constexpr size_t kAlign = 256;
 
 struct Layout {
@@ -133,12 +163,17 @@ fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, 
     cufftDestroy(hd);
     return plan_err(P, FKREG_ERR_CUFFT, "cufftMakePlanMany64 failed (" + std::to_string(int(r)) + ")");
   }
-  if (P->ws && work > P->r_fftwork.bytes) {
+  // the inverse grid transforms run beside the others: their own work area
+  const fk::Region& wr = kind == 1 ? P->r_fftwork_g : P->r_fftwork;
+  if (P->ws && work > wr.bytes) {
     cufftDestroy(hd);
     return plan_err(P, FKREG_ERR_WORKSPACE, "cuFFT work area larger than the reserved region");
   }
-  if (P->ws) cufftSetWorkArea(hd, P->ws + P->r_fftwork.off);
-  P->fft_work_reserved = std::max(P->fft_work_reserved, work);
+  if (P->ws) cufftSetWorkArea(hd, P->ws + wr.off);
+  if (kind == 1)
+    P->fft_work_reserved_g = std::max(P->fft_work_reserved_g, work);
+  else
+    P->fft_work_reserved = std::max(P->fft_work_reserved, work);
   P->ffts[key] = hd;
   *h = hd;
   return FKREG_OK;
@@ -332,6 +367,13 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
     }
   }
   L.take(P->r_fftwork, std::max<size_t>(P->fft_work_reserved, 256));
+  L.take(P->r_fftwork_g, std::max<size_t>(P->fft_work_reserved_g, 256));
+  if (cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    fkreg_plan_destroy(P);
+    return set_global_error(FKREG_ERR_CUDA, "stream or event creation failed");
+  }
   P->ws_bytes = L.cur + kAlign;
   *out = P;
   return FKREG_OK;
@@ -354,9 +396,11 @@ fkreg_status fkreg_set_workspace(fkreg_plan P, void* ws, size_t bytes, void* str
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   P->ws = static_cast<char*>(ws);
   P->ws_given = bytes;
-  for (auto& kv : P->ffts)
-    if (cufftSetWorkArea(kv.second, P->ws + P->r_fftwork.off) != CUFFT_SUCCESS)
+  for (auto& kv : P->ffts) {
+    const fk::Region& wr = std::get<0>(kv.first) == 1 ? P->r_fftwork_g : P->r_fftwork;
+    if (cufftSetWorkArea(kv.second, P->ws + wr.off) != CUFFT_SUCCESS)
       return plan_err(P, FKREG_ERR_CUFFT, "cufftSetWorkArea failed");
+  }
   cudaError_t e;
   if ((e = cudaMemsetAsync(P->ws + P->r_err.off, 0, 256, s)) != cudaSuccess) return cuda_err(P, e, "memset");
   if ((e = cudaMemcpyAsync(P->ws + P->r_bw.off, P->bw.data(), sizeof(fk::BwDev) * P->nbw,
@@ -498,23 +542,40 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
     FK_STATUS(exec_fft(P, 0, P->g.nf, S, P->ws + P->r_fine.off, P->ws + P->r_spec.off, s));
   }
   const bool grid = out && (out->mhat_grid || out->mask || out->moments);
+  const bool at = want_df || n_probes > 0 || (out && (out->mhat_at_x || out->rss));
+  // The grid branch (kernel multiply, inverse transform, grid solve) and the
+  // type-2 branch both only read the forward spectrum: with both wanted, the
+  // grid branch runs on the plan's second stream, forked from and joined
+  // back into the caller's stream (a captured graph gets the same fork).
+  Join join;
   if (grid) {
-    {
-      FK_STAGE(FKREG_STAGE_KMUL_GRID);
-      FK_CHECK(fk::run_kmul_grid(P, 0, 1, P->nrhs_real, 0, P->nbw, P->ws + P->r_gspec.off, s),
-               "kmul grid");
+    cudaStream_t sg = s;
+    if (at && P->aux) {
+      cudaError_t e = cudaEventRecord(P->ev_fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(P->aux, P->ev_fork, 0);
+      if (e != cudaSuccess) return cuda_err(P, e, "fork the grid branch");
+      sg = P->aux;
+      join = Join{P, sg, s};
     }
     {
-      FK_STAGE(FKREG_STAGE_FFT_GRID);
-      FK_STATUS(exec_fft(P, 1, P->g.ldft, P->nbw * P->fgrid, P->ws + P->r_gspec.off,
-                         P->ws + P->r_gfield.off, s));
-    }
-    {
-      FK_STAGE(FKREG_STAGE_GRID_SOLVE);
-      FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, nullptr, out, nullptr, s), "grid solve");
+      const cudaStream_t s = sg;  // the branch's own stream for its stages
+      {
+        FK_STAGE(FKREG_STAGE_KMUL_GRID);
+        FK_CHECK(fk::run_kmul_grid(P, 0, 1, P->nrhs_real, 0, P->nbw, P->ws + P->r_gspec.off, s),
+                 "kmul grid");
+      }
+      {
+        FK_STAGE(FKREG_STAGE_FFT_GRID);
+        FK_STATUS(exec_fft(P, 1, P->g.ldft, P->nbw * P->fgrid, P->ws + P->r_gspec.off,
+                           P->ws + P->r_gfield.off, s));
+      }
+      {
+        FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+        FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, nullptr, out, nullptr, s),
+                 "grid solve");
+      }
     }
   }
-  const bool at = want_df || n_probes > 0 || (out && (out->mhat_at_x || out->rss));
   if (at) {
     const int n_rhs_str = P->nrhs_real + n_probes;
     const int f2 = P->ns + n_rhs_str * P->nt;
@@ -536,6 +597,7 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
     FK_STAGE(FKREG_STAGE_FINALIZE);
     FK_CHECK(fk::run_finalize(P, n_probes, out, s), "finalize");
   }
+  if (join.P && !join.done()) return cuda_err(P, cudaErrorUnknown, "join the grid branch");
   (void)T;
   P->dens_valid = true;
   return FKREG_OK;
@@ -806,6 +868,9 @@ void fkreg_plan_destroy(fkreg_plan P) {
     cudaEventDestroy(pe.b);
   }
   for (auto e : P->ev_pool) cudaEventDestroy(e);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->aux) cudaStreamDestroy(P->aux);
   delete P;
 }
 

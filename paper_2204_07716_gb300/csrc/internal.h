@@ -110,12 +110,14 @@ struct fkreg_plan_s {
   fk::Region r_err, r_bw, r_tab, r_xs, r_keys0, r_vals0, r_keys1, r_vals1, r_counts,
       r_binstart, r_nsub, r_substart, r_subbin, r_subfirst, r_hist, r_scan, r_str,
       r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork,
+      r_fftwork_g,
       r_bV, r_bdx, r_bsc, r_bpart;
   bool backward = false;        // workspace reserved for fkreg_backward
   bool direct = false;          // compact kernel: direct sums instead of the NUFFT
   int f2bwd = 0;                // fields of the backward passes (one response + probes)
   size_t ws_bytes = 0;
   size_t fft_work_reserved = 0;
+  size_t fft_work_reserved_g = 0;  // inverse grid transforms (their own area: they overlap)
   char* ws = nullptr;
   size_t ws_given = 0;
 
@@ -139,6 +141,10 @@ struct fkreg_plan_s {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
+  // second stream for the grid branch of a df/smooth call, which runs beside
+  // the type-2 branch (both only read the forward spectrum)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double stage_ms[FKREG_N_STAGES] = {0};
   int64_t stage_calls[FKREG_N_STAGES] = {0};
 };
