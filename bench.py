@@ -141,6 +141,22 @@ def dist_setup(args):
 TRAFFIC = {"interp": 79523328, "spread": None}
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The job's time: the slowest rank's (all-reduce MAX over the ranks)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_step: float, steps: int, world: int, total_ms: float) -> float:
+    """Units all ranks processed (each rank runs one replica) per second of the job."""
+    return world * units_per_step * steps / (total_ms / 1e3)
+
+
 def algorithmic(plan, n, n_probes):
     """Algorithmic bytes / flops per launch of the spreading and interpolation kernels."""
     T = 4
@@ -228,13 +244,9 @@ def run_ours(args, world, rank, local):
     plan.sync()
     stage_ms, stage_calls, launches = plan.stage_times()
     plan.set_timing(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     units_per_step = n * (1 + N_PROBES + 1) * plan.n_bw
-    value = world * units_per_step * args.steps / (total_ms / 1e3)
+    value = whole_job_value(units_per_step, args.steps, world, total_ms)
 
     # e2e: host pinned inputs, copies inside the timed region, results read back
     xh = torch.tensor(w.x, dtype=torch.float32).pin_memory()
@@ -258,12 +270,8 @@ def run_ours(args, world, rank, local):
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     plan.sync()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * units_per_step * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), world, dev)
+    e2e_value = whole_job_value(units_per_step, args.steps, world, e2e_ms)
     h2d = xh.numel() * 4 + yh.numel() * 4
     d2h = mh_host.numel() * 4 + gcv_host.numel() * 8 + s2_host.numel() * 4
 
