@@ -248,28 +248,63 @@ def run_ours(args, world, rank, local):
     units_per_step = n * (1 + N_PROBES + 1) * plan.n_bw
     value = whole_job_value(units_per_step, args.steps, world, total_ms)
 
-    # e2e: host pinned inputs, copies inside the timed region, results read back
+    # e2e: host pinned inputs, copies inside the timed region, results read
+    # back.  Two input buffers, each with its own captured graph, let the next
+    # step's host-to-device copy (a stream of its own) run under the current
+    # step's kernels; each step's interval runs from its graph's start (the
+    # first step: from its copy) to the end of its results' device-to-host
+    # copy, so nothing that is not hidden under a timed graph goes unmeasured.
     xh = torch.tensor(w.x, dtype=torch.float32).pin_memory()
     yh = torch.tensor(w.y, dtype=torch.float32).pin_memory()
-    mh_host = torch.empty((plan.n_bw, 1) + w.grid_n, dtype=torch.float32).pin_memory()
-    gcv_host = torch.empty((plan.n_bw, 1), dtype=torch.float64).pin_memory()
-    s2_host = torch.empty((plan.n_bw, 1) + w.grid_n, dtype=torch.float32).pin_memory()
+    x2 = torch.empty_like(x)
+    y2 = torch.empty_like(y)
+    x2.copy_(x)
+    y2.copy_(y)
+    graph2 = fkreg.StepGraph(lambda: step(0, x2, y2))
+    bufs = [(x, y, graph), (x2, y2, graph2)]
+    hosts = [(torch.empty((plan.n_bw, 1) + w.grid_n, dtype=torch.float32).pin_memory(),
+              torch.empty((plan.n_bw, 1), dtype=torch.float64).pin_memory(),
+              torch.empty((plan.n_bw, 1) + w.grid_n, dtype=torch.float32).pin_memory())
+             for _ in range(2)]
+    h2d_stream, d2h_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
+
+    def h2d_into(j):
+        h2d_stream.wait_stream(stream)        # after the flush and the graph that used buffer j
+        with torch.cuda.stream(h2d_stream):
+            bufs[j][0].copy_(xh, non_blocking=True)
+            bufs[j][1].copy_(yh, non_blocking=True)
+            ev_in[j].record(h2d_stream)
+
     torch.cuda.synchronize(dev)
-    gout, gs2 = graph.outputs
+    e2e_ev[0][0].record(stream)
+    h2d_into(0)
     for k in range(args.steps):
-        flush.fill_(float(k))
-        e2e_ev[k][0].record(stream)
-        x.copy_(xh, non_blocking=True)        # the graph's input buffers
-        y.copy_(yh, non_blocking=True)
-        graph.replay()
-        mh_host.copy_(gout["mhat_grid"], non_blocking=True)
-        gcv_host.copy_(gout["gcv"], non_blocking=True)
-        s2_host.copy_(gs2, non_blocking=True)
+        i = k % 2
+        if k > 0:
+            flush.fill_(float(k))             # between timed steps, outside the intervals
+            e2e_ev[k][0].record(stream)
+        if k + 1 < args.steps:
+            h2d_into((k + 1) % 2)             # the next step's inputs, under this step's kernels
+        stream.wait_event(ev_in[i])
+        bufs[i][2].replay()
+        ev_done[i].record(stream)
+        d2h_stream.wait_event(ev_done[i])
+        gout, gs2 = bufs[i][2].outputs
+        with torch.cuda.stream(d2h_stream):
+            hosts[i][0].copy_(gout["mhat_grid"], non_blocking=True)
+            hosts[i][1].copy_(gout["gcv"], non_blocking=True)
+            hosts[i][2].copy_(gs2, non_blocking=True)
+            ev_out[i].record(d2h_stream)
+        stream.wait_event(ev_out[i])
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     plan.sync()
+    mh_host, gcv_host, s2_host = hosts[0]
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), world, dev)
     e2e_value = whole_job_value(units_per_step, args.steps, world, e2e_ms)
     h2d = xh.numel() * 4 + yh.numel() * 4
@@ -308,7 +343,9 @@ def run_ours(args, world, rank, local):
                    "graph": "whole step captured once; one CUDA graph replay per step",
                    "parallelism": f"replicas{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
+                "copies": "pinned host buffers; two input buffers, the next step's "
+                          "host-to-device copy under the current step's kernels"},
         "gpu_launches": int(launches),   # eager steps = graph replays: same kernels
         "roofline": roof,
         "stages_ms_per_step": {k: round(v / args.steps, 4) for k, v in stage_ms.items()},
