@@ -605,6 +605,37 @@ def test_empty_and_single_sample():
     assert torch.allclose(m, torch.full_like(m, 2.5), rtol=1e-9)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_compact_empty_and_single_sample(prec):
+    # direct path: no samples (everything masked) and one sample, whose NW
+    # estimate is its own response inside its support (up to the rounding of
+    # t / s) and masked (NaN) outside it; so is its at-sample value
+    w = inputs.random_small(82, 2, 1, 20, 0, [0.12], precision=prec,
+                            tol=1e-12 if prec == "f64" else 1e-6)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    p = plan_for(w, kernel="epanechnikov")
+    p.set_points(torch.zeros((0, 2), dtype=dt))
+    out = p.smooth(torch.zeros((1, 0), dtype=dt), want=("mhat_grid", "mask"))
+    p.sync()
+    assert out["mask"].sum().item() == 0
+    assert torch.isnan(out["mhat_grid"]).all()
+    p.set_points(torch.tensor(w.x, dtype=dt))
+    out = p.smooth(torch.tensor([[2.5]], dtype=dt), want=("mhat_grid", "mask", "mhat_at_x"))
+    p.sync()
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    x = w.x.astype(np.float32).astype(np.float64) if prec == "f32" else w.x
+    z = (gp - x[0]) / 0.12
+    inside = np.sum(z * z, axis=1) < 0.999
+    outside = np.sum(z * z, axis=1) > 1.001
+    mask = out["mask"][0].reshape(-1).cpu().numpy().astype(bool)
+    mg = out["mhat_grid"][0, 0].reshape(-1).cpu().numpy()
+    assert inside.sum() > 10 and mask[inside].all() and not mask[outside].any()
+    rt = 1e-12 if prec == "f64" else 1e-6
+    np.testing.assert_allclose(mg[inside], 2.5, rtol=rt)
+    assert np.isnan(mg[outside]).all()
+    assert out["mhat_at_x"][0, 0, 0].item() == pytest.approx(2.5, rel=rt)
+
+
 def test_points_outside_the_box_are_flagged():
     from paper_2204_07716_gb300.fkreg import FkregError
     w = inputs.random_small(81, 1, 100, 20, 0, [0.1], precision="f64", tol=1e-12)
