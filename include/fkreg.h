@@ -200,7 +200,13 @@ fkreg_status fkreg_spread_kernel_ft(int kind, int w, double beta, int64_t nf,
 /*
  * Create a plan for up to max_n samples.  Computes the geometry and the
  * spreading-kernel tables on the host and creates the cuFFT plans (needs a
- * current CUDA device).  The plan owns host tables and cuFFT handles only.
+ * current CUDA device).  The plan owns host tables, cuFFT handles, and one
+ * non-blocking CUDA stream with two events on the current device: a
+ * fkreg_smooth / fkreg_df call that wants both grid and at-sample outputs
+ * runs its grid branch on that stream, forked from the caller's stream and
+ * joined back into it before the call returns (so every call stays ordered
+ * on the caller's stream, and a stream capture records the two branches).
+ * It allocates no device memory.
  */
 fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan* out);
 
