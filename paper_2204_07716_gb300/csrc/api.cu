@@ -285,7 +285,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
     t2_half = std::max(t2_half, half_cells(B.nf, d));
   }
   const int64_t ntiles = (max_n + fk::kSortTileKeys - 1) / fk::kSortTileKeys;
-  const int64_t scan_len = std::max<int64_t>(256 * ntiles, nb + 1);
+  const int64_t scan_len = std::max<int64_t>(1024 * ntiles, nb + 1);  // up to 10-bit digits
   Layout L;
   L.take(P->r_err, 256);
   L.take(P->r_bw, sizeof(fk::BwDev) * P->nbw);
@@ -299,7 +299,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   L.take(P->r_substart, 4 * (nb + 1));
   L.take(P->r_subbin, 4 * P->nsub_max);
   L.take(P->r_subfirst, 4 * P->nsub_max);
-  L.take(P->r_hist, 4 * (256 * ntiles + 1));
+  L.take(P->r_hist, 4 * (1024 * ntiles + 1));
   L.take(P->r_scan, 4 * (scan_len / 1024 + 2));
   L.take(P->r_str, T * strengths_total * std::max<int64_t>(1, max_n));
   // the direct path (compact kernels) needs only the grid fields

@@ -209,12 +209,13 @@ __global__ void scan_apply(const uint32_t* in, int64_t n, const uint32_t* __rest
 // writes each key at offset + rank among the equal digits of lower lanes.
 // Order is preserved within a round, across rounds, across warps and across
 // tiles, so every pass is stable.
-// Lanes of the warp holding the same 9-bit value (a digit, or 256 for "no
-// key"): one ballot per bit, AND of the agreeing masks.
+// Lanes of the warp holding the same (B + 1)-bit value (a digit, or 2^B
+// for "no key"): one ballot per bit, AND of the agreeing masks.
+template <int B>
 __device__ __forceinline__ uint32_t match_digit(uint32_t dig) {
   uint32_t m = 0xffffffffu;
 #pragma unroll
-  for (int b = 0; b < 9; ++b) {
+  for (int b = 0; b <= B; ++b) {
     const uint32_t bit = (dig >> b) & 1u;
     const uint32_t bal = __ballot_sync(0xffffffffu, bit);
     m &= bit ? bal : ~bal;
@@ -222,11 +223,14 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t dig) {
   return m;
 }
 
+// B-bit digits (R = 2^B buckets); hist[digit][tile]
+template <int B>
 __global__ void __launch_bounds__(kSortThreads)
 radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
               uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+  constexpr uint32_t R = 1u << B;
+  __shared__ uint32_t h[R];
+  for (uint32_t d = threadIdx.x; d < R; d += kSortThreads) h[d] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
@@ -234,32 +238,46 @@ radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t n
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + int64_t(r) * kSortThreads + threadIdx.x;
-    dg[r] = i < n ? (keys[i] >> shift) & 255u : 256u;
+    dg[r] = i < n ? (keys[i] >> shift) & (R - 1u) : R;
   }
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const uint32_t dig = dg[r];
-    const uint32_t peers = match_digit(dig);
-    if (dig < 256u && (__ffs(peers) - 1) == lane) atomicAdd(&h[dig], uint32_t(__popc(peers)));
+    const uint32_t peers = match_digit<B>(dig);
+    if (dig < R && (__ffs(peers) - 1) == lane) atomicAdd(&h[dig], uint32_t(__popc(peers)));
   }
   __syncthreads();
-  hist[int64_t(threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
+  for (uint32_t d = threadIdx.x; d < R; d += kSortThreads)
+    hist[int64_t(d) * ntiles + blockIdx.x] = h[d];
 }
 
+// dynamic shared memory of radix_downsweep<B>
+template <int B>
+constexpr size_t radix_down_smem() {
+  return sizeof(uint32_t) * ((kSortThreads / 32 + 2) * (size_t(1) << B) + kSortThreads / 32 +
+                             2 * size_t(kSortTile));
+}
+
+template <int B>
 __global__ void __launch_bounds__(kSortThreads, 2)
 radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 int64_t n, int shift, int64_t ntiles, const uint32_t* __restrict__ hist_scanned,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
   constexpr int NW = kSortThreads / 32;
   constexpr int RW = kSortTile / NW / 32;  // rounds of 32 keys per warp
-  static_assert(kSortThreads == 256 && RW * NW * 32 == kSortTile, "one thread per digit");
-  __shared__ uint32_t wh[NW][256];        // per-warp digit counts, then offsets in the tile
-  __shared__ uint32_t dstart[256];        // first tile position of each digit
-  __shared__ uint32_t gbase[256];         // first output position of each digit
-  __shared__ uint32_t wsum[NW];
-  __shared__ uint32_t skey[kSortTile], sval[kSortTile];
+  constexpr uint32_t R = 1u << B;
+  constexpr int DPT = int(R) / kSortThreads;  // digits per thread
+  static_assert(RW * NW * 32 == kSortTile && DPT >= 1 && DPT * kSortThreads == int(R),
+                "tile and digit layout");
+  extern __shared__ __align__(16) uint32_t dsm[];
+  uint32_t* wh = dsm;                  // [NW][R] per-warp counts, then offsets in the digit's run
+  uint32_t* dstart = wh + NW * R;      // [R] first tile position of each digit
+  uint32_t* gbase = dstart + R;        // [R] first output position of each digit
+  uint32_t* wsum = gbase + R;          // [NW]
+  uint32_t* skey = wsum + NW;          // [kSortTile]
+  uint32_t* sval = skey + kSortTile;   // [kSortTile]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int w = 0; w < NW; ++w) wh[w][tid] = 0;
+  for (uint32_t d = tid; d < NW * R; d += kSortThreads) wh[d] = 0;
   __syncthreads();
   const int64_t tbase = int64_t(blockIdx.x) * kSortTile;
   const int64_t wbase = tbase + int64_t(warp) * (RW * 32);
@@ -274,48 +292,60 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 #pragma unroll
   for (int r = 0; r < RW; ++r) {
     const int64_t i = wbase + r * 32 + lane;
-    const uint32_t dig = i < n ? (key[r] >> shift) & 255u : 256u;
-    const uint32_t peers = match_digit(dig);
-    if (dig < 256u && (peers & lt_mask) == 0) wh[warp][dig] += __popc(peers);
+    const uint32_t dig = i < n ? (key[r] >> shift) & (R - 1u) : R;
+    const uint32_t peers = match_digit<B>(dig);
+    if (dig < R && (peers & lt_mask) == 0) wh[warp * R + dig] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // thread tid = digit: per-warp offsets inside the digit's run, the digit's
-  // total, then an exclusive scan of the totals over the 256 digits
-  uint32_t tot = 0;
-  for (int w = 0; w < NW; ++w) {
-    const uint32_t t = wh[w][tid];
-    wh[w][tid] = tot;
-    tot += t;
+  // thread tid owns digits [tid DPT, (tid + 1) DPT): per-warp offsets inside
+  // each digit's run, the digits' totals, then an exclusive scan of the
+  // totals over all R digits
+  uint32_t tot[DPT], own = 0;
+#pragma unroll
+  for (int u = 0; u < DPT; ++u) {
+    const uint32_t d = uint32_t(tid * DPT + u);
+    uint32_t t = 0;
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t c = wh[w * R + d];
+      wh[w * R + d] = t;
+      t += c;
+    }
+    tot[u] = t;
+    own += t;
+    gbase[d] = hist_scanned[int64_t(d) * ntiles + blockIdx.x];
   }
-  uint32_t inc = tot;
+  uint32_t inc = own;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += v;
   }
   if (lane == 31) wsum[warp] = inc;
-  gbase[tid] = hist_scanned[int64_t(tid) * ntiles + blockIdx.x];
   __syncthreads();
-  uint32_t before = 0;
-  for (int w = 0; w < warp; ++w) before += wsum[w];
-  dstart[tid] = before + inc - tot;
+  uint32_t run = inc - own;
+  for (int w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+  for (int u = 0; u < DPT; ++u) {
+    dstart[tid * DPT + u] = run;
+    run += tot[u];
+  }
   __syncthreads();
   // tile-local scatter into shared memory (sorted by digit, stable)
 #pragma unroll
   for (int r = 0; r < RW; ++r) {
     const int64_t i = wbase + r * 32 + lane;
-    const uint32_t dig = i < n ? (key[r] >> shift) & 255u : 256u;
-    const uint32_t peers = match_digit(dig);
+    const uint32_t dig = i < n ? (key[r] >> shift) & (R - 1u) : R;
+    const uint32_t peers = match_digit<B>(dig);
     uint32_t off = 0;
-    if (dig < 256u) {
-      off = wh[warp][dig];
+    if (dig < R) {
+      off = wh[warp * R + dig];
       const uint32_t lp = dstart[dig] + off + __popc(peers & lt_mask);
       skey[lp] = key[r];
       sval[lp] = val[r];
     }
     __syncwarp();  // every lane has read its group's offset
-    if (dig < 256u && (peers & lt_mask) == 0) wh[warp][dig] = off + __popc(peers);
+    if (dig < R && (peers & lt_mask) == 0) wh[warp * R + dig] = off + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
@@ -324,12 +354,13 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
   const int cnt = int(n - tbase < kSortTile ? n - tbase : kSortTile);
   for (int t = tid; t < cnt; t += kSortThreads) {
     const uint32_t k = skey[t];
-    const uint32_t dig = (k >> shift) & 255u;
+    const uint32_t dig = (k >> shift) & (R - 1u);
     const uint32_t pos = gbase[dig] + uint32_t(t) - dstart[dig];
     keys_out[pos] = k;
     vals_out[pos] = sval[t];
   }
 }
+
 
 template <typename T>
 __global__ void gather_coords_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
@@ -418,6 +449,27 @@ cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_
   return cudaGetLastError();
 }
 
+// One LSD pass with B-bit digits: tile histograms, their scan, the scatter.
+template <int B>
+cudaError_t radix_pass(const uint32_t* kin, const uint32_t* vin, int64_t n, int shift,
+                       int64_t ntiles, uint32_t* hist, uint32_t* scratch, uint32_t* kout,
+                       uint32_t* vout, cudaStream_t s, int64_t* launches) {
+  radix_upsweep<B><<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, n, shift, ntiles, hist);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = exclusive_scan(hist, hist, (int64_t(1) << B) * ntiles, scratch, s, launches)) !=
+      cudaSuccess)
+    return e;
+  constexpr size_t sm = radix_down_smem<B>();
+  if ((e = cudaFuncSetAttribute(radix_downsweep<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(sm))) != cudaSuccess)
+    return e;
+  radix_downsweep<B><<<unsigned(ntiles), kSortThreads, sm, s>>>(kin, vin, n, shift, ntiles, hist,
+                                                                kout, vout);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) {
@@ -458,20 +510,20 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
   // radix passes over the significant bits of the key
   int bits = g.kbits;
   while ((int64_t(1) << (bits - g.kbits)) < nbins) ++bits;
-  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  // keys of 17..20 bits: two passes of 10-bit digits; otherwise 8-bit digits
+  const int dbits = (bits > 16 && bits <= 20) ? 10 : kRadixBits;
+  const int passes = (bits + dbits - 1) / dbits;
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   uint32_t* hist = wsp<uint32_t>(P, P->r_hist);
   uint32_t *kin = keys0, *vin = vals0, *kout = keys1, *vout = vals1;
   int in_is_1 = 0;
   for (int p = 0; p < passes && n > 0; ++p) {
-    const int shift = p * kRadixBits;
-    radix_upsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, n, shift, ntiles, hist);
-    P->launches += 2;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = exclusive_scan(hist, hist, 256 * ntiles, scratch, s, &P->launches)) != cudaSuccess) return e;
-    radix_downsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, vin, n, shift, ntiles, hist, kout,
-                                                              vout);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int shift = p * dbits;
+    e = dbits == 10 ? radix_pass<10>(kin, vin, n, shift, ntiles, hist, scratch, kout, vout, s,
+                                     &P->launches)
+                    : radix_pass<8>(kin, vin, n, shift, ntiles, hist, scratch, kout, vout, s,
+                                    &P->launches);
+    if (e != cudaSuccess) return e;
     std::swap(kin, kout);
     std::swap(vin, vout);
     in_is_1 ^= 1;
@@ -615,12 +667,9 @@ extern "C" fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const 
   uint32_t *kin = keys0, *vin = vals0, *kout = keys1, *vout = vals1;
   for (int p = 0; p < passes && n > 0; ++p) {
     const int shift = p * kRadixBits;
-    radix_upsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, n, shift, ntiles, hist);
-    if (cudaGetLastError() != cudaSuccess) return FKREG_ERR_CUDA;
-    if (exclusive_scan(hist, hist, 256 * ntiles, scan, s, &launches) != cudaSuccess) return FKREG_ERR_CUDA;
-    radix_downsweep<<<unsigned(ntiles), kSortThreads, 0, s>>>(kin, vin, n, shift, ntiles, hist, kout,
-                                                              vout);
-    if (cudaGetLastError() != cudaSuccess) return FKREG_ERR_CUDA;
+    if (radix_pass<8>(kin, vin, n, shift, ntiles, hist, scan, kout, vout, s, &launches) !=
+        cudaSuccess)
+      return FKREG_ERR_CUDA;
     std::swap(kin, kout);
     std::swap(vin, vout);
   }

@@ -107,12 +107,14 @@ def cpu_keys(x, geom, precision):
     return (bins << kb) | local, bins
 
 
-@pytest.mark.parametrize("case", ["d1", "d2clip", "d3", "dups", "one"])
+@pytest.mark.parametrize("case", ["d1", "d2clip", "d2full", "d3", "dups", "one"])
 def test_sort_is_bit_exact(case):
     if case == "d1":
         w = inputs.nw1d()
     elif case == "d2clip":
         w = inputs.ll2d(n=200_000)
+    elif case == "d2full":
+        w = inputs.ll2d()          # the bench's size: 19-bit keys, two 10-bit passes
     elif case == "d3":
         w = inputs.random_small(1, 3, 50_000, 16, 0, [0.05], precision="f32", tol=1e-6)
     elif case == "dups":
