@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="ll2d",
-                    choices=["ll2d", "nw1d", "nw3d_df", "ll2d_gcv", "uneven",
+                    choices=["ll2d", "ll2d_sort", "nw1d", "nw3d_df", "ll2d_gcv", "uneven",
                              "ll2d_plain64", "ll2d_plain32", "ll2d_logvar", "ll2d_epan"],
                     help="ll2d is the headline line; the others measure the remaining "
                          "configurations (1-D NW FP64, 3-D NW + DF sweep, 2-D LL GCV "
@@ -470,6 +470,19 @@ def run_extra(args):
                "n_total": sum(w.n for w in ws), "problems": len(ws),
                "dims": [w.d for w in ws].count(2), "graph": "one captured CUDA graph"}
         dtype = "f32+f64solve"
+    elif wl == "ll2d_sort":
+        # the bin sort of the headline step alone (fkreg_set_points)
+        w = inputs.ll2d(n=int(1_000_000 * sc))
+        plan = fkreg.Plan(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, n_rhs=1,
+                          max_probes=10, tol=w.tol, precision="f32", device=dev)
+        x = torch.tensor(w.x, dtype=torch.float32, device=dev)
+
+        def step(k):
+            plan.set_points(x)
+        units = w.n
+        cfg = {"workload": "ll2d-1M-256sq-bin-sort", "n": w.n, "geometry": plan.geom}
+        dtype = "u32 keys"
+        extra["plan"] = plan
     elif wl == "ll2d_epan":
         # the headline step (df with y + 10 probes, then the variance pass)
         # with the compact Epanechnikov kernel: direct sums, no NUFFT
