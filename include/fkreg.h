@@ -202,8 +202,8 @@ fkreg_status fkreg_spread_kernel_ft(int kind, int w, double beta, int64_t nf,
  * spreading-kernel tables on the host and creates the cuFFT plans (needs a
  * current CUDA device).  The plan owns host tables, cuFFT handles, and one
  * non-blocking CUDA stream with two events on the current device: a
- * fkreg_smooth / fkreg_df call that wants both grid and at-sample outputs
- * runs its grid branch on that stream, forked from the caller's stream and
+ * fkreg_smooth / fkreg_df call on at least 65,536 samples that wants both
+ * grid and at-sample outputs runs its grid branch on that stream, forked from the caller's stream and
  * joined back into it before the call returns (so every call stays ordered
  * on the caller's stream, and a stream capture records the two branches).
  * It allocates no device memory.

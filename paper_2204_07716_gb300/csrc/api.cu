@@ -547,10 +547,13 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
   // type-2 branch both only read the forward spectrum: with both wanted, the
   // grid branch runs on the plan's second stream, forked from and joined
   // back into the caller's stream (a captured graph gets the same fork).
+  // Small problems, whose kernels take microseconds, stay on one stream:
+  // there the fork's own cost is larger than the overlap.
+  constexpr int64_t kForkMinSamples = int64_t(1) << 16;
   Join join;
   if (grid) {
     cudaStream_t sg = s;
-    if (at && P->aux) {
+    if (at && P->aux && P->n >= kForkMinSamples) {
       cudaError_t e = cudaEventRecord(P->ev_fork, s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(P->aux, P->ev_fork, 0);
       if (e != cudaSuccess) return cuda_err(P, e, "fork the grid branch");
