@@ -59,6 +59,22 @@ def test_geometry_covers_tail_and_spectrum(lib):
         assert g["inv_h"][j] == pytest.approx(g["nf"][j] / g["period"][j], rel=1e-7)
 
 
+def test_direct_geometry_for_compact_kernels(lib):
+    # compact kernels: bins on the output lattice (n_f = M), cells of the
+    # grid spacing, a quarter of the widest support half-width per bin
+    for sig, grid in ((0.01, 256), (0.08, 64), (0.3, 40)):
+        g = fkreg.geometry(**opts(grid_n=(grid, grid), H=np.diag([sig ** 2, (1.5 * sig) ** 2]),
+                                  kernel="epanechnikov"))
+        for j in range(2):
+            delta = 1.0 / (grid - 1)
+            assert g["nf"][j] == grid
+            assert g["inv_h"][j] == pytest.approx((grid - 1), rel=1e-7)
+            rmax = 1.5 * sig / delta if j == 1 else sig / delta
+            want = max(1, min(64, math.ceil(0.25 * rmax)))
+            assert g["tile"][j] == min(want, grid)
+            assert g["nbins"][j] == -(-grid // g["tile"][j])
+
+
 def test_width_follows_tolerance(lib):
     for tol, w in ((1e-6, 7), (1e-9, 10), (1e-12, 13), (1e-3, 4)):
         assert fkreg.geometry(**opts(tol=tol))["w"] == w

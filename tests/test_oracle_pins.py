@@ -385,6 +385,28 @@ def test_compact_kernel_smoothing(name):
         assert r["mhat"][0, 0] == pytest.approx(np.mean(y[u2 <= 1]), rel=1e-12)
 
 
+@pytest.mark.parametrize("name", ["epanechnikov", "triweight"])
+def test_compact_kernel_full_bandwidth_matrix(name):
+    # a correlated H: the support is the rotated ellipse z^T H^-1 z <= 1 and
+    # the scale is |H|^-1/2; the moment sums equal brute-force weighted sums
+    # over the samples inside it, and the first moments change sign with z
+    rng = np.random.default_rng(71)
+    x = rng.random((300, 2))
+    H = np.array([[0.04, 0.018], [0.018, 0.02]])
+    q = np.array([[0.45, 0.55]])
+    z = x - q[0]
+    u2 = np.einsum("ia,ab,ib->i", z, np.linalg.inv(H), z)
+    w = oracle.compact_profile(name, 2, u2) / math.sqrt(np.linalg.det(H))
+    y = rng.standard_normal(300)
+    m = oracle.moment_sums_compact(x, np.stack([np.ones(300), y]), H, 2, q, name)[0]
+    ex = [tuple(e) for e in oracle.monomials(2, 2)]
+    for f, e in enumerate(ex):
+        mono = z[:, 0] ** e[0] * z[:, 1] ** e[1]
+        assert m[0, f] == pytest.approx(np.sum(w * mono), rel=1e-12, abs=1e-14)
+        assert m[1, f] == pytest.approx(np.sum(w * mono * y), rel=1e-11, abs=1e-13)
+    assert np.sum(u2 <= 1) > 10 and np.sum((u2 > 1) & (np.abs(z).max(axis=1) < 0.2)) > 0
+
+
 def test_kde_integrates_to_one():
     # eq. 8: s_0 / N is a density (Gaussian K has unit mass)
     rng = np.random.default_rng(3)
