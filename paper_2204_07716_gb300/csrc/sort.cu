@@ -510,10 +510,12 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
   // radix passes over the significant bits of the key
   int bits = g.kbits;
   while ((int64_t(1) << (bits - g.kbits)) < nbins) ++bits;
-  // keys of 17..20 bits: two passes of 10-bit digits; otherwise 8-bit digits
-  const int dbits = (bits > 16 && bits <= 20) ? 10 : kRadixBits;
-  const int passes = (bits + dbits - 1) / dbits;
+  // keys of 17..20 bits over at least 16 tiles: two passes of 10-bit digits;
+  // otherwise 8-bit digits (small sorts are bound by the per-pass fixed
+  // costs, which grow with the digit range)
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const int dbits = (bits > 16 && bits <= 20 && ntiles >= 16) ? 10 : kRadixBits;
+  const int passes = (bits + dbits - 1) / dbits;
   uint32_t* hist = wsp<uint32_t>(P, P->r_hist);
   uint32_t *kin = keys0, *vin = vals0, *kout = keys1, *vout = vals1;
   int in_is_1 = 0;
