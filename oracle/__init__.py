@@ -18,6 +18,12 @@ built on top of those sums, each written from its definition in the paper:
                        Hutchinson mean of w_p^T S w_p.
 * ``gcv``              eq. 22.
 * ``variance_pass``    eq. 23: a local-linear smooth of squared residuals.
+* ``log_variance``     eqs. 24-26: smooth of log(r + 1/N), kappa, sigma^2.
+* ``interval``         eq. 28: mhat -/+ z_(1 - alpha/2) sqrt(variance).
+* ``predict``          grid estimates at new points (multilinear with linear
+                       extension; Keys cubic convolution), Sec. 1.1.
+* ``compact_profile``, ``moment_sums_compact``, ``smooth_at_compact``
+                       the compact kernels of Table 1 by direct sums.
 * ``get_hlist``        the bandwidth list helper of Sec. 4.
 * ``select_h``         the GCV argmin relaxed by ``dstd`` (Table 1).
 * ``probes``           the counter-based Gaussian probe generator.
