@@ -85,7 +85,9 @@ enum {
 /*
  * Problem description (the arguments of cv_fkreg in Sec. 4 and Table 1).
  *   dim            d, 1..3
- *   order          l: 0 = Nadaraya-Watson (eq. 7), 1 = local linear (eq. 3)
+ *   order          l: 0 = Nadaraya-Watson (eq. 7), 1 = local linear (eq. 3),
+ *                  2 = local quadratic (d <= 2; 3-D and its backward are
+ *                  refused with UNSUPPORTED)
  *   kernel         FKREG_KERNEL_GAUSSIAN: the NUFFT path (the transform of the
  *                  Gaussian moment kernels decays fast enough for tol to
  *                  control the truncation).  The compact kernels
@@ -93,7 +95,9 @@ enum {
  *                  mass in d dimensions, K_H(z) = |H|^(-1/2) K(H^(-1/2) z))
  *                  use exact direct sums over the binned samples inside each
  *                  point's support instead (tol and spread_kernel unused);
- *                  fkreg_backward and FKREG_WANT_BACKWARD are refused for them.
+ *                  fkreg_backward and FKREG_WANT_BACKWARD are refused for
+ *                  them, and so is a plan whose s-fields plus the t-fields
+ *                  of (n_rhs + max_probes) strengths exceed 64 (UNSUPPORTED).
  *   spread_kernel  NUFFT spreading kernel: exponential of semicircle (default)
  *                  or the Gaussian of Sec. 1.2 eq. 17 (about twice as wide)
  *   precision      FKREG_F32 (spreading, FFT, interpolation in float, FP64
@@ -109,7 +113,9 @@ enum {
  *   tol            NUFFT tolerance (e.g. 1e-6 for F32, 1e-12 for F64)
  *   mask_rho       grid points with s_0(g) < mask_rho * max_g s_0 are masked
  *                  (NaN estimate, mask byte 0); 0 selects the default 1e-3
- *   tile           spreading tile edge in fine-grid cells per axis (0 = auto)
+ *   tile           spreading tile edge in fine-grid cells per axis (0 = auto:
+ *                  for the compact kernels a quarter of the widest support
+ *                  half-width, in grid cells)
  *   flags          FKREG_GCV_EXACT_TRACE, FKREG_WANT_BACKWARD
  */
 typedef struct {
