@@ -79,28 +79,57 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons around a region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    The sampler is running (its first line written) before the region
+    starts; the samples stamped inside the region, widened by one sampling
+    interval on each side, are kept.  A region shorter than the interval
+    may hold none: the sample nearest to it then stands in, and
+    ``in_region`` says which case it was.
+    """
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 20):
         self.index = index
+        self.iv = interval_ms / 1e3
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms",
+                                       str(int(self.iv * 1e3))],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        t = time.time()
+        while time.time() - t < 5.0 and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.005)
+        self.t0 = time.time()
+
+    @staticmethod
+    def _stamp(text: str):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def stop(self):
+        self.t1 = time.time()
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(2 * self.iv)   # the sample just after the region
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -108,24 +137,34 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in self.f.read().splitlines():
-            parts = [s.strip() for s in line.split(",")]
-            if len(parts) < 9:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                sm, smax = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+            active = {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}
+            rows.append((self._stamp(parts[0]), sm, smax, active))
         os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        t0 = self.t0 if self.t0 is not None else self.t1
+        inside = [r for r in rows
+                  if r[0] is not None and t0 - self.iv <= r[0] <= self.t1 + self.iv]
+        keep = inside
+        if not keep:
+            stamped = [r for r in rows if r[0] is not None]
+            mid = 0.5 * (t0 + self.t1)
+            keep = [min(stamped, key=lambda r: abs(r[0] - mid))] if stamped else rows
+        reasons = set()
+        for r in keep:
+            reasons |= r[3]
+        return {"sm_mhz": statistics.median(r[1] for r in keep) if keep else None,
+                "sm_max_mhz": max(r[2] for r in keep) if keep else None,
+                "reasons": sorted(reasons), "samples": len(keep), "in_region": bool(inside),
+                "interval_ms": int(self.iv * 1e3), "region_ms": round((self.t1 - t0) * 1e3, 1)}
 
 
 def dist_setup(args):
