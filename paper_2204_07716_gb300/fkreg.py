@@ -438,6 +438,50 @@ class Plan:
         return out
 
 
+def bandwidth_list(n, ranges, spacing: str = "log") -> np.ndarray:
+    """Candidate bandwidths (Sec. 4, get_hList) as the H matrices a plan takes.
+
+    ``n`` is the number of candidates per axis (an int, or one per axis),
+    ``ranges`` the (lo, hi) standard-deviation range per axis, ``spacing``
+    "log" (lo to hi evenly in log10, both ends included) or "lin".  One axis
+    gives sigma values; several axes give every combination (axis 0 varies
+    slowest), each as H = diag(sigma^2).  Returns [n_bw, d, d] float64.
+    """
+    rng = np.asarray(ranges, dtype=np.float64).reshape(-1, 2)
+    d = rng.shape[0]
+    counts = [int(n)] * d if np.ndim(n) == 0 else [int(v) for v in n]
+    if len(counts) != d or min(counts) < 1 or np.any(rng <= 0) or np.any(rng[:, 1] < rng[:, 0]):
+        raise FkregError("bandwidth_list: one count >= 1 and one 0 < lo <= hi range per axis")
+    axes = []
+    for (lo, hi), k in zip(rng, counts):
+        if spacing == "log":
+            e = np.linspace(np.log10(lo), np.log10(hi), k) if k > 1 else np.array([np.log10(lo)])
+            axes.append(np.power(10.0, e))
+        elif spacing == "lin":
+            axes.append(np.linspace(lo, hi, k) if k > 1 else np.array([lo]))
+        else:
+            raise FkregError(f"bandwidth_list: unknown spacing {spacing!r}")
+    mesh = np.meshgrid(*axes, indexing="ij")
+    sig = np.stack([m.reshape(-1) for m in mesh], axis=1)          # [n_bw, d]
+    H = np.zeros((sig.shape[0], d, d))
+    for j in range(d):
+        H[:, j, j] = sig[:, j] ** 2
+    return H
+
+
+def select_bandwidth(gcv, dstd: float = 0.0) -> int:
+    """Index of the chosen candidate (Table 1's dstd rule, with the GCV values
+    of a candidate list in increasing bandwidth order): the last candidate
+    whose GCV is at most min GCV + dstd * std(GCV); dstd = 0 is the argmin,
+    ties going to the later candidate.  NaN values are ignored."""
+    g = np.asarray(gcv, dtype=np.float64).reshape(-1)
+    ok = np.isfinite(g)
+    if not ok.any():
+        raise FkregError("select_bandwidth: no finite GCV value")
+    lim = np.min(g[ok]) + (dstd * float(np.std(g[ok])) if dstd else 0.0)
+    return int(np.nonzero(ok & (g <= lim))[0].max())
+
+
 def interval(mhat, var, alpha: float = 0.05):
     """Pointwise interval of eq. 28 on device tensors of one dtype (float32 or
     float64): returns (lower, upper) = mhat -/+ z_(1-alpha/2) sqrt(var)."""
