@@ -482,6 +482,60 @@ def select_bandwidth(gcv, dstd: float = 0.0) -> int:
     return int(np.nonzero(ok & (g <= lim))[0].max())
 
 
+def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: int = 10,
+             dstd: float = 0.0, seed: int = 0, precision: str = "f32", tol=None,
+             kernel: str = "gaussian", variance: bool = False, device=None) -> Dict[str, object]:
+    """Bandwidth selection and smoothing in one call (Sec. 4's cv_fkreg).
+
+    x: [n, d] (or [n] for d = 1) sample locations; y: [n] or [R, n] responses
+    (complex for complex responses); hlist: [n_bw, d, d] candidate H (see
+    ``bandwidth_list``); grid_n: grid points per axis; lo/hi: the grid's
+    box, by default the samples' extent.  One plan holds every candidate:
+    the samples are sorted once and ``df`` returns every candidate's GCV
+    (eq. 22, Girard probes drawn on the device from ``seed``).  The
+    candidate is chosen on the first response's GCV by ``select_bandwidth``
+    with ``dstd``.  Returns a dict: "index", "H" [d, d], "gcv" [n_bw],
+    "trace" [n_bw, 3] (Girard, Hutchinson, exact), "mhat_grid" [R, *grid],
+    "mask" [*grid], "mhat_at_x" [R, n], and with ``variance`` "sigma2"
+    [R, *grid] (eq. 23) of the chosen candidate; "plan" is the plan.
+    """
+    import torch
+    xt = torch.as_tensor(x)
+    if xt.is_complex():          # complex locations: the points (Re z, Im z)
+        xt = torch.view_as_real(xt.reshape(-1))
+    if xt.dim() == 1:
+        xt = xt.reshape(-1, 1)
+    n, d = int(xt.shape[0]), int(xt.shape[1])
+    xh = xt.detach().to("cpu", torch.float64).numpy()
+    lo = [float(v) for v in (xh.min(axis=0) if lo is None else np.atleast_1d(lo))]
+    hi = [float(v) for v in (xh.max(axis=0) if hi is None else np.atleast_1d(hi))]
+    hi = [h if h > l else l + 1.0 for l, h in zip(lo, hi)]
+    H = np.asarray(hlist, dtype=np.float64).reshape(-1, d, d)
+    yt = torch.as_tensor(y)
+    if yt.dim() == 1:
+        yt = yt.reshape(1, -1)
+    R = int(yt.shape[0])
+    cplx = bool(yt.is_complex())
+    if tol is None:
+        tol = 1e-6 if precision == "f32" else 1e-12
+    grid_n = [int(v) for v in np.atleast_1d(grid_n)]
+    if len(grid_n) == 1 and d > 1:
+        grid_n = grid_n * d
+    plan = Plan(d, order, grid_n, lo, hi, H, max_n=max(n, 1), n_rhs=R, max_probes=n_probes,
+                tol=tol, precision=precision, y_complex=cplx, device=device, kernel=kernel)
+    plan.set_points(xt)
+    out = plan.df(yt, n_probes, seed=seed, want=("mhat_grid", "mask", "mhat_at_x"))
+    gcv = out["gcv"][:, 0].detach().cpu().numpy()
+    k = select_bandwidth(gcv, dstd)
+    res = {"index": k, "H": H[k], "gcv": gcv, "trace": out["trace"].detach().cpu().numpy(),
+           "mhat_grid": out["mhat_grid"][k], "mask": out["mask"][k],
+           "mhat_at_x": out["mhat_at_x"][k], "plan": plan}
+    if variance:
+        res["sigma2"] = plan.variance(yt, out["mhat_at_x"])[k]
+    plan.sync()
+    return res
+
+
 def interval(mhat, var, alpha: float = 0.05):
     """Pointwise interval of eq. 28 on device tensors of one dtype (float32 or
     float64): returns (lower, upper) = mhat -/+ z_(1-alpha/2) sqrt(var)."""

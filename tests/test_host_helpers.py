@@ -43,3 +43,59 @@ def test_select_bandwidth_dstd_rule():
     s = float(np.std([5.0, 2.0, 2.1, 9.0]))
     assert fkreg.select_bandwidth([5.0, 2.0, 2.1, 9.0], 0.15 / s) == 2
     assert fkreg.select_bandwidth([float("nan"), 3.0, 1.0, float("nan")]) == 2
+
+
+class _FakePlan:
+    """Stands in for fkreg.Plan: records the arguments, returns outputs of the
+    shapes the real plan returns, with a GCV curve whose minimum is known."""
+    made = []
+
+    def __init__(self, d, order, grid_n, lo, hi, H, max_n, n_rhs=1, max_probes=0, tol=1e-6,
+                 precision="f32", y_complex=False, device=None, kernel="gaussian"):
+        import torch
+        self.args = dict(d=d, order=order, grid_n=list(grid_n), lo=list(lo), hi=list(hi),
+                         H=np.array(H), max_n=max_n, n_rhs=n_rhs, max_probes=max_probes,
+                         tol=tol, precision=precision, y_complex=y_complex, kernel=kernel)
+        self.nb, self.grid = np.array(H).shape[0], tuple(grid_n)
+        self.torch = torch
+        _FakePlan.made.append(self)
+
+    def set_points(self, x):
+        self.x = x
+
+    def df(self, y, n_probes, seed=0, want=()):
+        t = self.torch
+        nb, R, n = self.nb, self.args["n_rhs"], self.args["max_n"]
+        g = t.tensor([(k - 2.0) ** 2 + 1.0 for k in range(nb)], dtype=t.float64)
+        return {"gcv": t.stack([g] * R, dim=1), "trace": t.zeros((nb, 3), dtype=t.float64),
+                "mhat_grid": t.arange(nb, dtype=t.float32).reshape(nb, 1, 1).expand(nb, R, int(np.prod(self.grid))).reshape((nb, R) + self.grid),
+                "mask": t.ones((nb,) + self.grid, dtype=t.uint8),
+                "mhat_at_x": t.zeros((nb, R, n))}
+
+    def variance(self, y, mh):
+        t = self.torch
+        return t.full((self.nb, self.args["n_rhs"]) + self.grid, 7.0)
+
+    def sync(self):
+        pass
+
+
+def test_cv_fkreg_orchestration(monkeypatch):
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(fkreg, "Plan", _FakePlan)
+    _FakePlan.made.clear()
+    x = np.column_stack([np.linspace(0.2, 0.9, 50), np.linspace(-1.0, 3.0, 50)])
+    y = np.sin(x[:, 0])
+    H = fkreg.bandwidth_list(6, [(0.05, 0.5), (0.05, 0.5)])[:6]
+    r = fkreg.cv_fkreg(x, y, H, 16, order=1, n_probes=4, variance=True)
+    p = _FakePlan.made[-1]
+    assert p.args["lo"] == pytest.approx([0.2, -1.0]) and p.args["hi"] == pytest.approx([0.9, 3.0])
+    assert p.args["grid_n"] == [16, 16] and p.args["n_rhs"] == 1 and p.args["max_probes"] == 4
+    assert r["index"] == 2 and np.array_equal(r["H"], H[2])
+    assert r["mhat_grid"].shape == (1, 16, 16) and float(r["mhat_grid"][0, 0, 0]) == 2.0
+    assert r["sigma2"].shape == (1, 16, 16) and r["gcv"].shape == (6,)
+    # complex locations become the 2-D points (Re z, Im z)
+    z = x[:, 0] + 1j * x[:, 1]
+    fkreg.cv_fkreg(z, y, H, [16, 16])
+    q = _FakePlan.made[-1]
+    assert q.args["d"] == 2 and q.args["lo"] == pytest.approx([0.2, -1.0])
