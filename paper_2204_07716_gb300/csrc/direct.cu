@@ -3,9 +3,10 @@
 // decay only algebraically, so the NUFFT's truncation cannot be controlled by
 // a tolerance; instead the moment sums of eq. 9 are summed exactly over the
 // samples inside each point's support (an ellipsoid |H^(-1/2) z| <= 1), found
-// through the bins of the sort.  This file computes the grid fields; the
-// grid solve (solve.cu) and the at-sample pass (interp.cu) follow as for the
-// Gaussian path.
+// through the bins of the sort.  This file holds both passes: the grid
+// fields (warp per grid point) and the at-sample pass with its phase B (lane
+// per sample); the grid solve (solve.cu) and the reductions follow as for
+// the Gaussian path.
 #include <cuda_runtime.h>
 
 #include <algorithm>
