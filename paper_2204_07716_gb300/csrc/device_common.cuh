@@ -1,4 +1,5 @@
-// Device helpers shared by the spreading, interpolation and solve kernels.
+// Device helpers shared by the spreading, interpolation, direct-sum and
+// solve kernels.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -1,7 +1,8 @@
-// Device helpers shared by the interpolation kernels (interp.cu and
-// interp_direct.cu): bulk-copy / mbarrier / cp.async primitives, the bin
-// window staging, the lane-per-sample gathers and the per-warp reduction
-// accumulators.
+// Device helpers shared by the at-sample kernels (interp.cu,
+// interp_direct.cu, interp_global.cu and the compact-kernel pass of
+// direct.cu): bulk-copy / mbarrier / cp.async primitives, the bin window
+// staging, the lane-per-sample gathers, the per-warp reduction accumulators
+// and phase B (finish_pass: the at-sample solve and the DF / RSS sums).
 #pragma once
 
 #include <cuda_runtime.h>
