@@ -536,6 +536,46 @@ def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: in
     return res
 
 
+def gcv(x, y, log_sigma, grid_n, lo, hi, order: int = 1, n_probes: int = 10, seed: int = 0,
+        precision: str = "f32", tol=None, device=None):
+    """GCV (eq. 22) of one diagonal bandwidth H = diag(exp(2 log_sigma)) as a
+    differentiable torch function of the samples x [n, d], the responses
+    y [n] and log_sigma [d]: ``fkreg_backward`` computes the value and the
+    three gradients in one call (Monte-Carlo trace of Sec. 2.1 with probes
+    drawn from ``seed``, held fixed), and autograd chains them.  Each call
+    builds a plan for the current bandwidth (a plan's H is fixed).
+    """
+    import torch
+
+    class _GCV(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xx, yy, ls):
+            d = int(xx.shape[1])
+            sig = torch.exp(ls.detach().to("cpu", torch.float64)).numpy()
+            H = np.diag(sig * sig).reshape(1, d, d)
+            t = tol if tol is not None else (1e-6 if precision == "f32" else 1e-12)
+            plan = Plan(d, order, grid_n, lo, hi, H, max_n=max(int(xx.shape[0]), 1), n_rhs=1,
+                        max_probes=n_probes, tol=t, precision=precision,
+                        flags=FKREG_WANT_BACKWARD, device=device)
+            plan.set_points(xx.detach())
+            out = plan.backward(yy.detach(), n_probes, seed=seed, b=0)
+            plan.sync()
+            ctx.save_for_backward(out["dx"].to(xx.device, xx.dtype),
+                                  out["dy"].to(yy.device, yy.dtype),
+                                  out["dlogh"].to(ls.device, ls.dtype))
+            return out["gcv"][0].to(ls.device, ls.dtype)
+
+        @staticmethod
+        def backward(ctx, g):
+            dx, dy, dl = ctx.saved_tensors
+            return g * dx, g * dy, g * dl
+
+    xt = torch.as_tensor(x)
+    if xt.dim() == 1:
+        xt = xt.reshape(-1, 1)
+    return _GCV.apply(xt, torch.as_tensor(y).reshape(-1), torch.as_tensor(log_sigma).reshape(-1))
+
+
 def interval(mhat, var, alpha: float = 0.05):
     """Pointwise interval of eq. 28 on device tensors of one dtype (float32 or
     float64): returns (lower, upper) = mhat -/+ z_(1-alpha/2) sqrt(var)."""

@@ -99,3 +99,46 @@ def test_cv_fkreg_orchestration(monkeypatch):
     fkreg.cv_fkreg(z, y, H, [16, 16])
     q = _FakePlan.made[-1]
     assert q.args["d"] == 2 and q.args["lo"] == pytest.approx([0.2, -1.0])
+
+
+class _FakeBackwardPlan:
+    """Stands in for fkreg.Plan in fkreg.gcv: returns known gradients."""
+    made = []
+
+    def __init__(self, d, order, grid_n, lo, hi, H, max_n, n_rhs=1, max_probes=0, tol=1e-6,
+                 precision="f32", flags=0, device=None, **kw):
+        import torch
+        self.torch, self.d, self.n = torch, d, max_n
+        self.args = dict(H=np.array(H), flags=flags, order=order, max_probes=max_probes)
+        _FakeBackwardPlan.made.append(self)
+
+    def set_points(self, x):
+        self.x = x
+
+    def backward(self, y, n_probes, seed=0, b=0):
+        t = self.torch
+        n, d = self.n, self.d
+        return {"gcv": t.tensor([0.25], dtype=t.float64),
+                "dlogh": t.arange(1, d + 1, dtype=t.float64),
+                "dy": t.full((n,), 0.5, dtype=t.float32),
+                "dx": t.arange(n * d, dtype=t.float32).reshape(n, d)}
+
+    def sync(self):
+        pass
+
+
+def test_gcv_autograd_chains_the_backward(monkeypatch):
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(fkreg, "Plan", _FakeBackwardPlan)
+    x = torch.rand(20, 2, dtype=torch.float64, requires_grad=True)
+    y = torch.rand(20, dtype=torch.float64, requires_grad=True)
+    ls = torch.log(torch.tensor([0.1, 0.2], dtype=torch.float64)).requires_grad_()
+    g = fkreg.gcv(x, y, ls, [16, 16], [0, 0], [1, 1], n_probes=4)
+    (3.0 * g).backward()
+    p = _FakeBackwardPlan.made[-1]
+    assert p.args["flags"] & fkreg.FKREG_WANT_BACKWARD
+    assert np.allclose(np.diag(p.args["H"][0]), [0.01, 0.04])
+    assert float(g.detach()) == 0.25
+    assert torch.allclose(ls.grad, torch.tensor([3.0, 6.0], dtype=torch.float64))
+    assert torch.allclose(y.grad, torch.full((20,), 1.5, dtype=torch.float64))
+    assert torch.allclose(x.grad, 3.0 * torch.arange(40, dtype=torch.float64).reshape(20, 2))
