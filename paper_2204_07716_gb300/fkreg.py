@@ -484,7 +484,8 @@ def select_bandwidth(gcv, dstd: float = 0.0) -> int:
 
 def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: int = 10,
              dstd: float = 0.0, seed: int = 0, precision: str = "f32", tol=None,
-             kernel: str = "gaussian", variance: bool = False, device=None) -> Dict[str, object]:
+             kernel: str = "gaussian", variance: bool = False, standardize: bool = False,
+             device=None) -> Dict[str, object]:
     """Bandwidth selection and smoothing in one call (Sec. 4's cv_fkreg).
 
     x: [n, d] (or [n] for d = 1) sample locations; y: [n] or [R, n] responses
@@ -498,6 +499,11 @@ def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: in
     "trace" [n_bw, 3] (Girard, Hutchinson, exact), "mhat_grid" [R, *grid],
     "mask" [*grid], "mhat_at_x" [R, n], and with ``variance`` "sigma2"
     [R, *grid] (eq. 23) of the chosen candidate; "plan" is the plan.
+    With ``standardize`` (the toolbox's convention, Sec. 4) every axis of x,
+    lo and hi is divided by the samples' standard deviation (N - 1
+    normalisation) and hlist is read on that scale; "H" is then the chosen
+    candidate on the standardised scale and "H_original" = S H S with
+    S = diag(std) on the samples' own scale.
     """
     import torch
     xt = torch.as_tensor(x)
@@ -510,6 +516,13 @@ def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: in
     lo = [float(v) for v in (xh.min(axis=0) if lo is None else np.atleast_1d(lo))]
     hi = [float(v) for v in (xh.max(axis=0) if hi is None else np.atleast_1d(hi))]
     hi = [h if h > l else l + 1.0 for l, h in zip(lo, hi)]
+    sd = np.ones(d)
+    if standardize:
+        sd = xh.std(axis=0, ddof=1) if n > 1 else np.ones(d)
+        sd = np.where(sd > 0, sd, 1.0)
+        xt = xt / torch.as_tensor(sd, dtype=xt.dtype, device=xt.device)
+        lo = [l / s_ for l, s_ in zip(lo, sd)]
+        hi = [h / s_ for h, s_ in zip(hi, sd)]
     H = np.asarray(hlist, dtype=np.float64).reshape(-1, d, d)
     yt = torch.as_tensor(y)
     if yt.dim() == 1:
@@ -527,7 +540,8 @@ def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: in
     out = plan.df(yt, n_probes, seed=seed, want=("mhat_grid", "mask", "mhat_at_x"))
     gcv = out["gcv"][:, 0].detach().cpu().numpy()
     k = select_bandwidth(gcv, dstd)
-    res = {"index": k, "H": H[k], "gcv": gcv, "trace": out["trace"].detach().cpu().numpy(),
+    res = {"index": k, "H": H[k], "H_original": np.diag(sd) @ H[k] @ np.diag(sd), "gcv": gcv,
+           "trace": out["trace"].detach().cpu().numpy(),
            "mhat_grid": out["mhat_grid"][k], "mask": out["mask"][k],
            "mhat_at_x": out["mhat_at_x"][k], "plan": plan}
     if variance:

@@ -142,3 +142,21 @@ def test_gcv_autograd_chains_the_backward(monkeypatch):
     assert torch.allclose(ls.grad, torch.tensor([3.0, 6.0], dtype=torch.float64))
     assert torch.allclose(y.grad, torch.full((20,), 1.5, dtype=torch.float64))
     assert torch.allclose(x.grad, 3.0 * torch.arange(40, dtype=torch.float64).reshape(20, 2))
+
+
+def test_cv_fkreg_standardises_x(monkeypatch):
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(fkreg, "Plan", _FakePlan)
+    _FakePlan.made.clear()
+    rng = np.random.default_rng(4)
+    x = rng.random(200) * 20.0
+    y = np.sin(x)
+    H = fkreg.bandwidth_list(10, [(0.01, 1.0)])
+    r = fkreg.cv_fkreg(x, y, H, 100, order=0, standardize=True)
+    p = _FakePlan.made[-1]
+    sd = float(np.std(x, ddof=1))
+    xs = p.x.numpy().reshape(-1)
+    assert np.allclose(xs, x / sd)
+    assert p.args["lo"][0] == pytest.approx(x.min() / sd) and p.args["hi"][0] == pytest.approx(x.max() / sd)
+    # the printed Bessel example reports h on both scales: original = normalised * std(x)
+    assert np.sqrt(r["H_original"][0, 0]) == pytest.approx(np.sqrt(r["H"][0, 0]) * sd)
