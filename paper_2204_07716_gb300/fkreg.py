@@ -1,10 +1,20 @@
 """Thin Python binding of libfkreg.so (argument marshalling only).
 
-Every computation happens inside the CUDA library; this module only builds
-the C structs, hands device pointers of torch tensors and the current CUDA
-stream to the C ABI declared in ``include/fkreg.h``, and raises on a non-OK
-status.  There is no CPU fallback: if the library is missing the import of
-a plan fails loudly.
+Every computation of the smoother happens inside the CUDA library; this
+module only builds the C structs, hands device pointers of torch tensors and
+the current CUDA stream to the C ABI declared in ``include/fkreg.h``, and
+raises on a non-OK status.  There is no CPU fallback: if the library is
+missing the import of a plan fails loudly.
+
+Contents: ``Plan`` (one problem: set_points, smooth, df, variance,
+log_variance, backward), ``Batch`` (uneven problems in one captured graph),
+``StepGraph`` (a sequence of calls captured as one graph), ``predict`` and
+``interval`` (device post-processing calls), and host-side conveniences
+that only orchestrate those calls or work on host scalars:
+``bandwidth_list`` (candidate H lists, get_hList of Sec. 4),
+``select_bandwidth`` (the dstd rule of Table 1), ``cv_fkreg`` (Sec. 4's
+one-call bandwidth selection and smoothing), ``gcv`` (GCV as a
+differentiable torch function through fkreg_backward), ``autotune_tile``.
 """
 from __future__ import annotations
 
