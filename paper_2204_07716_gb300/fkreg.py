@@ -29,8 +29,8 @@ LIB_PATH = os.path.join(HERE, "libfkreg.so")
 
 FKREG_F32, FKREG_F64 = 0, 1
 FKREG_SPREAD_ES, FKREG_SPREAD_GAUSS = 0, 1
-KERNELS = {"gaussian": 0, "uniform": 1, "epanechnikov": 2, "triangle": 3, "biweight": 4,
-           "triweight": 5}
+KERNELS = {"gaussian": 0, "uniform": 1, "box": 1, "epanechnikov": 2, "triangle": 3,
+           "biweight": 4, "triweight": 5}
 FKREG_GCV_EXACT_TRACE = 1
 FKREG_WANT_BACKWARD = 2
 STAGES = ["sort", "strengths", "spread", "fft_fwd", "kmul_grid", "fft_grid", "grid_solve",
@@ -159,6 +159,12 @@ def make_opts(d: int, order: int, grid_n: Sequence[int], lo: Sequence[float],
               spread_kernel: str = "es", mask_rho: float = 0.0, tile: int = 0,
               flags: int = 0, kernel: str = "gaussian"):
     """Build an Opts struct; returns (opts, keepalive) -- keep both alive."""
+    if kernel not in KERNELS:
+        raise FkregError(f"unknown kernel {kernel!r} (one of {sorted(KERNELS)})")
+    if spread_kernel not in ("es", "gauss"):
+        raise FkregError(f"unknown spread_kernel {spread_kernel!r} ('es' or 'gauss')")
+    if precision not in ("f32", "f64"):
+        raise FkregError(f"unknown precision {precision!r} ('f32' or 'f64')")
     H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1, d, d))
     o = Opts()
     o.dim, o.order, o.kernel = d, order, KERNELS[kernel]

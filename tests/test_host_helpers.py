@@ -160,3 +160,13 @@ def test_cv_fkreg_standardises_x(monkeypatch):
     assert p.args["lo"][0] == pytest.approx(x.min() / sd) and p.args["hi"][0] == pytest.approx(x.max() / sd)
     # the printed Bessel example reports h on both scales: original = normalised * std(x)
     assert np.sqrt(r["H_original"][0, 0]) == pytest.approx(np.sqrt(r["H"][0, 0]) * sd)
+
+
+def test_option_names_are_checked():
+    H = np.diag([0.01, 0.02])
+    base = dict(d=2, order=1, grid_n=(32, 32), lo=(0, 0), hi=(1, 1), H=H)
+    for bad in (dict(kernel="gauss"), dict(spread_kernel="gaussian"), dict(precision="fp32")):
+        with pytest.raises(fkreg.FkregError):
+            fkreg.make_opts(**base, **bad)
+    # Table 1 calls the uniform kernel "box"
+    assert fkreg.make_opts(**base, kernel="box")[0].kernel == fkreg.make_opts(**base, kernel="uniform")[0].kernel
