@@ -9,7 +9,10 @@ query point, Gaussian elimination in FP64).  This module adds the quantities
 built on top of those sums, each written from its definition in the paper:
 
 * ``grid_points``      the uniform grid of eq. 6, endpoints included.
-* ``moment_sums``      s_g and t_a of eq. 9 at arbitrary query points.
+* ``moment_sums``      s_g and t_a of eq. 9 at arbitrary query points; with
+                       ``cutoff=True`` the pairs beyond the Mahalanobis radius
+                       CUTOFF_R2 are left out (a cell list finds the rest),
+                       which keeps N = 10^6 affordable.
 * ``smooth_at``        mhat = e_1^T S^-1 t (eqs. 3, 10, 11) at query points.
 * ``smoother_diag``    S_ii = K_H(0) [S(x_i)^-1]_11, the i-th diagonal entry of
                        the smoother matrix S of eq. 3 applied at the samples.
@@ -71,6 +74,10 @@ def lib():
         L.or_moment_sums.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int, dp, dp,
                                      ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int]
         L.or_moment_sums.restype = ctypes.c_int
+        L.or_moment_sums_cutoff.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int, dp,
+                                            dp, ctypes.c_int, ctypes.c_int64, dp,
+                                            ctypes.c_double, dp, ctypes.c_int]
+        L.or_moment_sums_cutoff.restype = ctypes.c_int
         L.or_lpr_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int,
                                    dp, dp, dp]
         L.or_lpr_solve.restype = ctypes.c_int
@@ -126,11 +133,18 @@ def grid_points(grid_n: Sequence[int], lo: Sequence[float], hi: Sequence[float])
     return np.stack([g.reshape(-1) for g in mesh], axis=1)
 
 
+# Mahalanobis radius of the cutoff mode: a skipped pair has
+# K_H(z) < 1e-18 K_H(0), below the FP64 rounding of any sum near its centre.
+CUTOFF_R2 = 2.0 * math.log(1e18)
+
+
 def moment_sums(x: np.ndarray, c: np.ndarray, H: np.ndarray, deg: int,
-                q: np.ndarray, nthreads: int = 0) -> np.ndarray:
+                q: np.ndarray, nthreads: int = 0, cutoff: bool = False) -> np.ndarray:
     """s/t moment sums of eq. 9, [nq, nstr, nmono(d, deg)].
 
     ``c`` is [nstr, n] (use ones for the s-fields, y for the t-fields).
+    ``cutoff=True`` skips the pairs with z^T H^-1 z > CUTOFF_R2 (found
+    through a cell list); the result equals the full sum to rounding.
     """
     x = _c64(x)
     n, d = x.shape
@@ -139,8 +153,12 @@ def moment_sums(x: np.ndarray, c: np.ndarray, H: np.ndarray, deg: int,
     H = _c64(H)
     nm = nmono(d, deg)
     out = np.zeros((q.shape[0], c.shape[0], nm))
-    rc = lib().or_moment_sums(d, n, _dp(x), c.shape[0], _dp(c), _dp(H), deg,
-                              q.shape[0], _dp(q), _dp(out), nthreads)
+    if cutoff:
+        rc = lib().or_moment_sums_cutoff(d, n, _dp(x), c.shape[0], _dp(c), _dp(H), deg,
+                                         q.shape[0], _dp(q), CUTOFF_R2, _dp(out), nthreads)
+    else:
+        rc = lib().or_moment_sums(d, n, _dp(x), c.shape[0], _dp(c), _dp(H), deg,
+                                  q.shape[0], _dp(q), _dp(out), nthreads)
     if rc != 0:
         raise ValueError(f"oracle moment sums failed ({rc}): H must be SPD, d in 1..3")
     return out
@@ -229,27 +247,28 @@ def lpr_solve(d: int, order: int, s: np.ndarray, t: np.ndarray):
 
 
 def smooth_at(x: np.ndarray, y: np.ndarray, H: np.ndarray, order: int,
-              q: np.ndarray, nthreads: int = 0):
+              q: np.ndarray, nthreads: int = 0, cutoff: bool = False):
     """Local-polynomial estimate at query points q.
 
     Returns a dict with ``mhat`` [nq, nrhs], ``s`` [nq, ns] (s-fields),
-    ``t`` [nq, nrhs, nt] (t-fields) and ``sinv11`` [nq].
+    ``t`` [nq, nrhs, nt] (t-fields) and ``sinv11`` [nq].  ``cutoff`` as in
+    ``moment_sums``.
     """
     x = _c64(x)
     d = x.shape[1]
     y = _c64(np.atleast_2d(y))
     nrhs = y.shape[0]
     ones = np.ones((1, x.shape[0]))
-    s = moment_sums(x, ones, H, 2 * order, q, nthreads)[:, 0, :]
-    t = moment_sums(x, y, H, order, q, nthreads)
+    s = moment_sums(x, ones, H, 2 * order, q, nthreads, cutoff)[:, 0, :]
+    t = moment_sums(x, y, H, order, q, nthreads, cutoff)
     mh, si = lpr_solve(d, order, s, t)
     return {"mhat": mh, "s": s, "t": t, "sinv11": si}
 
 
 def scale_field(x: np.ndarray, c: np.ndarray, H: np.ndarray, q: np.ndarray,
-                nthreads: int = 0) -> np.ndarray:
+                nthreads: int = 0, cutoff: bool = False) -> np.ndarray:
     """a(q) = sum_i K_H(x_i - q) |c_i| : the natural size of a moment field."""
-    return moment_sums(x, np.abs(np.atleast_2d(c)), H, 0, q, nthreads)[:, :, 0]
+    return moment_sums(x, np.abs(np.atleast_2d(c)), H, 0, q, nthreads, cutoff)[:, :, 0]
 
 
 def smoother_diag(x: np.ndarray, H: np.ndarray, order: int, idx=None,

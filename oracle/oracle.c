@@ -174,6 +174,151 @@ int or_moment_sums(int d, int64_t n, const double* x, int nstr, const double* c,
   return 0;
 }
 
+/*
+ * The moment sums of or_moment_sums with the far pairs left out (the cutoff
+ * mode for large N): a term with Mahalanobis radius z^T H^-1 z > r2max is
+ * skipped.  With r2max = 2 ln(1e18) every skipped kernel value is below
+ * 1e-18 K_H(0), beneath the FP64 rounding of any sum that holds a term near
+ * its centre, so the result equals the full sum of eq. 9 to rounding.
+ *
+ * Neighbours are found through a uniform cell list over the samples (a
+ * counting sort by cell, built here on every call).  The ellipse
+ * z^T H^-1 z <= r2max lies in the box |z_j| <= sqrt(r2max H_jj); cells are at
+ * least that wide per axis, so every neighbour of a query lies in the 3^d
+ * cells around the query's own cell.  Inside a cell the samples keep their
+ * input order.  Same arguments and output layout as or_moment_sums.
+ * Returns 0, -1 if H is not SPD, -2 for a bad d or r2max, -3 if out of memory.
+ */
+int or_moment_sums_cutoff(int d, int64_t n, const double* x, int nstr, const double* c,
+                          const double* H, int deg, int64_t nq, const double* q,
+                          double r2max, double* out, int nthreads) {
+  double Hinv[9], det;
+  if (d < 1 || d > OR_MAXD || !(r2max > 0)) return -2;
+  if (inv_det(d, H, Hinv, &det)) return -1;
+  const double norm = 1.0 / sqrt(pow(2.0 * M_PI, d) * det);
+  const int nm = or_nmono(d, deg);
+  int exps[OR_MAXMONO * OR_MAXD];
+  or_monomials(d, deg, exps);
+  /* cell list: cell edge >= the half-width of the ellipse's bounding box */
+  double lo[OR_MAXD] = {0, 0, 0}, cs[OR_MAXD] = {1, 1, 1};
+  int64_t nc[OR_MAXD] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) {
+    double mn = INFINITY, mx = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+      mn = fmin(mn, x[i * d + a]);
+      mx = fmax(mx, x[i * d + a]);
+    }
+    if (n == 0) mn = mx = 0.0;
+    lo[a] = mn;
+    cs[a] = sqrt(r2max * H[a * d + a]) * (1.0 + 1e-9);
+    nc[a] = (int64_t)floor((mx - mn) / cs[a]) + 1;
+  }
+  const int64_t cap = n > 0 ? 2 * n + 64 : 64;
+  for (;;) {
+    int64_t tot = 1;
+    for (int a = 0; a < d; ++a) tot *= nc[a];
+    if (tot <= cap) break;
+    for (int a = 0; a < d; ++a) {
+      cs[a] *= 2.0;
+      nc[a] = nc[a] / 2 + 1;
+    }
+  }
+  int64_t ncell = 1;
+  for (int a = 0; a < d; ++a) ncell *= nc[a];
+  int64_t* start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+  int64_t* cell_of = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!start || !cell_of || !order) {
+    free(start);
+    free(cell_of);
+    free(order);
+    return -3;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t k = 0;
+    for (int a = 0; a < d; ++a) {
+      int64_t kj = (int64_t)floor((x[i * d + a] - lo[a]) / cs[a]);
+      if (kj < 0) kj = 0;
+      if (kj > nc[a] - 1) kj = nc[a] - 1;
+      k = k * nc[a] + kj;
+    }
+    cell_of[i] = k;
+    start[k + 1] += 1;
+  }
+  for (int64_t k = 0; k < ncell; ++k) start[k + 1] += start[k];
+  {
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    if (!fill) {
+      free(start);
+      free(cell_of);
+      free(order);
+      return -3;
+    }
+    memcpy(fill, start, sizeof(int64_t) * (size_t)ncell);
+    for (int64_t i = 0; i < n; ++i) order[fill[cell_of[i]]++] = i;
+    free(fill);
+  }
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t k = 0; k < nq; ++k) {
+    double acc[16 * OR_MAXMONO];
+    double* accp = acc;
+    double* heap = NULL;
+    if (nstr * nm > 16 * OR_MAXMONO) {
+      heap = (double*)malloc(sizeof(double) * (size_t)nstr * nm);
+      accp = heap;
+    }
+    memset(accp, 0, sizeof(double) * (size_t)nstr * nm);
+    const double* qk = q + k * d;
+    /* the 3^d cells around the query's cell, clipped to the list */
+    int64_t klo[OR_MAXD] = {0, 0, 0}, khi[OR_MAXD] = {0, 0, 0};
+    int empty = (n == 0);
+    for (int a = 0; a < d; ++a) {
+      const double f = floor((qk[a] - lo[a]) / cs[a]);
+      const double fl = f - 1.0 < 0.0 ? 0.0 : f - 1.0;
+      const double fh = f + 1.0 > (double)(nc[a] - 1) ? (double)(nc[a] - 1) : f + 1.0;
+      if (fl > fh) empty = 1;
+      klo[a] = (int64_t)fl;
+      khi[a] = (int64_t)fh;
+    }
+    int64_t kk[OR_MAXD] = {klo[0], klo[1], klo[2]};
+    while (!empty) {
+      int64_t cell = 0;
+      for (int a = 0; a < d; ++a) cell = cell * nc[a] + kk[a];
+      for (int64_t p = start[cell]; p < start[cell + 1]; ++p) {
+        const int64_t i = order[p];
+        double z[OR_MAXD];
+        for (int a = 0; a < d; ++a) z[a] = x[i * d + a] - qk[a];
+        double e = 0;
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) e += z[a] * Hinv[a * d + b] * z[b];
+        if (e > r2max) continue;
+        const double kv = norm * exp(-0.5 * e);
+        for (int m = 0; m < nm; ++m) {
+          double mono = kv;
+          for (int a = 0; a < d; ++a)
+            for (int pp = 0; pp < exps[m * d + a]; ++pp) mono *= z[a];
+          for (int s = 0; s < nstr; ++s) accp[s * nm + m] += mono * c[(int64_t)s * n + i];
+        }
+      }
+      /* next cell of the neighbourhood (last axis fastest) */
+      int a = d - 1;
+      while (a >= 0 && kk[a] == khi[a]) {
+        kk[a] = klo[a];
+        --a;
+      }
+      if (a < 0) break;
+      kk[a] += 1;
+    }
+    memcpy(out + k * (int64_t)nstr * nm, accp, sizeof(double) * (size_t)nstr * nm);
+    free(heap);
+  }
+  free(start);
+  free(cell_of);
+  free(order);
+  return 0;
+}
+
 /* Position of the monomial with exponent vector e inside the table. */
 static int mono_index(int d, int nm, const int* exps, const int* e) {
   for (int m = 0; m < nm; ++m) {

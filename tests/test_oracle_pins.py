@@ -422,3 +422,75 @@ def test_grid_points_eq6():
     assert g.shape == (15, 2)
     np.testing.assert_allclose(g[:5, 1], [-1, -0.5, 0, 0.5, 1])
     np.testing.assert_allclose(g[::5, 0], [0, 0.5, 1])
+
+
+# ------------------------------------------------------------ cutoff mode ----
+@pytest.mark.parametrize("d,deg", [(1, 2), (2, 2), (2, 4), (3, 2)])
+def test_cutoff_sums_equal_the_full_sums(d, deg):
+    # the cell-list sums leave out only pairs with K_H < 1e-18 K_H(0): on small
+    # inputs they equal the plain O(N) sums of eq. 9 to rounding, with a
+    # correlated H, clustered samples and queries inside and outside the box
+    rng = np.random.default_rng(300 + d + deg)
+    H = rand_spd(rng, d, 0.04)
+    x = np.concatenate([rng.random((1500, d)), 0.5 + 0.01 * rng.standard_normal((500, d))])
+    c = np.stack([np.ones(x.shape[0]), rng.standard_normal(x.shape[0])])
+    q = np.concatenate([rng.random((60, d)), rng.random((20, d)) * 1.6 - 0.3])
+    full = oracle.moment_sums(x, c, H, deg, q)
+    cut = oracle.moment_sums(x, c, H, deg, q, cutoff=True)
+    scale = oracle.moment_sums(x, np.abs(c), H, 0, q)[:, :, :1]      # sum of |terms| per point
+    sig = np.sqrt(np.max(np.diag(H)))
+    expo = oracle.monomials(d, deg).sum(axis=1)
+    # pointwise inside the sample cloud, normwise (against the largest sum of
+    # |terms|) at the queries outside it, where every term is tiny
+    ref = scale * sig ** expo[None, None, :]
+    err_in = np.abs(cut - full)[:60] / ref[:60]
+    err_all = np.abs(cut - full) / np.max(ref, axis=0, keepdims=True)
+    assert np.max(err_in) < 1e-12
+    assert np.max(err_all) < 1e-12
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_cutoff_neighbour_search_finds_every_pair(d):
+    # with a small radius most pairs are cut: the cell-list sum must equal a
+    # brute-force sum over exactly the pairs with z^T H^-1 z <= r2 (numpy, all
+    # pairs), so a cell the search skipped would show up
+    rng = np.random.default_rng(310 + d)
+    H = rand_spd(rng, d, 0.08)
+    n = 3000
+    x = rng.random((n, d))
+    y = rng.standard_normal(n)
+    q = np.concatenate([rng.random((50, d)), x[:10]])
+    r2 = 2.0
+    L = oracle.lib()
+    out = np.zeros((q.shape[0], 2, d + 1))
+    c = np.ascontiguousarray(np.stack([np.ones(n), y]))
+    rc = L.or_moment_sums_cutoff(d, n, oracle._dp(np.ascontiguousarray(x)), 2, oracle._dp(c),
+                                 oracle._dp(np.ascontiguousarray(H)), 1, q.shape[0],
+                                 oracle._dp(np.ascontiguousarray(q)), r2, oracle._dp(out), 0)
+    assert rc == 0
+    Hinv = np.linalg.inv(H)
+    norm = 1.0 / math.sqrt((2 * math.pi) ** d * np.linalg.det(H))
+    counts = []
+    for k, qq in enumerate(q):
+        z = x - qq
+        e = np.einsum("ni,ij,nj->n", z, Hinv, z)
+        inside = e <= r2
+        counts.append(int(inside.sum()))
+        kv = np.where(inside, norm * np.exp(-0.5 * e), 0.0)
+        mono = np.concatenate([np.ones((n, 1)), z], axis=1)
+        ref = np.stack([kv @ mono, (kv * y) @ mono])
+        np.testing.assert_allclose(out[k], ref, rtol=1e-12, atol=1e-12 * max(np.abs(ref).max(), 1.0))
+    counts = np.array(counts)
+    assert np.mean((counts > 0) & (counts < n)) > 0.8 and np.all(counts[50:] > 0)
+
+
+def test_cutoff_sums_without_neighbours_or_samples():
+    H = np.diag([1e-4, 1e-4])
+    x = np.array([[0.2, 0.2], [0.25, 0.2]])
+    q = np.array([[0.9, 0.9], [0.2, 0.2]])
+    m = oracle.moment_sums(x, np.ones((1, 2)), H, 2, q, cutoff=True)
+    assert np.all(m[0] == 0.0)
+    np.testing.assert_allclose(m[1], oracle.moment_sums(x, np.ones((1, 2)), H, 2, q[1:]) [0],
+                               rtol=1e-14)
+    e = oracle.moment_sums(np.zeros((0, 2)), np.ones((1, 0)), H, 1, q, cutoff=True)
+    assert e.shape == (2, 1, 3) and np.all(e == 0.0)
