@@ -214,6 +214,24 @@ def algorithmic(plan, n, n_probes):
     return {"spread": (spread_bytes, spread_flops), "interp": (interp_bytes, interp_flops)}
 
 
+STEP_WANT = ("mhat_grid", "mask", "mhat_at_x")
+
+
+def ll2d_plan(w, device):
+    """The plan of the headline step (2-D local linear, FP32, y + N_PROBES probes)."""
+    from paper_2204_07716_gb300 import fkreg
+    return fkreg.Plan(2, 1, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, n_rhs=1, max_probes=N_PROBES,
+                      tol=w.tol, precision="f32", device=device)
+
+
+def ll2d_step(plan, x, y, seed):
+    """One headline step: bin sort, df with y and N_PROBES device probes, variance pass."""
+    plan.set_points(x)
+    out = plan.df(y, N_PROBES, seed=seed, want=STEP_WANT)
+    s2 = plan.variance(y, out["mhat_at_x"])
+    return out, s2
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -232,19 +250,14 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     w = inputs.ll2d()
     n = w.n
-    plan = fkreg.Plan(2, 1, w.grid_n, w.lo, w.hi, w.H, max_n=n, n_rhs=1, max_probes=N_PROBES,
-                      tol=w.tol, precision="f32", device=dev)
+    plan = ll2d_plan(w, dev)
     x = torch.tensor(w.x, dtype=torch.float32, device=dev)
     y = torch.tensor(w.y, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    want = ("mhat_grid", "mask", "mhat_at_x")
 
     def step(k, xx, yy):
-        plan.set_points(xx)
-        out = plan.df(yy, N_PROBES, seed=1000 + k, want=want)
-        s2 = plan.variance(yy, out["mhat_at_x"])
-        return out, s2
+        return ll2d_step(plan, xx, yy, 1000 + k)
 
     for k in range(args.warmup):
         step(k, x, y)

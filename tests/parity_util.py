@@ -11,6 +11,11 @@ its natural size (see the test tolerances):
   i.e. the error of the numerator t_0 that the estimate inherits; a plain
   relative error is undefined where mhat crosses zero and grows like
   tol / density in sparse regions for any tolerance-controlled method.
+
+A point where the oracle's value is finite and the point is valid (not
+masked) must be finite on the GPU too: mhat_error returns infinity there, so
+a GPU NaN never hides behind the metric.  ``check_mask`` compares the GPU's
+density mask with the oracle's s_0 in both directions.
 """
 import numpy as np
 
@@ -26,12 +31,29 @@ def mhat_error(mg, mo, s0, a_y, valid=None):
     mg = np.asarray(mg, dtype=np.float64).reshape(-1)
     mo = np.asarray(mo, dtype=np.float64).reshape(-1)
     s0 = np.asarray(s0, dtype=np.float64).reshape(-1)
-    ok = np.isfinite(mg) & np.isfinite(mo)
+    ok = np.isfinite(mo)
     if valid is not None:
         ok &= np.asarray(valid).reshape(-1)
     if not ok.any():
         return 0.0
+    if not np.all(np.isfinite(mg[ok])):
+        return float("inf")
     return float(np.max(s0[ok] * np.abs(mg[ok] - mo[ok])) / np.max(np.abs(a_y)))
+
+
+def check_mask(mask, s0_oracle, s0_max, rho=1e-3, margin=0.01):
+    """The GPU's mask (s_0(g) >= rho max s_0) against the oracle's s_0.
+
+    Points the oracle puts clearly above the threshold must be unmasked and
+    points clearly below it masked; within ``margin`` of it either is right.
+    """
+    mask = np.asarray(mask).reshape(-1).astype(bool)
+    s0 = np.asarray(s0_oracle, dtype=np.float64).reshape(-1)
+    thr = rho * s0_max
+    dense = s0 >= (1 + margin) * thr
+    sparse = s0 <= (1 - margin) * thr
+    assert np.all(mask[dense]), f"{int(np.sum(~mask[dense]))} dense points masked"
+    assert not np.any(mask[sparse]), f"{int(np.sum(mask[sparse]))} sparse points unmasked"
 
 
 def field_error(g, o, a, sigma_scale):

@@ -67,6 +67,15 @@ def test_batch_graph_matches_standalone_plans_and_oracle():
         r = oracle.smooth_at(x32, yy[None], w.H[0], 1, gp[idx])
         ay = oracle.scale_field(x32, yy[None], w.H[0], gp[idx])[:, 0]
         assert mhat_error(gg, r["mhat"][:, 0], r["s"][:, 0], ay, mask) < 1e-5, part
+    # its conditional-variance pass (eq. 23) from the batch's own m-hat(x_i):
+    # r_i = |y_i - mhat(x_i)|^2 smoothed with the same bandwidth
+    mx = outs[i]["mhat_at_x"][0, 0].cpu().numpy()
+    rr = np.abs(w.y[0].astype(np.complex64) - mx).astype(np.float64) ** 2
+    ov = oracle.smooth_at(x32, rr[None], w.H[0], 1, gp[idx])
+    ar = oracle.scale_field(x32, rr[None], w.H[0], gp[idx])[:, 0]
+    s2 = outs[i]["sigma2"][0, 0].reshape(-1).cpu().numpy()[idx]
+    assert np.all(np.isnan(s2[~mask]))
+    assert mhat_error(s2, ov["mhat"][:, 0], ov["s"][:, 0], ar, mask) < 1e-5
 
 
 def test_autotuner_picks_a_candidate():

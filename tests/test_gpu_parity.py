@@ -11,7 +11,8 @@ import pytest
 
 import oracle
 from paper_2204_07716_gb300 import inputs
-from parity_util import field_error, field_scale_sigma, mhat_error, sample_grid_indices
+from parity_util import (check_mask, field_error, field_scale_sigma, mhat_error,
+                         sample_grid_indices)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -43,18 +44,24 @@ def as_seen(w):
     return w.x, w.y
 
 
-def check_grid(w, out, b=0, idx=None, bar=None):
-    """Compare mhat and the moment fields on (a subset of) the grid."""
+def check_grid(w, out, b=0, idx=None, bar=None, cutoff=False):
+    """Compare mhat, the mask and the moment fields on (a subset of) the grid.
+
+    With a subset the mask threshold needs max_g s_0 over the whole grid:
+    the GPU's s_0 grid gives the location of the maximum and the oracle's
+    s_0 there (checked against the GPU's) gives its value.
+    """
     bar = bar or BAR[(w.precision, w.tol)]
     x, y = as_seen(w)
     H = w.H[b]
     gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
-    if idx is None:
+    full = idx is None
+    if full:
         idx = np.arange(gp.shape[0])
     q = gp[idx]
-    r = oracle.smooth_at(x, y, H, w.order, q)
-    a1 = oracle.scale_field(x, np.ones((1, w.n)), H, q)[:, 0]
-    ay = oracle.scale_field(x, y, H, q)
+    r = oracle.smooth_at(x, y, H, w.order, q, cutoff=cutoff)
+    a1 = oracle.scale_field(x, np.ones((1, w.n)), H, q, cutoff=cutoff)[:, 0]
+    ay = oracle.scale_field(x, y, H, q, cutoff=cutoff)
     mg = out["mhat_grid"][b].reshape(y.shape[0], -1).cpu().numpy()[:, idx]
     mask = out["mask"][b].reshape(-1).cpu().numpy()[idx].astype(bool)
     errs = {}
@@ -70,9 +77,17 @@ def check_grid(w, out, b=0, idx=None, bar=None):
                 g = mom[r["s"].shape[1] + rr * r["t"].shape[2] + f]
                 errs[f"t{rr}_{f}"] = field_error(g, r["t"][:, rr, f], ay[:, rr],
                                                  field_scale_sigma(H, ex[f]))
-    # masked points have too little density; the oracle agrees they are sparse
-    s0max = np.max(r["s"][:, 0])
-    assert np.all(r["s"][~mask, 0] < 2e-3 * max(s0max, 1e-300) + 1e-300) or idx.size < gp.shape[0]
+    # the density mask, both ways, against the oracle's s_0
+    if full:
+        s0max = np.max(r["s"][:, 0])
+    else:
+        assert "moments" in out, "a sampled grid check needs the GPU's s_0 grid"
+        s0g = out["moments"][b, 0].reshape(-1).cpu().numpy().astype(np.float64)
+        am = int(np.argmax(s0g))
+        s0max = float(oracle.moment_sums(x, np.ones((1, w.n)), H, 0, gp[am:am + 1],
+                                         cutoff=cutoff)[0, 0, 0])
+        assert abs(s0g[am] - s0max) <= 1e-4 * s0max
+    check_mask(mask, r["s"][:, 0], s0max)
     worst = max(errs.values())
     assert worst <= bar, {k: f"{v:.2e}" for k, v in errs.items()}
     return errs
@@ -250,7 +265,7 @@ def test_ll2d_full_size_sampled():
     w = inputs.ll2d()
     _, out = smooth(w)
     idx = sample_grid_indices(w.grid_n, 300, seed=1)
-    check_grid(w, out, idx=idx)
+    check_grid(w, out, idx=idx, cutoff=True)
 
 
 # --------------------------------------------------------- sample parity ----
@@ -333,6 +348,42 @@ def test_fp32_df_sweep():
         assert abs(out["trace"][b, 1].item() - f["hutchinson"]) <= 1e-5 * scale
         tr = oracle.trace_exact(x, w.H[b], 0)
         assert out["trace"][b, 2].item() == pytest.approx(tr, rel=1e-5)
+
+
+def test_nw3d_df_full_size_sampled():
+    # the 3-D DF sweep at its full size (N = 4e6, 64^3 grid, 16 bandwidths,
+    # y + 32 device probes, FP32, tol 1e-6): per bandwidth, m-hat and the mask
+    # at 512 sampled grid points and m-hat(x_i) at 16 sampled samples against
+    # the oracle's cutoff sums
+    w = inputs.nw3d_df()
+    p = plan_for(w, n_probes=w.n_probes)
+    p.set_points(torch.tensor(w.x, dtype=torch.float32))
+    out = p.df(torch.tensor(w.y, dtype=torch.float32), w.n_probes, seed=17,
+               want=("mhat_grid", "mask", "moments", "mhat_at_x"))
+    p.sync()
+    x, y = as_seen(w)
+    gp = oracle.grid_points(w.grid_n, w.lo, w.hi)
+    rng = np.random.default_rng(21)
+    gi = rng.choice(gp.shape[0], 512, replace=False)
+    c = np.concatenate([np.ones((1, w.n)), y, np.abs(y)])
+    for b in range(w.n_bw):
+        H = w.H[b]
+        s0g = out["moments"][b, 0].reshape(-1).cpu().numpy().astype(np.float64)
+        am = int(np.argmax(s0g))
+        m = oracle.moment_sums(x, c, H, 0, np.concatenate([gp[gi], gp[am:am + 1]]),
+                               cutoff=True)[:, :, 0]
+        s0max = m[-1, 0]
+        assert abs(s0g[am] - s0max) <= 1e-4 * s0max
+        m = m[:-1]
+        mask = out["mask"][b].reshape(-1).cpu().numpy().astype(bool)[gi]
+        check_mask(mask, m[:, 0], s0max)
+        mg = out["mhat_grid"][b, 0].reshape(-1).cpu().numpy()[gi]
+        mo = m[:, 1] / m[:, 0]
+        assert mhat_error(mg, mo, m[:, 0], m[:, 2], mask) < 1e-5, b
+        si = rng.choice(w.n, 16, replace=False)
+        mx = oracle.moment_sums(x, c, H, 0, x[si], cutoff=True)[:, :, 0]
+        got = out["mhat_at_x"][b, 0].cpu().numpy()[si]
+        assert mhat_error(got, mx[:, 1] / mx[:, 0], mx[:, 0], mx[:, 2]) < 1e-5, b
 
 
 # --------------------------------------------------------- variance pass ----
