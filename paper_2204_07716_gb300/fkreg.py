@@ -529,16 +529,24 @@ def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: in
         xt = xt.reshape(-1, 1)
     n, d = int(xt.shape[0]), int(xt.shape[1])
     xh = xt.detach().to("cpu", torch.float64).numpy()
+    sd = np.ones(d)
+    if standardize:
+        # divide in FP64, then round to x's own type; the default box is the
+        # extent of those rounded values and a given box is divided likewise
+        # and widened to hold them, so no sample falls outside the box that
+        # the device compares against in its own precision
+        sd = xh.std(axis=0, ddof=1) if n > 1 else np.ones(d)
+        sd = np.where(sd > 0, sd, 1.0)
+        xs = torch.as_tensor(xh / sd).to(xt.dtype)
+        xh = xs.numpy().astype(np.float64)
+        xt = xs.to(xt.device)
+        if lo is not None:
+            lo = np.minimum(np.atleast_1d(np.asarray(lo, dtype=np.float64)) / sd, xh.min(axis=0))
+        if hi is not None:
+            hi = np.maximum(np.atleast_1d(np.asarray(hi, dtype=np.float64)) / sd, xh.max(axis=0))
     lo = [float(v) for v in (xh.min(axis=0) if lo is None else np.atleast_1d(lo))]
     hi = [float(v) for v in (xh.max(axis=0) if hi is None else np.atleast_1d(hi))]
     hi = [h if h > l else l + 1.0 for l, h in zip(lo, hi)]
-    sd = np.ones(d)
-    if standardize:
-        sd = xh.std(axis=0, ddof=1) if n > 1 else np.ones(d)
-        sd = np.where(sd > 0, sd, 1.0)
-        xt = xt / torch.as_tensor(sd, dtype=xt.dtype, device=xt.device)
-        lo = [l / s_ for l, s_ in zip(lo, sd)]
-        hi = [h / s_ for h, s_ in zip(hi, sd)]
     H = np.asarray(hlist, dtype=np.float64).reshape(-1, d, d)
     yt = torch.as_tensor(y)
     if yt.dim() == 1:

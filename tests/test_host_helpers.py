@@ -170,3 +170,28 @@ def test_option_names_are_checked():
             fkreg.make_opts(**base, **bad)
     # Table 1 calls the uniform kernel "box"
     assert fkreg.make_opts(**base, kernel="box")[0].kernel == fkreg.make_opts(**base, kernel="uniform")[0].kernel
+
+
+@pytest.mark.parametrize("box", [None, (-0.5, 21.0)])
+def test_cv_fkreg_standardised_float32_samples_stay_in_the_box(monkeypatch, box):
+    # the device keeps a sample only if lo <= x <= hi in the sample's own
+    # precision (lo, hi rounded to it): every standardised float32 sample
+    # passes that test, with the default box and with a given one
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(fkreg, "Plan", _FakePlan)
+    _FakePlan.made.clear()
+    rng = np.random.default_rng(9)
+    for trial in range(20):
+        x = torch.tensor(rng.random(5000) * 20.0 + 1e-3 * trial, dtype=torch.float32)
+        x[0], x[1] = x.min(), x.max()
+        lo, hi = (None, None) if box is None else box
+        fkreg.cv_fkreg(x, torch.sin(x), fkreg.bandwidth_list(4, [(0.05, 0.5)]), 64, lo=lo, hi=hi,
+                       order=0, standardize=True)
+        p = _FakePlan.made[-1]
+        xs = p.x.reshape(-1)
+        assert xs.dtype == torch.float32
+        lo32 = np.float32(p.args["lo"][0])
+        hi32 = np.float32(p.args["hi"][0])
+        assert bool(torch.all(xs >= float(lo32))) and bool(torch.all(xs <= float(hi32)))
+        sd = float(np.std(x.numpy().astype(np.float64), ddof=1))
+        np.testing.assert_allclose(xs.numpy(), x.numpy().astype(np.float64) / sd, rtol=1e-6)
