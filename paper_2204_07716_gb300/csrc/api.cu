@@ -260,7 +260,15 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   for (int a = 0; a < d; ++a) nb *= P->g.nbins[a];
   P->nbins_total = nb;
   P->nsub_max = nb + (max_n + fk::kSubMax - 1) / fk::kSubMax;
-  P->nblk_interp = 152 * 8;
+  // device and its SM count (persistent grids are sized from it)
+  if (cudaGetDevice(&P->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, P->device) !=
+          cudaSuccess ||
+      P->sm_count < 1) {
+    delete P;
+    return set_global_error(FKREG_ERR_CUDA, "no CUDA device");
+  }
+  P->nblk_interp = int64_t(P->sm_count) * 8;
   // tile + halo must fit shared memory for one strength
   {
     size_t cells = 1;
@@ -269,11 +277,6 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
       delete P;
       return set_global_error(FKREG_ERR_UNSUPPORTED, "spreading tile too large for shared memory");
     }
-  }
-  // device
-  if (cudaGetDevice(&P->device) != cudaSuccess) {
-    delete P;
-    return set_global_error(FKREG_ERR_CUDA, "no CUDA device");
   }
   // workspace layout
   const size_t T = P->tsize;

@@ -104,6 +104,7 @@ struct fkreg_plan_s {
   int64_t nbins_total = 0;
   int64_t nsub_max = 0;
   int64_t nblk_interp = 0;      // blocks of the interpolation kernel (partials)
+  int sm_count = 0;             // streaming multiprocessors of the plan's device
   int nacc = 0;                 // accumulators per (block, bandwidth)
 
   // workspace regions

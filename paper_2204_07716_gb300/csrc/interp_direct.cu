@@ -298,7 +298,7 @@ cudaError_t run_interp_direct(fkreg_plan_s* P, int b, int n_rhs_real, int n_prob
   if (wins + per_warp * 8 > budget) return cudaSuccess;
   const int nw = int(std::min<size_t>(kLWarps, (budget - wins) / std::max<size_t>(per_warp, 1)));
   const size_t smem = wins + per_warp * size_t(nw);
-  const unsigned grid = unsigned(std::min<int64_t>(152, std::max<int64_t>(1, P->nsub_max)));
+  const unsigned grid = unsigned(std::min<int64_t>(P->sm_count, std::max<int64_t>(1, P->nsub_max)));
   float* vo = static_cast<float*>(vout);
   *launched = true;
 #define FK_A(DD, OO, GG)                                                                        \

@@ -489,7 +489,7 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
     const unsigned blocks = unsigned((n + 255) / 256);
     const bool shared_hist = nbins <= 8192;
     if (shared_hist) {
-      const unsigned hb = unsigned(std::min<int64_t>((n + 2047) / 2048, 152 * 4));
+      const unsigned hb = unsigned(std::min<int64_t>((n + 2047) / 2048, int64_t(P->sm_count) * 4));
       const size_t hs = sizeof(uint32_t) * nbins;
       if (P->prec == FKREG_F32)
         bin_keys_hist_kernel<float><<<hb, 512, hs, s>>>(g, n, nbins, static_cast<const float*>(x),

@@ -47,7 +47,8 @@ EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create"
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
            "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
            "fkreg_batch_capture", "fkreg_batch_launch", "fkreg_batch_latencies",
-           "fkreg_batch_plan", "fkreg_batch_last_error", "fkreg_batch_destroy"]
+           "fkreg_batch_plan", "fkreg_batch_last_error", "fkreg_batch_destroy",
+           "fkreg_measure_peaks"]
 
 
 class Opts(ctypes.Structure):
@@ -83,6 +84,16 @@ class Outputs(ctypes.Structure):
 
 
 _lib = None
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int), ("sm_mhz", ctypes.c_double),
+                ("fp32_tflops", ctypes.c_double), ("fp32x2_tflops", ctypes.c_double),
+                ("smem_load_gbs", ctypes.c_double * 3), ("smem_bcast16_gbs", ctypes.c_double),
+                ("smem_atomic_gops", ctypes.c_double), ("gmem_atomic_gops", ctypes.c_double)]
+
+
+PEAKS_SCRATCH_BYTES = 4 << 20
 
 
 class FkregError(RuntimeError):
@@ -144,6 +155,7 @@ def load():
     L.fkreg_batch_last_error.restype = ctypes.c_char_p
     L.fkreg_batch_destroy.argtypes = [vp]
     L.fkreg_batch_destroy.restype = None
+    L.fkreg_measure_peaks.argtypes = [ctypes.POINTER(Peaks), vp, ctypes.c_size_t, vp]
     no_status = ("fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy", "fkreg_batch_plan",
                  "fkreg_batch_last_error", "fkreg_batch_destroy")
     for name in EXPORTS:
@@ -201,6 +213,31 @@ def spread_kernel_ft(kind: str, w: int, beta: float, nf: int, nk: int) -> np.nda
     if st != 0:
         raise FkregError(L.fkreg_global_error().decode())
     return out
+
+
+def measure_peaks(device=None) -> dict:
+    """SM-side peaks of the GPU (fkreg_measure_peaks): SM count and clock,
+    FP32 FMA TFLOP/s (scalar, packed), shared-memory load GB/s for 4/8/16-byte
+    lanes and a 16-byte broadcast, shared and global atomic Gop/s, and the
+    shared-memory bytes per clock per SM that the 16-byte rate implies."""
+    import torch
+    L = load()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    scratch = torch.empty(PEAKS_SCRATCH_BYTES, dtype=torch.uint8, device=dev)
+    out = Peaks()
+    with torch.cuda.device(dev):
+        st = L.fkreg_measure_peaks(ctypes.byref(out), ctypes.c_void_p(scratch.data_ptr()),
+                                   PEAKS_SCRATCH_BYTES,
+                                   ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+    if st != 0:
+        raise FkregError(f"fkreg_measure_peaks failed ({STATUS.get(st, st)})")
+    r = {"sm_count": out.sm_count, "sm_mhz": out.sm_mhz, "fp32_tflops": out.fp32_tflops,
+         "fp32x2_tflops": out.fp32x2_tflops, "smem_load_gbs": list(out.smem_load_gbs),
+         "smem_bcast16_gbs": out.smem_bcast16_gbs, "smem_atomic_gops": out.smem_atomic_gops,
+         "gmem_atomic_gops": out.gmem_atomic_gops}
+    clk = out.sm_count * out.sm_mhz * 1e6
+    r["smem_bytes_per_clk_sm"] = [v * 1e9 / clk for v in out.smem_load_gbs] if clk > 0 else None
+    return r
 
 
 def _ptr(t) -> Optional[int]:

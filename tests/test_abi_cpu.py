@@ -2,6 +2,7 @@
 symbol, validates arguments, and its host planner is right.  No GPU needed."""
 import ctypes
 import math
+import glob
 import os
 import re
 
@@ -22,9 +23,11 @@ def lib():
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "fkreg.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fkreg_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(fkreg_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
