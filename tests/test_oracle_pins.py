@@ -494,3 +494,27 @@ def test_cutoff_sums_without_neighbours_or_samples():
                                rtol=1e-14)
     e = oracle.moment_sums(np.zeros((0, 2)), np.ones((1, 0)), H, 1, q, cutoff=True)
     assert e.shape == (2, 1, 3) and np.all(e == 0.0)
+
+
+def test_effective_weight_is_s0_for_nw_and_pins_the_error_bound():
+    # parity_util.effective_weight: 1/||S~^-1 e_1||_1 equals s_0 for
+    # Nadaraya-Watson, and bounds the m-hat change under a field perturbation
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from parity_util import effective_weight
+    rng = np.random.default_rng(77)
+    H = np.diag([0.05 ** 2, 0.08 ** 2])
+    x = rng.random((400, 2))
+    q = rng.random((50, 2))
+    y = rng.standard_normal((1, 400))
+    s = oracle.moment_sums(x, np.ones((1, 400)), H, 0, q)[:, 0, :]
+    np.testing.assert_allclose(effective_weight(s, H, 2, 0), s[:, 0], rtol=1e-14)
+    r = oracle.smooth_at(x, y, H, 1, q)
+    w = effective_weight(r["s"], H, 2, 1)
+    assert np.all(w > 0) and np.all(w <= r["s"][:, 0] * (1 + 1e-12))
+    # perturb the t-fields by delta (scaled basis): |dm| <= max|delta~| / w
+    sig = np.sqrt(np.diag(H))
+    delta = 1e-6 * rng.standard_normal(r["t"].shape)
+    m2, _ = oracle.lpr_solve(2, 1, r["s"], r["t"] + delta)
+    dt_scaled = np.abs(delta[:, 0, :] / np.array([1.0, sig[0], sig[1]]))
+    assert np.all(np.abs(m2[:, 0] - r["mhat"][:, 0]) <= dt_scaled.max(axis=1) / w * (1 + 1e-9))
