@@ -21,6 +21,21 @@ constexpr int kMaxAcc = 512;  // bound on the reduced sums of one at-sample laun
 
 constexpr uint32_t kMaxSpin = 1u << 22;  // bounded mbarrier wait
 constexpr int kLWarps = 16;              // lane-per-sample kernels: warps per block (upper bound)
+constexpr int kMmaMaxRows = 16;          // tensor-core union gather: union rows (padded to 8)
+constexpr int kMmaMaxCols = 24;          // and columns at most
+
+// Transpose row (floats) of the union gather for NQ quads of fields: 4 NQ
+// rounded to an odd number of 16-byte quads (eight lanes reading eight rows
+// then hit distinct banks).
+__host__ __device__ constexpr int mma_stage_row(int nq) { return 4 * nq + ((nq & 1) ? 0 : 4); }
+
+// Quads of fields (4 floats) the persistent kernel keeps per sample for F2
+// fields: the compile-time sizes it is instantiated for.
+inline int interp_quads(int F2) {
+  const int nqn = (F2 + 3) / 4;
+  for (int q : {2, 4, 6, 8, 10, 12}) if (nqn <= q) return q;
+  return 16;
+}
 
 // ---- bulk-copy / mbarrier primitives (inline PTX) --------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -184,6 +199,148 @@ __device__ __forceinline__ void lane_gather_global(const float* __restrict__ fld
         }
     }
   }
+}
+
+// ---- warp-union gather on the tensor cores (2-D, FP32 fields) -----------
+// The 32 sorted samples of a warp share most of their w x w windows.  Over
+// the union of the windows (rows padded to a multiple of 8) the warp forms
+//   V[s][f] = sum_c A[s][c] G[c][f],   A[s][c] = phi(z_s0 + r) phi(z_s1 + col)
+// (A is 0 outside sample s's own window, since phi vanishes there) as
+// mma.m16n8k8 products: M = 32 samples (two m-tiles), N = fields in tiles of
+// 8, one k-step per union column of 8 rows.  FP32 accuracy comes from the
+// three-term split x = hi + lo of both operands into TF32
+// (lo*hi + hi*lo + hi*hi): hi is x rounded to TF32, lo = x - hi exactly,
+// and the tensor core reads lo's top 19 bits; the dropped lo*lo term and the
+// truncation of lo are below 2^-20 of each product.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = __float_as_uint(x - __uint_as_float(hi));  // exact: hi is x rounded to 11 bits
+}
+// d += a * b for one m16n8k8 tile; a, b hold TF32 operands.  Fragment
+// layout (g = lane / 4, t = lane % 4): a = A[g][t], A[g+8][t], A[g][t+4],
+// A[g+8][t+4]; b = B[t][g], B[t+4][g]; d = D[g][2t], D[g][2t+1],
+// D[g+8][2t], D[g+8][2t+1].
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// win: the staged window; the union is rows [r0, r0 + 8 nrb) x columns
+// [c0, c0 + ncol) of it (inside the window).  zr / zc: this lane's z of the
+// union's first row / column (a large value for a lane without a sample).
+// Fields f < 8 NTL are read from each cell (the caller keeps that inside the
+// staged rows).  The result goes through stg (this warp's [8][SROW] floats of
+// shared memory) so that lane s ends with its own sample's fields in
+// acc[q] = fields 4q .. 4q + 3.
+template <int W, int NTL, int NQ, int SROW>
+__device__ __forceinline__ void mma_union_gather(const float* win, int rec, int pitch, int r0,
+                                                 int nrb, int c0, int ncol, int lane, float zr,
+                                                 float zc, int skind, float beta, float* stg,
+                                                 float4 (&acc)[NQ]) {
+  static_assert(2 * NTL <= NQ, "fields of the n-tiles must fit the accumulators");
+  const int g = lane >> 2, tq = lane & 3;
+  // The A rows of this lane are samples g + 8 j (j = 0..3), the same for the
+  // four lanes of a quad.  Their row weights differ per lane (rows tq and
+  // tq + 4); their column weights do not, so lane tq of the quad evaluates
+  // sample g + 8 tq's and the quad exchanges them.
+  float zrs[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) zrs[j] = __shfl_sync(0xffffffffu, zr, g + 8 * j);
+  const float zc_q = __shfl_sync(0xffffffffu, zc, g + 8 * tq);
+  const int qbase = lane & ~3;
+  float d[2][NTL][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NTL; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d[mt][nt][k] = 0.f;
+  const float* base = win + size_t(r0 + tq) * pitch + size_t(c0) * rec + g;
+#pragma unroll 1
+  for (int rb = 0; rb < nrb; ++rb) {
+    // row weights of rows 8 rb + tq and 8 rb + tq + 4 for the four samples
+    float wra[4], wrb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      wra[j] = phi<float>(skind, W, beta, zrs[j] + float(8 * rb + tq));
+      wrb[j] = phi<float>(skind, W, beta, zrs[j] + float(8 * rb + tq + 4));
+    }
+    const float* rowp = base + size_t(8 * rb) * pitch;
+#pragma unroll 1
+    for (int c = 0; c < ncol; ++c) {
+      const float wc_own = phi<float>(skind, W, beta, zc_q + float(c));
+      uint32_t ah[2][4], al[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const float wc0 = __shfl_sync(0xffffffffu, wc_own, qbase + 2 * mt);
+        const float wc1 = __shfl_sync(0xffffffffu, wc_own, qbase + 2 * mt + 1);
+        split_tf32(wra[2 * mt] * wc0, ah[mt][0], al[mt][0]);
+        split_tf32(wra[2 * mt + 1] * wc1, ah[mt][1], al[mt][1]);
+        split_tf32(wrb[2 * mt] * wc0, ah[mt][2], al[mt][2]);
+        split_tf32(wrb[2 * mt + 1] * wc1, ah[mt][3], al[mt][3]);
+      }
+      const float* cp = rowp + size_t(c) * rec;
+      // n-tiles in pairs: four independent tiles between the three products
+      // of one tile, and only two n-tiles' operands held at a time
+#pragma unroll
+      for (int np = 0; np < NTL; np += 2) {
+        constexpr int kP = 2;
+        uint32_t bh[kP][2], bl[kP][2];
+#pragma unroll
+        for (int u = 0; u < kP; ++u)
+          if (np + u < NTL) {
+            split_tf32(cp[8 * (np + u)], bh[u][0], bl[u][0]);
+            split_tf32(cp[size_t(4) * pitch + 8 * (np + u)], bh[u][1], bl[u][1]);
+          }
+#pragma unroll
+        for (int u = 0; u < kP; ++u)
+          if (np + u < NTL)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) mma_tf32(d[mt][np + u], al[mt], bh[u][0], bh[u][1]);
+#pragma unroll
+        for (int u = 0; u < kP; ++u)
+          if (np + u < NTL)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) mma_tf32(d[mt][np + u], ah[mt], bl[u][0], bl[u][1]);
+#pragma unroll
+        for (int u = 0; u < kP; ++u)
+          if (np + u < NTL)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) mma_tf32(d[mt][np + u], ah[mt], bh[u][0], bh[u][1]);
+      }
+    }
+  }
+  // transpose through shared memory, one group of 8 samples at a time:
+  // group k = 2 mt + h holds samples 16 mt + 8 h + g (lanes 8k .. 8k + 7)
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int mt = k >> 1, h = k & 1;
+#pragma unroll
+    for (int nt = 0; nt < NTL; ++nt)
+      *reinterpret_cast<float2*>(stg + g * SROW + 8 * nt + 2 * tq) =
+          make_float2(d[mt][nt][2 * h], d[mt][nt][2 * h + 1]);
+    __syncwarp();
+    // every lane reads its row; the lanes of group k keep it (acc is first
+    // written in group 0, so it holds no value while the products run)
+    const bool mine = (lane >> 3) == k;
+#pragma unroll
+    for (int q = 0; q < 2 * NTL; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(stg + (lane & 7) * SROW + 4 * q);
+      acc[q] = mine ? v : (k == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[q]);
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int q = 2 * NTL; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __device__ __forceinline__ float quad_comp(const float4& v, int c) {

@@ -1,11 +1,15 @@
 // Type-2 interpolation, persistent form (FP32, width 7, 1-D / 2-D, every
 // field in one pass): see interp.cu for the method.  For every field in one
-// pass (F2 <= 64) and a compile-time system (order, dimension) the
-// lane-per-sample gather leaves a sample's fields in registers and phase B
-// reads them there, so no staging rows are needed and two bin windows fit
-// shared memory.  One block per SM walks its sub-problems in turn; while it
-// gathers from one window the bulk copies fill the other.  The gather-only
-// form (GONLY) writes V[f][s] for the backward instead of phase B.
+// pass (F2 <= 64) and a compile-time system (order, dimension) a sample's
+// fields end in its lane's registers and phase B reads them there, so no
+// staging rows are needed and two bin windows fit shared memory.  One block
+// per SM walks its sub-problems in turn; while it gathers from one window the
+// bulk copies fill the other.  In 2-D a warp whose 32 samples' windows lie
+// in a small union (rows padded to 8 at most 16, at most 24 columns) gathers
+// on the tensor cores (mma_union_gather: split-TF32 products over the
+// union); other warps, and 1-D plans, gather lane per sample with packed FP32
+// FMAs.  The gather-only form (GONLY) writes V[f][s] for the backward instead
+// of phase B.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,18 +38,36 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
   constexpr int NS = ORD == 0 ? 1 : (D == 1 ? 3 : 6);   // s-fields
   constexpr int NT = ORD == 0 ? 1 : D + 1;              // t-fields per response (= p)
   constexpr int QMAX = GONLY ? 0 : (4 * NQ - NS) / NT;  // responses + probes held
+  constexpr bool MMA = D == 2;                          // tensor-core union gather
+  constexpr int NTL = NQ / 2;                           // its n-tiles of 8 fields
+  constexpr int SROW = MMA ? mma_stage_row(NQ) : 0;     // its transpose row (floats)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = int(blockDim.x >> 5);
   T* wins = reinterpret_cast<T*>(smem_raw);
-  double* red_all = reinterpret_cast<double*>(wins + 2 * size_t(win_floats));
+  // layout: two windows, the warps' transpose rows [nwarps][8][SROW], the
+  // warps' reduction accumulators [nwarps][nacc]
+  float* stg = wins + 2 * size_t(win_floats) + size_t(warp) * 8 * SROW;
+  double* red_all = reinterpret_cast<double*>(wins + 2 * size_t(win_floats) +
+                                              size_t(nwarps) * 8 * SROW);
   double* red = red_all + warp * nacc;
+  // Work sharing: sub-problem k (of the block's sequence it = 0, 1, ...) sits
+  // in buffer it % 2.  Warps claim its groups of 32 samples from s_claim and
+  // move on to the next sub-problem when none is left; the last warp to leave
+  // a sub-problem refills its buffer with the sub-problem two ahead.  So warps
+  // never wait for each other at a block barrier, and are at most one
+  // sub-problem apart.
+  __shared__ int s_claim[2], s_left[2], s_issued[2], s_failed;
   for (int a = lane; a < nacc; a += 32) red[a] = 0.0;
   if (threadIdx.x == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
     fence_mbar_init();
+    s_claim[0] = s_claim[1] = 0;
+    s_left[0] = s_left[1] = 0;
+    s_issued[0] = s_issued[1] = 0;
+    s_failed = 0;
   }
   __syncthreads();
   const BwDev& B = bwt[b];
@@ -68,100 +90,113 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
     o0 = int(floor(double(bj0 * g.tile[0]) * r0)) - g.pad - lo_slack;
     o1 = D > 1 ? int(floor(double(bj1 * g.tile[1]) * r1)) - g.pad - lo_slack : 0;
   };
-  if (threadIdx.x == 0 && blockIdx.x < nsub) {
-    int a0, a1;
-    window_of(blockIdx.x, a0, a1);
-    issue_window_copies<T, D>(fld, rec, nf0, nf1, a0, a1, wm0, wm1, pitch, wins, &mbar[0]);
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t kj = blockIdx.x + uint32_t(j) * gridDim.x;
+      if (kj < nsub) {
+        int a0, a1;
+        window_of(kj, a0, a1);
+        s_issued[j] = 1;
+        issue_window_copies<T, D>(fld, rec, nf0, nf1, a0, a1, wm0, wm1, pitch,
+                                  wins + size_t(j) * win_floats, &mbar[j]);
+      }
+    }
   }
-  bool failed = false;
-  int it = 0;
-  for (uint32_t k = blockIdx.x; k < nsub; k += gridDim.x, ++it) {
+  volatile int* failed_flag = &s_failed;
+  for (int it = 0;; ++it) {
+    const uint32_t k = blockIdx.x + uint32_t(it) * gridDim.x;
+    if (k >= nsub || *failed_flag) break;
     const int cur = it & 1;
     const uint32_t parity = uint32_t(it >> 1) & 1u;
+    bool ok = false;
+    for (uint32_t i = 0; i < kMaxSpin && !ok; ++i) ok = mbar_try_wait(&mbar[cur], parity);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) {
+        atomicOr(errw, 2);
+        *failed_flag = 1;
+      }
+      break;
+    }
     const T* win = wins + size_t(cur) * win_floats;
     int o0, o1;
     window_of(k, o0, o1);
     const uint32_t first = sub_first[k];
     const uint32_t last = min(first + uint32_t(kSubMax), bin_start[sub_bin[k] + 1]);
-    // the other buffer's readers finished at the barrier that ended the last
-    // sub-problem: fill it with the next window now
-    const bool more = k + gridDim.x < nsub;
-    if (threadIdx.x == 0 && more) {
-      int a0, a1;
-      window_of(k + gridDim.x, a0, a1);
-      issue_window_copies<T, D>(fld, rec, nf0, nf1, a0, a1, wm0, wm1, pitch,
-                                wins + size_t(cur ^ 1) * win_floats, &mbar[cur ^ 1]);
-    }
-    bool ok = false;
-    for (uint32_t i = 0; i < kMaxSpin && !ok; ++i) ok = mbar_try_wait(&mbar[cur], parity);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(errw, 2);
-      // wait (bounded) for the copies still in flight before leaving
-      bool late = ok;
-      for (uint32_t i = 0; i < kMaxSpin && !late; ++i) late = mbar_try_wait(&mbar[cur], parity);
-      if (more) {
-        const uint32_t pn = uint32_t((it + 1) >> 1) & 1u;
-        bool late2 = false;
-        for (uint32_t i = 0; i < kMaxSpin && !late2; ++i) late2 = mbar_try_wait(&mbar[cur ^ 1], pn);
-      }
-      failed = true;
-      break;
-    }
     const int ngr = int((last - first + 31) / 32);
-    T xn0 = T(0), xn1 = T(0);
-    if (warp < ngr) {
-      const int64_t sn = min(int64_t(first) + int64_t(warp) * 32 + lane, int64_t(last) - 1);
-      xn0 = xs[sn];
-      if (D > 1) xn1 = xs[n + sn];
-    }
-    for (int gi = warp; gi < ngr; gi += nwarps) {
+    for (;;) {
+      int gi = 0;
+      if (lane == 0) gi = atomicAdd(&s_claim[cur], 1);
+      gi = __shfl_sync(0xffffffffu, gi, 0);
+      if (gi >= ngr) break;
       const int64_t s0 = int64_t(first) + int64_t(gi) * 32;
       const int cnt = int(min(int64_t(32), int64_t(last) - s0));
       const int64_t s = s0 + lane;
       const bool valid = lane < cnt;
-      const T x0 = xn0, x1 = xn1;
-      if (gi + nwarps < ngr) {
-        const int64_t sn =
-            min(int64_t(first) + int64_t(gi + nwarps) * 32 + lane, int64_t(last) - 1);
-        xn0 = xs[sn];
-        if (D > 1) xn1 = xs[n + sn];
-      }
-      // strengths and original index, loaded ahead of the gather
-      uint32_t orig = 0u;
-      T cv[QMAX > 0 ? QMAX : 1];
-      if (!GONLY) {
-        orig = valid ? perm[s] : 0u;
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) cv[q] = (valid && q < nq) ? str[int64_t(1 + q) * n + s] : T(0);
-      }
+      const int64_t sx = valid ? s : s0;
+      const T x0 = xs[sx];
+      const T x1 = D > 1 ? xs[n + sx] : T(0);
       const T u0 = __fmul_rn(x0, ih0);
       const T fo0 = ceilf(__fsub_rn(u0, halfw));
       const int i0 = int(fo0);
       const T off0 = fo0 - u0;
       int i1 = 0;
-      T off1 = T(0);
+      T off1 = T(0), u1 = T(0);
       if (D > 1) {
-        const T u1 = __fmul_rn(x1, ih1);
+        u1 = __fmul_rn(x1, ih1);
         const T fo1 = ceilf(__fsub_rn(u1, halfw));
         i1 = int(fo1);
         off1 = fo1 - u1;
       }
       const int l0 = i0 - o0, l1 = D > 1 ? i1 - o1 : 0;
       const bool inside = l0 >= 0 && l0 + W <= wm0 && (D == 1 || (l1 >= 0 && l1 + W <= wm1));
-      T pl[W];
-#pragma unroll
-      for (int t = 0; t < W; ++t) pl[t] = phi<T>(skind, W, beta, (D > 1 ? off1 : off0) + T(t));
       const int nqd = (F2 + 3) >> 2;
       float4 acc[NQ];
+      // the union of the warp's windows (rows padded to a multiple of 8)
+      bool use_mma = false;
+      int ur0 = 0, unrb = 0, uc0 = 0, uncol = 0;
+      if constexpr (MMA) {
+        if (__all_sync(0xffffffffu, !valid || inside)) {
+          const int lo0 = __reduce_min_sync(0xffffffffu, valid ? l0 : INT_MAX);
+          const int hi0 = __reduce_max_sync(0xffffffffu, valid ? l0 : INT_MIN) + W;
+          const int lo1 = __reduce_min_sync(0xffffffffu, valid ? l1 : INT_MAX);
+          const int hi1 = __reduce_max_sync(0xffffffffu, valid ? l1 : INT_MIN) + W;
+          const int rows = (hi0 - lo0 + 7) & ~7;
+          if (rows <= kMmaMaxRows && rows <= wm0 && hi1 - lo1 <= kMmaMaxCols) {
+            use_mma = true;
+            unrb = rows >> 3;
+            ur0 = min(lo0, wm0 - rows);
+            uc0 = lo1;
+            uncol = hi1 - lo1;
+          }
+        }
+      }
+      if (use_mma) {
+        const T zr = valid ? T(o0 + ur0) - u0 : T(1e4f);
+        const T zc = valid ? T(o1 + uc0) - u1 : T(1e4f);
+        mma_union_gather<W, NTL, NQ, SROW>(win, rec, pitch, ur0, unrb, uc0, uncol, lane, zr, zc,
+                                           skind, beta, stg, acc);
+      } else {
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (inside)
-        lane_gather_smem<D, W, NQ>(win + size_t(l0) * (D > 1 ? pitch : rec) + l1 * rec, rec, pitch,
-                                   nqd, skind, beta, off0, pl, acc);
-      if (__any_sync(0xffffffffu, valid && !inside)) {
-        if (valid && !inside)
-          lane_gather_global<D, W, NQ>(fld, rec, 0, nqd, i0, i1, nf0, nf1, skind, beta, off0, pl,
-                                       acc);
+        for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        T pl[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) pl[t] = phi<T>(skind, W, beta, (D > 1 ? off1 : off0) + T(t));
+        if (inside)
+          lane_gather_smem<D, W, NQ>(win + size_t(l0) * (D > 1 ? pitch : rec) + l1 * rec, rec,
+                                     pitch, nqd, skind, beta, off0, pl, acc);
+        if (__any_sync(0xffffffffu, valid && !inside)) {
+          if (valid && !inside)
+            lane_gather_global<D, W, NQ>(fld, rec, 0, nqd, i0, i1, nf0, nf1, skind, beta, off0, pl,
+                                         acc);
+        }
+      }
+      // strengths and original index (phase B)
+      uint32_t orig = 0u;
+      T cv[QMAX > 0 ? QMAX : 1];
+      if (!GONLY) {
+        orig = valid ? perm[s] : 0u;
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) cv[q] = (valid && q < nq) ? str[int64_t(1 + q) * n + s] : T(0);
       }
       if (GONLY) {
         if (valid)
@@ -219,10 +254,37 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
         }
       }
     }
-    __syncthreads();  // every read of this window is done before it is refilled
+    // this warp leaves sub-problem k; the last to leave refills the buffer
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&s_left[cur], 1) == nwarps - 1) {
+        s_claim[cur] = 0;
+        s_left[cur] = 0;
+        const uint32_t k2 = k + 2 * gridDim.x;
+        if (k2 < nsub && !*failed_flag) {
+          int a0, a1;
+          window_of(k2, a0, a1);
+          s_issued[cur] += 1;
+          __threadfence_block();
+          issue_window_copies<T, D>(fld, rec, nf0, nf1, a0, a1, wm0, wm1, pitch,
+                                    wins + size_t(cur) * win_floats, &mbar[cur]);
+        }
+      }
+    }
   }
-  if (failed) return;
   __syncthreads();
+  if (*failed_flag) {
+    // wait (bounded) for the copies still in flight before leaving
+    if (threadIdx.x == 0)
+      for (int j = 0; j < 2; ++j)
+        if (s_issued[j] > 0) {
+          const uint32_t pj = uint32_t(s_issued[j] - 1) & 1u;
+          bool late = false;
+          for (uint32_t i = 0; i < kMaxSpin && !late; ++i) late = mbar_try_wait(&mbar[j], pj);
+        }
+    return;
+  }
   for (int a = threadIdx.x; a < nacc; a += blockDim.x) {
     double t = 0.0;
     for (int wv = 0; wv < nwarps; ++wv) t += red_get<T>(red_all, wv * nacc + a);
@@ -258,18 +320,19 @@ cudaError_t launch_direct_q(fkreg_plan_s* P, int b, int n_rhs_real, int n_probes
                             void* mhat_at_x, cudaStream_t st, int nacc, int F2, float* vout,
                             int rec, int wm0, int wm1, int pitch, int slack, int win_floats,
                             int nw, size_t smem, unsigned grid) {
-  const int nqn = (F2 + 3) / 4;
 #define FK_Q(Q)                                                                                  \
   return launch_direct_k<D, Q, ORD, GONLY>(P, b, n_rhs_real, n_probes, mhat_at_x, st, nacc, F2, \
                                            vout, rec, wm0, wm1, pitch, slack, win_floats, nw,     \
                                            smem, grid)
-  if (nqn <= 2) FK_Q(2);
-  if (nqn <= 4) FK_Q(4);
-  if (nqn <= 6) FK_Q(6);
-  if (nqn <= 8) FK_Q(8);
-  if (nqn <= 10) FK_Q(10);
-  if (nqn <= 12) FK_Q(12);
-  FK_Q(16);
+  switch (interp_quads(F2)) {
+    case 2: FK_Q(2);
+    case 4: FK_Q(4);
+    case 6: FK_Q(6);
+    case 8: FK_Q(8);
+    case 10: FK_Q(10);
+    case 12: FK_Q(12);
+    default: FK_Q(16);
+  }
 #undef FK_Q
 }
 
@@ -289,12 +352,23 @@ cudaError_t run_interp_direct(fkreg_plan_s* P, int b, int n_rhs_real, int n_prob
   const int wm0 = tma_window(P->geo, B, 0);
   const int wm1 = D > 1 ? tma_window(P->geo, B, 1) : 1;
   if (wm0 > B.nf[0] || (D > 1 && wm1 > B.nf[1])) return cudaSuccess;
-  const int pitch = D > 1 ? wm1 * rec + 4 : wm0 * rec;
+  const int nq = interp_quads(F2);
+  // 2-D rows end in a pad that keeps the pitch at 8 (mod 32) floats, so the
+  // eight rows of a tensor-core k-step start in distinct bank groups, and
+  // that holds the fields up to 4 nq a union-gather lane reads in a row's
+  // last cell
+  int pitch = wm0 * rec;
+  if (D > 1) {
+    int pad = std::max(4, 4 * nq - rec);
+    while ((wm1 * rec + pad) % 32 != 8) pad += 4;
+    pitch = wm1 * rec + pad;
+  }
   const int win_floats = ((D > 1 ? wm0 : 1) * pitch + 31) / 32 * 32;
   const int slack = std::max(tma_slack(P->geo, B, 0), D > 1 ? tma_slack(P->geo, B, 1) : 0);
   const size_t budget = 225 * 1024;
   const size_t wins = 2 * sizeof(float) * size_t(win_floats);
-  const size_t per_warp = sizeof(double) * nacc;
+  const size_t per_warp =
+      sizeof(double) * nacc + (D > 1 ? sizeof(float) * 8 * size_t(mma_stage_row(nq)) : 0);
   if (wins + per_warp * 8 > budget) return cudaSuccess;
   const int nw = int(std::min<size_t>(kLWarps, (budget - wins) / std::max<size_t>(per_warp, 1)));
   const size_t smem = wins + per_warp * size_t(nw);
