@@ -230,7 +230,9 @@ fkreg_status fkreg_set_workspace(fkreg_plan plan, void* ws_dev, size_t bytes, vo
  *     b_j = c_j / tile_j, bin = row-major index of b over nbins;
  *   the centre cell of its spreading window, relative to the bin,
  *     e_j = clamp(ceil(fl(u_j - w/2)) + floor(w/2) - b_j tile_j, 0, tile_j),
- *     local = row-major index of e over (tile_j + 1) values per axis;
+ *     local = serpentine index of e over (tile_j + 1) values per axis:
+ *     local_0 = e_0, local_j = local_(j-1) (tile_j + 1) + e'_j with
+ *     e'_j = tile_j - e_j if local_(j-1) is odd, else e_j;
  * and the key (bin << kbits) | local, kbits = bits of prod_j (tile_j + 1)
  * (kbits = 0, i.e. bin-only keys, if the key would exceed 32 bits).  A stable
  * counting sort orders the samples by key, then by original index: the
@@ -407,9 +409,11 @@ fkreg_status fkreg_stage_times(fkreg_plan plan, double* ms, int64_t* launches,
  *                  was not finite (it is then sorted into the first bin along
  *                  that axis), else 0
  * Larger n or more bins return FKREG_ERR_INVALID_ARG before anything runs.
- * The call allocates nothing.  Its first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call on a device
+ * The call allocates nothing.  Outside a stream capture every call looks up
+ * the array's device address (cudaGetSymbolAddress) with the current device,
+ * so a device reset that reloads the library's module is followed; inside a
+ * capture the address found by an earlier call on that device is used, so
+ * make the first call on a device before any stream capture.  Every call on a device
  * shares the one array and the array keeps the previous call's contents
  * (the call clears what must start at zero), so calls whose work overlaps on
  * the GPU (other streams, other host threads) race: serialise them.

@@ -18,6 +18,8 @@
  *                       blocks / their event-timed duration
  *   fp32_tflops         scalar FFMA (2 flop per lane) over 8 independent chains
  *   fp32x2_tflops       packed FFMA2 (4 flop per lane)
+ *   tf32_mma_tflops     warp-level TF32 tensor products (mma.sync m16n8k8,
+ *                       FP32 accumulation; 2 x 16 x 8 x 8 flop each)
  *   smem_load_gbs[k]    shared-memory loads of 4, 8, 16 bytes per lane at
  *                       consecutive addresses (no bank conflicts), bytes
  *                       delivered to the lanes per second
@@ -48,6 +50,7 @@ typedef struct {
   double sm_mhz;
   double fp32_tflops;
   double fp32x2_tflops;
+  double tf32_mma_tflops;
   double smem_load_gbs[3];
   double smem_bcast16_gbs;
   double smem_atomic_gops;

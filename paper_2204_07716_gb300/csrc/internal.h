@@ -43,9 +43,9 @@ struct GeoDev {
   int kern;         // regression kernel: FKREG_KERNEL_GAUSSIAN (NUFFT) or a compact one (direct)
 };
 
-// Sort keys are (bin << kbits) | local, local = row-major index of the centre
-// cell of the sample's spreading window relative to its bin's first cell,
-// tile_j + 1 values per axis.  kbits = 0 (bin-only keys) if the key would not
+// Sort keys are (bin << kbits) | local, local = serpentine index of the
+// centre cell of the sample's spreading window relative to its bin's first
+// cell, tile_j + 1 values per axis.  kbits = 0 (bin-only keys) if the key would not
 // fit 32 bits.
 inline int key_local_bits(int d, const int64_t* tile, const int64_t* nbins) {
   int64_t cells = 1, bins = 1;

@@ -209,16 +209,14 @@ __device__ __forceinline__ void lane_gather_global(const float* __restrict__ fld
 // mma.m16n8k8 products: M = 32 samples (two m-tiles), N = fields in tiles of
 // 8, one k-step per union column of 8 rows.  FP32 accuracy comes from the
 // three-term split x = hi + lo of both operands into TF32
-// (lo*hi + hi*lo + hi*hi): hi is x rounded to TF32, lo = x - hi exactly,
-// and the tensor core reads lo's top 19 bits; the dropped lo*lo term and the
-// truncation of lo are below 2^-20 of each product.
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+// (lo*hi + hi*lo + hi*hi): hi is x rounded to TF32 (11 significant bits,
+// ties away from zero), lo = x - hi exactly, and the tensor core reads lo's
+// top 19 bits; the dropped lo*lo term and the truncation of lo are below
+// 2^-21 of each product.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_rna(x);
+  // rounding the magnitude bits at bit 13 (finite x; a carry into the
+  // exponent is the correct rounding)
+  hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
   lo = __float_as_uint(x - __uint_as_float(hi));  // exact: hi is x rounded to 11 bits
 }
 // d += a * b for one m16n8k8 tile; a, b hold TF32 operands.  Fragment
@@ -238,15 +236,13 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 // [c0, c0 + ncol) of it (inside the window).  zr / zc: this lane's z of the
 // union's first row / column (a large value for a lane without a sample).
 // Fields f < 8 NTL are read from each cell (the caller keeps that inside the
-// staged rows).  The result goes through stg (this warp's [8][SROW] floats of
-// shared memory) so that lane s ends with its own sample's fields in
-// acc[q] = fields 4q .. 4q + 3.
-template <int W, int NTL, int NQ, int SROW>
-__device__ __forceinline__ void mma_union_gather(const float* win, int rec, int pitch, int r0,
-                                                 int nrb, int c0, int ncol, int lane, float zr,
-                                                 float zc, int skind, float beta, float* stg,
-                                                 float4 (&acc)[NQ]) {
-  static_assert(2 * NTL <= NQ, "fields of the n-tiles must fit the accumulators");
+// staged rows).  d[mt][nt] receives the D fragments of m-tile mt (samples
+// 16 mt .. 16 mt + 15) and n-tile nt (fields 8 nt .. 8 nt + 7).
+template <int W, int NTL>
+__device__ __forceinline__ void mma_union_products(const float* win, int rec, int pitch, int r0,
+                                                   int nrb, int c0, int ncol, int lane, float zr,
+                                                   float zc, int skind, float beta,
+                                                   float (&d)[2][NTL][4]) {
   const int g = lane >> 2, tq = lane & 3;
   // The A rows of this lane are samples g + 8 j (j = 0..3), the same for the
   // four lanes of a quad.  Their row weights differ per lane (rows tq and
@@ -257,7 +253,6 @@ __device__ __forceinline__ void mma_union_gather(const float* win, int rec, int 
   for (int j = 0; j < 4; ++j) zrs[j] = __shfl_sync(0xffffffffu, zr, g + 8 * j);
   const float zc_q = __shfl_sync(0xffffffffu, zc, g + 8 * tq);
   const int qbase = lane & ~3;
-  float d[2][NTL][4];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -275,9 +270,33 @@ __device__ __forceinline__ void mma_union_gather(const float* win, int rec, int 
       wrb[j] = phi<float>(skind, W, beta, zrs[j] + float(8 * rb + tq + 4));
     }
     const float* rowp = base + size_t(8 * rb) * pitch;
+    // software pipeline: the next column's weight and field values are
+    // fetched while this column's products run
+    float wc_next = phi<float>(skind, W, beta, zc_q);
+    float bn[NTL][2];
+#pragma unroll
+    for (int nt = 0; nt < NTL; ++nt) {
+      bn[nt][0] = rowp[8 * nt];
+      bn[nt][1] = rowp[size_t(4) * pitch + 8 * nt];
+    }
 #pragma unroll 1
     for (int c = 0; c < ncol; ++c) {
-      const float wc_own = phi<float>(skind, W, beta, zc_q + float(c));
+      const float wc_own = wc_next;
+      float bv[NTL][2];
+#pragma unroll
+      for (int nt = 0; nt < NTL; ++nt) {
+        bv[nt][0] = bn[nt][0];
+        bv[nt][1] = bn[nt][1];
+      }
+      if (c + 1 < ncol) {
+        wc_next = phi<float>(skind, W, beta, zc_q + float(c + 1));
+        const float* cpn = rowp + size_t(c + 1) * rec;
+#pragma unroll
+        for (int nt = 0; nt < NTL; ++nt) {
+          bn[nt][0] = cpn[8 * nt];
+          bn[nt][1] = cpn[size_t(4) * pitch + 8 * nt];
+        }
+      }
       uint32_t ah[2][4], al[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
@@ -288,9 +307,8 @@ __device__ __forceinline__ void mma_union_gather(const float* win, int rec, int 
         split_tf32(wrb[2 * mt] * wc0, ah[mt][2], al[mt][2]);
         split_tf32(wrb[2 * mt + 1] * wc1, ah[mt][3], al[mt][3]);
       }
-      const float* cp = rowp + size_t(c) * rec;
       // n-tiles in pairs: four independent tiles between the three products
-      // of one tile, and only two n-tiles' operands held at a time
+      // of one tile
 #pragma unroll
       for (int np = 0; np < NTL; np += 2) {
         constexpr int kP = 2;
@@ -298,8 +316,8 @@ __device__ __forceinline__ void mma_union_gather(const float* win, int rec, int 
 #pragma unroll
         for (int u = 0; u < kP; ++u)
           if (np + u < NTL) {
-            split_tf32(cp[8 * (np + u)], bh[u][0], bl[u][0]);
-            split_tf32(cp[size_t(4) * pitch + 8 * (np + u)], bh[u][1], bl[u][1]);
+            split_tf32(bv[np + u][0], bh[u][0], bl[u][0]);
+            split_tf32(bv[np + u][1], bh[u][1], bl[u][1]);
           }
 #pragma unroll
         for (int u = 0; u < kP; ++u)
@@ -319,8 +337,17 @@ __device__ __forceinline__ void mma_union_gather(const float* win, int rec, int 
       }
     }
   }
-  // transpose through shared memory, one group of 8 samples at a time:
-  // group k = 2 mt + h holds samples 16 mt + 8 h + g (lanes 8k .. 8k + 7)
+}
+
+// The D fragments to one sample per lane, through shared memory one group of
+// 8 samples at a time (group k = 2 mt + h holds samples 16 mt + 8 h + g,
+// lanes 8k .. 8k + 7): stg is this warp's [8][SROW] floats; lane s ends with
+// its own sample's fields in acc[q] = fields 4q .. 4q + 3.
+template <int NTL, int NQ, int SROW>
+__device__ __forceinline__ void mma_union_transpose(const float (&d)[2][NTL][4], int lane,
+                                                    float* stg, float4 (&acc)[NQ]) {
+  static_assert(2 * NTL <= NQ, "fields of the n-tiles must fit the accumulators");
+  const int g = lane >> 2, tq = lane & 3;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int mt = k >> 1, h = k & 1;
@@ -329,8 +356,7 @@ __device__ __forceinline__ void mma_union_gather(const float* win, int rec, int 
       *reinterpret_cast<float2*>(stg + g * SROW + 8 * nt + 2 * tq) =
           make_float2(d[mt][nt][2 * h], d[mt][nt][2 * h + 1]);
     __syncwarp();
-    // every lane reads its row; the lanes of group k keep it (acc is first
-    // written in group 0, so it holds no value while the products run)
+    // every lane reads its row; the lanes of group k keep it
     const bool mine = (lane >> 3) == k;
 #pragma unroll
     for (int q = 0; q < 2 * NTL; ++q) {

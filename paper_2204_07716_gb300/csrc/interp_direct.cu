@@ -22,8 +22,14 @@ namespace fk {
 
 namespace {
 
+// Warps per block: 16 for the 1-D lane-per-sample kernel; 12 in 2-D, where
+// the tensor-core gather's fragments need the registers that a 384-thread
+// block leaves each thread.
+template <int D>
+constexpr int direct_warps() { return D == 2 ? 12 : kLWarps; }
+
 template <int D, int W, int NQ, int ORD, bool GONLY>
-__global__ void __launch_bounds__(kLWarps * 32, 1)
+__global__ void __launch_bounds__(direct_warps<D>() * 32, 1)
 interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
                      const float* __restrict__ xs, const float* __restrict__ str,
                      const uint32_t* __restrict__ perm, const float* __restrict__ fld, int rec,
@@ -123,18 +129,30 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
     const uint32_t first = sub_first[k];
     const uint32_t last = min(first + uint32_t(kSubMax), bin_start[sub_bin[k] + 1]);
     const int ngr = int((last - first + 31) / 32);
-    for (;;) {
-      int gi = 0;
-      if (lane == 0) gi = atomicAdd(&s_claim[cur], 1);
-      gi = __shfl_sync(0xffffffffu, gi, 0);
-      if (gi >= ngr) break;
+    // groups are claimed one ahead: the next group's coordinates load while
+    // this one is processed
+    auto claim = [&]() {
+      int v = 0;
+      if (lane == 0) v = atomicAdd(&s_claim[cur], 1);
+      return __shfl_sync(0xffffffffu, v, 0);
+    };
+    auto coords = [&](int gq, T& c0v, T& c1v) {
+      const int64_t sq = min(int64_t(first) + int64_t(gq) * 32 + lane, int64_t(last) - 1);
+      c0v = xs[sq];
+      c1v = D > 1 ? xs[n + sq] : T(0);
+    };
+    int gnext = claim();
+    T xn0 = T(0), xn1 = T(0);
+    if (gnext < ngr) coords(gnext, xn0, xn1);
+    while (gnext < ngr) {
+      const int gi = gnext;
+      const T x0 = xn0, x1 = xn1;
+      gnext = claim();
+      if (gnext < ngr) coords(gnext, xn0, xn1);
       const int64_t s0 = int64_t(first) + int64_t(gi) * 32;
       const int cnt = int(min(int64_t(32), int64_t(last) - s0));
       const int64_t s = s0 + lane;
       const bool valid = lane < cnt;
-      const int64_t sx = valid ? s : s0;
-      const T x0 = xs[sx];
-      const T x1 = D > 1 ? xs[n + sx] : T(0);
       const T u0 = __fmul_rn(x0, ih0);
       const T fo0 = ceilf(__fsub_rn(u0, halfw));
       const int i0 = int(fo0);
@@ -170,12 +188,28 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
           }
         }
       }
+      // strengths and original index (phase B), issued before the transpose
+      // of the tensor-core path so their latency overlaps it
+      uint32_t orig = 0u;
+      T cv[QMAX > 0 ? QMAX : 1];
+      auto load_strengths = [&]() {
+        if (!GONLY) {
+          orig = valid ? perm[s] : 0u;
+#pragma unroll
+          for (int q = 0; q < QMAX; ++q)
+            cv[q] = (valid && q < nq) ? str[int64_t(1 + q) * n + s] : T(0);
+        }
+      };
       if (use_mma) {
         const T zr = valid ? T(o0 + ur0) - u0 : T(1e4f);
         const T zc = valid ? T(o1 + uc0) - u1 : T(1e4f);
-        mma_union_gather<W, NTL, NQ, SROW>(win, rec, pitch, ur0, unrb, uc0, uncol, lane, zr, zc,
-                                           skind, beta, stg, acc);
+        float dfr[2][NTL][4];
+        mma_union_products<W, NTL>(win, rec, pitch, ur0, unrb, uc0, uncol, lane, zr, zc, skind,
+                                   beta, dfr);
+        load_strengths();
+        mma_union_transpose<NTL, NQ, SROW>(dfr, lane, stg, acc);
       } else {
+        load_strengths();
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         T pl[W];
@@ -189,14 +223,6 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
             lane_gather_global<D, W, NQ>(fld, rec, 0, nqd, i0, i1, nf0, nf1, skind, beta, off0, pl,
                                          acc);
         }
-      }
-      // strengths and original index (phase B)
-      uint32_t orig = 0u;
-      T cv[QMAX > 0 ? QMAX : 1];
-      if (!GONLY) {
-        orig = valid ? perm[s] : 0u;
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) cv[q] = (valid && q < nq) ? str[int64_t(1 + q) * n + s] : T(0);
       }
       if (GONLY) {
         if (valid)
@@ -370,7 +396,8 @@ cudaError_t run_interp_direct(fkreg_plan_s* P, int b, int n_rhs_real, int n_prob
   const size_t per_warp =
       sizeof(double) * nacc + (D > 1 ? sizeof(float) * 8 * size_t(mma_stage_row(nq)) : 0);
   if (wins + per_warp * 8 > budget) return cudaSuccess;
-  const int nw = int(std::min<size_t>(kLWarps, (budget - wins) / std::max<size_t>(per_warp, 1)));
+  const int nw = int(std::min<size_t>(D > 1 ? direct_warps<2>() : direct_warps<1>(),
+                                      (budget - wins) / std::max<size_t>(per_warp, 1)));
   const size_t smem = wins + per_warp * size_t(nw);
   const unsigned grid = unsigned(std::min<int64_t>(P->sm_count, std::max<int64_t>(1, P->nsub_max)));
   float* vo = static_cast<float*>(vout);

@@ -1,7 +1,8 @@
 // Microbenchmarks of the SM-side rates that bound the spreading and
 // interpolation kernels (fkreg_measure_peaks): FP32 FMA throughput (scalar
-// and packed), shared-memory load delivery for 4/8/16-byte lanes and for a
-// warp-wide broadcast, and shared / global atomic rates.  Each test runs
+// and packed), warp-level TF32 tensor products, shared-memory load delivery
+// for 4/8/16-byte lanes and for a warp-wide broadcast, and shared / global
+// atomic rates.  Each test runs
 // a fixed amount of work on every SM in one wave, timed with CUDA events on
 // the caller's stream after an untimed warm-up launch.  The SM clock is read
 // from clock64() inside the FP32 test; no device setting is touched.
@@ -56,6 +57,34 @@ __global__ void __launch_bounds__(kThreads) fma2_kernel(int iters, float seed,
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < 8; ++k) s += a[k].x + a[k].y;
+  if (s == -1.0f) sink[blockIdx.x] = s;
+}
+
+// Warp-level TF32 tensor products (mma.sync m16n8k8, FP32 accumulate): eight
+// independent accumulator tiles per warp, operands held in registers.
+__global__ void __launch_bounds__(kThreads) mma_tf32_kernel(int iters, float* __restrict__ sink) {
+  uint32_t a[4], b[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = __float_as_uint(1.0f + 1e-3f * float(threadIdx.x + k));
+  b[0] = __float_as_uint(0.5f);
+  b[1] = __float_as_uint(0.25f + 1e-3f * float(threadIdx.x & 7));
+  float d[8][4];
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[t][k] = 0.f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      asm volatile(
+          "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+          "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+          : "+f"(d[t][0]), "+f"(d[t][1]), "+f"(d[t][2]), "+f"(d[t][3])
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) s += d[t][0] + d[t][1] + d[t][2] + d[t][3];
   if (s == -1.0f) sink[blockIdx.x] = s;
 }
 
@@ -200,6 +229,11 @@ extern "C" fkreg_status fkreg_measure_peaks(fkreg_peaks* out, void* scratch_dev,
   if (!t.time([&] { fma2_kernel<<<blocks, kThreads, 0, s>>>(it_fma, 1.0f, sinkf); }, &ms))
     return FKREG_ERR_CUDA;
   out->fp32x2_tflops = 4.0 * 8.0 * it_fma * threads / (ms * 1e-3) / 1e12;
+  // TF32 tensor products through mma.sync (2 x 16 x 8 x 8 flop per warp-instruction)
+  const int it_mma = 1 << 12;
+  if (!t.time([&] { mma_tf32_kernel<<<blocks, kThreads, 0, s>>>(it_mma, sinkf); }, &ms))
+    return FKREG_ERR_CUDA;
+  out->tf32_mma_tflops = 2.0 * 16 * 8 * 8 * 8.0 * it_mma * (threads / 32.0) / (ms * 1e-3) / 1e12;
   // shared-memory loads
   const int it_ld = 1 << 13;
   const double loads = double(it_ld) * kUnroll * threads;

@@ -6,8 +6,10 @@
 //   bin   = row-major index of (c_j / tile_j)
 // and, inside the bin, the centre cell of its spreading window
 //   o_j   = ceil(fl(u_j - w/2)),   e_j = o_j + floor(w/2)   (c_j or c_j + 1)
-//   local = row-major index of clamp(e_j - b_j tile_j, 0, tile_j) over
-//           (tile_j + 1) values per axis
+//   local = serpentine index of c_j = clamp(e_j - b_j tile_j, 0, tile_j) over
+//           (tile_j + 1) values per axis: local = local (tile_j + 1) + c_j, with
+//           c_j replaced by tile_j - c_j when the local of the axes before is
+//           odd
 // The key (bin << kbits) | local orders the samples by bin and, inside a bin,
 // by the window they touch, so consecutive sorted samples share windows.
 // The samples are ordered by key with a least-significant-digit radix sort
@@ -69,7 +71,10 @@ __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
     int64_t e = int64_t(ceil(sub_rn(u, halfw))) + g.w / 2 - b * g.tile[j];
     e = e < 0 ? 0 : (e > g.tile[j] ? g.tile[j] : e);
     bin = bin * uint32_t(g.nbins[j]) + uint32_t(b);
-    local = local * uint32_t(g.tile[j] + 1) + uint32_t(e);
+    // serpentine order: an axis runs backwards when the index of the axes
+    // before it is odd, so consecutive keys are neighbouring windows
+    local = local * uint32_t(g.tile[j] + 1) +
+            uint32_t((local & 1u) ? g.tile[j] - e : e);
   }
   if (bad) atomicOr(errw, 1);
   keys[i] = g.kbits ? (bin << g.kbits) | local : bin;
@@ -109,7 +114,7 @@ __global__ void bin_keys_hist_kernel(GeoDev g, int64_t n, int64_t nbins, const T
       int e = int(ceil(sub_rn(u, halfw))) + g.w / 2 - b * tj;
       e = e < 0 ? 0 : (e > tj ? tj : e);
       bin = bin * uint32_t(g.nbins[j]) + uint32_t(b);
-      local = local * uint32_t(tj + 1) + uint32_t(e);
+      local = local * uint32_t(tj + 1) + uint32_t((local & 1u) ? tj - e : e);
     }
     keys[i] = g.kbits ? (bin << g.kbits) | local : bin;
     vals[i] = uint32_t(i);
@@ -612,14 +617,20 @@ extern "C" fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const 
     nbins *= geom->nbins[j];
   }
   if (nbins > kStaticMaxBins) return FKREG_ERR_INVALID_ARG;
-  // one-time set-up per device: the device address of the array (host code
-  // cannot use the symbol itself, which names a host-side shadow)
+  // the device address of the array (host code cannot use the symbol itself,
+  // which names a host-side shadow): looked up on every call outside a stream
+  // capture, so a device reset that reloads the module is followed; during a
+  // capture the address from an earlier call on this device is used
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FKREG_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool capturing =
+      cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
   uint32_t* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_base[dev]) {
+    if (!capturing || !g_static_base[dev]) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return FKREG_ERR_CUDA;
       g_static_base[dev] = static_cast<uint32_t*>(p);
@@ -639,7 +650,6 @@ extern "C" fkreg_status fkreg_bin_sort_static(const fkreg_geometry* geom, const 
   }
   g.w = geom->w;
   g.kbits = key_local_bits(d, g.tile, g.nbins);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t* keys0 = base + kOffKeys0;
   uint32_t* vals0 = base + kOffVals0;
   uint32_t* keys1 = base + kOffKeys1;

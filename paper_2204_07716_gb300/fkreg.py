@@ -89,7 +89,7 @@ _lib = None
 class Peaks(ctypes.Structure):
     _fields_ = [("sm_count", ctypes.c_int), ("sm_mhz", ctypes.c_double),
                 ("fp32_tflops", ctypes.c_double), ("fp32x2_tflops", ctypes.c_double),
-                ("smem_load_gbs", ctypes.c_double * 3), ("smem_bcast16_gbs", ctypes.c_double),
+                ("tf32_mma_tflops", ctypes.c_double), ("smem_load_gbs", ctypes.c_double * 3), ("smem_bcast16_gbs", ctypes.c_double),
                 ("smem_atomic_gops", ctypes.c_double), ("gmem_atomic_gops", ctypes.c_double)]
 
 
@@ -217,7 +217,8 @@ def spread_kernel_ft(kind: str, w: int, beta: float, nf: int, nk: int) -> np.nda
 
 def measure_peaks(device=None) -> dict:
     """SM-side peaks of the GPU (fkreg_measure_peaks): SM count and clock,
-    FP32 FMA TFLOP/s (scalar, packed), shared-memory load GB/s for 4/8/16-byte
+    FP32 FMA TFLOP/s (scalar, packed), TF32 mma.sync TFLOP/s, shared-memory
+    load GB/s for 4/8/16-byte
     lanes and a 16-byte broadcast, shared and global atomic Gop/s, and the
     shared-memory bytes per clock per SM that the 16-byte rate implies."""
     import torch
@@ -232,7 +233,8 @@ def measure_peaks(device=None) -> dict:
     if st != 0:
         raise FkregError(f"fkreg_measure_peaks failed ({STATUS.get(st, st)})")
     r = {"sm_count": out.sm_count, "sm_mhz": out.sm_mhz, "fp32_tflops": out.fp32_tflops,
-         "fp32x2_tflops": out.fp32x2_tflops, "smem_load_gbs": list(out.smem_load_gbs),
+         "fp32x2_tflops": out.fp32x2_tflops, "tf32_mma_tflops": out.tf32_mma_tflops,
+         "smem_load_gbs": list(out.smem_load_gbs),
          "smem_bcast16_gbs": out.smem_bcast16_gbs, "smem_atomic_gops": out.smem_atomic_gops,
          "gmem_atomic_gops": out.gmem_atomic_gops}
     clk = out.sm_count * out.sm_mhz * 1e6

@@ -112,7 +112,7 @@ def cpu_keys(x, geom, precision):
         e = np.ceil((u - ft(0.5 * w)).astype(ft)).astype(np.int64) + w // 2 - b * tile[j]
         e = np.clip(e, 0, tile[j])
         bins = bins * nbins[j] + b
-        local = local * (tile[j] + 1) + e
+        local = local * (tile[j] + 1) + np.where(local & 1, tile[j] - e, e)   # serpentine
         cells *= tile[j] + 1
         nb *= nbins[j]
     kb = int(np.ceil(np.log2(cells))) if cells > 1 else 0

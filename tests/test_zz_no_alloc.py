@@ -3,7 +3,8 @@
 Callers that cannot allocate device memory while they run (a memory pool
 that owns the whole device, a plug-in without an allocator) use this entry
 point; its scratch is an array the library owns.  Its permutation and bin
-offsets must equal those of the workspace-based sort (fkreg_set_points +
+offsets must equal numpy's stable argsort of the bin rule's keys (computed on
+the CPU) and those of the workspace-based sort (fkreg_set_points +
 fkreg_get_sort) bit for bit, on consecutive calls that reuse the array.
 """
 import ctypes
@@ -12,6 +13,7 @@ import numpy as np
 import pytest
 
 from paper_2204_07716_gb300 import fkreg, inputs
+from test_gpu_parity import cpu_keys
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -73,6 +75,13 @@ def test_static_sort_equals_workspace_sort_on_consecutive_calls():
         st, perm, bstart, bad = static_sort(w, x)
         assert st == 0
         assert bad == 0
+        # against the keys of the bin rule, computed on the CPU
+        geom = geometry_struct(w).as_dict()
+        key, bins = cpu_keys(w.x, geom, w.precision)
+        assert np.array_equal(perm.astype(np.int64), np.argsort(key, kind="stable"))
+        counts = np.bincount(bins, minlength=int(np.prod(geom["nbins"])))
+        assert np.array_equal(bstart.astype(np.int64), np.concatenate([[0], np.cumsum(counts)]))
+        # and against the workspace sort
         assert np.array_equal(perm, ref[0])
         assert np.array_equal(bstart, ref[1])
         assert bstart[-1] == w.n
@@ -85,6 +94,9 @@ def test_static_sort_limits_and_flag():
     st, perm, bstart, bad = static_sort(w, x)
     assert st == 0 and bad == 1
     assert sorted(perm.tolist()) == list(range(w.n))
+    # the flagged sample is sorted into the first bin along its axis
+    pos = int(np.where(perm == 3)[0][0])
+    assert bstart[0] <= pos < bstart[1]
     big = torch.zeros((MAX_N + 1, 1), dtype=torch.float64, device="cuda")
     st, *_ = static_sort(w, big)
     assert st == 1                                  # FKREG_ERR_INVALID_ARG, nothing launched
