@@ -76,6 +76,24 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Transposed warp sum: v[j] (j < 32) are this lane's values of 32 sums; on
+// return lane L holds the warp total of sum L.  Five exchange levels, each
+// halving the values a lane keeps: 31 shuffles for 32 sums instead of 5 per
+// sum.
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const float send = up ? v[k] : v[k + o];
+      const float keep = up ? v[k + o] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
 // Per-warp accumulators of the reductions (written by lane 0).  FP64 runs
 // accumulate in double; FP32 runs keep an unevaluated sum hi + lo of two
 // floats in the same 8 bytes (two_sum), which keeps the FP64 pipe (a small
@@ -356,12 +374,13 @@ __device__ __forceinline__ void mma_union_transpose(const float (&d)[2][NTL][4],
       *reinterpret_cast<float2*>(stg + g * SROW + 8 * nt + 2 * tq) =
           make_float2(d[mt][nt][2 * h], d[mt][nt][2 * h + 1]);
     __syncwarp();
-    // every lane reads its row; the lanes of group k keep it
-    const bool mine = (lane >> 3) == k;
+    // group 0: every lane reads (acc holds no value while the products run,
+    // and lanes of later groups overwrite theirs); later groups: only the
+    // group's lanes read
+    if (k == 0 || (lane >> 3) == k) {
 #pragma unroll
-    for (int q = 0; q < 2 * NTL; ++q) {
-      const float4 v = *reinterpret_cast<const float4*>(stg + (lane & 7) * SROW + 4 * q);
-      acc[q] = mine ? v : (k == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[q]);
+      for (int q = 0; q < 2 * NTL; ++q)
+        acc[q] = *reinterpret_cast<const float4*>(stg + (lane & 7) * SROW + 4 * q);
     }
     __syncwarp();
   }

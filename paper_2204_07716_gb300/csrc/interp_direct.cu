@@ -108,6 +108,11 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
       }
     }
   }
+  // per-lane running sums (hi + lo) of the slots of phase B (see below)
+  constexpr int NCH = GONLY ? 1 : (2 * QMAX + 1 + 31) / 32;
+  float rs_hi[NCH], rs_lo[NCH];
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) rs_hi[ch] = rs_lo[ch] = 0.f;
   volatile int* failed_flag = &s_failed;
   for (int it = 0;; ++it) {
     const uint32_t k = blockIdx.x + uint32_t(it) * gridDim.x;
@@ -247,10 +252,13 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
       T af[NT];
 #pragma unroll
       for (int k2 = 0; k2 < NT; ++k2) af[k2] = okv ? a[k2] * dsc[k2 < 3 ? k2 : 0] : T(0);
-      {
-        const T tv = warp_sum_t<T>(okv ? k0t * a[0] : T(0));
-        if (lane == 0) red_add<T>(red, nacc - 1, tv);
-      }
+      // this sample's terms of the sums of eq. 22 and Sec. 2.1, by slot:
+      // [0, QMAX) the squared residual (responses) or w_p S w_p (probes),
+      // [QMAX, 2 QMAX) w_p w_p (probes), 2 QMAX the exact-trace term
+      float vals[32 * NCH];
+#pragma unroll
+      for (int j = 0; j < 32 * NCH; ++j) vals[j] = 0.f;
+      vals[2 * QMAX] = okv ? k0t * a[0] : T(0);
 #pragma unroll
       for (int q = 0; q < QMAX; ++q) {
         if (q >= nq) break;
@@ -262,22 +270,28 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
         }
         if (q < n_rhs_real) {
           const T r = valid ? cv[q] - mh : T(0);
-          const T v = warp_sum_t<T>(r * r);
-          if (lane == 0) red_add<T>(red, q, v);
+          vals[q] = r * r;
           if (valid && mhat_at_x) {
             const int mult = cplx ? 2 : 1;
             const int rr = q / mult, pt = q % mult;
             mhat_at_x[((int64_t(b) * n_rhs_out + rr) * n + orig) * mult + pt] = mh;
           }
         } else {
-          const int pp = q - n_rhs_real;
-          const T v1 = warp_sum_t<T>(valid ? cv[q] * mh : T(0));
-          const T v2 = warp_sum_t<T>(valid ? cv[q] * cv[q] : T(0));
-          if (lane == 0) {
-            red_add<T>(red, n_rhs_real + pp, v1);
-            red_add<T>(red, n_rhs_real + n_probes + pp, v2);
-          }
+          vals[q] = valid ? cv[q] * mh : T(0);
+          vals[QMAX + q] = valid ? cv[q] * cv[q] : T(0);
         }
+      }
+      // the warp's totals, one slot per lane, added to the lane's
+      // compensated running sums
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        float part32[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) part32[j] = vals[32 * ch + j];
+        const float t = warp_transpose_sum(part32, lane);
+        float e;
+        rs_hi[ch] = two_sum(rs_hi[ch], t, e);
+        rs_lo[ch] += e;
       }
     }
     // this warp leaves sub-problem k; the last to leave refills the buffer
@@ -297,6 +311,20 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
                                     wins + size_t(cur) * win_floats, &mbar[cur]);
         }
       }
+    }
+  }
+  // slot j -> accumulator of the partial-sum layout: responses' RSS and the
+  // probes' w S w at j, the probes' w w at n_rhs_real + n_probes + p, the
+  // exact-trace term at nacc - 1
+  if (!GONLY) {
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+      const int j = 32 * ch + lane;
+      int a = -1;
+      if (j < nq) a = j;
+      else if (j >= QMAX && j < QMAX + nq && j - QMAX >= n_rhs_real) a = n_probes + j - QMAX;
+      else if (j == 2 * QMAX) a = nacc - 1;
+      if (a >= 0) reinterpret_cast<float2*>(red)[a] = make_float2(rs_hi[ch], rs_lo[ch]);
     }
   }
   __syncthreads();
