@@ -36,6 +36,7 @@ N_PROBES = 10
 WORKLOAD = "ll2d-1M-256sq-LL-f32-tol1e-6"
 METRIC = "sample-pts/sec of NUFFT smoothing at rel err<=1e-5 vs plain FP64; % HBM roofline"
 UNIT = "sample-pts/s"
+DTYPE_F32 = "f32 fields, f64 grid solves, compensated-f32 sample solves"
 
 
 def parse():
@@ -45,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other configurations after the headline line's measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="ll2d",
                     choices=["ll2d", "ll2d_sort", "nw1d", "nw3d_df", "ll2d_gcv", "uneven",
@@ -383,7 +386,8 @@ def run_ours(args, world, rank, local):
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64solve", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_F32, "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "grid": list(w.grid_n), "order": 1,
                    "bandwidth_sd": [0.01, 0.015], "probes": N_PROBES, "tol": w.tol,
                    "units_per_step": units_per_step, "l2": "flushed (512 MB write) between steps",
@@ -401,6 +405,26 @@ def run_ours(args, world, rank, local):
                      for k, v in sm.items()},
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_extra:
+        # the other configurations and the plain single-response FP64 form of
+        # this step, each timed on its own (device events, L2 flushed)
+        plan.close()
+        del graph, graph2, bufs
+        torch.cuda.empty_cache()
+        cfgs = {}
+        for wl, st, wu in EXTRA_RUNS:
+            try:
+                r = measure_workload(wl, st, wu, 1.0, dev)
+                cfgs[wl] = {k: r[k] for k in ("ms_per_step", "value", "unit", "dtype", "config",
+                                              "steps", "warmup", "latency_ms", "clocks",
+                                              "stages_ms_per_step") if k in r}
+            except Exception as e:          # reported, not hidden: the line still prints
+                cfgs[wl] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        result["configs"] = cfgs
+        p64 = cfgs.get("ll2d_plain64", {})
+        if "ms_per_step" in p64:
+            result["plain_f64_ms_per_step"] = p64["ms_per_step"]
+            result["batched_vs_plain"] = p64["ms_per_step"] / result["ms_per_step"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if rank == 0:
@@ -491,20 +515,34 @@ def run_reference(args, world, rank):
 
 
 def run_extra(args):
-    """Timed steps of the other configurations (one GPU, device events)."""
-    import numpy as np
+    """Timed steps of one of the other configurations (one GPU, device events)."""
     import torch
 
     from paper_2204_07716_gb300 import build as fkbuild
-    from paper_2204_07716_gb300 import fkreg, inputs
 
     fkbuild.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    res = measure_workload(args.workload, args.steps, args.warmup, args.scale, dev)
+    print(json.dumps(res), flush=True)
+
+
+# The other configurations, timed after the headline in the default run: a
+# few steps each (the 3-D sweep's step is about 0.7 s), so the whole run ends
+# within minutes.
+EXTRA_RUNS = (("ll2d_plain64", 5, 3), ("nw1d", 20, 3), ("nw3d_df", 3, 3), ("ll2d_gcv", 10, 3),
+              ("uneven", 10, 3), ("ll2d_epan", 5, 3), ("ll2d_logvar", 10, 3))
+
+
+def measure_workload(wl, steps, warmup, sc, dev):
+    """Timed steps of configuration wl on device dev; returns the result line."""
+    import numpy as np
+    import torch
+
+    from paper_2204_07716_gb300 import fkreg, inputs
+
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     extra = {}
-    wl = args.workload
-    sc = args.scale
     if wl == "uneven":
         ws = inputs.uneven(scale=sc)
         probs = [dict(d=w.d, order=1, grid_n=w.grid_n, lo=w.lo, hi=w.hi, H=w.H, max_n=w.n,
@@ -519,7 +557,7 @@ def run_extra(args):
         cfg = {"workload": f"uneven-{len(ws)}problems-complex-LL+variance",
                "n_total": sum(w.n for w in ws), "problems": len(ws),
                "dims": [w.d for w in ws].count(2), "graph": "one captured CUDA graph"}
-        dtype = "f32+f64solve"
+        dtype = DTYPE_F32
     elif wl == "ll2d_sort":
         # the bin sort of the headline step alone (fkreg_set_points)
         w = inputs.ll2d(n=int(1_000_000 * sc))
@@ -551,7 +589,7 @@ def run_extra(args):
         units = w.n * (1 + np_ + 1)
         cfg = {"workload": "ll2d-1M-256sq-LL-epanechnikov-direct-f32", "n": w.n,
                "grid": list(w.grid_n), "probes": np_, "geometry": plan.geom}
-        dtype = "f32+f64solve"
+        dtype = DTYPE_F32
         extra["plan"] = plan
     elif wl == "ll2d_logvar":
         # smooth y, then the log-variance estimator on its residuals
@@ -568,7 +606,7 @@ def run_extra(args):
         units = w.n * 2
         cfg = {"workload": "ll2d-1M-256sq-LL-smooth+logvariance-f32-tol1e-6", "n": w.n,
                "grid": list(w.grid_n), "geometry": plan.geom}
-        dtype = "f32+f64solve"
+        dtype = DTYPE_F32
         extra["plan"] = plan
     elif wl in ("ll2d_plain64", "ll2d_plain32"):
         # the ll2d step without stacking: y and each of the 10 probes is its
@@ -592,7 +630,7 @@ def run_extra(args):
         cfg = {"workload": f"ll2d-1M-256sq-LL-plain-{prec}-1rhs-per-call-tol1e-6",
                "n": w.n, "grid": list(w.grid_n), "responses_per_call": 1,
                "calls_per_step": 1 + np_, "geometry": plan.geom}
-        dtype = "f64" if prec == "f64" else "f32+f64solve"
+        dtype = "f64" if prec == "f64" else DTYPE_F32
         extra["plan"] = plan
     else:
         if wl == "nw1d":
@@ -630,27 +668,27 @@ def run_extra(args):
                             "ll2d_gcv": "ll2d-2M-512sq-LL-GCV-fwd+bwd-f32-tol1e-6"}[wl],
                "n": w.n, "grid": list(w.grid_n), "bandwidths": w.n_bw, "probes": np_,
                "geometry": plan.geom}
-        dtype = "f64" if w.precision == "f64" else "f32+f64solve"
+        dtype = "f64" if w.precision == "f64" else DTYPE_F32
         extra["plan"] = plan
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k)
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     clocks = Clocks(0)
     clocks.start()
     stream = torch.cuda.current_stream(dev)
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        step(args.warmup + k)
+        step(warmup + k)
         ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
-    res = {"metric": METRIC, "value": units * args.steps / (sum(ms) / 1e3), "unit": UNIT,
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": sum(ms) / args.steps, "ms_step_median": float(np.median(ms)),
+    res = {"metric": METRIC, "value": units * steps / (sum(ms) / 1e3), "unit": UNIT,
+           "n_gpus": 1, "steps": steps, "warmup": warmup,
+           "ms_per_step": sum(ms) / steps, "ms_step_median": float(np.median(ms)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
            "data": "synthetic", "config": cfg, "clocks": clk}
     if wl == "uneven":
@@ -686,7 +724,11 @@ def run_extra(args):
         plan.set_timing(False)
         res["stages_ms_per_step"] = {k: round(v, 4) for k, v in st_ms.items()}
         res["gpu_launches_per_step"] = launches
-    print(json.dumps(res), flush=True)
+    for v in list(extra.values()) + ([batch] if wl == "uneven" else []):
+        v.close()
+    del flush
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():
