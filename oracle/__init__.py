@@ -20,6 +20,11 @@ built on top of those sums, each written from its definition in the paper:
 * ``fmc_trace``        Girard's fast Monte-Carlo estimate (Sec. 2.1) and the
                        Hutchinson mean of w_p^T S w_p.
 * ``gcv``              eq. 22.
+* ``estimate_vjp``     analytic gradient of sum_q gbar(q) mhat(q) (eqs. 3, 9,
+                       11) with respect to the responses, the samples (and
+                       the query points when they are the samples) and
+                       log sigma_j of a diagonal H.
+* ``gcv_grad``         analytic gradient of GCV (eq. 22) with fixed probes.
 * ``variance_pass``    eq. 23: a local-linear smooth of squared residuals.
 * ``log_variance``     eqs. 24-26: smooth of log(r + 1/N), kappa, sigma^2.
 * ``interval``         eq. 28: mhat -/+ z_(1 - alpha/2) sqrt(variance).
@@ -324,6 +329,122 @@ def fmc_trace(x: np.ndarray, w: np.ndarray, H: np.ndarray, order: int,
 def gcv(rss: float, n: int, tr: float) -> float:
     """Eq. 22: (RSS / N) / (tr(I - S) / N)^2."""
     return (rss / n) / ((1.0 - tr / n) ** 2)
+
+
+def estimate_vjp(x: np.ndarray, Y: np.ndarray, sigma, order: int, q: np.ndarray,
+                 gbar: np.ndarray, q_is_x: bool = False) -> dict:
+    """Analytic gradient of L = sum_q sum_v gbar[v, q] mhat_v(q) (eqs. 3, 9, 11).
+
+    Y [V, n] responses, H = diag(sigma^2), q [nq, d] query points, gbar [V, nq].
+    With z_j = x_j - q, K_j = K_H(z_j) and a = S^-1 e_1, beta_v = S^-1 t_v:
+      dL/dt_(v,a) = gbar_v a_a,  dL/ds_g = -sum_(a+b = g) a_a sum_v gbar_v beta_(v,b),
+    so each source j carries the weight function
+      phi_j(z) = K_H(z) P_j(z),  P_j(z) = sum_g sbar_g z^g + sum_v Y_(v,j) sum_a tbar_(v,a) z^a,
+    and
+      dL/dY_(v,j)     = K_j sum_a tbar_(v,a) z_j^a
+      dL/dx_j         = grad phi_j(z_j) = K_j (grad P_j(z_j) - P_j(z_j) H^-1 z_j)
+      dL/dlog sigma_k = sum_j phi_j(z_j) (z_(j,k)^2 / sigma_k^2 - 1)
+    (dK_H/dlog sigma_k = K_H (z_k^2 / sigma_k^2 - 1) for a diagonal H).  With
+    q_is_x the query points are the samples themselves and also move with
+    x: dL/dq_i = -sum_j grad phi_j(z_j) is added to dL/dx_i.  Query points whose
+    system is singular contribute nothing.  Pure numpy, a loop over q: small
+    inputs only.  Returns dY [V, n], dx [n, d], dlogsigma [d].
+    """
+    x = _c64(x)
+    n, d = x.shape
+    Y = _c64(np.atleast_2d(Y))
+    V = Y.shape[0]
+    q = _c64(np.atleast_2d(q))
+    gbar = _c64(np.atleast_2d(gbar))
+    sig = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (d,)).copy()
+    hinv = 1.0 / sig ** 2
+    norm = 1.0 / math.sqrt((2 * math.pi) ** d * np.prod(sig ** 2))
+    e2 = monomials(d, 2 * order)
+    e1 = monomials(d, order)
+    p = e1.shape[0]
+    pair = [[[a, b] for a in range(p) for b in range(p)
+             if np.array_equal(e1[a] + e1[b], e2[gi])] for gi in range(e2.shape[0])]
+    sidx = np.array([[next(gi for gi in range(e2.shape[0]) if np.array_equal(e1[a] + e1[b], e2[gi]))
+                      for b in range(p)] for a in range(p)])
+    dY = np.zeros_like(Y)
+    dx = np.zeros((n, d))
+    dls = np.zeros(d)
+
+    def mono(z, ex):
+        return np.prod(z[:, None, :] ** ex[None, :, :], axis=2)          # [n, m]
+
+    def dmono(z, ex):                                                     # [n, m, d]
+        out = np.zeros((z.shape[0], ex.shape[0], d))
+        for k in range(d):
+            e = ex.copy()
+            c = e[:, k].astype(np.float64)
+            e[:, k] = np.maximum(e[:, k] - 1, 0)
+            out[:, :, k] = c[None, :] * np.prod(z[:, None, :] ** e[None, :, :], axis=2)
+        return out
+
+    for qi, qq in enumerate(q):
+        z = x - qq
+        K = norm * np.exp(-0.5 * np.sum(z * z * hinv, axis=1))
+        m2 = mono(z, e2)
+        m1 = m2[:, : p]
+        s = K @ m2
+        S = s[sidx]
+        try:
+            Sinv = np.linalg.inv(S)
+        except np.linalg.LinAlgError:
+            continue
+        if not np.all(np.isfinite(Sinv)):
+            continue
+        a = Sinv[:, 0]
+        t = (Y * K[None, :]) @ m1                                        # [V, p]
+        beta = t @ Sinv.T                                                 # [V, p]
+        g = gbar[:, qi]
+        tbar = g[:, None] * a[None, :]                                    # [V, p]
+        bbar = g @ beta                                                   # [p]
+        sbar = np.array([-sum(a[u] * bbar[v] for u, v in pr) for pr in pair])
+        dY += K[None, :] * (tbar @ m1.T)
+        P = m2 @ sbar + np.sum(Y * (tbar @ m1.T), axis=0)                 # [n]
+        dP = np.einsum("nmk,m->nk", dmono(z, e2), sbar) + \
+            np.einsum("vn,nmk,vm->nk", Y, dmono(z, e1), tbar)
+        grad = K[:, None] * (dP - P[:, None] * z * hinv[None, :])         # [n, d]
+        dx += grad
+        if q_is_x:
+            dx[qi] -= np.sum(grad, axis=0)
+        dls += np.sum((K * P)[:, None] * (z * z * hinv[None, :] - 1.0), axis=0)
+    return {"dY": dY, "dx": dx, "dlogsigma": dls}
+
+
+def gcv_grad(x: np.ndarray, y: np.ndarray, w: np.ndarray, sigma, order: int) -> dict:
+    """GCV (eq. 22) with the Girard trace of Sec. 2.1 over fixed probes w [np, n]
+    and its analytic gradient with respect to y, x and log sigma_j (H = diag(sigma^2)).
+
+    GCV = (RSS/N) / (1 - tr/N)^2 with RSS = sum_i (y_i - mhat_y(x_i))^2 and
+    tr = (N/Np) sum_p w_p^T S w_p / w_p^T w_p.  The adjoints of the at-sample
+    estimates are dGCV/dmhat_y(x_i) = -2 L_RSS (y_i - mhat_y(x_i)) and
+    dGCV/dmhat_p(x_i) = L_tr (N/Np) w_pi / w_p^T w_p, L_RSS = (1/N)/(1 - tr/N)^2,
+    L_tr = 2 (RSS/N) / (N (1 - tr/N)^3); estimate_vjp carries them to the
+    parameters (the evaluation points are the samples), plus the explicit
+    term 2 L_RSS (y_i - mhat_y(x_i)) of dGCV/dy_i.
+    """
+    x = _c64(x)
+    n, d = x.shape
+    y = _c64(y).reshape(-1)
+    w = _c64(np.atleast_2d(w))
+    npb = w.shape[0]
+    H = np.diag(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (d,)) ** 2)
+    Y = np.concatenate([y[None], w])
+    mh = smooth_at(x, Y, H, order, x)["mhat"].T                          # [1 + np, n]
+    r = y - mh[0]
+    rss = float(r @ r)
+    ww = np.sum(w * w, axis=1)
+    tr = n * float(np.mean(np.sum(w * mh[1:], axis=1) / ww))
+    den = 1.0 - tr / n
+    L_rss = (1.0 / n) / den ** 2
+    L_tr = 2.0 * (rss / n) / (n * den ** 3)
+    gbar = np.concatenate([(-2.0 * L_rss * r)[None], L_tr * (n / npb) * w / ww[:, None]])
+    g = estimate_vjp(x, Y, np.sqrt(np.diag(H)), order, x, gbar, q_is_x=True)
+    return {"gcv": (rss / n) / den ** 2, "dy": g["dY"][0] + 2.0 * L_rss * r,
+            "dx": g["dx"], "dlogsigma": g["dlogsigma"]}
 
 
 def variance_pass(x: np.ndarray, y: np.ndarray, mhat_at_x: np.ndarray,

@@ -518,3 +518,107 @@ def test_effective_weight_is_s0_for_nw_and_pins_the_error_bound():
     m2, _ = oracle.lpr_solve(2, 1, r["s"], r["t"] + delta)
     dt_scaled = np.abs(delta[:, 0, :] / np.array([1.0, sig[0], sig[1]]))
     assert np.all(np.abs(m2[:, 0] - r["mhat"][:, 0]) <= dt_scaled.max(axis=1) / w * (1 + 1e-9))
+
+
+# ------------------------------------------------------- oracle gradients ----
+def _fd(f, eps=1e-5):
+    return (f(eps) - f(-eps)) / (2 * eps)
+
+
+@pytest.mark.parametrize("d,order", [(1, 0), (1, 1), (2, 1), (2, 0)])
+def test_estimate_vjp_matches_finite_differences_of_the_estimate(d, order):
+    # the analytic gradient of sum_q gbar(q) mhat(q) against central
+    # differences of the oracle's own estimates (eqs. 3, 9, 11)
+    rng = np.random.default_rng(400 + 10 * d + order)
+    n = 60
+    x = rng.random((n, d))
+    Y = np.stack([np.cos(3 * x.sum(axis=1)) + 0.1 * rng.standard_normal(n),
+                  rng.standard_normal(n)])
+    sig = np.array([0.12, 0.17][:d])
+    q = rng.random((7, d)) * 0.8 + 0.1
+    gbar = rng.standard_normal((2, 7))
+
+    def L(xx, YY, s):
+        H = np.diag(s ** 2)
+        return float(np.sum(gbar * oracle.smooth_at(xx, YY, H, order, q)["mhat"].T))
+
+    g = oracle.estimate_vjp(x, Y, sig, order, q, gbar)
+    for j in range(d):
+        def f(e, j=j):
+            s = sig.copy()
+            s[j] *= np.exp(e)
+            return L(x, Y, s)
+        assert g["dlogsigma"][j] == pytest.approx(_fd(f), rel=1e-6, abs=1e-9)
+    for i in (0, 13, 41):
+        for v in range(2):
+            def fy(e, i=i, v=v):
+                YY = Y.copy()
+                YY[v, i] += e
+                return L(x, YY, sig)
+            assert g["dY"][v, i] == pytest.approx(_fd(fy), rel=1e-6, abs=1e-9)
+        for a in range(d):
+            def fx(e, i=i, a=a):
+                xx = x.copy()
+                xx[i, a] += e
+                return L(xx, Y, sig)
+            assert g["dx"][i, a] == pytest.approx(_fd(fx), rel=1e-6, abs=1e-8)
+
+
+def test_estimate_vjp_at_the_samples_moves_the_query_points():
+    # q = x: the estimate at each sample moves with the sample (target side)
+    rng = np.random.default_rng(431)
+    n, d = 40, 2
+    x = rng.random((n, d))
+    Y = np.sin(4 * x[:, :1].T) + 0.1 * rng.standard_normal((1, n))
+    sig = np.array([0.15, 0.2])
+    gbar = rng.standard_normal((1, n))
+
+    def L(xx):
+        return float(np.sum(gbar * oracle.smooth_at(xx, Y, np.diag(sig ** 2), 1, xx)["mhat"].T))
+
+    g = oracle.estimate_vjp(x, Y, sig, 1, x, gbar, q_is_x=True)
+    for i in (2, 17, 33):
+        for a in range(d):
+            def fx(e, i=i, a=a):
+                xx = x.copy()
+                xx[i, a] += e
+                return L(xx)
+            assert g["dx"][i, a] == pytest.approx(_fd(fx), rel=1e-6, abs=1e-8)
+
+
+def test_gcv_grad_matches_finite_differences():
+    # eq. 22 with fixed probes: the analytic gradient against central
+    # differences of the oracle's GCV
+    rng = np.random.default_rng(440)
+    n, d = 50, 2
+    x = rng.random((n, d))
+    y = np.cos(3 * x.sum(axis=1)) + 0.2 * rng.standard_normal(n)
+    w = oracle.probes(3, 2, n)
+    sig = np.array([0.14, 0.18])
+
+    def G(xx, yy, s):
+        H = np.diag(s ** 2)
+        m = oracle.apply_smoother(xx, yy[None], H, 1)[:, 0]
+        f = oracle.fmc_trace(xx, w, H, 1)
+        return oracle.gcv(float(np.sum((yy - m) ** 2)), n, f["girard"])
+
+    g = oracle.gcv_grad(x, y, w, sig, 1)
+    assert g["gcv"] == pytest.approx(G(x, y, sig), rel=1e-12)
+    for j in range(d):
+        def f(e, j=j):
+            s = sig.copy()
+            s[j] *= np.exp(e)
+            return G(x, y, s)
+        assert g["dlogsigma"][j] == pytest.approx(_fd(f), rel=1e-6, abs=1e-10)
+    for i in (1, 22, 47):
+        def fy(e, i=i):
+            yy = y.copy()
+            yy[i] += e
+            return G(x, yy, sig)
+        assert g["dy"][i] == pytest.approx(_fd(fy), rel=1e-6, abs=1e-10)
+        for a in range(d):
+            def fx(e, i=i, a=a):
+                xx = x.copy()
+                xx[i, a] += e
+                return G(xx, y, sig)
+            assert g["dx"][i, a] == pytest.approx(_fd(fx), rel=1e-6, abs=1e-9)
