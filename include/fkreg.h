@@ -361,6 +361,35 @@ fkreg_status fkreg_backward(fkreg_plan plan, const void* y_dev, int n_probes, ui
                             void* dy_dev, void* dx_dev, void* stream);
 
 /*
+ * Vector-Jacobian product of the grid estimate (eqs. 3, 9, 11) of bandwidth b:
+ * for L = sum_r sum_g Gbar_r(g) mhat_r(g) over the unmasked grid points, the
+ * gradients of L with respect to the log bandwidths, the responses and the
+ * samples.  Runs the forward grid path itself (spreading, FFT, kernel
+ * multiply, inverse FFT, the FP64 per-grid-point solves and the mask), then
+ * the hand-written backward: the adjoint of each grid point's solve
+ * (dmhat = a^T dt - a^T dS S^-1 t with a = S^-1 e_1) as adjoint fields on the
+ * grid lattice, their forward DFT (the adjoint of the inverse DFT onto the
+ * grid), the kernel multipliers and a type-2 evaluation at the samples (the
+ * adjoint of type-1 spreading) for dy and the x-gradient, and a spectral
+ * inner product with the derivative of the kernel transform for d/dlog sigma.
+ * Requires a plan created with FKREG_WANT_BACKWARD, the Gaussian kernel, real
+ * responses, order 0 or 1 and a diagonal H for bandwidth b (the derivative is
+ * in log sigma_j, H = diag(sigma^2)); otherwise FKREG_ERR_UNSUPPORTED.
+ *   y_dev         [n_rhs][n] responses (plan precision, original order)
+ *   grad_mhat_dev [n_rhs][M] dL/dmhat on the grid of bandwidth b (plan
+ *                 precision); values at masked points and non-finite values
+ *                 are ignored
+ *   dlogh_dev     [dim] double, dL/dlog sigma_j (may be NULL)
+ *   dy_dev        [n_rhs][n] dL/dy, original order (may be NULL)
+ *   dx_dev        [n][dim] dL/dx, original order (may be NULL)
+ * The call overwrites the plan's internal buffers (a later fkreg_variance
+ * needs a new fkreg_smooth / fkreg_df first).
+ */
+fkreg_status fkreg_backward_grid(fkreg_plan plan, const void* y_dev, const void* grad_mhat_dev,
+                                 int b, double* dlogh_dev, void* dy_dev, void* dx_dev,
+                                 void* stream);
+
+/*
  * Stage timers (profiling).  With timing enabled every stage of a call is
  * bracketed by CUDA events recorded on the call's stream; fkreg_stage_times
  * waits for those events, returns the accumulated milliseconds and launch

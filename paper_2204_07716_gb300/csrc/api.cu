@@ -126,7 +126,8 @@ int64_t full_cells(const int64_t* n, int d) {
 namespace fk {
 
 // kind 0: forward R2C, kind 1: inverse C2R, kind 2: inverse C2R in place whose
-// outputs exec_fft then interleaves into cell records
+// outputs exec_fft then interleaves into cell records, kind 3: forward R2C
+// (the lattice adjoint fields of the grid-estimate backward)
 fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, cufftHandle* h) {
   auto key = std::make_tuple(kind, dims[0], P->d > 1 ? dims[1] : 1, P->d > 2 ? dims[2] : 1, batch);
   auto it = P->ffts.find(key);
@@ -139,10 +140,11 @@ fkreg_status fft_get(fkreg_plan_s* P, int kind, const int64_t* dims, int batch, 
   cufftSetAutoAllocation(hd, 0);
   long long n[3] = {dims[0], dims[1], dims[2]};
   cufftType type;
+  const bool fwd = kind == 0 || kind == 3;
   if (P->prec == FKREG_F32)
-    type = kind == 0 ? CUFFT_R2C : CUFFT_C2R;
+    type = fwd ? CUFFT_R2C : CUFFT_C2R;
   else
-    type = kind == 0 ? CUFFT_D2Z : CUFFT_Z2D;
+    type = fwd ? CUFFT_D2Z : CUFFT_Z2D;
   size_t work = 0;
   cufftResult r;
   if (kind == 2) {
@@ -241,8 +243,11 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   P->direct = opts->kernel != FKREG_KERNEL_GAUSSIAN;
   P->f2bwd = P->ns + (1 + P->max_probes) * P->nt;
   const int nout_bwd = 1 + (2 + P->max_probes) * opts->dim;
+  // grid-estimate backward: adjoint values per response, gradients per class
+  const int nout_grid = P->nrhs_real + (1 + P->nrhs_real) * opts->dim;
   const int strengths_total = P->smax + (P->backward ? P->f2bwd : 0);
-  const int t2_fields = std::max(P->f2max, P->backward ? std::max(P->f2bwd, nout_bwd) : 0);
+  const int t2_fields =
+      std::max(P->f2max, P->backward ? std::max(std::max(P->f2bwd, nout_bwd), nout_grid) : 0);
   if (P->nacc > 512) {
     delete P;
     return set_global_error(FKREG_ERR_UNSUPPORTED, "n_rhs (real parts) + 2 max_probes must be <= 511");
@@ -318,7 +323,14 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   L.take(P->r_smax, 8 * size_t(P->nbw));
   if (P->backward) {
     const int64_t nn = std::max<int64_t>(1, max_n);
-    L.take(P->r_bV, T * size_t(1 + 2 * d) * std::max(P->f2bwd, nout_bwd) * nn);
+    int64_t mtot = 1;
+    for (int a = 0; a < d; ++a) mtot *= opts->grid_n[a];
+    int64_t gblk = 1;
+    for (int b = 0; b < P->nbw; ++b) gblk = std::max(gblk, fk::run_dlogh_lattice_blocks(P, b));
+    L.take(P->r_gmask, size_t(P->nbw) * mtot);
+    L.take(P->r_gadj, T * size_t(P->ns + P->nrhs_real * P->nt) * l_cells);
+    L.take(P->r_gpart, 8 * 3 * size_t(gblk));
+    L.take(P->r_bV, T * size_t(1 + 2 * d) * std::max(std::max(P->f2bwd, nout_bwd), nout_grid) * nn);
     L.take(P->r_bdx, T * size_t(d + 1) * nn);
     L.take(P->r_bsc, 8 * 16);
     L.take(P->r_bpart, 8 * 3 * size_t((nn + 255) / 256 + 1));
@@ -352,6 +364,13 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
         fkreg_plan_destroy(P);
         return set_global_error(st, m);
       }
+      // the lattice adjoint fields of the grid-estimate backward
+      for (int a = 0; a < 3; ++a) dims[a] = P->g.ldft[a];
+      if ((st = fk::fft_get(P, 3, dims, P->ns + P->nrhs_real * P->nt, &h)) != FKREG_OK) {
+        std::string m = P->err;
+        fkreg_plan_destroy(P);
+        return set_global_error(st, m);
+      }
     }
     for (const auto& B : P->bw) {
       for (int a = 0; a < 3; ++a) dims[a] = B.nf[a];
@@ -360,6 +379,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
       if (P->backward) {
         bts.push_back(P->f2bwd);
         bts.push_back(nout_bwd);
+        bts.push_back(nout_grid);
       }
       for (int bt : bts)
         if ((st = fk::fft_get(P, 2, dims, bt, &h)) != FKREG_OK) {
@@ -467,12 +487,13 @@ fkreg_status exec_fft(fkreg_plan_s* P, int kind, const int64_t* dims, int batch,
   if (cufftSetStream(h, s) != CUFFT_SUCCESS) return plan_err(P, FKREG_ERR_CUFFT, "cufftSetStream failed");
   cufftResult r;
   void* dst = kind == 2 ? in : out;  // kind 2 runs in place, then interleaves into out
+  const bool fwd = kind == 0 || kind == 3;
   if (P->prec == FKREG_F32) {
-    r = kind == 0 ? cufftExecR2C(h, static_cast<cufftReal*>(in), static_cast<cufftComplex*>(dst))
-                  : cufftExecC2R(h, static_cast<cufftComplex*>(in), static_cast<cufftReal*>(dst));
+    r = fwd ? cufftExecR2C(h, static_cast<cufftReal*>(in), static_cast<cufftComplex*>(dst))
+            : cufftExecC2R(h, static_cast<cufftComplex*>(in), static_cast<cufftReal*>(dst));
   } else {
-    r = kind == 0 ? cufftExecD2Z(h, static_cast<cufftDoubleReal*>(in), static_cast<cufftDoubleComplex*>(dst))
-                  : cufftExecZ2D(h, static_cast<cufftDoubleComplex*>(in), static_cast<cufftDoubleReal*>(dst));
+    r = fwd ? cufftExecD2Z(h, static_cast<cufftDoubleReal*>(in), static_cast<cufftDoubleComplex*>(dst))
+            : cufftExecZ2D(h, static_cast<cufftDoubleComplex*>(in), static_cast<cufftDoubleReal*>(dst));
   }
   if (r != CUFFT_SUCCESS) return plan_err(P, FKREG_ERR_CUFFT, "cuFFT exec failed (" + std::to_string(int(r)) + ")");
   if (kind == 2) {
@@ -682,6 +703,86 @@ fkreg_status fkreg_backward(fkreg_plan P, const void* y, int n_probes, uint64_t 
     cudaError_t e = cudaMemcpyAsync(gcv, P->ws + P->r_bsc.off + 2 * sizeof(double), sizeof(double),
                                     cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_err(P, e, "copy gcv");
+  }
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_backward_grid(fkreg_plan P, const void* y, const void* grad_mhat, int b,
+                                 double* dlogh, void* dy, void* dx, void* stream) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (!P->backward)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED,
+                    "fkreg_backward_grid needs a plan created with FKREG_WANT_BACKWARD");
+  if (P->direct) return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward_grid needs the Gaussian kernel");
+  if (P->o.y_complex)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward_grid takes real responses");
+  if (P->order > 1)
+    return plan_err(P, FKREG_ERR_UNSUPPORTED, "fkreg_backward_grid supports orders 0 and 1");
+  if (!P->ws) return plan_err(P, FKREG_ERR_STATE, "fkreg_set_workspace must come first");
+  if (!P->points_set) return plan_err(P, FKREG_ERR_STATE, "fkreg_set_points must come first");
+  if (b < 0 || b >= P->nbw) return plan_err(P, FKREG_ERR_INVALID_ARG, "bandwidth index out of range");
+  if (!grad_mhat || (P->n > 0 && !y))
+    return plan_err(P, FKREG_ERR_INVALID_ARG, "y and grad_mhat are required");
+  {
+    const double* Hb = P->H.data() + size_t(b) * P->d * P->d;
+    for (int i = 0; i < P->d; ++i)
+      for (int j = 0; j < P->d; ++j)
+        if (i != j && Hb[i * P->d + j] != 0.0)
+          return plan_err(P, FKREG_ERR_UNSUPPORTED,
+                          "fkreg_backward_grid needs a diagonal bandwidth matrix");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d = P->d;
+  const int R = P->nrhs;
+  const int fgrid = P->ns + R * P->nt;
+  const int nout = R + (1 + R) * d;
+  P->dens_valid = false;
+  // forward grid fields of bandwidth b: strengths, spreading, forward FFT,
+  // kernel multiply, inverse FFT onto the lattice, and the mask of the solve
+  {
+    FK_STAGE(FKREG_STAGE_STRENGTHS);
+    FK_CHECK(fk::run_gather_strengths(P, y, 0, 0, 0, nullptr, 1, s), "strengths");
+  }
+  {
+    FK_STAGE(FKREG_STAGE_SPREAD);
+    FK_CHECK(fk::run_spread(P, 0, 1 + R, s), "spread");
+  }
+  {
+    FK_STAGE(FKREG_STAGE_FFT_FWD);
+    FK_STATUS(exec_fft(P, 0, P->g.nf, 1 + R, P->ws + P->r_fine.off, P->ws + P->r_spec.off, s));
+  }
+  {
+    FK_STAGE(FKREG_STAGE_KMUL_GRID);
+    FK_CHECK(fk::run_kmul_grid(P, 0, 1, R, b, 1, P->ws + P->r_gspec.off, s), "kmul grid");
+  }
+  {
+    FK_STAGE(FKREG_STAGE_FFT_GRID);
+    FK_STATUS(exec_fft(P, 1, P->g.ldft, fgrid, P->ws + P->r_gspec.off, P->ws + P->r_gfield.off, s));
+  }
+  uint8_t* mask = reinterpret_cast<uint8_t*>(P->ws + P->r_gmask.off);
+  {
+    FK_STAGE(FKREG_STAGE_GRID_SOLVE);
+    fkreg_outputs mo{};
+    mo.mask = mask;  // the solve writes bandwidth b's mask at mask + b M
+    FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, &mo, nullptr, s), "grid solve");
+  }
+  int64_t mtot = 1;
+  for (int a = 0; a < d; ++a) mtot *= P->o.grid_n[a];
+  FK_STAGE(FKREG_STAGE_BACKWARD);
+  // adjoints of the per-grid-point solves as lattice fields, and their spectra
+  void* qbar = P->ws + P->r_gadj.off;
+  FK_CHECK(fk::run_grid_adjoint(P, b, R, mask + size_t(b) * mtot, grad_mhat, qbar, s),
+           "grid adjoints");
+  FK_STATUS(exec_fft(P, 3, P->g.ldft, fgrid, qbar, P->ws + P->r_gspec.off, s));
+  if (dlogh)
+    FK_CHECK(fk::run_dlogh_lattice(P, b, R, P->ws + P->r_gspec.off,
+                                   reinterpret_cast<double*>(P->ws + P->r_gpart.off), dlogh, s),
+             "bandwidth gradient");
+  if ((dy || dx) && P->n > 0) {
+    FK_CHECK(fk::run_kmul_adj_lattice(P, b, R, P->ws + P->r_gspec.off, s), "adjoint spectra");
+    FK_STATUS(exec_fft(P, 2, P->bw[b].nf, nout, P->ws + P->r_t2spec.off, P->ws + P->r_t2field.off, s));
+    FK_CHECK(fk::run_gather_fields(P, b, nout, P->ws + P->r_bV.off, s), "gather adjoint functions");
+    FK_CHECK(fk::run_combine_grid(P, R, P->ws + P->r_bV.off, dy, dx, s), "combine");
   }
   return FKREG_OK;
 }

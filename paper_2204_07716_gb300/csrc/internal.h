@@ -112,7 +112,7 @@ struct fkreg_plan_s {
       r_binstart, r_nsub, r_substart, r_subbin, r_subfirst, r_hist, r_scan, r_str,
       r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork,
       r_fftwork_g,
-      r_bV, r_bdx, r_bsc, r_bpart;
+      r_bV, r_bdx, r_bsc, r_bpart, r_gmask, r_gadj, r_gpart;
   bool backward = false;        // workspace reserved for fkreg_backward
   bool direct = false;          // compact kernel: direct sums instead of the NUFFT
   int f2bwd = 0;                // fields of the backward passes (one response + probes)
@@ -183,6 +183,21 @@ cudaError_t run_kmul_t2(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n
 cudaError_t run_kmul_t2_mode(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
                              int kind, int axis, cudaStream_t s);
 cudaError_t run_kmul_adj(fkreg_plan_s* P, int b, int sb, int n_classes, cudaStream_t s);
+// grid-estimate backward: type-2 spectra of the adjoint functions of the
+// lattice adjoint fields (their R2C spectra E [fgrid][L half]), and
+// d L / d log sigma as a spectral inner product (part: FP64 partial sums of
+// run_dlogh_lattice_blocks blocks x 3)
+cudaError_t run_kmul_adj_lattice(fkreg_plan_s* P, int b, int nrhs, const void* E, cudaStream_t s);
+int64_t run_dlogh_lattice_blocks(const fkreg_plan_s* P, int b);
+cudaError_t run_dlogh_lattice(fkreg_plan_s* P, int b, int nrhs, const void* E, double* part,
+                              double* dlogh, cudaStream_t s);
+// backward_grid.cu: adjoint of the per-grid-point solves -> lattice adjoint
+// fields qbar [fgrid][L cells] (zero where masked); and the combination of
+// the gathered adjoint functions into dy [nrhs][n] and dx [n][d] (original order)
+cudaError_t run_grid_adjoint(fkreg_plan_s* P, int b, int nrhs, const uint8_t* mask,
+                             const void* gbar, void* qbar, cudaStream_t s);
+cudaError_t run_combine_grid(fkreg_plan_s* P, int nrhs, const void* V, void* dy, void* dx,
+                             cudaStream_t s);
 
 // backward.cu
 cudaError_t run_gather_fields(fkreg_plan_s* P, int b, int F, void* V, cudaStream_t s);

@@ -589,6 +589,255 @@ __global__ void kmul_adj_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
   out[int64_t(o) * t2half + j] = acc;
 }
 
+// ---- vector-Jacobian product of the grid estimate ---------------------------
+// The grid fields are T_f(lo + m delta) = sum_|k|<K/2 A_f[k] exp(2 pi i k m / L)
+// with A_f[k] = W_f(k/P) F_k / prod P (see the top of this file).  For adjoint
+// grid values Qbar_f(m) (zero off the output points) the adjoint map gives
+//   Fbar_k = (1 / prod P) conj(W_f(k/P)) Ebar_f[k],  Ebar_f[k] = sum_m Qbar_f(m) exp(-2 pi i k m / L),
+// i.e. Ebar_f is the length-L forward DFT of Qbar_f, periodic in k with period
+// L (the adjoint of the fold), and conj(W_f) = w^_f.  Evaluating
+// sum_k Fbar_k exp(2 pi i k (x - lo) / P) at the samples (type 2) gives the
+// adjoint function E_f(x) = sum_g Qbar_f(g) w_f(x - g) and, with the factor
+// 2 pi i xi_d, its gradient.
+
+// Ebar at signed mode kk from the R2C half spectrum of a real field on the
+// length-L lattice (periodic in k, Hermitian).
+template <typename T, typename C>
+__device__ __forceinline__ C fetch_lattice(const GeoDev& g, const C* __restrict__ E,
+                                           const int64_t kk[3], int D) {
+  int64_t k[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) {
+    k[a] = kk[a] % g.L[a];
+    if (k[a] < 0) k[a] += g.L[a];
+  }
+  const bool cj = k[D - 1] > g.L[D - 1] / 2;
+  if (cj)
+    for (int a = 0; a < D; ++a) k[a] = (g.L[a] - k[a]) % g.L[a];
+  int64_t idx = 0;
+  for (int a = 0; a < D; ++a) idx = idx * ((a == D - 1) ? (g.L[a] / 2 + 1) : g.L[a]) + k[a];
+  C v = E[idx];
+  if (cj) v.y = -v.y;
+  return v;
+}
+
+// Type-2 spectra on bandwidth b's fine grid of the adjoint functions:
+//   output r (< nrhs)        : sum_{f in t-fields of response r} w^_f Ebar_f      (d/dy)
+//   output nrhs + c D + d    : sum_{f in class c} 2 pi i xi_d w^_f Ebar_f           (d/dx)
+// classes: c = 0 the s-fields (density), c = 1 + r the t-fields of response r.
+// Thread per (fine half-spectrum index, output).
+template <typename T, int D>
+__global__ void kmul_adj_lattice_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
+                                        const double* __restrict__ tab, MonoTab mono,
+                                        const typename Cx<T>::type* __restrict__ E, int64_t lhalf,
+                                        int nrhs, int64_t t2half,
+                                        typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
+  const int nout = nrhs + (1 + nrhs) * D;
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= t2half * nout) return;
+  const int64_t j = gid % t2half;
+  const int o = int(gid / t2half);
+  const BwDev& B = bwt[b];
+  int64_t kk[3] = {0, 0, 0};
+  bool inside = true;
+  {
+    int64_t rem = j;
+    for (int a = D - 1; a >= 0; --a) {
+      const int64_t nn = (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+      const int64_t idx = rem % nn;
+      rem /= nn;
+      const int64_t k = (a == D - 1) ? idx : (idx < (B.nf[a] + 1) / 2 ? idx : idx - B.nf[a]);
+      kk[a] = k;
+      if ((k < 0 ? -k : k) > B.K[a] / 2 - 1) inside = false;
+    }
+  }
+  C acc{T(0), T(0)};
+  if (inside) {
+    T dec = T(1);
+    T xi[3] = {T(0), T(0), T(0)};
+    for (int a = 0; a < D; ++a) {
+      const int64_t ak = kk[a] < 0 ? -kk[a] : kk[a];
+      dec *= T(tab[B.phi2_off[a] + ak] / g.P[a]);
+      xi[a] = T(kk[a]) / T(g.P[a]);
+    }
+    const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
+    int cls, kind, axis = 0;
+    if (o < nrhs) {
+      cls = 1 + o;
+      kind = 3;
+    } else {
+      cls = (o - nrhs) / D;
+      axis = (o - nrhs) % D;
+      kind = 4;
+    }
+    const int f0 = cls == 0 ? 0 : mono.n + (cls - 1) * mono.nt;
+    const int nf = cls == 0 ? mono.n : mono.nt;
+    for (int q = 0; q < nf; ++q) {
+      const C e = fetch_lattice<T, C>(g, E + int64_t(f0 + q) * lhalf, kk, D);
+      const C W = field_mult<T, C>(mono, q, kind, axis, xi, m, B);
+      const C t = cmul<C, T>(W, e);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    acc.x *= dec;
+    acc.y *= dec;
+  }
+  out[int64_t(o) * t2half + j] = acc;
+}
+
+// d L / d log sigma_j = sum_f sum_m Qbar_f(m) dT_f(m)/dlog sigma_j
+//   = sum_|k|<K/2 Re[ dW_f(k/P)/dlog sigma_j (F_k / prod P) conj(Ebar_f[k]) ]
+// (Parseval on the lattice; the terms of k and -k are conjugate, so the sum
+// runs over k_last >= 0 with weight 2 for k_last > 0).  Thread per mode of
+// that half box; per-block FP64 partial sums part[block][3].
+template <typename T, int D>
+__global__ void dlogh_lattice_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b,
+                                     const double* __restrict__ tab, int64_t phi1_0,
+                                     int64_t phi1_1, int64_t phi1_2, MonoTab mono,
+                                     const typename Cx<T>::type* __restrict__ F, int64_t fine_half,
+                                     const typename Cx<T>::type* __restrict__ E, int64_t lhalf,
+                                     int nrhs, int64_t nmodes, double* __restrict__ part) {
+  using C = typename Cx<T>::type;
+  __shared__ double red[8][3];
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const BwDev& B = bwt[b];
+  double dth[3] = {0.0, 0.0, 0.0};
+  if (gid < nmodes) {
+    int64_t kk[3] = {0, 0, 0};
+    int64_t rem = gid;
+    for (int a = D - 1; a >= 0; --a) {
+      const int64_t hk = B.K[a] / 2 - 1;
+      const int64_t nn = (a == D - 1) ? (hk + 1) : (2 * hk + 1);
+      const int64_t idx = rem % nn;
+      rem /= nn;
+      kk[a] = (a == D - 1) ? idx : idx - hk;
+    }
+    const int64_t phi1[3] = {phi1_0, phi1_1, phi1_2};
+    double dec = 1.0;
+    T xi[3] = {T(0), T(0), T(0)};
+    for (int a = 0; a < D; ++a) {
+      const int64_t ak = kk[a] < 0 ? -kk[a] : kk[a];
+      dec *= tab[phi1[a] + ak] / g.P[a];
+      xi[a] = T(kk[a]) / T(g.P[a]);
+    }
+    const double wgt = kk[D - 1] == 0 ? 1.0 : 2.0;
+    const ModeMul<T> m = mode_mul<T>(g, B, kk, D);
+    const int fgrid = mono.n + nrhs * mono.nt;
+    for (int f = 0; f < fgrid; ++f) {
+      const int strength = f < mono.n ? 0 : 1 + (f - mono.n) / mono.nt;
+      const int mf = f < mono.n ? f : (f - mono.n) % mono.nt;
+      const C Fk = fetch_F<T, C>(g, F + int64_t(strength) * fine_half, kk, D);
+      const C e = fetch_lattice<T, C>(g, E + int64_t(f) * lhalf, kk, D);
+      // (F_k / prod P) conj(Ebar)
+      const double px = dec * (double(Fk.x) * double(e.x) + double(Fk.y) * double(e.y));
+      const double py = dec * (double(Fk.y) * double(e.x) - double(Fk.x) * double(e.y));
+      for (int j = 0; j < D; ++j) {
+        const C W2 = field_mult<T, C>(mono, mf, 2, j, xi, m, B);
+        dth[j] += wgt * (double(W2.x) * px - double(W2.y) * py);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 0; d < 3; ++d) {
+    double v = dth[d];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][d] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int wv = 0; wv < int(blockDim.x >> 5); ++wv) t += red[wv][threadIdx.x];
+    part[int64_t(blockIdx.x) * 3 + threadIdx.x] = t;
+  }
+}
+
+__global__ void sum_partials3(const double* __restrict__ part, int64_t nblk, int D,
+                              double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int d = blockIdx.x;
+  double t = 0.0;
+  for (int64_t k = threadIdx.x; k < nblk; k += blockDim.x) t += part[k * 3 + d];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[d] = sh[0];
+}
+
+template <typename T>
+cudaError_t launch_adj_lattice(fkreg_plan_s* P, int b, int nrhs, const void* E, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const GeoDev& g = P->geo;
+  const int D = P->d;
+  const BwDev& B = P->bw[b];
+  int64_t t2half = 1, lhalf = 1;
+  for (int a = 0; a < D; ++a) {
+    t2half *= (a == D - 1) ? (B.nf[a] / 2 + 1) : B.nf[a];
+    lhalf *= (a == D - 1) ? (g.L[a] / 2 + 1) : g.L[a];
+  }
+  const int nout = nrhs + (1 + nrhs) * D;
+  const unsigned blocks = unsigned((t2half * nout + 255) / 256);
+  const C* Ein = static_cast<const C*>(E);
+  C* o = wsp<C>(P, P->r_t2spec);
+#define FK_KL(DD)                                                                               \
+  kmul_adj_lattice_kernel<T, DD><<<blocks, 256, 0, st>>>(g, wsp<BwDev>(P, P->r_bw), b,          \
+                                                         wsp<double>(P, P->r_tab), P->mono, Ein, \
+                                                         lhalf, nrhs, t2half, o)
+  if (D == 1)
+    FK_KL(1);
+  else if (D == 2)
+    FK_KL(2);
+  else
+    FK_KL(3);
+#undef FK_KL
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
+int64_t dlogh_modes(const fkreg_plan_s* P, int b) {
+  const BwDev& B = P->bw[b];
+  int64_t nm = 1;
+  for (int a = 0; a < P->d; ++a) {
+    const int64_t hk = B.K[a] / 2 - 1;
+    nm *= (a == P->d - 1) ? (hk + 1) : (2 * hk + 1);
+  }
+  return nm;
+}
+
+template <typename T>
+cudaError_t launch_dlogh_lattice(fkreg_plan_s* P, int b, int nrhs, const void* E, double* part,
+                                 double* dlogh, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const GeoDev& g = P->geo;
+  const int D = P->d;
+  int64_t lhalf = 1, fhalf = 1;
+  for (int a = 0; a < D; ++a) {
+    lhalf *= (a == D - 1) ? (g.L[a] / 2 + 1) : g.L[a];
+    fhalf *= (a == D - 1) ? (g.nf[a] / 2 + 1) : g.nf[a];
+  }
+  const int64_t nmodes = dlogh_modes(P, b);
+  const int64_t nblk = (nmodes + 255) / 256;
+  const C* Ein = static_cast<const C*>(E);
+#define FK_DL(DD)                                                                                  \
+  dlogh_lattice_kernel<T, DD><<<unsigned(nblk), 256, 0, st>>>(                                     \
+      g, wsp<BwDev>(P, P->r_bw), b, wsp<double>(P, P->r_tab), P->phi1_off[0], P->phi1_off[1],      \
+      P->phi1_off[2], P->mono, wsp<C>(P, P->r_spec), fhalf, Ein, lhalf, nrhs, nmodes, part)
+  if (D == 1)
+    FK_DL(1);
+  else if (D == 2)
+    FK_DL(2);
+  else
+    FK_DL(3);
+#undef FK_DL
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sum_partials3<<<D, 256, 0, st>>>(part, nblk, D, dlogh);
+  P->launches += 2;
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_t2_mode(fkreg_plan_s* P, int b, int str_dens, int str_rhs, int n_rhs_str,
                            int kind, int axis, cudaStream_t st) {
@@ -680,6 +929,21 @@ cudaError_t run_kmul_t2_mode(fkreg_plan_s* P, int b, int str_dens, int str_rhs, 
 cudaError_t run_kmul_adj(fkreg_plan_s* P, int b, int sb, int n_classes, cudaStream_t st) {
   return P->prec == FKREG_F32 ? launch_adj<float>(P, b, sb, n_classes, st)
                               : launch_adj<double>(P, b, sb, n_classes, st);
+}
+
+cudaError_t run_kmul_adj_lattice(fkreg_plan_s* P, int b, int nrhs, const void* E, cudaStream_t st) {
+  return P->prec == FKREG_F32 ? launch_adj_lattice<float>(P, b, nrhs, E, st)
+                              : launch_adj_lattice<double>(P, b, nrhs, E, st);
+}
+
+int64_t run_dlogh_lattice_blocks(const fkreg_plan_s* P, int b) {
+  return (dlogh_modes(P, b) + 255) / 256;
+}
+
+cudaError_t run_dlogh_lattice(fkreg_plan_s* P, int b, int nrhs, const void* E, double* part,
+                              double* dlogh, cudaStream_t st) {
+  return P->prec == FKREG_F32 ? launch_dlogh_lattice<float>(P, b, nrhs, E, part, dlogh, st)
+                              : launch_dlogh_lattice<double>(P, b, nrhs, E, part, dlogh, st);
 }
 
 }  // namespace fk

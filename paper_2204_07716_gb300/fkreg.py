@@ -41,7 +41,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA"
 
 EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
-           "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_variance",
+           "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_backward_grid", "fkreg_variance",
            "fkreg_log_variance", "fkreg_interval", "fkreg_predict", "fkreg_set_timing",
            "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
@@ -127,6 +127,7 @@ def load():
                                 ctypes.c_int64, vp, ctypes.c_int, vp, vp]
     L.fkreg_backward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.c_int, vp, vp,
                                  vp, vp, vp]
+    L.fkreg_backward_grid.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, vp, vp]
     L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
     L.fkreg_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]
@@ -459,6 +460,27 @@ class Plan:
         self._y_keep = (y, pr)
         return out
 
+    def backward_grid(self, y, grad_mhat, b: int = 0, want=("dlogh", "dy", "dx")) -> Dict[str, object]:
+        """Gradients of L = sum grad_mhat * mhat_grid (bandwidth b) with respect to
+        log sigma [d], y [n_rhs, n] and x [n, d] (fkreg_backward_grid)."""
+        t = self.torch
+        y = self._y(y)
+        gm = self._as_dev(grad_mhat).reshape(self.n_rhs, self.M).contiguous()
+        n = max(self.n, 1)
+        out = {}
+        if "dlogh" in want:
+            out["dlogh"] = t.empty(self.d, dtype=t.float64, device=self.device)
+        if "dy" in want:
+            out["dy"] = t.empty((self.n_rhs, n), dtype=self.dtype, device=self.device)
+        if "dx" in want:
+            out["dx"] = t.empty((n, self.d), dtype=self.dtype, device=self.device)
+        ptr = lambda k: ctypes.c_void_p(out[k].data_ptr()) if k in out else None
+        self._check(self.L.fkreg_backward_grid(self.h, ctypes.c_void_p(y.data_ptr()),
+                                               ctypes.c_void_p(gm.data_ptr()), int(b),
+                                               ptr("dlogh"), ptr("dy"), ptr("dx"), self._stream()))
+        self._y_keep = (y, gm)
+        return out
+
     def variance(self, y, mhat_at_x):
         t = self.torch
         y = self._y(y)
@@ -613,14 +635,32 @@ def cv_fkreg(x, y, hlist, grid_n, lo=None, hi=None, order: int = 1, n_probes: in
     return res
 
 
+class _PlanCache:
+    """The plan of the last differentiable call, reused while its options (the
+    bandwidth included: a plan's H is fixed) and sample count stay the same."""
+
+    def __init__(self):
+        self.key, self.plan = None, None
+
+    def get(self, key, make):
+        if self.key != key:
+            self.plan, self.key = make(), key
+        return self.plan
+
+
+_GCV_PLANS = _PlanCache()
+_GRID_PLANS = _PlanCache()
+
+
 def gcv(x, y, log_sigma, grid_n, lo, hi, order: int = 1, n_probes: int = 10, seed: int = 0,
         precision: str = "f32", tol=None, device=None):
     """GCV (eq. 22) of one diagonal bandwidth H = diag(exp(2 log_sigma)) as a
     differentiable torch function of the samples x [n, d], the responses
     y [n] and log_sigma [d]: ``fkreg_backward`` computes the value and the
     three gradients in one call (Monte-Carlo trace of Sec. 2.1 with probes
-    drawn from ``seed``, held fixed), and autograd chains them.  Each call
-    builds a plan for the current bandwidth (a plan's H is fixed).
+    drawn from ``seed``, held fixed), and autograd chains them.  A plan is
+    built for each new bandwidth (a plan's H is fixed) and reused while the
+    bandwidth and the problem's shape stay the same.
     """
     import torch
 
@@ -631,9 +671,12 @@ def gcv(x, y, log_sigma, grid_n, lo, hi, order: int = 1, n_probes: int = 10, see
             sig = torch.exp(ls.detach().to("cpu", torch.float64)).numpy()
             H = np.diag(sig * sig).reshape(1, d, d)
             t = tol if tol is not None else (1e-6 if precision == "f32" else 1e-12)
-            plan = Plan(d, order, grid_n, lo, hi, H, max_n=max(int(xx.shape[0]), 1), n_rhs=1,
-                        max_probes=n_probes, tol=t, precision=precision,
-                        flags=FKREG_WANT_BACKWARD, device=device)
+            n = max(int(xx.shape[0]), 1)
+            key = (d, order, tuple(grid_n), tuple(lo), tuple(hi), tuple(sig.tolist()), n,
+                   n_probes, precision, t, str(device))
+            plan = _GCV_PLANS.get(key, lambda: Plan(
+                d, order, grid_n, lo, hi, H, max_n=n, n_rhs=1, max_probes=n_probes, tol=t,
+                precision=precision, flags=FKREG_WANT_BACKWARD, device=device))
             plan.set_points(xx.detach())
             out = plan.backward(yy.detach(), n_probes, seed=seed, b=0)
             plan.sync()
@@ -651,6 +694,61 @@ def gcv(x, y, log_sigma, grid_n, lo, hi, order: int = 1, n_probes: int = 10, see
     if xt.dim() == 1:
         xt = xt.reshape(-1, 1)
     return _GCV.apply(xt, torch.as_tensor(y).reshape(-1), torch.as_tensor(log_sigma).reshape(-1))
+
+
+def smooth_grid(x, y, log_sigma, grid_n, lo, hi, order: int = 1, precision: str = "f64",
+                tol=None, mask_rho: float = 0.0, device=None):
+    """The grid estimate of eq. 11 as a differentiable torch function of the
+    samples x [n, d], the responses y ([n] or [R, n]) and log_sigma [d]
+    (H = diag(exp(2 log_sigma))): returns mhat [R, *grid_n] (NaN where masked).
+    The backward is ``fkreg_backward_grid``: the adjoints of the per-grid-point
+    solves, the adjoint of the inverse grid transform and a type-2 evaluation
+    at the samples, and a spectral inner product for log sigma; masked points
+    and non-finite incoming gradients contribute nothing.  A plan is built for
+    each new bandwidth and reused while it and the problem's shape stay the
+    same.
+    """
+    import torch
+
+    class _Smooth(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xx, yy, ls):
+            d = int(xx.shape[1])
+            R = int(yy.shape[0])
+            sig = torch.exp(ls.detach().to("cpu", torch.float64)).numpy()
+            H = np.diag(sig * sig).reshape(1, d, d)
+            t = tol if tol is not None else (1e-6 if precision == "f32" else 1e-12)
+            n = max(int(xx.shape[0]), 1)
+            key = (d, order, tuple(grid_n), tuple(lo), tuple(hi), tuple(sig.tolist()), n, R,
+                   precision, t, mask_rho, str(device))
+            plan = _GRID_PLANS.get(key, lambda: Plan(
+                d, order, grid_n, lo, hi, H, max_n=n, n_rhs=R, tol=t, precision=precision,
+                mask_rho=mask_rho, flags=FKREG_WANT_BACKWARD, device=device))
+            plan.set_points(xx.detach())
+            out = plan.smooth(yy.detach(), want=("mhat_grid",))
+            plan.sync()
+            ctx.plan = plan
+            ctx.save_for_backward(xx, yy, ls)
+            return out["mhat_grid"][0].to(yy.device, yy.dtype)
+
+        @staticmethod
+        def backward(ctx, g):
+            xx, yy, ls = ctx.saved_tensors
+            plan = ctx.plan
+            plan.set_points(xx.detach())
+            r = plan.backward_grid(yy.detach(), torch.nan_to_num(g.detach(), nan=0.0), b=0)
+            plan.sync()
+            return (r["dx"][: xx.shape[0]].to(xx.device, xx.dtype).reshape(xx.shape),
+                    r["dy"][:, : yy.shape[1]].to(yy.device, yy.dtype).reshape(yy.shape),
+                    r["dlogh"].to(ls.device, ls.dtype))
+
+    xt = torch.as_tensor(x)
+    if xt.dim() == 1:
+        xt = xt.reshape(-1, 1)
+    yt = torch.as_tensor(y)
+    if yt.dim() == 1:
+        yt = yt.reshape(1, -1)
+    return _Smooth.apply(xt, yt, torch.as_tensor(log_sigma).reshape(-1))
 
 
 def interval(mhat, var, alpha: float = 0.05):
