@@ -488,6 +488,18 @@ fkreg_plan fkreg_batch_plan(fkreg_batch batch, int p);
 const char* fkreg_batch_last_error(fkreg_batch batch);
 void fkreg_batch_destroy(fkreg_batch batch);
 
+/*
+ * Failure-path knob (the paper has no counterpart): the kernels that stage
+ * field windows in shared memory wait for each window's bulk copies with a
+ * bounded number of polls, then record FKREG_ERR_TIMEOUT in the error word
+ * that fkreg_sync_status reports, wait (with the full budget) for any copy
+ * still in flight and return.  polls >= 0 sets that number for this plan's
+ * later calls (0 gives up at the first wait, which tests the failure path);
+ * polls < 0 restores the default (2^22 polls).  Results of a call that timed
+ * out are not valid; the plan stays usable.
+ */
+fkreg_status fkreg_set_wait_limit(fkreg_plan plan, int64_t polls);
+
 /* Synchronise the stream and report device-detected errors (then clear them). */
 fkreg_status fkreg_sync_status(fkreg_plan plan, void* stream);
 

@@ -10,6 +10,8 @@
 //   -> DF / GCV finalisation.
 // No host synchronisation happens inside a call.
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -217,6 +219,7 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
     return set_global_error(st, err);
   }
   P->o = *opts;
+  P->geo.wait_limit = fk::kDefaultWaitLimit;
   const int d = opts->dim;
   P->H.assign(opts->H, opts->H + size_t(opts->n_bw) * d * d);
   P->o.H = P->H.data();
@@ -915,6 +918,13 @@ fkreg_status fkreg_log_variance(fkreg_plan P, const void* y, const void* mhat_at
       FK_CHECK(fk::run_kappa_sigma2(P, b, y, mhat_at_x, v_at_x, v_grid, kappa, sigma2, s), "kappa");
     }
   }
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_set_wait_limit(fkreg_plan P, int64_t polls) {
+  if (!P) return FKREG_ERR_INVALID_ARG;
+  if (polls > int64_t(UINT32_MAX)) return plan_err(P, FKREG_ERR_INVALID_ARG, "polls must be < 2^32");
+  P->geo.wait_limit = polls < 0 ? fk::kDefaultWaitLimit : uint32_t(polls);
   return FKREG_OK;
 }
 

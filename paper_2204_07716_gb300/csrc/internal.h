@@ -20,6 +20,7 @@ constexpr int kMaxP = 10;        // unknowns of the local-quadratic system in 3-
 constexpr int kSubMax = 1024;    // samples per spreading sub-problem
 constexpr int kRadixBits = 8;
 constexpr int kSortTileKeys = 4096;  // keys per radix-sort tile (one block)
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // polls of a staged-window wait
 
 // Geometry of the whole plan, passed to kernels by value.
 struct GeoDev {
@@ -41,6 +42,7 @@ struct GeoDev {
   int64_t nbins[3];
   int kbits;        // within-bin bits of the sort key (see key_local_bits)
   int kern;         // regression kernel: FKREG_KERNEL_GAUSSIAN (NUFFT) or a compact one (direct)
+  uint32_t wait_limit;  // polls of a staged-window wait before it gives up (fkreg_set_wait_limit)
 };
 
 // Sort keys are (bin << kbits) | local, local = serpentine index of the

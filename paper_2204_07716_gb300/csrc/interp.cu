@@ -298,7 +298,7 @@ interp_tma_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b, 
     if (threadIdx.x == 0)
       issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, wm1 * rec, win, &mbar);
     bool ok = false;
-    for (uint32_t it = 0; it < kMaxSpin && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
+    for (uint32_t it = 0; it < g.wait_limit && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicOr(errw, 2);
       bool late = false;
@@ -484,7 +484,7 @@ interp_lane_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int b,
     if (threadIdx.x == 0)
       issue_window_copies<T, D>(fld, rec, nf0, nf1, o0, o1, wm0, wm1, pitch, win, &mbar);
     bool ok = false;
-    for (uint32_t it = 0; it < kMaxSpin && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
+    for (uint32_t it = 0; it < g.wait_limit && !ok; ++it) ok = mbar_try_wait(&mbar, parity);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicOr(errw, 2);
       bool late = false;

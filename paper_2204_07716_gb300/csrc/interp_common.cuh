@@ -19,7 +19,11 @@ namespace {
 
 constexpr int kMaxAcc = 512;  // bound on the reduced sums of one at-sample launch
 
-constexpr uint32_t kMaxSpin = 1u << 22;  // bounded mbarrier wait
+// Bounded mbarrier waits: a staged-window wait polls GeoDev::wait_limit
+// times (kMaxSpin unless fkreg_set_wait_limit changed it) before the kernel
+// records a timeout; the wait for copies still in flight before an early
+// exit always polls kMaxSpin times.
+constexpr uint32_t kMaxSpin = 1u << 22;
 constexpr int kLWarps = 16;              // lane-per-sample kernels: warps per block (upper bound)
 constexpr int kMmaMaxRows = 16;          // tensor-core union gather: union rows (padded to 8)
 constexpr int kMmaMaxCols = 24;          // and columns at most

@@ -120,7 +120,7 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
     const int cur = it & 1;
     const uint32_t parity = uint32_t(it >> 1) & 1u;
     bool ok = false;
-    for (uint32_t i = 0; i < kMaxSpin && !ok; ++i) ok = mbar_try_wait(&mbar[cur], parity);
+    for (uint32_t i = 0; i < g.wait_limit && !ok; ++i) ok = mbar_try_wait(&mbar[cur], parity);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) {
         atomicOr(errw, 2);

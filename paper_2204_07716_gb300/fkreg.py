@@ -43,7 +43,8 @@ EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create"
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
            "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_backward_grid", "fkreg_variance",
            "fkreg_log_variance", "fkreg_interval", "fkreg_predict", "fkreg_set_timing",
-           "fkreg_stage_times", "fkreg_bin_sort_static", "fkreg_sync_status",
+           "fkreg_stage_times", "fkreg_set_wait_limit", "fkreg_bin_sort_static",
+           "fkreg_sync_status",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
            "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
            "fkreg_batch_capture", "fkreg_batch_launch", "fkreg_batch_latencies",
@@ -129,6 +130,7 @@ def load():
                                  vp, vp, vp]
     L.fkreg_backward_grid.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, vp, vp]
     L.fkreg_set_timing.argtypes = [vp, ctypes.c_int]
+    L.fkreg_set_wait_limit.argtypes = [vp, i64]
     L.fkreg_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]
     L.fkreg_bin_sort_static.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(ctypes.c_double),
@@ -351,6 +353,11 @@ class Plan:
 
     def sync(self):
         self._check(self.L.fkreg_sync_status(self.h, self._stream()))
+
+    def set_wait_limit(self, polls: int = -1):
+        """Polls of a staged-window wait before a call gives up with a timeout
+        (fkreg_set_wait_limit; < 0 restores the default)."""
+        self._check(self.L.fkreg_set_wait_limit(self.h, int(polls)))
 
     def set_timing(self, enable: bool = True):
         self._check(self.L.fkreg_set_timing(self.h, int(bool(enable))))
