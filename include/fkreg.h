@@ -262,11 +262,14 @@ fkreg_status fkreg_smooth(fkreg_plan plan, const void* y_dev, const fkreg_output
  * Smooth y together with n_probes Gaussian probe vectors w_p (Sec. 2.1) and
  * return the DF estimates and GCV (eq. 22) for every bandwidth, plus any of
  * the smoothing outputs.  probes_dev [n_probes][n] (plan precision, ORIGINAL
- * sample order) or NULL: then probe (p, i) is drawn on the device from the
- * counter-based generator c = splitmix64(seed XOR splitmix64((p << 40) XOR i)),
- * then Box-Muller w = sqrt(-2 ln u1) cos(2 pi u2) in the plan precision:
- * FKREG_F64: u1 = ((c >> 11) + 1) 2^-53, u2 = (splitmix64(c) >> 11) 2^-53;
- * FKREG_F32: u1 = ((c >> 40) + 1) 2^-24, u2 = (splitmix64(c) >> 40) 2^-24.
+ * sample order) or NULL: then the probes are drawn on the device in
+ * Box-Muller pairs from the SplitMix64 stream seeded with `seed` (word k >= 1
+ * is splitmix64(seed + (k - 1) gamma), gamma = 0x9E3779B97F4A7C15): pair
+ * j = p / 2 of original sample i takes the words a = 2c + 1 and b = 2c + 2,
+ * c = (j << 40) | i, and gives probes 2j and 2j + 1 as r cos(2 pi u2) and
+ * r sin(2 pi u2), r = sqrt(-2 ln u1), in the plan precision:
+ * FKREG_F64: u1 = ((a >> 11) + 1) 2^-53, u2 = (b >> 11) 2^-53;
+ * FKREG_F32: u1 = ((a >> 40) + 1) 2^-24, u2 = (b >> 40) 2^-24.
  * n_probes <= max_probes.
  */
 fkreg_status fkreg_df(fkreg_plan plan, const void* y_dev, int n_probes, uint64_t seed,

@@ -413,38 +413,51 @@ static uint64_t splitmix64(uint64_t z) {
 
 /*
  * Counter-based Gaussian probes for the Monte-Carlo DF estimate (Sec. 2.1,
- * step i).  Probe value (p, i), with i the ORIGINAL sample index:
- *   c  = splitmix64(seed XOR splitmix64((p << 40) XOR i))
- *   u1 = ((c >> 11) + 1) * 2^-53,  u2 = (splitmix64(c) >> 11) * 2^-53
- *   z  = sqrt(-2 ln u1) cos(2 pi u2)            (Box-Muller, 1958)
- * out[p][i] for p < np, i < n.
+ * step i; the paper leaves the generator open).  Word k >= 1 of the SplitMix64
+ * stream seeded with `seed` is splitmix64(seed + (k - 1) gamma), gamma the
+ * generator's increment.  Probes come in Box-Muller pairs (Box & Muller,
+ * 1958): for pair j = p / 2 and ORIGINAL sample index i, with
+ * c = (j << 40) | i, the two words
+ *   a = word 2c + 1,  b = word 2c + 2
+ * give u1 = ((a >> 11) + 1) 2^-53 in (0, 1], u2 = (b >> 11) 2^-53 in [0, 1),
+ * r = sqrt(-2 ln u1), and
+ *   probe 2j = r cos(2 pi u2),  probe 2j + 1 = r sin(2 pi u2).
+ * out[p][i] for p < np, i < n (an odd np uses the cosine of its last pair).
  */
+#define OR_GAMMA 0x9E3779B97F4A7C15ULL
+
+static void or_probe_words(uint64_t seed, int p, int64_t i, uint64_t* a, uint64_t* b) {
+  const uint64_t c = ((uint64_t)(p >> 1) << 40) | (uint64_t)i;
+  *a = splitmix64(seed + (2 * c) * OR_GAMMA);
+  *b = splitmix64(seed + (2 * c + 1) * OR_GAMMA);
+}
+
 void or_probes(uint64_t seed, int np, int64_t n, double* out) {
   for (int p = 0; p < np; ++p)
     for (int64_t i = 0; i < n; ++i) {
-      uint64_t ctr = ((uint64_t)p << 40) ^ (uint64_t)i;
-      uint64_t c = splitmix64(seed ^ splitmix64(ctr));
-      uint64_t c2 = splitmix64(c);
-      double u1 = ((double)(c >> 11) + 1.0) * 0x1.0p-53;
-      double u2 = (double)(c2 >> 11) * 0x1.0p-53;
-      out[(int64_t)p * n + i] = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+      uint64_t a, b;
+      or_probe_words(seed, p, i, &a, &b);
+      const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;
+      const double u2 = (double)(b >> 11) * 0x1.0p-53;
+      const double r = sqrt(-2.0 * log(u1)), t = 2.0 * M_PI * u2;
+      out[(int64_t)p * n + i] = (p & 1) ? r * sin(t) : r * cos(t);
     }
 }
 
 /*
  * The same probes evaluated in single precision (the generator an FP32 plan
- * draws on the device): 24-bit uniforms u1 = ((c >> 40) + 1) 2^-24,
- * u2 = (splitmix64(c) >> 40) 2^-24, Box-Muller in float.
+ * draws on the device): the same words, 24-bit uniforms
+ * u1 = ((a >> 40) + 1) 2^-24, u2 = (b >> 40) 2^-24, Box-Muller in float.
  */
 void or_probes_f32(uint64_t seed, int np, int64_t n, float* out) {
   for (int p = 0; p < np; ++p)
     for (int64_t i = 0; i < n; ++i) {
-      uint64_t ctr = ((uint64_t)p << 40) ^ (uint64_t)i;
-      uint64_t c = splitmix64(seed ^ splitmix64(ctr));
-      uint64_t c2 = splitmix64(c);
-      float u1 = (float)((uint32_t)(c >> 40) + 1u) * 0x1.0p-24f;
-      float u2 = (float)(uint32_t)(c2 >> 40) * 0x1.0p-24f;
-      out[(int64_t)p * n + i] = sqrtf(-2.0f * logf(u1)) * cosf(2.0f * (float)M_PI * u2);
+      uint64_t a, b;
+      or_probe_words(seed, p, i, &a, &b);
+      const float u1 = (float)((uint32_t)(a >> 40) + 1u) * 0x1.0p-24f;
+      const float u2 = (float)(uint32_t)(b >> 40) * 0x1.0p-24f;
+      const float r = sqrtf(-2.0f * logf(u1)), t = 2.0f * (float)M_PI * u2;
+      out[(int64_t)p * n + i] = (p & 1) ? r * sinf(t) : r * cosf(t);
     }
 }
 

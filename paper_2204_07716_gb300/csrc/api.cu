@@ -311,6 +311,8 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   L.take(P->r_subbin, 4 * P->nsub_max);
   L.take(P->r_subfirst, 4 * P->nsub_max);
   L.take(P->r_hist, 4 * (1024 * ntiles + 1));
+  L.take(P->r_hist2, 4 * (1024 * ntiles + 1));
+  L.take(P->r_dtot, 4 * 2048);
   L.take(P->r_scan, 4 * (scan_len / 1024 + 2));
   L.take(P->r_str, T * strengths_total * std::max<int64_t>(1, max_n));
   // the direct path (compact kernels) needs only the grid fields

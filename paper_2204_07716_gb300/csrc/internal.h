@@ -111,7 +111,7 @@ struct fkreg_plan_s {
 
   // workspace regions
   fk::Region r_err, r_bw, r_tab, r_xs, r_keys0, r_vals0, r_keys1, r_vals1, r_counts,
-      r_binstart, r_nsub, r_substart, r_subbin, r_subfirst, r_hist, r_scan, r_str,
+      r_binstart, r_nsub, r_substart, r_subbin, r_subfirst, r_hist, r_hist2, r_dtot, r_scan, r_str,
       r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork,
       r_fftwork_g,
       r_bV, r_bdx, r_bsc, r_bpart, r_gmask, r_gadj, r_gpart;

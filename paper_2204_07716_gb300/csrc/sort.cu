@@ -82,48 +82,227 @@ __global__ void bin_keys_kernel(GeoDev g, int64_t n, const T* __restrict__ x,
   if (counts) atomicAdd(&counts[bin], 1u);
 }
 
-// Keys and bin counts in one pass for plans with few bins: grid-stride
-// blocks count into a shared-memory histogram and add it to the global
-// counters once per block (few global atomics, no contention).
+// The key of sample i (see the header of this file); `bad` is set when the
+// sample lies outside the box (it is then keyed as if at the lower corner).
 template <typename T>
-__global__ void bin_keys_hist_kernel(GeoDev g, int64_t n, int64_t nbins, const T* __restrict__ x,
-                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                     uint32_t* __restrict__ counts, int* __restrict__ errw) {
-  extern __shared__ uint32_t h[];
-  for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
-  __syncthreads();
+__device__ __forceinline__ uint32_t sample_key(const GeoDev& g, const T* __restrict__ x, int64_t i,
+                                               bool& bad, uint32_t& bin) {
   const T halfw = T(0.5) * T(g.w);
-  bool bad = false;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    uint32_t bin = 0, local = 0;
-    for (int j = 0; j < g.d; ++j) {
-      T xv = x[i * g.d + j];
-      const T lo = T(g.lo[j]), hi = T(g.hi[j]);
-      if (!(xv >= lo && xv <= hi)) {
-        bad = true;
-        xv = lo;
-      }
-      const T u = mul_rn(sub_rn(xv, lo), inv_h_of<T>(g, j));
-      // 32-bit integer arithmetic: cells, tiles and bins are below 2^31
-      const int nfj = int(g.nf[j]), tj = int(g.tile[j]);
-      int c = int(floor(u));
-      if (c < 0) c = 0;
-      if (c > nfj - 1) c = nfj - 1;
-      const int b = c / tj;
-      int e = int(ceil(sub_rn(u, halfw))) + g.w / 2 - b * tj;
-      e = e < 0 ? 0 : (e > tj ? tj : e);
-      bin = bin * uint32_t(g.nbins[j]) + uint32_t(b);
-      local = local * uint32_t(tj + 1) + uint32_t((local & 1u) ? tj - e : e);
+  uint32_t local = 0;
+  bin = 0;
+  for (int j = 0; j < g.d; ++j) {
+    T xv = x[i * g.d + j];
+    const T lo = T(g.lo[j]), hi = T(g.hi[j]);
+    if (!(xv >= lo && xv <= hi)) {
+      bad = true;
+      xv = lo;
     }
-    keys[i] = g.kbits ? (bin << g.kbits) | local : bin;
-    vals[i] = uint32_t(i);
-    atomicAdd(&h[bin], 1u);
+    const T u = mul_rn(sub_rn(xv, lo), inv_h_of<T>(g, j));
+    // 32-bit integer arithmetic: cells, tiles and bins are below 2^31
+    const int nfj = int(g.nf[j]), tj = int(g.tile[j]);
+    int c = int(floor(u));
+    if (c < 0) c = 0;
+    if (c > nfj - 1) c = nfj - 1;
+    const int b = c / tj;
+    int e = int(ceil(sub_rn(u, halfw))) + g.w / 2 - b * tj;
+    e = e < 0 ? 0 : (e > tj ? tj : e);
+    bin = bin * uint32_t(g.nbins[j]) + uint32_t(b);
+    local = local * uint32_t(tj + 1) + uint32_t((local & 1u) ? tj - e : e);
+  }
+  return g.kbits ? (bin << g.kbits) | local : bin;
+}
+
+// ---- fused sort (plans with at most kFusedMaxBins bins) --------------------
+// Five launches for two passes: keys with the bin counts and the first
+// pass's tile histograms; per pass one scan of the tile histograms and one
+// scatter.  A scatter that is not the last counts the next pass's digits of
+// the keys it writes, by destination tile (global atomics) and in total
+// (shared, then one atomic per digit and block); the last scatter writes the
+// permutation and the sorted, shifted coordinates, not the keys.  The first
+// scan's extra block turns the bin counts into bin starts and spreading
+// sub-problems.
+constexpr int64_t kFusedMaxBins = 8192;
+constexpr int kKeysThreads = 512;
+constexpr int kDigitScanWarps = 8;
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kKeysThreads)
+keys_tiles_kernel(GeoDev g, int64_t n, int64_t nbins, int64_t ntiles, const T* __restrict__ x,
+                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                  uint32_t* __restrict__ counts, uint32_t* __restrict__ hist,
+                  uint32_t* __restrict__ dtot, int* __restrict__ errw) {
+  constexpr uint32_t R = 1u << B;
+  extern __shared__ uint32_t ksm[];
+  uint32_t* hb = ksm;          // [nbins] bin counts of this block
+  uint32_t* hd = ksm + nbins;  // [R] digit counts of the current tile
+  for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x) hb[b] = 0;
+  bool bad = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) hd[d] = 0;
+    __syncthreads();
+    const int64_t base = t * kSortTile;
+    for (int k = threadIdx.x; k < kSortTile; k += blockDim.x) {
+      const int64_t i = base + k;
+      if (i >= n) break;
+      uint32_t bin;
+      const uint32_t key = sample_key<T>(g, x, i, bad, bin);
+      keys[i] = key;
+      vals[i] = uint32_t(i);
+      atomicAdd(&hb[bin], 1u);
+      atomicAdd(&hd[key & (R - 1u)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) {
+      const uint32_t c = hd[d];
+      hist[int64_t(d) * ntiles + t] = c;
+      if (c) atomicAdd(&dtot[d], c);
+    }
+    __syncthreads();
   }
   if (bad) atomicOr(errw, 1);
   __syncthreads();
   for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x)
-    if (h[b]) atomicAdd(&counts[b], h[b]);
+    if (hb[b]) atomicAdd(&counts[b], hb[b]);
+}
+
+// Bin starts and spreading sub-problems (at most kSubMax samples each) from
+// the bin counts, by one block of kDigitScanWarps warps: each thread owns a
+// contiguous chunk of bins, the block scans the chunk totals of samples and
+// sub-problems, and each thread writes its bins' starts and sub-problems.
+struct BinsArgs {
+  const uint32_t* counts;
+  int64_t nbins;
+  uint32_t* bin_start;  // [nbins + 1]
+  uint32_t* sub_start;  // [nbins + 1]
+  uint32_t* sub_bin;
+  uint32_t* sub_first;
+};
+
+__device__ void bins_block(const BinsArgs& a) {
+  constexpr int NT = kDigitScanWarps * 32;
+  __shared__ uint32_t wc[kDigitScanWarps], ws[kDigitScanWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t chunk = (a.nbins + NT - 1) / NT;
+  const int64_t b0 = min(a.nbins, int64_t(tid) * chunk), b1 = min(a.nbins, b0 + chunk);
+  uint32_t tc = 0, ts = 0;
+  for (int64_t b = b0; b < b1; ++b) {
+    const uint32_t c = a.counts[b];
+    tc += c;
+    ts += (c + kSubMax - 1) / kSubMax;
+  }
+  uint32_t ic = tc, is = ts;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t vc = __shfl_up_sync(0xffffffffu, ic, o);
+    const uint32_t vs = __shfl_up_sync(0xffffffffu, is, o);
+    if (lane >= o) {
+      ic += vc;
+      is += vs;
+    }
+  }
+  if (lane == 31) {
+    wc[warp] = ic;
+    ws[warp] = is;
+  }
+  __syncthreads();
+  uint32_t rc = ic - tc, rs = is - ts, totc = 0, tots = 0;
+  for (int w = 0; w < kDigitScanWarps; ++w) {
+    if (w < warp) {
+      rc += wc[w];
+      rs += ws[w];
+    }
+    totc += wc[w];
+    tots += ws[w];
+  }
+  for (int64_t b = b0; b < b1; ++b) {
+    const uint32_t c = a.counts[b], ns = (c + kSubMax - 1) / kSubMax;
+    a.bin_start[b] = rc;
+    a.sub_start[b] = rs;
+    for (uint32_t k = 0; k < ns; ++k) {
+      a.sub_bin[rs + k] = uint32_t(b);
+      a.sub_first[rs + k] = rc + k * kSubMax;
+    }
+    rc += c;
+    rs += ns;
+  }
+  if (tid == 0) {
+    a.bin_start[a.nbins] = totc;
+    a.sub_start[a.nbins] = tots;
+  }
+}
+
+// hist[d][t] (tile counts of digit d) -> first output position of digit d's
+// keys from tile t: the digits' exclusive prefix of the totals dtot plus the
+// exclusive prefix over the tiles before t.  One warp per digit; grid
+// R / kDigitScanWarps blocks (+1 when bins.counts is set: that block runs
+// bins_block).  With hist_next set, the same warps zero the next pass's
+// tile histograms and totals, which the scatter of this pass fills.
+template <int B>
+__global__ void __launch_bounds__(kDigitScanWarps * 32)
+digit_scan_kernel(uint32_t* __restrict__ hist, int64_t ntiles, const uint32_t* __restrict__ dtot,
+                  uint32_t* __restrict__ hist_next, uint32_t* __restrict__ dtot_next,
+                  BinsArgs bins) {
+  constexpr int R = 1 << B;
+  constexpr int NT = kDigitScanWarps * 32;
+  constexpr int DPT = R / NT;
+  static_assert(DPT * NT == R, "digits per thread");
+  if (bins.counts && blockIdx.x == gridDim.x - 1) {
+    bins_block(bins);
+    return;
+  }
+  __shared__ uint32_t base[R];
+  __shared__ uint32_t wsum[kDigitScanWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t v[DPT], own = 0;
+#pragma unroll
+  for (int u = 0; u < DPT; ++u) {
+    v[u] = dtot[tid * DPT + u];
+    own += v[u];
+  }
+  uint32_t inc = own;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t run = inc - own;
+  for (int w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+  for (int u = 0; u < DPT; ++u) {
+    base[tid * DPT + u] = run;
+    run += v[u];
+  }
+  __syncthreads();
+  const int d = blockIdx.x * kDigitScanWarps + warp;
+  uint32_t carry = base[d];
+  uint32_t* row = hist + int64_t(d) * ntiles;
+  constexpr int V = 8;  // consecutive tiles per lane and segment
+  for (int64_t t0 = 0; t0 < ntiles; t0 += 32 * V) {
+    uint32_t c[V], tot = 0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int64_t t = t0 + int64_t(lane) * V + k;
+      c[k] = t < ntiles ? row[t] : 0u;
+      tot += c[k];
+    }
+    uint32_t incl = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t r = carry + incl - tot;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int64_t t = t0 + int64_t(lane) * V + k;
+      if (t < ntiles) row[t] = r;
+      r += c[k];
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (hist_next) {
+    for (int64_t t = lane; t < ntiles; t += 32) hist_next[int64_t(d) * ntiles + t] = 0;
+    if (lane == 0) dtot_next[d] = 0;
+  }
 }
 
 // ---- exclusive scan of uint32 (three kernels, any length) ----------------
@@ -256,18 +435,33 @@ radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t n
     hist[int64_t(d) * ntiles + blockIdx.x] = h[d];
 }
 
-// dynamic shared memory of radix_downsweep<B>
+// What a scatter writes besides the plain keys and values (the fused sort):
+// kDownPlain  keys and values;
+// kDownCount  keys and values, and the next pass's digit counts per
+//             destination tile (hist_next[digit][tile]) and in total;
+// kDownLast   values (the permutation) and the sorted coordinates
+//             xs[j][pos] = x_ij - lo_j (a sample outside the box as at lo).
+constexpr int kDownPlain = 0, kDownCount = 1, kDownLast = 2;
+struct DownExtra {
+  uint32_t* hist_next;
+  uint32_t* dtot_next;
+  GeoDev g;
+  const void* x;
+  void* xs;
+};
+
+// dynamic shared memory of radix_downsweep<B, ...>
 template <int B>
 constexpr size_t radix_down_smem() {
-  return sizeof(uint32_t) * ((kSortThreads / 32 + 2) * (size_t(1) << B) + kSortThreads / 32 +
+  return sizeof(uint32_t) * ((kSortThreads / 32 + 3) * (size_t(1) << B) + kSortThreads / 32 +
                              2 * size_t(kSortTile));
 }
 
-template <int B>
+template <int B, int MODE = kDownPlain, typename T = float>
 __global__ void __launch_bounds__(kSortThreads, 2)
 radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 int64_t n, int shift, int64_t ntiles, const uint32_t* __restrict__ hist_scanned,
-                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, DownExtra ex) {
   constexpr int NW = kSortThreads / 32;
   constexpr int RW = kSortTile / NW / 32;  // rounds of 32 keys per warp
   constexpr uint32_t R = 1u << B;
@@ -281,8 +475,11 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
   uint32_t* wsum = gbase + R;          // [NW]
   uint32_t* skey = wsum + NW;          // [kSortTile]
   uint32_t* sval = skey + kSortTile;   // [kSortTile]
+  uint32_t* hn = sval + kSortTile;     // [R] next pass's digit totals (kDownCount)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint32_t d = tid; d < NW * R; d += kSortThreads) wh[d] = 0;
+  if (MODE == kDownCount)
+    for (uint32_t d = tid; d < R; d += kSortThreads) hn[d] = 0;
   __syncthreads();
   const int64_t tbase = int64_t(blockIdx.x) * kSortTile;
   const int64_t wbase = tbase + int64_t(warp) * (RW * 32);
@@ -361,8 +558,29 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     const uint32_t k = skey[t];
     const uint32_t dig = (k >> shift) & (R - 1u);
     const uint32_t pos = gbase[dig] + uint32_t(t) - dstart[dig];
-    keys_out[pos] = k;
-    vals_out[pos] = sval[t];
+    const uint32_t v = sval[t];
+    vals_out[pos] = v;
+    if (MODE != kDownLast) keys_out[pos] = k;
+    if (MODE == kDownCount) {
+      const uint32_t dn = (k >> (shift + B)) & (R - 1u);
+      atomicAdd(&ex.hist_next[int64_t(dn) * ntiles + pos / uint32_t(kSortTile)], 1u);
+      atomicAdd(&hn[dn], 1u);
+    }
+    if (MODE == kDownLast) {
+      const T* x = static_cast<const T*>(ex.x);
+      T* xs = static_cast<T*>(ex.xs);
+      for (int j = 0; j < ex.g.d; ++j) {
+        T xv = x[int64_t(v) * ex.g.d + j];
+        const T lo = T(ex.g.lo[j]), hi = T(ex.g.hi[j]);
+        if (!(xv >= lo && xv <= hi)) xv = lo;
+        xs[int64_t(j) * n + pos] = sub_rn(xv, lo);
+      }
+    }
+  }
+  if (MODE == kDownCount) {
+    __syncthreads();
+    for (uint32_t d = tid; d < R; d += kSortThreads)
+      if (hn[d]) atomicAdd(&ex.dtot_next[d], hn[d]);
   }
 }
 
@@ -470,48 +688,83 @@ cudaError_t radix_pass(const uint32_t* kin, const uint32_t* vin, int64_t n, int 
                                 int(sm))) != cudaSuccess)
     return e;
   radix_downsweep<B><<<unsigned(ntiles), kSortThreads, sm, s>>>(kin, vin, n, shift, ntiles, hist,
-                                                                kout, vout);
+                                                                kout, vout, DownExtra{});
   if (launches) *launches += 2;
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) {
+namespace {
+
+// The fused sort: keys_tiles, then per pass digit_scan and a scatter.
+template <int B, typename T>
+cudaError_t run_sort_fused(fkreg_plan_s* P, int64_t n, const T* x, int passes, int64_t ntiles,
+                           cudaStream_t s) {
   const GeoDev& g = P->geo;
-  uint32_t* keys0 = wsp<uint32_t>(P, P->r_keys0);
-  uint32_t* vals0 = wsp<uint32_t>(P, P->r_vals0);
-  uint32_t* keys1 = wsp<uint32_t>(P, P->r_keys1);
-  uint32_t* vals1 = wsp<uint32_t>(P, P->r_vals1);
-  uint32_t* counts = wsp<uint32_t>(P, P->r_counts);
-  uint32_t* bstart = wsp<uint32_t>(P, P->r_binstart);
-  uint32_t* scratch = wsp<uint32_t>(P, P->r_scan);
-  int* errw = wsp<int>(P, P->r_err);
   const int64_t nbins = P->nbins_total;
+  uint32_t* keys[2] = {wsp<uint32_t>(P, P->r_keys0), wsp<uint32_t>(P, P->r_keys1)};
+  uint32_t* vals[2] = {wsp<uint32_t>(P, P->r_vals0), wsp<uint32_t>(P, P->r_vals1)};
+  uint32_t* hist[2] = {wsp<uint32_t>(P, P->r_hist), wsp<uint32_t>(P, P->r_hist2)};
+  uint32_t* dtot[2] = {wsp<uint32_t>(P, P->r_dtot), wsp<uint32_t>(P, P->r_dtot) + 1024};
+  uint32_t* counts = wsp<uint32_t>(P, P->r_counts);
+  // the bin counts and the first pass's digit totals start at zero
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * nbins, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dtot[0], 0, sizeof(uint32_t) << B, s);
   if (e != cudaSuccess) return e;
-  if (n > 0) {
-    const unsigned blocks = unsigned((n + 255) / 256);
-    const bool shared_hist = nbins <= 8192;
-    if (shared_hist) {
-      const unsigned hb = unsigned(std::min<int64_t>((n + 2047) / 2048, int64_t(P->sm_count) * 4));
-      const size_t hs = sizeof(uint32_t) * nbins;
-      if (P->prec == FKREG_F32)
-        bin_keys_hist_kernel<float><<<hb, 512, hs, s>>>(g, n, nbins, static_cast<const float*>(x),
-                                                        keys0, vals0, counts, errw);
-      else
-        bin_keys_hist_kernel<double><<<hb, 512, hs, s>>>(g, n, nbins, static_cast<const double*>(x),
-                                                         keys0, vals0, counts, errw);
-    } else if (P->prec == FKREG_F32) {
-      bin_keys_kernel<float><<<blocks, 256, 0, s>>>(g, n, static_cast<const float*>(x), keys0, vals0,
-                                                    counts, errw);
+  const unsigned kb = unsigned(std::min<int64_t>(ntiles, int64_t(P->sm_count) * 2));
+  const size_t ks = sizeof(uint32_t) * (size_t(nbins) + (size_t(1) << B));
+  keys_tiles_kernel<T, B><<<kb, kKeysThreads, ks, s>>>(g, n, nbins, ntiles, x, keys[0], vals[0],
+                                                       counts, hist[0], dtot[0],
+                                                       wsp<int>(P, P->r_err));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  P->launches += 1;
+  constexpr size_t sm = radix_down_smem<B>();
+  const BinsArgs bins{counts,
+                      nbins,
+                      wsp<uint32_t>(P, P->r_binstart),
+                      wsp<uint32_t>(P, P->r_substart),
+                      wsp<uint32_t>(P, P->r_subbin),
+                      wsp<uint32_t>(P, P->r_subfirst)};
+  const unsigned sb = unsigned((1 << B) / kDigitScanWarps);
+  int cur = 0;
+  for (int p = 0; p < passes; ++p) {
+    const bool last = p == passes - 1;
+    const int nx = (p + 1) & 1;
+    digit_scan_kernel<B><<<sb + (p == 0 ? 1u : 0u), kDigitScanWarps * 32, 0, s>>>(
+        hist[p & 1], ntiles, dtot[p & 1], last ? nullptr : hist[nx], last ? nullptr : dtot[nx],
+        p == 0 ? bins : BinsArgs{});
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    DownExtra ex{last ? nullptr : hist[nx], last ? nullptr : dtot[nx], g, x,
+                 wsp<T>(P, P->r_xs)};
+    if (last) {
+      if ((e = cudaFuncSetAttribute(radix_downsweep<B, kDownLast, T>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm))) !=
+          cudaSuccess)
+        return e;
+      radix_downsweep<B, kDownLast, T><<<unsigned(ntiles), kSortThreads, sm, s>>>(
+          keys[cur], vals[cur], n, p * B, ntiles, hist[p & 1], keys[cur ^ 1], vals[cur ^ 1], ex);
     } else {
-      bin_keys_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), keys0,
-                                                     vals0, counts, errw);
+      if ((e = cudaFuncSetAttribute(radix_downsweep<B, kDownCount, T>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm))) !=
+          cudaSuccess)
+        return e;
+      radix_downsweep<B, kDownCount, T><<<unsigned(ntiles), kSortThreads, sm, s>>>(
+          keys[cur], vals[cur], n, p * B, ntiles, hist[p & 1], keys[cur ^ 1], vals[cur ^ 1], ex);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    P->launches += 1;
+    P->launches += 2;
+    cur ^= 1;
   }
+  P->perm_in_vals1 = cur;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) {
+  const GeoDev& g = P->geo;
+  const int64_t nbins = P->nbins_total;
   // radix passes over the significant bits of the key
   int bits = g.kbits;
   while ((int64_t(1) << (bits - g.kbits)) < nbins) ++bits;
@@ -521,6 +774,35 @@ cudaError_t run_sort(fkreg_plan_s* P, int64_t n, const void* x, cudaStream_t s) 
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   const int dbits = (bits > 16 && bits <= 20 && ntiles >= 16) ? 10 : kRadixBits;
   const int passes = (bits + dbits - 1) / dbits;
+  if (n > 0 && passes >= 1 && nbins <= kFusedMaxBins) {
+    const bool f32 = P->prec == FKREG_F32;
+    if (dbits == 10)
+      return f32 ? run_sort_fused<10>(P, n, static_cast<const float*>(x), passes, ntiles, s)
+                 : run_sort_fused<10>(P, n, static_cast<const double*>(x), passes, ntiles, s);
+    return f32 ? run_sort_fused<8>(P, n, static_cast<const float*>(x), passes, ntiles, s)
+               : run_sort_fused<8>(P, n, static_cast<const double*>(x), passes, ntiles, s);
+  }
+  uint32_t* keys0 = wsp<uint32_t>(P, P->r_keys0);
+  uint32_t* vals0 = wsp<uint32_t>(P, P->r_vals0);
+  uint32_t* keys1 = wsp<uint32_t>(P, P->r_keys1);
+  uint32_t* vals1 = wsp<uint32_t>(P, P->r_vals1);
+  uint32_t* counts = wsp<uint32_t>(P, P->r_counts);
+  uint32_t* bstart = wsp<uint32_t>(P, P->r_binstart);
+  uint32_t* scratch = wsp<uint32_t>(P, P->r_scan);
+  int* errw = wsp<int>(P, P->r_err);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * nbins, s);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    const unsigned blocks = unsigned((n + 255) / 256);
+    if (P->prec == FKREG_F32)
+      bin_keys_kernel<float><<<blocks, 256, 0, s>>>(g, n, static_cast<const float*>(x), keys0, vals0,
+                                                    counts, errw);
+    else
+      bin_keys_kernel<double><<<blocks, 256, 0, s>>>(g, n, static_cast<const double*>(x), keys0,
+                                                     vals0, counts, errw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    P->launches += 1;
+  }
   uint32_t* hist = wsp<uint32_t>(P, P->r_hist);
   uint32_t *kin = keys0, *vin = vals0, *kout = keys1, *vout = vals1;
   int in_is_1 = 0;

@@ -544,28 +544,49 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Gaussian probe value for (probe p, original index i): counter-based
-// SplitMix64 words and the Box-Muller transform, evaluated in the plan
-// precision (53-bit uniforms in FP64, 24-bit uniforms in FP32).
+// Gaussian probes in Box-Muller pairs from counter-based SplitMix64 words:
+// word k >= 1 of the stream seeded with `seed` is splitmix64(seed + (k-1) gamma);
+// pair j of ORIGINAL sample i takes words 2c+1 and 2c+2, c = (j << 40) | i, as
+// the uniforms u1 in (0, 1] and u2 in [0, 1) (53-bit in FP64, the words' top
+// 24 bits in FP32) and gives r cos(2 pi u2), r sin(2 pi u2), r = sqrt(-2 ln u1),
+// evaluated in the plan precision.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+__device__ __forceinline__ void probe_words(uint64_t seed, int j, uint32_t i, uint64_t& a,
+                                            uint64_t& b) {
+  const uint64_t c = (uint64_t(j) << 40) | uint64_t(i);
+  const uint64_t base = seed + (2 * c) * kGamma;
+  a = splitmix64(base);
+  b = splitmix64(base + kGamma);
+}
+
 template <typename T>
-__device__ __forceinline__ T probe_value(uint64_t seed, int p, uint32_t i);
+__device__ __forceinline__ void probe_pair(uint64_t seed, int j, uint32_t i, T& z0, T& z1);
 template <>
-__device__ __forceinline__ double probe_value<double>(uint64_t seed, int p, uint32_t i) {
-  const uint64_t ctr = (uint64_t(p) << 40) ^ uint64_t(i);
-  const uint64_t c = splitmix64(seed ^ splitmix64(ctr));
-  const uint64_t c2 = splitmix64(c);
-  const double u1 = (double(c >> 11) + 1.0) * 0x1.0p-53;
-  const double u2 = double(c2 >> 11) * 0x1.0p-53;
-  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+__device__ __forceinline__ void probe_pair<double>(uint64_t seed, int j, uint32_t i, double& z0,
+                                                   double& z1) {
+  uint64_t a, b;
+  probe_words(seed, j, i, a, b);
+  const double u1 = (double(a >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = double(b >> 11) * 0x1.0p-53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  z0 = r * cs;
+  z1 = r * sn;
 }
 template <>
-__device__ __forceinline__ float probe_value<float>(uint64_t seed, int p, uint32_t i) {
-  const uint64_t ctr = (uint64_t(p) << 40) ^ uint64_t(i);
-  const uint64_t c = splitmix64(seed ^ splitmix64(ctr));
-  const uint64_t c2 = splitmix64(c);
-  const float u1 = float(uint32_t(c >> 40) + 1u) * 0x1.0p-24f;
-  const float u2 = float(uint32_t(c2 >> 40)) * 0x1.0p-24f;
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+__device__ __forceinline__ void probe_pair<float>(uint64_t seed, int j, uint32_t i, float& z0,
+                                                  float& z1) {
+  uint64_t a, b;
+  probe_words(seed, j, i, a, b);
+  const float u1 = float(uint32_t(a >> 40) + 1u) * 0x1.0p-24f;
+  const float u2 = float(uint32_t(b >> 40)) * 0x1.0p-24f;
+  const float r = sqrtf(-2.0f * logf(u1));
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  z0 = r * cs;
+  z1 = r * sn;
 }
 
 template <typename T>
@@ -587,9 +608,15 @@ __global__ void gather_strengths_kernel(int64_t n, const uint32_t* __restrict__ 
       str[int64_t(k++) * n + s] = y[int64_t(r) * n + i];
     }
   }
-  for (int p = 0; p < n_probes; ++p) {
-    const T v = probes ? probes[int64_t(p) * n + i] : probe_value<T>(seed, p, i);
-    str[int64_t(k++) * n + s] = v;
+  if (probes) {
+    for (int p = 0; p < n_probes; ++p) str[int64_t(k++) * n + s] = probes[int64_t(p) * n + i];
+  } else {
+    for (int p = 0; p < n_probes; p += 2) {
+      T z0, z1;
+      probe_pair<T>(seed, p >> 1, i, z0, z1);
+      str[int64_t(k++) * n + s] = z0;
+      if (p + 1 < n_probes) str[int64_t(k++) * n + s] = z1;
+    }
   }
 }
 

@@ -227,6 +227,13 @@ def test_probe_generator_is_standard_normal():
     assert z32.dtype == np.float32
     for p in range(2):
         assert stats.kstest(z32[p].astype(np.float64), "norm").pvalue > 1e-4
+    # Box-Muller pairs: probes 2j and 2j+1 share the radius r, and r^2 of a pair
+    # of independent standard normals is exponential with mean 2
+    r2 = z[0] ** 2 + z[1] ** 2
+    assert stats.kstest(r2, "expon", args=(0, 2)).pvalue > 1e-4
+    # an odd count draws the cosine of its last pair: the first probes agree
+    z3 = oracle.probes(2024, 3, 50_000)
+    np.testing.assert_array_equal(z3, z[:3])
     # the single-precision variant draws from the same counters (24-bit uniforms)
     assert np.corrcoef(z[0], z32[0].astype(np.float64))[0, 1] > 0.999
     # SplitMix64 is a bijection on 64-bit words: no collisions on a run of counters
