@@ -172,7 +172,7 @@ def dist_setup(args):
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
 # capture of the bench command (see profiles/); None where the kernel changed
 # after the counters were taken.
-TRAFFIC = {"interp": 79832320, "spread": None}
+TRAFFIC = {"interp": None, "spread": None}
 
 
 def max_over_ranks(ms: float, world: int, device) -> float:

@@ -204,6 +204,19 @@ fkreg_status fkreg_spread_kernel_ft(int kind, int w, double beta, int64_t nf,
                                     int64_t nk, double* phihat);
 
 /*
+ * Device: the spreading kernel phi(z) of Sec. 1.2 (eq. 17 for
+ * FKREG_SPREAD_GAUSS, the exponential of semicircle for FKREG_SPREAD_ES) at
+ * n offsets z_dev[i] (fine cells), evaluated by the same device function the
+ * spreading and interpolation kernels call, in `precision` (FKREG_F32: float
+ * z and out, FKREG_F64: double).  out_dev[i] = phi(z_dev[i]), 0 outside
+ * |z| <= w/2.  One launch on `stream`; no synchronisation.  Returns
+ * FKREG_ERR_INVALID_ARG for a bad kind, precision, w outside [2, 32], n < 0
+ * or a NULL pointer with n > 0, FKREG_ERR_CUDA if the launch fails.
+ */
+fkreg_status fkreg_spread_kernel_values(int kind, int w, double beta, int precision, int64_t n,
+                                        const void* z_dev, void* out_dev, void* stream);
+
+/*
  * Create a plan for up to max_n samples.  Computes the geometry and the
  * spreading-kernel tables on the host and creates the cuFFT plans (needs a
  * current CUDA device).  The plan owns host tables, cuFFT handles, and one

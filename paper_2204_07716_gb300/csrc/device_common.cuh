@@ -31,6 +31,30 @@ __device__ __forceinline__ T phi(int kind, int w, T beta, T z) {
   return (fabs(z) <= T(0.5) * T(w)) ? exp(-beta * z * z) : T(0);
 }
 
+// FP32: the same kernels from the hardware reciprocal square root and base-2
+// exponential (rsqrtf, exp2f), with exp(x) = 2^(x log2 e).  sqrt(a) is taken
+// as s = a rsqrt(a) plus one Newton step on the exact residual a - s^2
+// (fmaf), which brings s to within about one unit in the last place, as a
+// correctly rounded square root would be; the exponent beta log2e (s - 1) is
+// one fused multiply-add.  The error of the value, relative, stays near
+// beta 2^-23 at the centre (the amplification of the rounding of s that the
+// formula itself has) and far below the FP32 tolerance of the transform.
+template <>
+__device__ __forceinline__ float phi<float>(int kind, int w, float beta, float z) {
+  constexpr float kLog2e = 1.4426950408889634f;
+  const float bl = beta * kLog2e;
+  if (kind == FKREG_SPREAD_ES) {
+    const float t = z * (2.f / float(w));
+    const float a = fmaf(-t, t, 1.f);
+    if (!(a > 0.f)) return 0.f;
+    const float r = rsqrtf(a);
+    float s = a * r;
+    s = fmaf(0.5f * r, fmaf(-s, s, a), s);
+    return exp2f(fmaf(s, bl, -bl));
+  }
+  return (fabsf(z) <= 0.5f * float(w)) ? exp2f(-bl * z * z) : 0.f;
+}
+
 // Compact radial profile k(|u|^2) of the regression kernels (unit ball;
 // normalisation in BwDev::kscale): uniform, Epanechnikov, triangle,
 // biweight, triweight.

@@ -231,15 +231,16 @@ __device__ __forceinline__ void lane_gather_global(const float* __restrict__ fld
 // mma.m16n8k8 products: M = 32 samples (two m-tiles), N = fields in tiles of
 // 8, one k-step per union column of 8 rows.  FP32 accuracy comes from the
 // three-term split x = hi + lo of both operands into TF32
-// (lo*hi + hi*lo + hi*hi): hi is x rounded to TF32 (11 significant bits,
-// ties away from zero), lo = x - hi exactly, and the tensor core reads lo's
-// top 19 bits; the dropped lo*lo term and the truncation of lo are below
-// 2^-21 of each product.
+// (lo*hi + hi*lo + hi*hi): hi is x cut to TF32 (11 significant bits, two
+// instructions where rounding takes three), lo = x - hi exactly, and the
+// tensor core reads lo's top 19 bits; the dropped lo*lo term and the two
+// cuts of lo are each below 2^-20 of the product, 3 * 2^-20 in all.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  // rounding the magnitude bits at bit 13 (finite x; a carry into the
-  // exponent is the correct rounding)
-  hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
-  lo = __float_as_uint(x - __uint_as_float(hi));  // exact: hi is x rounded to 11 bits
+  // hi: x with its 13 low mantissa bits cleared (the tensor cores read no
+  // more of a TF32 operand); lo = x - hi is exact, |lo| < 2^-10 |x|, and the
+  // tensor cores drop its own low 13 bits, an error below 2^-20 |x|
+  hi = __float_as_uint(x) & 0xFFFFE000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
 }
 // d += a * b for one m16n8k8 tile; a, b hold TF32 operands.  Fragment
 // layout (g = lane / 4, t = lane % 4): a = A[g][t], A[g+8][t], A[g][t+4],

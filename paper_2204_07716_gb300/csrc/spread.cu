@@ -590,6 +590,13 @@ __device__ __forceinline__ void probe_pair<float>(uint64_t seed, int j, uint32_t
 }
 
 template <typename T>
+__global__ void kernel_values_kernel(int kind, int w, T beta, int64_t n, const T* __restrict__ z,
+                                     T* __restrict__ out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = phi<T>(kind, w, beta, z[i]);
+}
+
+template <typename T>
 __global__ void gather_strengths_kernel(int64_t n, const uint32_t* __restrict__ perm,
                                         const T* __restrict__ y, int n_rhs, int y_complex,
                                         int with_density, int n_probes, uint64_t seed,
@@ -732,3 +739,24 @@ cudaError_t run_logres_strengths(fkreg_plan_s* P, const void* y, const void* mha
 }
 
 }  // namespace fk
+
+extern "C" fkreg_status fkreg_spread_kernel_values(int kind, int w, double beta, int precision,
+                                                   int64_t n, const void* z_dev, void* out_dev,
+                                                   void* stream) {
+  using namespace fk;
+  if (kind != FKREG_SPREAD_ES && kind != FKREG_SPREAD_GAUSS) return FKREG_ERR_INVALID_ARG;
+  if (precision != FKREG_F32 && precision != FKREG_F64) return FKREG_ERR_INVALID_ARG;
+  if (w < 2 || w > 32 || n < 0 || (n > 0 && (!z_dev || !out_dev))) return FKREG_ERR_INVALID_ARG;
+  if (n == 0) return FKREG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned blocks = unsigned((n + 255) / 256);
+  if (precision == FKREG_F32)
+    kernel_values_kernel<float><<<blocks, 256, 0, s>>>(kind, w, float(beta), n,
+                                                       static_cast<const float*>(z_dev),
+                                                       static_cast<float*>(out_dev));
+  else
+    kernel_values_kernel<double><<<blocks, 256, 0, s>>>(kind, w, beta, n,
+                                                        static_cast<const double*>(z_dev),
+                                                        static_cast<double*>(out_dev));
+  return cudaGetLastError() == cudaSuccess ? FKREG_OK : FKREG_ERR_CUDA;
+}

@@ -39,7 +39,8 @@ STAGES = ["sort", "strengths", "spread", "fft_fwd", "kmul_grid", "fft_grid", "gr
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA", 5: "CUFFT",
           6: "TIMEOUT", 7: "DEVICE", 8: "STATE"}
 
-EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_plan_create",
+EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_spread_kernel_values",
+           "fkreg_plan_create",
            "fkreg_workspace_bytes", "fkreg_set_workspace", "fkreg_set_points", "fkreg_get_sort",
            "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_backward_grid", "fkreg_variance",
            "fkreg_log_variance", "fkreg_interval", "fkreg_predict", "fkreg_set_timing",
@@ -114,6 +115,8 @@ def load():
     L.fkreg_geometry_query.argtypes = [ctypes.POINTER(Opts), ctypes.POINTER(Geometry)]
     L.fkreg_spread_kernel_ft.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64, i64,
                                          ctypes.POINTER(ctypes.c_double)]
+    L.fkreg_spread_kernel_values.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, i64, vp, vp, vp]
     L.fkreg_plan_create.argtypes = [ctypes.POINTER(Opts), i64, ctypes.POINTER(vp)]
     L.fkreg_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.fkreg_set_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -215,6 +218,23 @@ def spread_kernel_ft(kind: str, w: int, beta: float, nf: int, nk: int) -> np.nda
                                   beta, nf, nk, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if st != 0:
         raise FkregError(L.fkreg_global_error().decode())
+    return out
+
+
+def spread_kernel_values(kind: str, w: int, beta: float, z):
+    """phi(z) on the device (fkreg_spread_kernel_values) for a CUDA tensor z
+    of float32 or float64 offsets, in z's precision."""
+    import torch
+    L = load()
+    if not (z.is_cuda and z.is_contiguous() and z.dtype in (torch.float32, torch.float64)):
+        raise FkregError("z must be a contiguous float32 or float64 CUDA tensor")
+    out = torch.empty_like(z)
+    prec = FKREG_F32 if z.dtype == torch.float32 else FKREG_F64
+    st = L.fkreg_spread_kernel_values(FKREG_SPREAD_ES if kind == "es" else FKREG_SPREAD_GAUSS, w,
+                                      beta, prec, z.numel(), z.data_ptr(), out.data_ptr(),
+                                      torch.cuda.current_stream(z.device).cuda_stream)
+    if st != 0:
+        raise FkregError(f"fkreg_spread_kernel_values: {STATUS.get(st, st)}")
     return out
 
 
