@@ -534,6 +534,30 @@ EXTRA_RUNS = (("ll2d_plain64", 5, 3), ("nw1d", 20, 3), ("nw3d_df", 3, 3), ("ll2d
               ("uneven", 10, 3), ("ll2d_epan", 5, 3), ("ll2d_logvar", 10, 3))
 
 
+def sweep_roofline(plan, w, n_probes, st_ms, st_calls, dev):
+    """Roofline of the dominant own stage of the 3-D sweep: the spreading
+    (N w^d strengths multiply-adds per launch) or the interpolation (N w^d
+    fields multiply-adds per launch, one launch per bandwidth), against the
+    FP32 FMA rate measured on this GPU."""
+    own = {k: v for k, v in st_ms.items() if k in ("spread", "interp") and st_calls[k]}
+    if not own:
+        return None
+    dom = max(own, key=own.get)
+    wd = plan.geom["w"] ** w.d
+    per_sample = (1 + w.y.shape[0] + n_probes) if dom == "spread" else \
+        (plan.ns + (w.y.shape[0] + n_probes) * plan.nt)
+    flops = 2.0 * w.n * wd * per_sample
+    per_launch_ms = st_ms[dom] / st_calls[dom]
+    sm = fkreg.measure_peaks(dev)
+    peak = max(sm["fp32_tflops"], sm["fp32x2_tflops"])
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 2), "peak": round(peak, 1),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": "measured in this run: FP32 FMA microbenchmark (fkreg_measure_peaks)",
+            "launch_ms": round(per_launch_ms, 3), "launches_per_step": int(st_calls[dom]),
+            "algorithmic_flops_per_launch": flops}
+
+
 def measure_workload(wl, steps, warmup, sc, dev):
     """Timed steps of configuration wl on device dev; returns the result line."""
     import numpy as np
@@ -643,8 +667,15 @@ def measure_workload(wl, steps, warmup, sc, dev):
             w = inputs.ll2d_gcv(n=int(2_000_000 * sc))
             np_ = w.n_probes
         flags = fkreg.FKREG_WANT_BACKWARD if wl == "ll2d_gcv" else 0
-        plan = fkreg.Plan(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, max_probes=np_,
-                          tol=w.tol, precision=w.precision, flags=flags, device=dev)
+        if wl == "nw3d_df":
+            # the bandwidth sweep with a Fourier period per group of bandwidths
+            plan = fkreg.Sweep(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n,
+                               max_probes=np_, tol=w.tol, precision=w.precision, device=dev,
+                               max_groups=2)
+        else:
+            plan = fkreg.Plan(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n,
+                              max_probes=np_, tol=w.tol, precision=w.precision, flags=flags,
+                              device=dev)
         dt = torch.float32 if w.precision == "f32" else torch.float64
         x = torch.tensor(w.x, dtype=dt, device=dev)
         y = torch.tensor(w.y, dtype=dt, device=dev)
@@ -668,6 +699,11 @@ def measure_workload(wl, steps, warmup, sc, dev):
                             "ll2d_gcv": "ll2d-2M-512sq-LL-GCV-fwd+bwd-f32-tol1e-6"}[wl],
                "n": w.n, "grid": list(w.grid_n), "bandwidths": w.n_bw, "probes": np_,
                "geometry": plan.geom}
+        if wl == "nw3d_df":
+            first, geoms = plan.groups()
+            cfg["period_groups"] = [{"bandwidths": [first[i], first[i + 1]],
+                                     "period": geoms[i]["period"][0], "nf": geoms[i]["nf"][0]}
+                                    for i in range(len(first) - 1)]
         dtype = "f64" if w.precision == "f64" else DTYPE_F32
         extra["plan"] = plan
     for k in range(warmup):
@@ -724,6 +760,8 @@ def measure_workload(wl, steps, warmup, sc, dev):
         plan.set_timing(False)
         res["stages_ms_per_step"] = {k: round(v, 4) for k, v in st_ms.items()}
         res["gpu_launches_per_step"] = launches
+        if wl == "nw3d_df":
+            res["roofline"] = sweep_roofline(plan, w, np_, st_ms, st_calls, dev)
     for v in list(extra.values()) + ([batch] if wl == "uneven" else []):
         v.close()
     del flush

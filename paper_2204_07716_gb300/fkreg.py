@@ -50,7 +50,12 @@ EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_spread_kerne
            "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
            "fkreg_batch_capture", "fkreg_batch_launch", "fkreg_batch_latencies",
            "fkreg_batch_plan", "fkreg_batch_last_error", "fkreg_batch_destroy",
-           "fkreg_measure_peaks"]
+           "fkreg_measure_peaks",
+           "fkreg_sweep_create", "fkreg_sweep_split", "fkreg_sweep_groups", "fkreg_sweep_workspace_bytes",
+           "fkreg_sweep_set_workspace", "fkreg_sweep_set_points", "fkreg_sweep_smooth",
+           "fkreg_sweep_df", "fkreg_sweep_variance", "fkreg_sweep_sync_status",
+           "fkreg_sweep_set_timing", "fkreg_sweep_stage_times", "fkreg_sweep_last_error",
+           "fkreg_sweep_destroy"]
 
 
 class Opts(ctypes.Structure):
@@ -162,8 +167,31 @@ def load():
     L.fkreg_batch_destroy.argtypes = [vp]
     L.fkreg_batch_destroy.restype = None
     L.fkreg_measure_peaks.argtypes = [ctypes.POINTER(Peaks), vp, ctypes.c_size_t, vp]
+    L.fkreg_sweep_create.argtypes = [ctypes.POINTER(Opts), i64, ctypes.c_int, ctypes.POINTER(vp)]
+    L.fkreg_sweep_split.argtypes = [ctypes.POINTER(Opts), i64, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double)]
+    L.fkreg_sweep_groups.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(Geometry)]
+    L.fkreg_sweep_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.fkreg_sweep_set_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.fkreg_sweep_set_points.argtypes = [vp, i64, vp, vp]
+    L.fkreg_sweep_smooth.argtypes = [vp, vp, ctypes.POINTER(Outputs), vp]
+    L.fkreg_sweep_df.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp,
+                                 ctypes.POINTER(Outputs), vp]
+    L.fkreg_sweep_variance.argtypes = [vp, vp, vp, vp, vp]
+    L.fkreg_sweep_sync_status.argtypes = [vp, vp]
+    L.fkreg_sweep_set_timing.argtypes = [vp, ctypes.c_int]
+    L.fkreg_sweep_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]
+    L.fkreg_sweep_last_error.argtypes = [vp]
+    L.fkreg_sweep_last_error.restype = ctypes.c_char_p
+    L.fkreg_sweep_destroy.argtypes = [vp]
+    L.fkreg_sweep_destroy.restype = None
     no_status = ("fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy", "fkreg_batch_plan",
-                 "fkreg_batch_last_error", "fkreg_batch_destroy")
+                 "fkreg_batch_last_error", "fkreg_batch_destroy", "fkreg_sweep_last_error",
+                 "fkreg_sweep_destroy")
     for name in EXPORTS:
         if name not in no_status:
             getattr(L, name).restype = st
@@ -219,6 +247,22 @@ def spread_kernel_ft(kind: str, w: int, beta: float, nf: int, nk: int) -> np.nda
     if st != 0:
         raise FkregError(L.fkreg_global_error().decode())
     return out
+
+
+def sweep_split(max_n: int, max_groups: int = 2, **kw):
+    """Host-only: the split of the bandwidth list a Sweep would use
+    (fkreg_sweep_split): (first bandwidth of each group + [n_bw], modelled
+    seconds).  Keyword arguments as for make_opts."""
+    L = load()
+    o, keep = make_opts(**kw)
+    ng = ctypes.c_int()
+    first = (ctypes.c_int * (o.n_bw + 1))()
+    cost = ctypes.c_double()
+    st = L.fkreg_sweep_split(ctypes.byref(o), int(max_n), int(max_groups), ctypes.byref(ng),
+                             first, ctypes.byref(cost))
+    if st != 0:
+        raise FkregError(f"fkreg_sweep_split: {STATUS.get(st, st)}")
+    return list(first[: ng.value + 1]), float(cost.value)
 
 
 def spread_kernel_values(kind: str, w: int, beta: float, z):
@@ -855,6 +899,131 @@ class StepGraph:
 
     def replay(self):
         self.graph.replay()
+
+
+class Sweep(Plan):
+    """A bandwidth sweep with one Fourier period per group of bandwidths
+    (fkreg_sweep_*): the bandwidth list split into contiguous groups, one
+    plan per group, run one after another.  ``max_groups=1`` is one plan.
+    Methods and output layouts as for Plan (set_points, smooth, df,
+    variance); ``groups`` gives the split."""
+
+    def __init__(self, d: int, order: int, grid_n, lo, hi, H, max_n: int, n_rhs: int = 1,
+                 max_probes: int = 0, tol: float = 1e-6, precision: str = "f32",
+                 y_complex: bool = False, spread_kernel: str = "es", mask_rho: float = 0.0,
+                 tile: int = 0, flags: int = 0, device=None, max_groups: int = 2):
+        import torch
+        self.torch = torch
+        self.L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.d, self.order, self.n_rhs = d, order, n_rhs
+        self.grid_n = tuple(int(v) for v in grid_n)
+        self.M = int(np.prod(self.grid_n))
+        self.max_probes = max_probes
+        self.precision = precision
+        self.y_complex = bool(y_complex)
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+        self.cdtype = torch.complex64 if precision == "f32" else torch.complex128
+        self._opts, self._keep = make_opts(d, order, grid_n, lo, hi, H, n_rhs, max_probes, tol,
+                                           precision, y_complex, spread_kernel, mask_rho, tile,
+                                           flags, "gaussian")
+        self.n_bw = self._opts.n_bw
+        g = Geometry()
+        self._check_global(self.L.fkreg_geometry_query(ctypes.byref(self._opts), ctypes.byref(g)))
+        self.geom = g.as_dict()
+        self.ns, self.nt = g.ns, g.nt
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._check_global(self.L.fkreg_sweep_create(ctypes.byref(self._opts), int(max_n),
+                                                         int(max_groups), ctypes.byref(h)))
+        self.h = h
+        nbytes = ctypes.c_size_t()
+        self._check(self.L.fkreg_sweep_workspace_bytes(self.h, ctypes.byref(nbytes)))
+        self.ws_bytes = int(nbytes.value)
+        self._ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        self._ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self._check(self.L.fkreg_sweep_set_workspace(self.h, ctypes.c_void_p(self._ws_ptr),
+                                                     self.ws_bytes, self._stream()))
+        self.n = 0
+
+    def _check(self, st):
+        if st != 0:
+            raise FkregError(f"{STATUS.get(st, st)}: {self.L.fkreg_sweep_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.fkreg_sweep_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def groups(self):
+        """(first bandwidth of each group + [n_bw], geometry dict per group)."""
+        ng = ctypes.c_int()
+        self._check(self.L.fkreg_sweep_groups(self.h, ctypes.byref(ng), None, None))
+        first = (ctypes.c_int * (ng.value + 1))()
+        geoms = (Geometry * ng.value)()
+        self._check(self.L.fkreg_sweep_groups(self.h, ctypes.byref(ng), first, geoms))
+        return list(first), [gg.as_dict() for gg in geoms]
+
+    def set_points(self, x):
+        x = self._as_dev(x)
+        n = int(x.shape[0])
+        self._x = x
+        self._check(self.L.fkreg_sweep_set_points(self.h, n, ctypes.c_void_p(x.data_ptr()),
+                                                  self._stream()))
+        self.n = n
+
+    def sync(self):
+        self._check(self.L.fkreg_sweep_sync_status(self.h, self._stream()))
+
+    def set_timing(self, enable: bool = True):
+        self._check(self.L.fkreg_sweep_set_timing(self.h, int(bool(enable))))
+
+    def stage_times(self):
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        calls = (ctypes.c_int64 * n)()
+        kl = ctypes.c_int64()
+        self._check(self.L.fkreg_sweep_stage_times(self.h, ms, calls, ctypes.byref(kl)))
+        return ({STAGES[i]: ms[i] for i in range(n)}, {STAGES[i]: calls[i] for i in range(n)},
+                int(kl.value))
+
+    def smooth(self, y, want=("mhat_grid", "mask")) -> Dict[str, object]:
+        y = self._y(y)
+        o = self._outputs(want, df=False)
+        s = self._struct(o)
+        self._check(self.L.fkreg_sweep_smooth(self.h, ctypes.c_void_p(y.data_ptr()),
+                                              ctypes.byref(s), self._stream()))
+        self._y_keep = y
+        return o
+
+    def df(self, y, n_probes: int, seed: int = 0, probes=None,
+           want=("mhat_grid", "mask")) -> Dict[str, object]:
+        y = self._y(y)
+        pr = None if probes is None else self._as_dev(probes)
+        o = self._outputs(want, df=True)
+        s = self._struct(o)
+        self._check(self.L.fkreg_sweep_df(self.h, ctypes.c_void_p(y.data_ptr()), int(n_probes),
+                                          ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                          None if pr is None else ctypes.c_void_p(pr.data_ptr()),
+                                          ctypes.byref(s), self._stream()))
+        self._y_keep = (y, pr)
+        return o
+
+    def variance(self, y, mhat_at_x):
+        t = self.torch
+        y = self._y(y)
+        mh = self._as_dev(mhat_at_x, complex_ok=self.y_complex)
+        out = t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
+        self._check(self.L.fkreg_sweep_variance(self.h, ctypes.c_void_p(y.data_ptr()),
+                                                ctypes.c_void_p(mh.data_ptr()),
+                                                ctypes.c_void_p(out.data_ptr()), self._stream()))
+        self._y_keep = (y, mh)
+        return out
+
+    def _unsupported(self, *a, **k):
+        raise FkregError("UNSUPPORTED: a sweep offers set_points, smooth, df and variance")
+
+    backward = backward_grid = log_variance = get_sort = set_wait_limit = _unsupported
 
 
 class Batch:

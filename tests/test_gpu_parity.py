@@ -352,11 +352,16 @@ def test_fp32_df_sweep():
 
 def test_nw3d_df_full_size_sampled():
     # the 3-D DF sweep at its full size (N = 4e6, 64^3 grid, 16 bandwidths,
-    # y + 32 device probes, FP32, tol 1e-6): per bandwidth, m-hat and the mask
-    # at 512 sampled grid points and m-hat(x_i) at 16 sampled samples against
-    # the oracle's cutoff sums
+    # y + 32 device probes, FP32, tol 1e-6), run as the bench runs it (a
+    # Sweep with a period per group of bandwidths): per bandwidth, m-hat and
+    # the mask at 512 sampled grid points and m-hat(x_i) at 16 sampled samples
+    # against the oracle's cutoff sums
+    from paper_2204_07716_gb300.fkreg import Sweep
     w = inputs.nw3d_df()
-    p = plan_for(w, n_probes=w.n_probes)
+    p = Sweep(w.d, w.order, w.grid_n, w.lo, w.hi, w.H, max_n=w.n, n_rhs=1,
+              max_probes=w.n_probes, tol=w.tol, precision=w.precision)
+    first, _ = p.groups()
+    assert len(first) == 3, first
     p.set_points(torch.tensor(w.x, dtype=torch.float32))
     out = p.df(torch.tensor(w.y, dtype=torch.float32), w.n_probes, seed=17,
                want=("mhat_grid", "mask", "moments", "mhat_at_x"))

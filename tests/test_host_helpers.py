@@ -195,3 +195,32 @@ def test_cv_fkreg_standardised_float32_samples_stay_in_the_box(monkeypatch, box)
         assert bool(torch.all(xs >= float(lo32))) and bool(torch.all(xs <= float(hi32)))
         sd = float(np.std(x.numpy().astype(np.float64), ddof=1))
         np.testing.assert_allclose(xs.numpy(), x.numpy().astype(np.float64) / sd, rtol=1e-6)
+
+
+def test_sweep_split_of_the_3d_sweep():
+    # sixteen bandwidths log-spaced over a decade: the narrow ones get their
+    # own, shorter period and smaller fine grid; one bandwidth, or a list
+    # whose members need the same period, stays one group
+    from paper_2204_07716_gb300 import fkreg, inputs
+    w = inputs.nw3d_df(n=10)
+    kw = dict(d=3, order=0, grid_n=w.grid_n, lo=w.lo, hi=w.hi, n_rhs=1, max_probes=32,
+              tol=1e-6, precision="f32")
+    first, cost2 = fkreg.sweep_split(4_000_000, 2, H=w.H, **kw)
+    assert len(first) == 3 and first[0] == 0 and first[-1] == 16 and 0 < first[1] < 16
+    one, cost1 = fkreg.sweep_split(4_000_000, 1, H=w.H, **kw)
+    assert one == [0, 16] and cost2 < 0.7 * cost1
+    g_all = fkreg.geometry(H=w.H, **kw)
+    g_narrow = fkreg.geometry(H=w.H[:first[1]], **kw)
+    g_wide = fkreg.geometry(H=w.H[first[1]:], **kw)
+    assert g_narrow["period"][0] < g_all["period"][0]
+    assert g_narrow["nf"][0] < g_all["nf"][0] and g_wide["nf"][0] < g_all["nf"][0]
+    # more groups allowed never raise the modelled cost
+    first3, cost3 = fkreg.sweep_split(4_000_000, 3, H=w.H, **kw)
+    assert cost3 <= cost2 + 1e-12
+    # a single bandwidth, and the headline's diagonal bandwidth
+    assert fkreg.sweep_split(4_000_000, 4, H=w.H[:1], **kw)[0] == [0, 1]
+    w2 = inputs.ll2d(n=10)
+    assert fkreg.sweep_split(1_000_000, 2, d=2, order=1, grid_n=w2.grid_n, lo=w2.lo, hi=w2.hi,
+                             H=w2.H, n_rhs=1, max_probes=10)[0] == [0, 1]
+    with pytest.raises(fkreg.FkregError):
+        fkreg.sweep_split(1000, 0, H=w.H, **kw)
