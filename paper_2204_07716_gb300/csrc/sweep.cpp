@@ -29,12 +29,14 @@ namespace {
 
 // Seconds per unit of the modelled step on GB300, from the 3-D sweep's
 // measured stage times: spreading per (sample, window cell, strength), the
-// type-1 transform (with its memset) per (fine cell, strength), and per
-// bandwidth the type-2 transform, record interleave and gather per (fine
-// cell, field); a fixed cost per group for its sort and launches.
+// type-1 transform (with its memset) per (fine cell, strength), per bandwidth
+// the type-2 transform and record interleave per (fine cell, field) and the
+// gather per (sample, window cell, field); a fixed cost per group for its
+// sort and launches.
 constexpr double kSpreadUnit = 1.3e-12;
 constexpr double kType1Unit = 1.7e-11;
-constexpr double kType2Unit = 2.9e-11;
+constexpr double kType2Unit = 1.6e-11;
+constexpr double kGatherUnit = 3.3e-13;
 constexpr double kGroupFixed = 3e-4;
 
 int64_t cells(const int64_t* nf, int d) {
@@ -61,7 +63,8 @@ double group_cost(const fkreg_opts& o, int64_t max_n, int b0, int b1) {
   for (int j = 0; j < d; ++j) wd *= geo.w;
   double c = kGroupFixed + S * (kSpreadUnit * double(max_n) * wd +
                                 kType1Unit * double(cells(geo.nf, d)));
-  for (const auto& B : bw) c += kType2Unit * F * double(cells(B.nf, d));
+  for (const auto& B : bw)
+    c += F * (kType2Unit * double(cells(B.nf, d)) + kGatherUnit * double(max_n) * wd);
   return c;
 }
 
