@@ -72,7 +72,8 @@ enum {
   FKREG_KERNEL_EPANECHNIKOV = 2,  /* k = 1 - |u|^2                             */
   FKREG_KERNEL_TRIANGLE = 3,      /* k = 1 - |u|                               */
   FKREG_KERNEL_BIWEIGHT = 4,      /* k = (1 - |u|^2)^2                         */
-  FKREG_KERNEL_TRIWEIGHT = 5      /* k = (1 - |u|^2)^3                         */
+  FKREG_KERNEL_TRIWEIGHT = 5,     /* k = (1 - |u|^2)^3                         */
+  FKREG_KERNEL_GAUSSIAN_DIRECT = 6 /* the Gaussian by direct sums (see below)   */
 };
 
 /* fkreg_opts.flags */
@@ -98,6 +99,14 @@ enum {
  *                  fkreg_backward and FKREG_WANT_BACKWARD are refused for
  *                  them, and so is a plan whose s-fields plus the t-fields
  *                  of (n_rhs + max_probes) strengths exceed 64 (UNSUPPORTED).
+ *                  FKREG_KERNEL_GAUSSIAN_DIRECT is the Gaussian kernel of
+ *                  FKREG_KERNEL_GAUSSIAN evaluated by the same direct sums,
+ *                  over the samples within Mahalanobis distance R of each
+ *                  point, R^2 = 2 ln(10 / tol): every dropped term is below
+ *                  tol / 10 of K_H(0).  It needs no Fourier grid, so it
+ *                  serves bandwidths so narrow that few samples fall within
+ *                  R (fkreg_sweep chooses it per group by its cost model);
+ *                  the limits of the compact kernels apply.
  *   spread_kernel  NUFFT spreading kernel: exponential of semicircle (default)
  *                  or the Gaussian of Sec. 1.2 eq. 17 (about twice as wide)
  *   precision      FKREG_F32 (spreading, FFT, interpolation in float, FP64

@@ -21,7 +21,10 @@
  * same probe vectors.  The split minimises a cost model of the step (per
  * group: spreading N w^d strengths, transforming the type-1 grid; per
  * bandwidth: the type-2 grid, its transform and gather) calibrated on GB300
- * measurements; a split is taken only when it cuts the modelled cost.
+ * measurements; a split is taken only when it cuts the modelled cost.  A
+ * Gaussian group whose bandwidths hold few samples within the cut radius is
+ * given direct sums (FKREG_KERNEL_GAUSSIAN_DIRECT) when the model finds them
+ * cheaper than its NUFFT; a sweep over a compact kernel is one group.
  *
  * Outputs have the layouts of fkreg_smooth / fkreg_df / fkreg_variance
  * (leading dimension n_bw, the caller's bandwidth order): each group writes
@@ -58,19 +61,24 @@ fkreg_status fkreg_sweep_create(const fkreg_opts* opts, int64_t max_n, int max_g
 /*
  * Host-only (no CUDA call): the split fkreg_sweep_create chooses for these
  * arguments.  *n_groups groups; first_bw (array of n_bw + 1, may be NULL)
- * receives the first bandwidth of each group and then n_bw; *modelled_s
- * (may be NULL) the cost model's seconds for the split.
+ * receives the first bandwidth of each group and then n_bw; group_kernel
+ * (array of n_bw, may be NULL) the regression kernel of each group's plan
+ * (for a Gaussian sweep FKREG_KERNEL_GAUSSIAN, the NUFFT, or
+ * FKREG_KERNEL_GAUSSIAN_DIRECT, direct sums, whichever the cost model finds
+ * cheaper for the group); *modelled_s (may be NULL) the model's seconds.
  */
 fkreg_status fkreg_sweep_split(const fkreg_opts* opts, int64_t max_n, int max_groups,
-                               int* n_groups, int* first_bw, double* modelled_s);
+                               int* n_groups, int* first_bw, int* group_kernel,
+                               double* modelled_s);
 
 /*
  * The split: *n_groups groups; first_bw[g] (array of n_groups + 1, may be
  * NULL) is the first bandwidth of group g, first_bw[n_groups] = n_bw;
- * geoms[g] (array of n_groups, may be NULL) the group plan's geometry.
- * Call once with first_bw = geoms = NULL to learn n_groups.
+ * group_kernel[g] (may be NULL) its plan's regression kernel; geoms[g]
+ * (array of n_groups, may be NULL) the group plan's geometry.  Call once
+ * with the arrays NULL to learn n_groups.
  */
-fkreg_status fkreg_sweep_groups(fkreg_sweep S, int* n_groups, int* first_bw,
+fkreg_status fkreg_sweep_groups(fkreg_sweep S, int* n_groups, int* first_bw, int* group_kernel,
                                 fkreg_geometry* geoms);
 
 /* Device bytes of the sweep's workspace (the groups' workspaces, each 256-byte aligned). */

@@ -57,9 +57,10 @@ __device__ __forceinline__ float phi<float>(int kind, int w, float beta, float z
 
 // Compact radial profile k(|u|^2) of the regression kernels (unit ball;
 // normalisation in BwDev::kscale): uniform, Epanechnikov, triangle,
-// biweight, triweight.
+// biweight, triweight, and the Gaussian cut at Mahalanobis radius R
+// (u = z / R in the bandwidth's metric, k = exp(-R^2 |u|^2 / 2), r2 = R^2).
 template <typename T>
-__device__ __forceinline__ T compact_k(int kern, T u2) {
+__device__ __forceinline__ T compact_k(int kern, T u2, T r2) {
   if (!(u2 <= T(1))) return T(0);
   const T e = T(1) - u2;
   switch (kern) {
@@ -67,6 +68,7 @@ __device__ __forceinline__ T compact_k(int kern, T u2) {
     case FKREG_KERNEL_EPANECHNIKOV: return e;
     case FKREG_KERNEL_TRIANGLE: return T(1) - sqrt(u2);
     case FKREG_KERNEL_BIWEIGHT: return e * e;
+    case FKREG_KERNEL_GAUSSIAN_DIRECT: return exp(T(-0.5) * r2 * u2);
     default: return e * e * e;
   }
 }
@@ -259,7 +261,7 @@ __device__ __forceinline__ void direct_warp_sums(const GeoDev& g, const BwDev& B
 #pragma unroll
     for (int c = 0; c < D; ++c) hi[a][c] = T(B.Hinv[a * 3 + c]);
   }
-  const T ks = T(B.kscale);
+  const T ks = T(B.kscale), kr2 = T(B.kr2);
   const int kern = g.kern;
   T acc[FMAX];
 #pragma unroll
@@ -310,7 +312,7 @@ __device__ __forceinline__ void direct_warp_sums(const GeoDev& g, const BwDev& B
             u2 += z[a] * ra;
           }
           in = u2 <= T(1);
-          if (in) wgt = ks * compact_k<T>(kern, u2);
+          if (in) wgt = ks * compact_k<T>(kern, u2, kr2);
         }
         const unsigned m = __ballot_sync(0xffffffffu, in);
         if (in) {

@@ -142,7 +142,7 @@ direct_interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int 
   for (int a = 0; a < D; ++a)
 #pragma unroll
     for (int e = 0; e < D; ++e) hi[a][e] = T(B.Hinv[a * 3 + e]);
-  const T ks = T(B.kscale);
+  const T ks = T(B.kscale), kr2 = T(B.kr2);
   const int kern = g.kern;
   const int64_t ngroups = (n + 31) / 32;
   for (int64_t grp = int64_t(blockIdx.x) * nwarps + warp; grp < ngroups;
@@ -211,7 +211,7 @@ direct_interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int 
               u2 += z[a] * ra;
             }
             if (u2 <= T(1)) {
-              const T wgt = ks * compact_k<T>(kern, u2);
+              const T wgt = ks * compact_k<T>(kern, u2, kr2);
               T mo[NS];
               mono_build<T, D, 2 * ORD>(mo, z);
               if constexpr (sizeof(T) == 4) {

@@ -72,6 +72,7 @@ struct BwDev {
   int64_t phi2_off[3]; // offset (doubles) of 1/phihat tables (k >= 0) for type-2
   double Hinv[9];      // H^-1 (compact kernels)
   double kscale;       // c_d / sqrt(det H): K_H(z) = kscale k(|H^(-1/2) z|^2) (compact kernels)
+  double kr2;          // R^2 of the truncated Gaussian (FKREG_KERNEL_GAUSSIAN_DIRECT), else 0
 };
 
 // Monomial exponents (degree <= 2) for device code.

@@ -189,6 +189,7 @@ static double compact_constant(int kernel, int d) {
     case FKREG_KERNEL_EPANECHNIKOV: return (d + 2) / (2.0 * vd);
     case FKREG_KERNEL_TRIANGLE: return (d + 1) / vd;
     case FKREG_KERNEL_BIWEIGHT: return (d + 2) * (d + 4) / (8.0 * vd);
+    case FKREG_KERNEL_GAUSSIAN_DIRECT: return std::pow(2.0 * M_PI, -0.5 * d);
     default: return (d + 2) * (d + 4) * (d + 6) / (48.0 * vd);
   }
 }
@@ -209,19 +210,24 @@ static fkreg_status compute_geometry_direct(const fkreg_opts* o, fkreg_geometry*
   g->beta = 0.0;
   std::vector<BwDev> bws(nbw);
   const double cd = compact_constant(o->kernel, d);
+  // the support is the unit ball of the metric H^-1 / r2: r2 = 1 for the
+  // compact kernels, R^2 for the Gaussian cut at Mahalanobis radius R
+  const bool gcut = o->kernel == FKREG_KERNEL_GAUSSIAN_DIRECT;
+  const double r2 = gcut ? 2.0 * std::log(10.0 / o->tol) : 1.0;
   for (int b = 0; b < nbw; ++b) {
     BwDev& B = bws[b];
     std::memset(&B, 0, sizeof(B));
     const double* Hb = o->H + size_t(b) * d * d;
     for (int a = 0; a < d; ++a)
       for (int c = 0; c < d; ++c) {
-        B.H[a * 3 + c] = Hb[a * d + c];
-        B.Hinv[a * 3 + c] = Hinv[size_t(b) * d * d + a * d + c];
+        B.H[a * 3 + c] = r2 * Hb[a * d + c];
+        B.Hinv[a * 3 + c] = Hinv[size_t(b) * d * d + a * d + c] / r2;
       }
     B.kscale = cd / std::sqrt(det[b]);
     B.k0 = B.kscale;
+    B.kr2 = gcut ? r2 : 0.0;
     for (int j = 0; j < 3; ++j) {
-      B.sigma[j] = j < d ? std::sqrt(Hb[j * d + j]) : 1.0;
+      B.sigma[j] = j < d ? std::sqrt(r2 * Hb[j * d + j]) : 1.0;
       B.K[j] = 1;
       B.nf[j] = j < d ? o->grid_n[j] : 1;
     }
@@ -293,7 +299,7 @@ fkreg_status compute_geometry(const fkreg_opts* o, fkreg_geometry* g, std::strin
   if (o->order < 0 || o->order > 2) return fail(err, FKREG_ERR_INVALID_ARG, "order must be 0, 1 or 2");
   if (o->order == 2 && o->dim > 2)
     return fail(err, FKREG_ERR_UNSUPPORTED, "order 2 (local quadratic) is supported in 1-D and 2-D");
-  if (o->kernel < FKREG_KERNEL_GAUSSIAN || o->kernel > FKREG_KERNEL_TRIWEIGHT)
+  if (o->kernel < FKREG_KERNEL_GAUSSIAN || o->kernel > FKREG_KERNEL_GAUSSIAN_DIRECT)
     return fail(err, FKREG_ERR_INVALID_ARG, "unknown regression kernel");
   if (o->kernel != FKREG_KERNEL_GAUSSIAN && (o->flags & FKREG_WANT_BACKWARD))
     return fail(err, FKREG_ERR_UNSUPPORTED, "the backward needs the Gaussian kernel");

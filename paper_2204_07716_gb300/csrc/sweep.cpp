@@ -4,6 +4,7 @@
 // caller's stream.  The groups' plans are ordinary plans; this file only
 // chooses the split and routes the calls and the output slices.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -16,6 +17,7 @@ struct fkreg_sweep_s {
   std::vector<double> H;
   std::vector<fkreg_plan> plans;
   std::vector<int> first;     // first bandwidth of each group, then n_bw
+  std::vector<int> kern;      // regression kernel of each group's plan
   std::vector<size_t> ws_off; // workspace offset of each group
   size_t ws_bytes = 0;
   int64_t M = 1;              // grid points
@@ -38,6 +40,9 @@ constexpr double kType1Unit = 1.7e-11;
 constexpr double kType2Unit = 1.6e-11;
 constexpr double kGatherUnit = 3.3e-13;
 constexpr double kGroupFixed = 3e-4;
+// The direct sums (FKREG_KERNEL_GAUSSIAN_DIRECT) per (sample pair, field),
+// from the at-sample pass of the compact-kernel path.
+constexpr double kPairUnit = 2.4e-13;
 
 int64_t cells(const int64_t* nf, int d) {
   int64_t c = 1;
@@ -45,9 +50,9 @@ int64_t cells(const int64_t* nf, int d) {
   return c;
 }
 
-// Modelled seconds of one group [b0, b1) of the sweep; < 0 if the group's
-// geometry is refused.
-double group_cost(const fkreg_opts& o, int64_t max_n, int b0, int b1) {
+// Modelled seconds of one group [b0, b1) of the sweep with the NUFFT path;
+// < 0 if the group's geometry is refused.
+double nufft_cost(const fkreg_opts& o, int64_t max_n, int b0, int b1) {
   fkreg_opts g = o;
   const int d = o.dim;
   g.n_bw = b1 - b0;
@@ -66,6 +71,55 @@ double group_cost(const fkreg_opts& o, int64_t max_n, int b0, int b1) {
   for (const auto& B : bw)
     c += F * (kType2Unit * double(cells(B.nf, d)) + kGatherUnit * double(max_n) * wd);
   return c;
+}
+
+// The same with direct sums over the samples within Mahalanobis radius R
+// (FKREG_KERNEL_GAUSSIAN_DIRECT): per bandwidth, (samples + grid points) x
+// the samples inside a support x the fields, the samples taken as spread
+// evenly over the box; < 0 where that path is refused.
+double direct_cost(const fkreg_opts& o, int64_t max_n, int b0, int b1) {
+  fkreg_opts g = o;
+  const int d = o.dim;
+  g.kernel = FKREG_KERNEL_GAUSSIAN_DIRECT;
+  g.n_bw = b1 - b0;
+  g.H = o.H + size_t(b0) * d * d;
+  g.flags &= ~FKREG_WANT_BACKWARD;
+  fkreg_geometry geo{};
+  std::vector<fk::BwDev> bw;
+  std::string err;
+  if (o.flags & FKREG_WANT_BACKWARD) return -1.0;
+  if (fk::compute_geometry(&g, &geo, &err, &bw, nullptr, nullptr, nullptr) != FKREG_OK) return -1.0;
+  const int nrhs_real = o.n_rhs * (o.y_complex ? 2 : 1);
+  const double F2 = geo.ns + double(nrhs_real + o.max_probes) * geo.nt;
+  const double Fg = geo.ns + double(nrhs_real) * geo.nt;
+  if (F2 > 64) return -1.0;
+  double vol = 1.0, M = 1.0;
+  for (int j = 0; j < d; ++j) {
+    vol *= o.grid_hi[j] - o.grid_lo[j];
+    M *= double(o.grid_n[j]);
+  }
+  const double vd = d == 1 ? 2.0 : (d == 2 ? M_PI : 4.0 * M_PI / 3.0);
+  double c = kGroupFixed;
+  for (const auto& B : bw) {
+    double ext = vd;  // volume of the support ellipsoid {z' H^-1 z <= R^2}
+    for (int j = 0; j < d; ++j) ext *= B.sigma[j];
+    // (a correlated H has a smaller ellipsoid than its axis extents give)
+    const double nbr = std::min(double(max_n), double(max_n) * ext / vol);
+    c += kPairUnit * nbr * (double(max_n) * F2 + M * Fg);
+  }
+  return c;
+}
+
+// The cheaper path for the group: its modelled seconds and its kernel.
+double group_cost(const fkreg_opts& o, int64_t max_n, int b0, int b1, int* kernel) {
+  const double cn = nufft_cost(o, max_n, b0, b1);
+  const double cd = direct_cost(o, max_n, b0, b1);
+  if (cd >= 0 && (cn < 0 || cd < cn)) {
+    *kernel = FKREG_KERNEL_GAUSSIAN_DIRECT;
+    return cd;
+  }
+  *kernel = FKREG_KERNEL_GAUSSIAN;
+  return cn;
 }
 
 fkreg_status sweep_err(fkreg_sweep S, fkreg_status st, const std::string& m) {
@@ -104,7 +158,8 @@ fkreg_outputs slice(const fkreg_sweep S, const fkreg_outputs* out, int b0) {
 extern "C" {
 
 fkreg_status fkreg_sweep_split(const fkreg_opts* opts, int64_t max_n, int max_groups,
-                               int* n_groups, int* first_bw, double* modelled_s) {
+                               int* n_groups, int* first_bw, int* group_kernel,
+                               double* modelled_s) {
   if (!opts || !opts->H || !n_groups || opts->n_bw < 1 || max_groups < 1 || max_n < 0 ||
       opts->dim < 1 || opts->dim > 3)
     return FKREG_ERR_INVALID_ARG;
@@ -113,8 +168,12 @@ fkreg_status fkreg_sweep_split(const fkreg_opts* opts, int64_t max_n, int max_gr
   // best[k][b] = least modelled cost of bandwidths [0, b) in k groups
   const int K = std::min(max_groups, nbw);
   std::vector<std::vector<double>> cost(nbw + 1, std::vector<double>(nbw + 1, -2.0));
+  std::vector<std::vector<int>> kern(nbw + 1, std::vector<int>(nbw + 1, opts->kernel));
+  const bool gauss = opts->kernel == FKREG_KERNEL_GAUSSIAN;
   auto gc = [&](int a, int b) {
-    if (cost[a][b] == -2.0) cost[a][b] = group_cost(*opts, max_n, a, b);
+    if (cost[a][b] == -2.0)
+      cost[a][b] = gauss ? group_cost(*opts, max_n, a, b, &kern[a][b])
+                         : (max_groups == 1 ? 0.0 : -1.0);
     return cost[a][b];
   };
   const double inf = 1e300;
@@ -147,6 +206,9 @@ fkreg_status fkreg_sweep_split(const fkreg_opts* opts, int64_t max_n, int max_gr
   std::reverse(cuts.begin(), cuts.end());
   *n_groups = int(cuts.size()) - 1;
   if (first_bw) std::copy(cuts.begin(), cuts.end(), first_bw);
+  if (group_kernel)
+    for (int gi = 0; gi + 1 < int(cuts.size()); ++gi)
+      group_kernel[gi] = kbest > 0 ? kern[cuts[gi]][cuts[gi + 1]] : opts->kernel;
   if (modelled_s) *modelled_s = kbest > 0 ? best[kbest][nbw] : -1.0;
   return FKREG_OK;
 }
@@ -157,7 +219,9 @@ fkreg_status fkreg_sweep_create(const fkreg_opts* opts, int64_t max_n, int max_g
   *out = nullptr;
   int ng0 = 0;
   std::vector<int> first(opts && opts->n_bw > 0 ? opts->n_bw + 1 : 1);
-  fkreg_status st0 = fkreg_sweep_split(opts, max_n, max_groups, &ng0, first.data(), nullptr);
+  std::vector<int> gk(first.size(), FKREG_KERNEL_GAUSSIAN);
+  fkreg_status st0 =
+      fkreg_sweep_split(opts, max_n, max_groups, &ng0, first.data(), gk.data(), nullptr);
   if (st0 != FKREG_OK) return st0;
   auto* S = new fkreg_sweep_s();
   S->o = *opts;
@@ -167,11 +231,13 @@ fkreg_status fkreg_sweep_create(const fkreg_opts* opts, int64_t max_n, int max_g
   for (int j = 0; j < d; ++j) S->M *= opts->grid_n[j];
   S->tsize = opts->precision == FKREG_F32 ? 4 : 8;
   S->first.assign(first.begin(), first.begin() + ng0 + 1);
+  S->kern.assign(gk.begin(), gk.begin() + ng0);
   const int ng = int(S->first.size()) - 1;
   for (int gi = 0; gi < ng; ++gi) {
     fkreg_opts g = S->o;
     g.n_bw = S->first[gi + 1] - S->first[gi];
     g.H = S->H.data() + size_t(S->first[gi]) * d * d;
+    g.kernel = S->kern[gi];
     fkreg_plan p = nullptr;
     const fkreg_status st = fkreg_plan_create(&g, max_n, &p);
     if (st != FKREG_OK) {
@@ -194,17 +260,20 @@ fkreg_status fkreg_sweep_create(const fkreg_opts* opts, int64_t max_n, int max_g
 }
 
 fkreg_status fkreg_sweep_groups(fkreg_sweep S, int* n_groups, int* first_bw,
-                                fkreg_geometry* geoms) {
+                                int* group_kernel, fkreg_geometry* geoms) {
   if (!S || !n_groups) return FKREG_ERR_INVALID_ARG;
   const int ng = int(S->plans.size());
   *n_groups = ng;
   if (first_bw)
     for (int gi = 0; gi <= ng; ++gi) first_bw[gi] = S->first[gi];
+  if (group_kernel)
+    for (int gi = 0; gi < ng; ++gi) group_kernel[gi] = S->kern[gi];
   if (geoms)
     for (int gi = 0; gi < ng; ++gi) {
       fkreg_opts g = S->o;
       g.n_bw = S->first[gi + 1] - S->first[gi];
       g.H = S->H.data() + size_t(S->first[gi]) * S->o.dim * S->o.dim;
+      g.kernel = S->kern[gi];
       const fkreg_status st = fkreg_geometry_query(&g, &geoms[gi]);
       if (st != FKREG_OK) return sweep_err(S, st, fkreg_global_error());
     }

@@ -30,7 +30,7 @@ LIB_PATH = os.path.join(HERE, "libfkreg.so")
 FKREG_F32, FKREG_F64 = 0, 1
 FKREG_SPREAD_ES, FKREG_SPREAD_GAUSS = 0, 1
 KERNELS = {"gaussian": 0, "uniform": 1, "box": 1, "epanechnikov": 2, "triangle": 3,
-           "biweight": 4, "triweight": 5}
+           "biweight": 4, "triweight": 5, "gaussian_direct": 6}
 FKREG_GCV_EXACT_TRACE = 1
 FKREG_WANT_BACKWARD = 2
 STAGES = ["sort", "strengths", "spread", "fft_fwd", "kmul_grid", "fft_grid", "grid_solve",
@@ -170,9 +170,9 @@ def load():
     L.fkreg_sweep_create.argtypes = [ctypes.POINTER(Opts), i64, ctypes.c_int, ctypes.POINTER(vp)]
     L.fkreg_sweep_split.argtypes = [ctypes.POINTER(Opts), i64, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                    ctypes.POINTER(ctypes.c_double)]
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.fkreg_sweep_groups.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(Geometry)]
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Geometry)]
     L.fkreg_sweep_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.fkreg_sweep_set_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.fkreg_sweep_set_points.argtypes = [vp, i64, vp, vp]
@@ -249,20 +249,29 @@ def spread_kernel_ft(kind: str, w: int, beta: float, nf: int, nk: int) -> np.nda
     return out
 
 
-def sweep_split(max_n: int, max_groups: int = 2, **kw):
+KERNEL_NAMES = {0: "gaussian", 1: "uniform", 2: "epanechnikov", 3: "triangle", 4: "biweight",
+                5: "triweight", 6: "gaussian_direct"}
+
+
+def sweep_split(max_n: int, max_groups: int = 2, with_kernels: bool = False, **kw):
     """Host-only: the split of the bandwidth list a Sweep would use
     (fkreg_sweep_split): (first bandwidth of each group + [n_bw], modelled
-    seconds).  Keyword arguments as for make_opts."""
+    seconds), and with ``with_kernels`` each group's kernel name after them.
+    Keyword arguments as for make_opts."""
     L = load()
     o, keep = make_opts(**kw)
     ng = ctypes.c_int()
     first = (ctypes.c_int * (o.n_bw + 1))()
+    kern = (ctypes.c_int * o.n_bw)()
     cost = ctypes.c_double()
     st = L.fkreg_sweep_split(ctypes.byref(o), int(max_n), int(max_groups), ctypes.byref(ng),
-                             first, ctypes.byref(cost))
+                             first, kern, ctypes.byref(cost))
     if st != 0:
         raise FkregError(f"fkreg_sweep_split: {STATUS.get(st, st)}")
-    return list(first[: ng.value + 1]), float(cost.value)
+    out = (list(first[: ng.value + 1]), float(cost.value))
+    if with_kernels:
+        out = out + ([KERNEL_NAMES[k] for k in kern[: ng.value]],)
+    return out
 
 
 def spread_kernel_values(kind: str, w: int, beta: float, z):
@@ -955,14 +964,19 @@ class Sweep(Plan):
             self.L.fkreg_sweep_destroy(self.h)
             self.h = ctypes.c_void_p()
 
-    def groups(self):
-        """(first bandwidth of each group + [n_bw], geometry dict per group)."""
+    def groups(self, with_kernels: bool = False):
+        """(first bandwidth of each group + [n_bw], geometry dict per group),
+        and with ``with_kernels`` each group's kernel name after them."""
         ng = ctypes.c_int()
-        self._check(self.L.fkreg_sweep_groups(self.h, ctypes.byref(ng), None, None))
+        self._check(self.L.fkreg_sweep_groups(self.h, ctypes.byref(ng), None, None, None))
         first = (ctypes.c_int * (ng.value + 1))()
+        kern = (ctypes.c_int * ng.value)()
         geoms = (Geometry * ng.value)()
-        self._check(self.L.fkreg_sweep_groups(self.h, ctypes.byref(ng), first, geoms))
-        return list(first), [gg.as_dict() for gg in geoms]
+        self._check(self.L.fkreg_sweep_groups(self.h, ctypes.byref(ng), first, kern, geoms))
+        out = (list(first), [gg.as_dict() for gg in geoms])
+        if with_kernels:
+            out = out + ([KERNEL_NAMES[k] for k in kern],)
+        return out
 
     def set_points(self, x):
         x = self._as_dev(x)

@@ -224,3 +224,28 @@ def test_sweep_split_of_the_3d_sweep():
                              H=w2.H, n_rhs=1, max_probes=10)[0] == [0, 1]
     with pytest.raises(fkreg.FkregError):
         fkreg.sweep_split(1000, 0, H=w.H, **kw)
+
+
+def test_sweep_picks_direct_sums_only_where_they_pay():
+    # narrow Gaussians over few samples: direct sums; the 3-D sweep's
+    # bandwidths over 4e6 samples: the NUFFT for every group
+    import numpy as np
+    from paper_2204_07716_gb300 import fkreg, inputs
+    H = np.array([np.eye(2) * s * s for s in (0.0015, 0.003, 0.05)])
+    first, _, kern = fkreg.sweep_split(200_000, 3, with_kernels=True, d=2, order=0,
+                                       grid_n=(100, 100), lo=(0, 0), hi=(1, 1), H=H, n_rhs=1,
+                                       max_probes=0, tol=1e-6, precision="f32")
+    assert kern[0] == "gaussian_direct" and kern[-1] == "gaussian"
+    w = inputs.nw3d_df(n=10)
+    _, _, kern3 = fkreg.sweep_split(4_000_000, 2, with_kernels=True, d=3, order=0,
+                                    grid_n=w.grid_n, lo=w.lo, hi=w.hi, H=w.H, n_rhs=1,
+                                    max_probes=32, tol=1e-6, precision="f32")
+    assert kern3 == ["gaussian", "gaussian"]
+    # the direct path's geometry: bins on the output lattice, sized from the
+    # cut radius R sigma, R^2 = 2 ln(10 / tol)
+    g = fkreg.geometry(d=2, order=1, grid_n=(128, 128), lo=(0, 0), hi=(1, 1), H=H[1:2],
+                       kernel="gaussian_direct", tol=1e-6)
+    assert g["nf"] == [128, 128] and g["modes"] == [1, 1]
+    with pytest.raises(fkreg.FkregError):
+        fkreg.geometry(d=2, order=1, grid_n=(128, 128), lo=(0, 0), hi=(1, 1), H=H[1:2],
+                       kernel="gaussian_direct", flags=fkreg.FKREG_WANT_BACKWARD)
