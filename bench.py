@@ -539,6 +539,7 @@ def sweep_roofline(plan, w, n_probes, st_ms, st_calls, dev):
     (N w^d strengths multiply-adds per launch) or the interpolation (N w^d
     fields multiply-adds per launch, one launch per bandwidth), against the
     FP32 FMA rate measured on this GPU."""
+    from paper_2204_07716_gb300 import fkreg
     own = {k: v for k, v in st_ms.items() if k in ("spread", "interp") and st_calls[k]}
     if not own:
         return None

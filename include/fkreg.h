@@ -528,6 +528,24 @@ fkreg_status fkreg_set_wait_limit(fkreg_plan plan, int64_t polls);
 /* Synchronise the stream and report device-detected errors (then clear them). */
 fkreg_status fkreg_sync_status(fkreg_plan plan, void* stream);
 
+/*
+ * The checked build.  libfkreg_checked.so is built from the same sources with
+ * FKREG_CHECKED defined: the main kernels (sort scatter, spreading tile and
+ * flush, interpolation window and field reads, grid solve, direct-sum bin
+ * ranges) range-check their index arithmetic before each access; a failed
+ * check skips the access and records the site and index in the plan's error
+ * word, which fkreg_sync_status reports as FKREG_ERR_DEVICE ("bounds check
+ * failed ..., site S, index I").  No check traps.
+ * fkreg_checked_build: 1 in the checked library, 0 otherwise.
+ * fkreg_check_selftest: launches one checked access at an index outside its
+ * logical bound (both inside the plan's error-word region, so the access
+ * cannot leave the workspace whether or not it is checked); in the checked
+ * library the next fkreg_sync_status reports site 15, index 20.  Needs the
+ * workspace; FKREG_ERR_CUDA if the launch fails.
+ */
+int fkreg_checked_build(void);
+fkreg_status fkreg_check_selftest(fkreg_plan plan, void* stream);
+
 /* Message of the last failing call on this plan ("" if none). */
 const char* fkreg_last_error(fkreg_plan plan);
 

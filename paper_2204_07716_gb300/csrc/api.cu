@@ -424,6 +424,7 @@ fkreg_status fkreg_set_workspace(fkreg_plan P, void* ws, size_t bytes, void* str
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   P->ws = static_cast<char*>(ws);
   P->ws_given = bytes;
+  P->geo.errw = reinterpret_cast<int*>(P->ws + P->r_err.off);
   for (auto& kv : P->ffts) {
     const fk::Region& wr = std::get<0>(kv.first) == 1 ? P->r_fftwork_g : P->r_fftwork;
     if (cufftSetWorkArea(kv.second, P->ws + wr.off) != CUFFT_SUCCESS)
@@ -966,12 +967,18 @@ fkreg_status fkreg_sync_status(fkreg_plan P, void* stream) {
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_err(P, e, "stream");
   if (!P->ws) return FKREG_OK;
-  int word = 0;
-  if ((e = cudaMemcpy(&word, P->ws + P->r_err.off, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+  int word[4] = {0, 0, 0, 0};
+  if ((e = cudaMemcpy(word, P->ws + P->r_err.off, sizeof(word), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_err(P, e, "read error word");
-  if (word) {
-    cudaMemset(P->ws + P->r_err.off, 0, sizeof(int));
-    if (word & 2) return plan_err(P, FKREG_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (word[0]) {
+    cudaMemset(P->ws + P->r_err.off, 0, sizeof(word));
+    if (word[0] & fk::kErrBounds) {
+      const int64_t idx = int64_t(uint64_t(uint32_t(word[2])) | (uint64_t(uint32_t(word[3])) << 32));
+      return plan_err(P, FKREG_ERR_DEVICE,
+                      "bounds check failed (checked build): site " + std::to_string(word[1]) +
+                          ", index " + std::to_string(idx));
+    }
+    if (word[0] & fk::kErrTimeout) return plan_err(P, FKREG_ERR_TIMEOUT, "a bounded device-side wait gave up");
     return plan_err(P, FKREG_ERR_DEVICE, "a sample lies outside the grid box or is not finite");
   }
   return FKREG_OK;

@@ -183,6 +183,9 @@ direct_interp_kernel(GeoDev g, MonoTab mono, const BwDev* __restrict__ bwt, int 
       for (int r1 = 0; r1 < o1; ++r1) {
         int64_t first, last;  // bins [first, last] are adjacent in sorted order
         if (!rows.row(g, r0, r1, first, last)) continue;
+        if (!in_range(g.errw, kSiteDirectBins, first, last + 1) ||
+            !in_range(g.errw, kSiteDirectBins, last, g.nbins[0] * g.nbins[1] * g.nbins[2]))
+          continue;
         const uint32_t i1 = bin_start[last + 1];
         for (uint32_t base = bin_start[first]; base < i1; base += 32) {
           const uint32_t i = base + uint32_t(lane);

@@ -43,7 +43,14 @@ struct GeoDev {
   int kbits;        // within-bin bits of the sort key (see key_local_bits)
   int kern;         // regression kernel: FKREG_KERNEL_GAUSSIAN (NUFFT) or a compact one (direct)
   uint32_t wait_limit;  // polls of a staged-window wait before it gives up (fkreg_set_wait_limit)
+  int* errw;            // the plan's error word (errw[0] bits kErr*; errw[1..3] the first
+                        // failed bounds check of a checked build: site, index low, high)
 };
+
+// Bits of the plan's device error word.
+constexpr int kErrOutside = 1;  // a sample outside the grid box or not finite
+constexpr int kErrTimeout = 2;  // a bounded device-side wait gave up
+constexpr int kErrBounds = 4;   // a bounds check of the checked build failed (access skipped)
 
 // Sort keys are (bin << kbits) | local, local = serpentine index of the
 // centre cell of the sample's spreading window relative to its bin's first

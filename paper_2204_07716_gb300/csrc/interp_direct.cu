@@ -190,6 +190,9 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
             ur0 = min(lo0, wm0 - rows);
             uc0 = lo1;
             uncol = hi1 - lo1;
+            if constexpr (kChecked)  // the union inside the staged window
+              use_mma = in_range(errw, kSiteInterpWindow, ur0, wm0 - rows + 1) &&
+                        in_range(errw, kSiteInterpWindow, uc0, wm1 - uncol + 1);
           }
         }
       }
@@ -220,7 +223,9 @@ interp_direct_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_t n,
         T pl[W];
 #pragma unroll
         for (int t = 0; t < W; ++t) pl[t] = phi<T>(skind, W, beta, (D > 1 ? off1 : off0) + T(t));
-        if (inside)
+        const int64_t last_read = (D > 1 ? int64_t(l0 + W - 1) * pitch + int64_t(l1 + W - 1) * rec
+                                         : int64_t(l0 + W - 1) * rec) + 4 * nqd - 1;
+        if (inside && in_range(errw, kSiteInterpWindow, last_read, win_floats))
           lane_gather_smem<D, W, NQ>(win + size_t(l0) * (D > 1 ? pitch : rec) + l1 * rec, rec,
                                      pitch, nqd, skind, beta, off0, pl, acc);
         if (__any_sync(0xffffffffu, valid && !inside)) {

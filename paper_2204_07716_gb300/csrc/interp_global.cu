@@ -93,6 +93,7 @@ interp_global_lane_kernel(GeoDev g, const BwDev* __restrict__ bwt, int b, int64_
         else rb = (r0 * nf1 + cm[t1]) * int64_t(nf2);
 #pragma unroll
         for (int t2 = 0; t2 < W; ++t2) {
+          if (!in_range(g.errw, kSiteInterpField, rb + cl[t2], int64_t(nf0) * nf1 * nf2)) continue;
           const float* cell = fld + (rb + cl[t2]) * rec;
           const T wgt = w01 * pl[t2];
 #pragma unroll

@@ -85,6 +85,7 @@ __global__ void grid_solve_kernel(GeoDev g, MonoTab mono, const BwDev* __restric
     rem /= g.M[a];
   }
   for (int a = 0; a < 3; ++a) lidx = lidx * g.L[a] + mi[a];
+  if (!in_range(g.errw, kSiteSolveField, lidx, lcells)) return;
   const T* f0 = field + int64_t(bb) * fgrid * lcells + lidx;
   const int ns = mono.n, nt = mono.nt;
   double s[kMaxMono];

@@ -23,6 +23,7 @@
 
 #include <mutex>
 
+#include "checked.cuh"
 #include "internal.h"
 
 namespace fk {
@@ -558,15 +559,17 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     const uint32_t k = skey[t];
     const uint32_t dig = (k >> shift) & (R - 1u);
     const uint32_t pos = gbase[dig] + uint32_t(t) - dstart[dig];
+    if (!in_range(ex.g.errw, kSiteSortScatter, pos, n)) continue;
     const uint32_t v = sval[t];
     vals_out[pos] = v;
     if (MODE != kDownLast) keys_out[pos] = k;
     if (MODE == kDownCount) {
       const uint32_t dn = (k >> (shift + B)) & (R - 1u);
-      atomicAdd(&ex.hist_next[int64_t(dn) * ntiles + pos / uint32_t(kSortTile)], 1u);
+      const int64_t hx = int64_t(dn) * ntiles + pos / uint32_t(kSortTile);
+      if (in_range(ex.g.errw, kSiteSortHist, hx, int64_t(R) * ntiles)) atomicAdd(&ex.hist_next[hx], 1u);
       atomicAdd(&hn[dn], 1u);
     }
-    if (MODE == kDownLast) {
+    if (MODE == kDownLast && in_range(ex.g.errw, kSiteSortCoords, v, n)) {
       const T* x = static_cast<const T*>(ex.x);
       T* xs = static_cast<T*>(ex.xs);
       for (int j = 0; j < ex.g.d; ++j) {

@@ -127,6 +127,11 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
           for (int t = 0; t < w; ++t) wt[j][t] = phi<T>(g.skind, w, beta, off + T(t));
         }
       }
+      if constexpr (kChecked) {  // the whole window inside the tile
+        bool okw = true;
+        for (int j = 0; j < D; ++j) okw = okw && in_range(g.errw, kSiteSpreadTile, l[j], W3[j] - w + 1);
+        if (!okw) continue;
+      }
       T cv[CN];
 #pragma unroll
       for (int c = 0; c < CN; ++c) cv[c] = str[int64_t(s0 + c0 + c) * n + p] * s_scale[c];
@@ -200,6 +205,7 @@ spread_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __restrict
         if (j < D) m = wrap_idx(o[j] + lj[j], g.nf[j]);
         gidx = gidx * g.nf[j] + m;
       }
+      if (!in_range(g.errw, kSiteSpreadFlush, gidx, fine_cells)) continue;
       for (int c = 0; c < cn; ++c) {
         const A a = sm[c * cells + idx];
         if (a != A(0)) atomicAdd(&fine[int64_t(s0 + c0 + c) * fine_cells + gidx], T(a) * s_inv[c]);
@@ -335,7 +341,7 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
       if (org != cur) {
 #pragma unroll
         for (int a = 0; a < CS; ++a)
-          if (act[a])
+          if (act[a] && in_range(g.errw, kSiteSpreadTile, cur + rel[a], cells))
 #pragma unroll
             for (int c = 0; c < CN; ++c) {
               TileAcc<T>::add(&sm[c * cells + cur + rel[a]], acc[a][c]);
@@ -371,7 +377,7 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
     }
 #pragma unroll
     for (int a = 0; a < CS; ++a)
-      if (act[a])
+      if (act[a] && in_range(g.errw, kSiteSpreadTile, cur + rel[a], cells))
 #pragma unroll
         for (int c = 0; c < CN; ++c) TileAcc<T>::add(&sm[c * cells + cur + rel[a]], acc[a][c]);
     __syncwarp();  // staging rows are rewritten by the next group
@@ -382,6 +388,7 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
     const int l0 = D == 2 ? idx / W3[1] : idx, l1 = D == 2 ? idx % W3[1] : 0;
     int64_t gidx = wrap_idx(o[0] + l0, g.nf[0]);
     if (D == 2) gidx = gidx * g.nf[1] + wrap_idx(o[1] + l1, g.nf[1]);
+    if (!in_range(g.errw, kSiteSpreadFlush, gidx, fine_cells)) continue;
     for (int c = 0; c < CN; ++c) {
       const A av = sm[c * cells + idx];
       if (av != A(0)) atomicAdd(&fine[int64_t(s0 + c) * fine_cells + gidx], T(av) * s_inv[c]);

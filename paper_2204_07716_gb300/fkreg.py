@@ -25,7 +25,10 @@ from typing import Dict, Iterable, Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfkreg.so")
+# FKREG_CHECKED=1 in the environment loads the checked build (range checks on
+# the kernels' index arithmetic, reported through fkreg_sync_status)
+CHECKED = os.environ.get("FKREG_CHECKED", "") == "1"
+LIB_PATH = os.path.join(HERE, "libfkreg_checked.so" if CHECKED else "libfkreg.so")
 
 FKREG_F32, FKREG_F64 = 0, 1
 FKREG_SPREAD_ES, FKREG_SPREAD_GAUSS = 0, 1
@@ -45,7 +48,7 @@ EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_spread_kerne
            "fkreg_smooth", "fkreg_df", "fkreg_backward", "fkreg_backward_grid", "fkreg_variance",
            "fkreg_log_variance", "fkreg_interval", "fkreg_predict", "fkreg_set_timing",
            "fkreg_stage_times", "fkreg_set_wait_limit", "fkreg_bin_sort_static",
-           "fkreg_sync_status",
+           "fkreg_sync_status", "fkreg_checked_build", "fkreg_check_selftest",
            "fkreg_last_error", "fkreg_global_error", "fkreg_plan_destroy",
            "fkreg_batch_create", "fkreg_batch_workspace_bytes", "fkreg_batch_set_workspace",
            "fkreg_batch_capture", "fkreg_batch_launch", "fkreg_batch_latencies",
@@ -168,6 +171,8 @@ def load():
     L.fkreg_batch_destroy.restype = None
     L.fkreg_measure_peaks.argtypes = [ctypes.POINTER(Peaks), vp, ctypes.c_size_t, vp]
     L.fkreg_sweep_create.argtypes = [ctypes.POINTER(Opts), i64, ctypes.c_int, ctypes.POINTER(vp)]
+    L.fkreg_checked_build.argtypes = []
+    L.fkreg_check_selftest.argtypes = [vp, vp]
     L.fkreg_sweep_split.argtypes = [ctypes.POINTER(Opts), i64, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -426,6 +431,11 @@ class Plan:
 
     def sync(self):
         self._check(self.L.fkreg_sync_status(self.h, self._stream()))
+
+    def check_selftest(self):
+        """One deliberately out-of-bounds checked access (fkreg_check_selftest);
+        in the checked build the next sync raises with site 15, index 20."""
+        self._check(self.L.fkreg_check_selftest(self.h, self._stream()))
 
     def set_wait_limit(self, polls: int = -1):
         """Polls of a staged-window wait before a call gives up with a timeout

@@ -38,6 +38,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(fkreg.EXPORTS)
 
 
+def test_checked_library_exports_the_same_symbols(lib):
+    # the range-checked variant: same sources with FKREG_CHECKED, same ABI
+    path = fkbuild.build(checked=True)
+    chk = ctypes.CDLL(path)
+    for name in declared_symbols():
+        assert hasattr(chk, name), name
+    chk.fkreg_checked_build.restype = ctypes.c_int
+    lib.fkreg_checked_build.restype = ctypes.c_int
+    assert chk.fkreg_checked_build() == 1 and lib.fkreg_checked_build() == 0
+
+
 def opts(**kw):
     base = dict(d=2, order=1, grid_n=(256, 256), lo=(0, 0), hi=(1, 1),
                 H=np.diag([0.01 ** 2, 0.015 ** 2]), tol=1e-6)
