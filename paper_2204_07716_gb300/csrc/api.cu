@@ -321,6 +321,11 @@ fkreg_status fkreg_plan_create(const fkreg_opts* opts, int64_t max_n, fkreg_plan
   L.take(P->r_spec, std::max<int64_t>(256, fft_scale * 2 * T * strengths_total * nf_half));
   L.take(P->r_gspec, std::max<int64_t>(256, fft_scale * 2 * T * int64_t(P->nbw) * P->fgrid * l_half));
   L.take(P->r_gfield, T * size_t(P->nbw) * P->fgrid * l_cells);
+  {
+    int64_t mt = 1;
+    for (int a = 0; a < d; ++a) mt *= opts->grid_n[a];
+    L.take(P->r_gavec, sizeof(double) * size_t(P->nbw) * P->p * mt);
+  }
   L.take(P->r_t2spec, std::max<int64_t>(256, fft_scale * 2 * T * int64_t(t2_fields) * t2_half));
   L.take(P->r_t2field,
          std::max<int64_t>(256, fft_scale * T * int64_t(fk::t2_record_stride(t2_fields)) * t2_cells));
@@ -443,6 +448,7 @@ fkreg_status fkreg_set_workspace(fkreg_plan P, void* ws, size_t bytes, void* str
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(P, e, "sync");
   P->points_set = false;
   P->dens_valid = false;
+  P->avec_valid = false;
   return FKREG_OK;
 }
 
@@ -454,6 +460,7 @@ fkreg_status fkreg_set_points(fkreg_plan P, int64_t n, const void* x, void* stre
   P->n = n;
   P->points_set = false;
   P->dens_valid = false;
+  P->avec_valid = false;
   cudaError_t e;
   {
     StageScope sc(P, FKREG_STAGE_SORT, static_cast<cudaStream_t>(stream));
@@ -533,6 +540,7 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
   const int64_t nf_cells = full_cells(P->g.nf, d);
   (void)nf_cells;
   P->dens_valid = false;
+  P->avec_valid = false;
 #define FK_STAGE(id) StageScope _sc##id(P, id, s)
   {
     FK_STAGE(FKREG_STAGE_STRENGTHS);
@@ -581,6 +589,7 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
   // there the fork's own cost is larger than the overlap.
   constexpr int64_t kForkMinSamples = int64_t(1) << 16;
   Join join;
+  bool grid_weights = false;  // the grid solve kept its weights for a variance pass
   if (grid) {
     cudaStream_t sg = s;
     if (at && P->aux && P->n >= kForkMinSamples) {
@@ -604,8 +613,10 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
       }
       {
         FK_STAGE(FKREG_STAGE_GRID_SOLVE);
-        FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, nullptr, out, nullptr, s),
+        FK_CHECK(fk::run_grid_solve(P, 0, P->nbw, P->nrhs_real, fk::wsp<double>(P, P->r_gavec), out,
+                                     nullptr, s),
                  "grid solve");
+        grid_weights = true;
       }
     }
   }
@@ -633,6 +644,7 @@ fkreg_status pipeline(fkreg_plan_s* P, const void* y, int n_probes, uint64_t see
   if (join.P && !join.done()) return cuda_err(P, cudaErrorUnknown, "join the grid branch");
   (void)T;
   P->dens_valid = true;
+  P->avec_valid = grid_weights;
   return FKREG_OK;
 }
 
@@ -743,6 +755,7 @@ fkreg_status fkreg_backward_grid(fkreg_plan P, const void* y, const void* grad_m
   const int fgrid = P->ns + R * P->nt;
   const int nout = R + (1 + R) * d;
   P->dens_valid = false;
+  P->avec_valid = false;
   // forward grid fields of bandwidth b: strengths, spreading, forward FFT,
   // kernel multiply, inverse FFT onto the lattice, and the mask of the solve
   {
@@ -827,18 +840,26 @@ fkreg_status fkreg_variance(fkreg_plan P, const void* y, const void* mhat_at_x, 
       FK_STATUS(exec_fft(P, 0, P->g.nf, R, P->ws + P->r_fine.off + P->tsize * nf_cells,
                          P->ws + P->r_spec.off + 2 * P->tsize * nf_half, s));
     }
+    // with the grid weights of the smoothing pass (same points, same
+    // s-fields, so the same systems and mask) only the residuals' t-fields
+    // are needed on the grid: sigma^2(g) = sum_k a_k(g) t_k(g)
+    const bool reuse = P->avec_valid;
     {
       FK_STAGE(FKREG_STAGE_KMUL_GRID);
-      FK_CHECK(fk::run_kmul_grid(P, 0, 1, R, b, 1, P->ws + P->r_gspec.off, s), "kmul grid");
+      FK_CHECK(fk::run_kmul_grid(P, reuse ? -1 : 0, 1, R, b, 1, P->ws + P->r_gspec.off, s),
+               "kmul grid");
     }
     {
       FK_STAGE(FKREG_STAGE_FFT_GRID);
-      FK_STATUS(exec_fft(P, 1, P->g.ldft, P->ns + R * P->nt, P->ws + P->r_gspec.off,
-                         P->ws + P->r_gfield.off, s));
+      FK_STATUS(exec_fft(P, 1, P->g.ldft, (reuse ? 0 : P->ns) + R * P->nt,
+                         P->ws + P->r_gspec.off, P->ws + P->r_gfield.off, s));
     }
     {
       FK_STAGE(FKREG_STAGE_GRID_SOLVE);
-      FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, sigma2, s), "grid solve");
+      if (reuse)
+        FK_CHECK(fk::run_grid_apply(P, b, R, sigma2, s), "grid weights");
+      else
+        FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, sigma2, s), "grid solve");
     }
   }
   return FKREG_OK;

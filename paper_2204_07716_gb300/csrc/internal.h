@@ -122,7 +122,7 @@ struct fkreg_plan_s {
       r_binstart, r_nsub, r_substart, r_subbin, r_subfirst, r_hist, r_hist2, r_dtot, r_scan, r_str,
       r_fine, r_spec, r_gspec, r_gfield, r_t2spec, r_t2field, r_part, r_smax, r_fftwork,
       r_fftwork_g,
-      r_bV, r_bdx, r_bsc, r_bpart, r_gmask, r_gadj, r_gpart;
+      r_bV, r_bdx, r_bsc, r_bpart, r_gmask, r_gadj, r_gpart, r_gavec;
   bool backward = false;        // workspace reserved for fkreg_backward
   bool direct = false;          // compact kernel: direct sums instead of the NUFFT
   int f2bwd = 0;                // fields of the backward passes (one response + probes)
@@ -139,6 +139,7 @@ struct fkreg_plan_s {
   int64_t n = 0;
   bool points_set = false;
   bool dens_valid = false;
+  bool avec_valid = false;      // r_gavec holds the grid weights of the last smooth/df
   int perm_in_vals1 = 0;        // which ping-pong buffer holds the permutation
   std::string err;
   int device = -1;
@@ -228,9 +229,13 @@ cudaError_t run_combine(fkreg_plan_s* P, int n_probes, void* dy, void* dx, doubl
                         cudaStream_t s);
 
 // solve.cu
+// avec (may be null): [bw][p][M] the solved weights a_k / tscale_k of each
+// grid point (NaN where masked), kept for a variance pass on the same points
 cudaError_t run_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int nrhs_fields,
-                           const void* y_complex_flag_dummy, const fkreg_outputs* out,
-                           void* sigma2, cudaStream_t s);
+                           double* avec, const fkreg_outputs* out, void* sigma2, cudaStream_t s);
+// sigma2[b][r][M] = sum_k avec[b][k] t_(r,k) from the grid t-fields alone
+// (r_gfield holds nrhs_fields x p t-fields; no s-fields, no solve)
+cudaError_t run_grid_apply(fkreg_plan_s* P, int b, int nrhs_fields, void* sigma2, cudaStream_t s);
 cudaError_t run_interp(fkreg_plan_s* P, int b, int n_rhs_str, int n_probes, const void* y,
                        void* mhat_at_x, cudaStream_t s);
 // direct path (compact kernels): grid fields of strengths [str_first, str_first + nstr)

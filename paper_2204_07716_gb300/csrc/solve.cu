@@ -65,6 +65,7 @@ struct GridOut {
   void* moments;      // [n_bw][ns + n_rhs*nt*(1+cplx)][M]
   int cplx;           // real fields come in (re, im) pairs
   int n_rhs_out;      // responses in the output (pairs collapse when cplx)
+  double* avec;       // [n_bw][p][M] a_k / tscale_k (NaN where masked), or null
 };
 
 template <typename T>
@@ -103,6 +104,10 @@ __global__ void grid_solve_kernel(GeoDev g, MonoTab mono, const BwDev* __restric
     }
   }
   const T nan = T(__longlong_as_double(0x7ff8000000000000LL));
+  if (out.avec)
+    for (int k = 0; k < p; ++k)
+      out.avec[(int64_t(b) * p + k) * Mtot + m] =
+          ok ? a[k] / tscale(mono, k, B.sigma) : __longlong_as_double(0x7ff8000000000000LL);
   const int mult = out.cplx ? 2 : 1;
   for (int q = 0; q < nrhs_fields; ++q) {
     double mh = 0.0;
@@ -129,9 +134,52 @@ __global__ void grid_solve_kernel(GeoDev g, MonoTab mono, const BwDev* __restric
   }
 }
 
+// sigma2[b][r][m] = sum_k avec[b][k][m] t_(r,k)(g_m): the estimate of the
+// variance pass from the grid weights a smoothing pass kept (NaN where that
+// pass masked the point); field holds the R x p t-fields only.
+template <typename T>
+__global__ void grid_apply_kernel(GeoDev g, int64_t Mtot, int p, int nrhs_fields,
+                                  const double* __restrict__ avec, const T* __restrict__ field,
+                                  int64_t lcells, T* __restrict__ sigma2) {
+  const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (m >= Mtot) return;
+  int64_t rem = m, lidx = 0, mi[3];
+  for (int a = 2; a >= 0; --a) {
+    mi[a] = rem % g.M[a];
+    rem /= g.M[a];
+  }
+  for (int a = 0; a < 3; ++a) lidx = lidx * g.L[a] + mi[a];
+  if (!in_range(g.errw, kSiteSolveField, lidx, lcells)) return;
+  double w[kMaxP];
+  for (int k = 0; k < p; ++k) w[k] = avec[int64_t(k) * Mtot + m];
+  for (int r = 0; r < nrhs_fields; ++r) {
+    double v = 0.0;
+    for (int k = 0; k < p; ++k) v += w[k] * double(field[(int64_t(r) * p + k) * lcells + lidx]);
+    sigma2[int64_t(r) * Mtot + m] = T(v);  // NaN weights give NaN
+  }
+}
+
+template <typename T>
+cudaError_t launch_grid_apply(fkreg_plan_s* P, int b, int nrhs_fields, void* sigma2,
+                              cudaStream_t st) {
+  const GeoDev& g = P->geo;
+  int64_t Mtot = 1, lcells = 1;
+  for (int a = 0; a < 3; ++a) {
+    Mtot *= g.M[a];
+    lcells *= g.L[a];
+  }
+  const unsigned blocks = unsigned((Mtot + 255) / 256);
+  grid_apply_kernel<T><<<blocks, 256, 0, st>>>(
+      g, Mtot, P->p, nrhs_fields, wsp<double>(P, P->r_gavec) + int64_t(b) * P->p * Mtot,
+      wsp<T>(P, P->r_gfield), lcells, static_cast<T*>(sigma2) + int64_t(b) * nrhs_fields * Mtot);
+  P->launches += 1;
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int nrhs_fields,
-                              const fkreg_outputs* out, void* sigma2, cudaStream_t st) {
+                              double* avec, const fkreg_outputs* out, void* sigma2,
+                              cudaStream_t st) {
   const GeoDev& g = P->geo;
   int64_t Mtot = 1, lcells = 1;
   for (int a = 0; a < 3; ++a) {
@@ -147,6 +195,7 @@ cudaError_t launch_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int n
   smax_kernel<T><<<blocks, 256, 0, st>>>(g, Mtot, field, fgrid, lcells, smax, bw_count);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   GridOut go{};
+  go.avec = avec;
   const double rho = P->o.mask_rho > 0 ? P->o.mask_rho : 1e-3;
   if (sigma2) {
     go.mhat = sigma2;
@@ -169,10 +218,15 @@ cudaError_t launch_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int n
 }  // namespace
 
 cudaError_t run_grid_solve(fkreg_plan_s* P, int bw_first, int bw_count, int nrhs_fields,
-                           const void*, const fkreg_outputs* out, void* sigma2, cudaStream_t st) {
+                           double* avec, const fkreg_outputs* out, void* sigma2, cudaStream_t st) {
   return P->prec == FKREG_F32
-             ? launch_grid_solve<float>(P, bw_first, bw_count, nrhs_fields, out, sigma2, st)
-             : launch_grid_solve<double>(P, bw_first, bw_count, nrhs_fields, out, sigma2, st);
+             ? launch_grid_solve<float>(P, bw_first, bw_count, nrhs_fields, avec, out, sigma2, st)
+             : launch_grid_solve<double>(P, bw_first, bw_count, nrhs_fields, avec, out, sigma2, st);
+}
+
+cudaError_t run_grid_apply(fkreg_plan_s* P, int b, int nrhs_fields, void* sigma2, cudaStream_t st) {
+  return P->prec == FKREG_F32 ? launch_grid_apply<float>(P, b, nrhs_fields, sigma2, st)
+                              : launch_grid_apply<double>(P, b, nrhs_fields, sigma2, st);
 }
 
 }  // namespace fk

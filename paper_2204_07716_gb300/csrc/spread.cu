@@ -336,6 +336,8 @@ spread_run_kernel(GeoDev g, int64_t n, const T* __restrict__ xs, const T* __rest
 #pragma unroll
       for (int c = 0; c < CN; ++c) acc[a][c] = T(0);
     int cur = org_row[0];
+    // two samples per iteration in flight (measured: 5 % off the spreading)
+#pragma unroll 2
     for (int j = 0; j < cnt; ++j) {
       const int org = org_row[j];
       if (org != cur) {
