@@ -913,16 +913,21 @@ fkreg_status fkreg_log_variance(fkreg_plan P, const void* y, const void* mhat_at
     }
     {
       FK_STAGE(FKREG_STAGE_KMUL_GRID);
-      FK_CHECK(fk::run_kmul_grid(P, 0, 1, R, b, 1, P->ws + P->r_gspec.off, s), "kmul grid");
+      FK_CHECK(fk::run_kmul_grid(P, P->avec_valid ? -1 : 0, 1, R, b, 1, P->ws + P->r_gspec.off, s),
+               "kmul grid");
     }
     {
       FK_STAGE(FKREG_STAGE_FFT_GRID);
-      FK_STATUS(exec_fft(P, 1, P->g.ldft, P->ns + R * P->nt, P->ws + P->r_gspec.off,
+      FK_STATUS(exec_fft(P, 1, P->g.ldft, (P->avec_valid ? 0 : P->ns) + R * P->nt, P->ws + P->r_gspec.off,
                          P->ws + P->r_gfield.off, s));
     }
     {
       FK_STAGE(FKREG_STAGE_GRID_SOLVE);
-      FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, v_grid, s), "grid solve");
+      // the grid weights of the smoothing pass, as in fkreg_variance
+      if (P->avec_valid)
+        FK_CHECK(fk::run_grid_apply(P, b, R, v_grid, s), "grid weights");
+      else
+        FK_CHECK(fk::run_grid_solve(P, b, 1, R, nullptr, nullptr, v_grid, s), "grid solve");
     }
     // v at the samples: type-2 of the same fields
     {
