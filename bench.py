@@ -172,7 +172,7 @@ def dist_setup(args):
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
 # capture of the bench command (see profiles/); None where the kernel changed
 # after the counters were taken.
-TRAFFIC = {"interp": None, "spread": None}
+TRAFFIC = {"interp": 79684864, "spread": 62001920}
 
 
 def max_over_ranks(ms: float, world: int, device) -> float:
@@ -417,7 +417,7 @@ def run_ours(args, world, rank, local):
                 r = measure_workload(wl, st, wu, 1.0, dev)
                 cfgs[wl] = {k: r[k] for k in ("ms_per_step", "value", "unit", "dtype", "config",
                                               "steps", "warmup", "latency_ms", "clocks",
-                                              "stages_ms_per_step") if k in r}
+                                              "stages_ms_per_step", "roofline") if k in r}
             except Exception as e:          # reported, not hidden: the line still prints
                 cfgs[wl] = {"error": f"{type(e).__name__}: {e}"[:300]}
         result["configs"] = cfgs
