@@ -296,6 +296,7 @@ adjoint_f32_kernel(const BwDev* __restrict__ bwt, int b, int64_t n, int F2, int 
     }
     float dx_t[3] = {0.f, 0.f, 0.f};
     const int R = 1 + n_probes;
+#pragma unroll 2
     for (int r = 0; r < R; ++r) {
       float t[P];
 #pragma unroll
@@ -379,12 +380,29 @@ __global__ void combine_kernel(int64_t n, int n_probes, const T* __restrict__ Va
   if (dx) {
     const int ncls = 2 + n_probes;
     for (int d = 0; d < D; ++d) {
-      double v = double(dxt[int64_t(d) * n + s]);
-      for (int c = 0; c < ncls; ++c) {
-        const double cc = c == 0 ? 1.0 : double(str[int64_t(c) * n + s]);
-        v += cc * double(Vadj[int64_t(1 + c * D + d) * n + s]);
+      if constexpr (sizeof(T) == 4) {
+        // compensated FP32 (exact products by fma, two-sum of the running
+        // total): FP64 arithmetic runs on GB300's narrow FP64 pipe
+        float hi = dxt[int64_t(d) * n + s], lo = 0.f;
+        for (int c = 0; c < ncls; ++c) {
+          const float cc = c == 0 ? 1.f : float(str[int64_t(c) * n + s]);
+          const float v = float(Vadj[int64_t(1 + c * D + d) * n + s]);
+          const float p = cc * v;
+          const float pe = fmaf(cc, v, -p);
+          const float t = hi + p;
+          const float z = t - hi;
+          lo += ((hi - (t - z)) + (p - z)) + pe;
+          hi = t;
+        }
+        dx[int64_t(i) * D + d] = T(hi + lo);
+      } else {
+        double v = double(dxt[int64_t(d) * n + s]);
+        for (int c = 0; c < ncls; ++c) {
+          const double cc = c == 0 ? 1.0 : double(str[int64_t(c) * n + s]);
+          v += cc * double(Vadj[int64_t(1 + c * D + d) * n + s]);
+        }
+        dx[int64_t(i) * D + d] = T(v);
       }
-      dx[int64_t(i) * D + d] = T(v);
     }
   }
 }
