@@ -132,10 +132,24 @@ __global__ void combine_grid_kernel(int64_t n, int nrhs, const T* __restrict__ V
     for (int r = 0; r < nrhs; ++r) dy[int64_t(r) * n + i] = V[int64_t(r) * n + s];
   if (dx)
     for (int d = 0; d < D; ++d) {
-      double v = double(V[int64_t(nrhs + d) * n + s]);
-      for (int r = 0; r < nrhs; ++r)
-        v += double(str[int64_t(1 + r) * n + s]) * double(V[int64_t(nrhs + (1 + r) * D + d) * n + s]);
-      dx[int64_t(i) * D + d] = T(v);
+      if constexpr (sizeof(T) == 4) {
+        // compensated FP32 (exact products by fma, two-sum of the total)
+        float hi = V[int64_t(nrhs + d) * n + s], lo = 0.f;
+        for (int r = 0; r < nrhs; ++r) {
+          const float c = str[int64_t(1 + r) * n + s];
+          const float v = V[int64_t(nrhs + (1 + r) * D + d) * n + s];
+          const float p = c * v, pe = fmaf(c, v, -p);
+          const float t = hi + p, z = t - hi;
+          lo += ((hi - (t - z)) + (p - z)) + pe;
+          hi = t;
+        }
+        dx[int64_t(i) * D + d] = T(hi + lo);
+      } else {
+        double v = double(V[int64_t(nrhs + d) * n + s]);
+        for (int r = 0; r < nrhs; ++r)
+          v += double(str[int64_t(1 + r) * n + s]) * double(V[int64_t(nrhs + (1 + r) * D + d) * n + s]);
+        dx[int64_t(i) * D + d] = T(v);
+      }
     }
 }
 
