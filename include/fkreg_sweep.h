@@ -103,6 +103,19 @@ fkreg_status fkreg_sweep_df(fkreg_sweep S, const void* y_dev, int n_probes, uint
 fkreg_status fkreg_sweep_variance(fkreg_sweep S, const void* y_dev, const void* mhat_at_x_dev,
                                   void* sigma2_grid_dev, void* stream);
 
+/* fkreg_log_variance over every group (eqs. 24-26); arrays as for the plan
+ * call, for all n_bw bandwidths. */
+fkreg_status fkreg_sweep_log_variance(fkreg_sweep S, const void* y_dev, const void* mhat_at_x_dev,
+                                      void* v_grid_dev, void* v_at_x_dev, double* kappa_dev,
+                                      void* sigma2_grid_dev, void* stream);
+
+/* fkreg_backward for bandwidth b (index in the caller's list), run by the
+ * plan of b's group (whose opts carry FKREG_WANT_BACKWARD if the sweep's
+ * did); outputs as for the plan call. */
+fkreg_status fkreg_sweep_backward(fkreg_sweep S, const void* y_dev, int n_probes, uint64_t seed,
+                                  const void* probes_dev, int b, double* gcv_dev,
+                                  double* dlogh_dev, void* dy_dev, void* dx_dev, void* stream);
+
 /* fkreg_sync_status of every group (the first failure is returned). */
 fkreg_status fkreg_sweep_sync_status(fkreg_sweep S, void* stream);
 

@@ -350,6 +350,38 @@ fkreg_status fkreg_sweep_variance(fkreg_sweep S, const void* y_dev, const void* 
   return FKREG_OK;
 }
 
+fkreg_status fkreg_sweep_log_variance(fkreg_sweep S, const void* y_dev, const void* mhat_at_x_dev,
+                                      void* v_grid_dev, void* v_at_x_dev, double* kappa_dev,
+                                      void* sigma2_grid_dev, void* stream) {
+  if (!S) return FKREG_ERR_INVALID_ARG;
+  const size_t R = size_t(S->o.n_rhs), T = S->tsize;
+  for (size_t gi = 0; gi < S->plans.size(); ++gi) {
+    const size_t b0 = size_t(S->first[gi]);
+    const void* mh = mhat_at_x_dev
+                         ? static_cast<const char*>(mhat_at_x_dev) + b0 * R * size_t(S->n) * T
+                         : nullptr;
+    const fkreg_status st = fkreg_log_variance(
+        S->plans[gi], y_dev, mh, byte_off(v_grid_dev, b0 * R * size_t(S->M) * T),
+        byte_off(v_at_x_dev, b0 * R * size_t(S->n) * T), kappa_dev ? kappa_dev + b0 * R : nullptr,
+        byte_off(sigma2_grid_dev, b0 * R * size_t(S->M) * T), stream);
+    if (st != FKREG_OK) return child_err(S, gi, st);
+  }
+  return FKREG_OK;
+}
+
+fkreg_status fkreg_sweep_backward(fkreg_sweep S, const void* y_dev, int n_probes, uint64_t seed,
+                                  const void* probes_dev, int b, double* gcv_dev,
+                                  double* dlogh_dev, void* dy_dev, void* dx_dev, void* stream) {
+  if (!S) return FKREG_ERR_INVALID_ARG;
+  if (b < 0 || b >= S->o.n_bw) return sweep_err(S, FKREG_ERR_INVALID_ARG, "b outside [0, n_bw)");
+  size_t gi = 0;
+  while (gi + 1 < S->plans.size() && b >= S->first[gi + 1]) ++gi;
+  const fkreg_status st = fkreg_backward(S->plans[gi], y_dev, n_probes, seed, probes_dev,
+                                         b - S->first[gi], gcv_dev, dlogh_dev, dy_dev, dx_dev,
+                                         stream);
+  return child_err(S, gi, st);
+}
+
 fkreg_status fkreg_sweep_sync_status(fkreg_sweep S, void* stream) {
   if (!S) return FKREG_ERR_INVALID_ARG;
   fkreg_status first = FKREG_OK;

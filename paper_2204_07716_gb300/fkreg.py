@@ -56,7 +56,8 @@ EXPORTS = ["fkreg_geometry_query", "fkreg_spread_kernel_ft", "fkreg_spread_kerne
            "fkreg_measure_peaks",
            "fkreg_sweep_create", "fkreg_sweep_split", "fkreg_sweep_groups", "fkreg_sweep_workspace_bytes",
            "fkreg_sweep_set_workspace", "fkreg_sweep_set_points", "fkreg_sweep_smooth",
-           "fkreg_sweep_df", "fkreg_sweep_variance", "fkreg_sweep_sync_status",
+           "fkreg_sweep_df", "fkreg_sweep_variance", "fkreg_sweep_log_variance",
+           "fkreg_sweep_backward", "fkreg_sweep_sync_status",
            "fkreg_sweep_set_timing", "fkreg_sweep_stage_times", "fkreg_sweep_last_error",
            "fkreg_sweep_destroy"]
 
@@ -185,6 +186,9 @@ def load():
     L.fkreg_sweep_df.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp,
                                  ctypes.POINTER(Outputs), vp]
     L.fkreg_sweep_variance.argtypes = [vp, vp, vp, vp, vp]
+    L.fkreg_sweep_log_variance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fkreg_sweep_backward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_uint64, vp, ctypes.c_int,
+                                       vp, vp, vp, vp, vp]
     L.fkreg_sweep_sync_status.argtypes = [vp, vp]
     L.fkreg_sweep_set_timing.argtypes = [vp, ctypes.c_int]
     L.fkreg_sweep_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -333,6 +337,10 @@ class Plan:
     The methods mirror the C calls: ``set_points`` (bin + stable sort),
     ``smooth``, ``df`` (Monte-Carlo DF + GCV), ``variance`` (eq. 23).
     """
+
+    # C entry points that a Sweep routes through its own (same arguments)
+    _fn_backward = "fkreg_backward"
+    _fn_log_variance = "fkreg_log_variance"
 
     def __init__(self, d: int, order: int, grid_n, lo, hi, H, max_n: int, n_rhs: int = 1,
                  max_probes: int = 0, tol: float = 1e-6, precision: str = "f32",
@@ -542,7 +550,7 @@ class Plan:
         if "dx" in want:
             out["dx"] = t.empty((n, self.d), dtype=self.dtype, device=self.device)
         ptr = lambda k: ctypes.c_void_p(out[k].data_ptr()) if k in out else None
-        self._check(self.L.fkreg_backward(self.h, ctypes.c_void_p(y.data_ptr()), int(n_probes),
+        self._check(getattr(self.L, self._fn_backward)(self.h, ctypes.c_void_p(y.data_ptr()), int(n_probes),
                                           ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
                                           None if pr is None else ctypes.c_void_p(pr.data_ptr()),
                                           int(b), ptr("gcv"), ptr("dlogh"), ptr("dy"), ptr("dx"),
@@ -593,7 +601,7 @@ class Plan:
         kappa = t.empty((self.n_bw, self.n_rhs), dtype=t.float64, device=self.device)
         s2 = (t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
               if want_sigma2 else None)
-        self._check(self.L.fkreg_log_variance(
+        self._check(getattr(self.L, self._fn_log_variance)(
             self.h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(mh.data_ptr()),
             ctypes.c_void_p(v_grid.data_ptr()), ctypes.c_void_p(v_x.data_ptr()),
             ctypes.c_void_p(kappa.data_ptr()),
@@ -1044,10 +1052,14 @@ class Sweep(Plan):
         self._y_keep = (y, mh)
         return out
 
-    def _unsupported(self, *a, **k):
-        raise FkregError("UNSUPPORTED: a sweep offers set_points, smooth, df and variance")
+    _fn_backward = "fkreg_sweep_backward"
+    _fn_log_variance = "fkreg_sweep_log_variance"
 
-    backward = backward_grid = log_variance = get_sort = set_wait_limit = _unsupported
+    def _unsupported(self, *a, **k):
+        raise FkregError("UNSUPPORTED: a sweep offers set_points, smooth, df, variance, "
+                         "log_variance and backward")
+
+    backward_grid = get_sort = set_wait_limit = _unsupported
 
 
 class Batch:

@@ -145,3 +145,50 @@ def test_single_group_is_a_plan():
     out = p.smooth(torch.tensor(w.y, dtype=torch.float32), want=("mhat_grid",))
     p.sync()
     assert out["mhat_grid"].shape == (w.n_bw, 1) + tuple(w.grid_n)
+
+
+def test_sweep_backward_and_log_variance_equal_group_plans():
+    # the GCV gradient of a bandwidth and the log-variance pass through a
+    # sweep equal the calls on the plan of that bandwidth's group
+    from paper_2204_07716_gb300 import fkreg
+    from paper_2204_07716_gb300.fkreg import Plan, Sweep
+    g = np.random.Generator(np.random.PCG64(123))
+    n = 50_000
+    x = g.random((n, 2))
+    y = np.cos(4 * x[:, 0]) * x[:, 1] + 0.1 * g.standard_normal(n)
+    H = np.array([np.eye(2) * s * s for s in (0.006, 0.01, 0.06, 0.1)])
+    kw = dict(max_n=n, max_probes=4, tol=1e-6, precision="f32", flags=fkreg.FKREG_WANT_BACKWARD)
+    sw = Sweep(2, 1, (64, 64), (0.0, 0.0), (1.0, 1.0), H, max_groups=2, **kw)
+    first, _ = sw.groups()
+    assert len(first) == 3, first
+    xt = torch.tensor(x, dtype=torch.float32)
+    yt = torch.tensor(y, dtype=torch.float32)
+    z = torch.tensor(g.standard_normal((4, n)), dtype=torch.float32)
+    sw.set_points(xt)
+    o = sw.smooth(yt, want=("mhat_grid", "mask", "mhat_at_x"))
+    lv = sw.log_variance(yt, o["mhat_at_x"])
+    sw.sync()
+    grads = {b: sw.backward(yt, 4, probes=z, b=b) for b in (1, 3)}
+    sw.sync()
+    for gi in range(2):
+        b0, b1 = first[gi], first[gi + 1]
+        p = Plan(2, 1, (64, 64), (0.0, 0.0), (1.0, 1.0), H[b0:b1], **kw)
+        p.set_points(xt)
+        op = p.smooth(yt, want=("mhat_grid", "mask", "mhat_at_x"))
+        lp = p.log_variance(yt, op["mhat_at_x"])
+        p.sync()
+        np.testing.assert_allclose(lv["kappa"][b0:b1].cpu().numpy(), lp["kappa"].cpu().numpy(),
+                                   rtol=1e-5)
+        a = lv["v_at_x"][b0:b1].double().cpu().numpy()
+        bref = lp["v_at_x"].double().cpu().numpy()
+        assert np.sum(np.abs(a - bref)) <= 1e-5 * np.sum(np.abs(bref)), gi
+        for b in (1, 3):
+            if not b0 <= b < b1:
+                continue
+            r = p.backward(yt, 4, probes=z, b=b - b0)
+            p.sync()
+            assert grads[b]["gcv"].item() == pytest.approx(r["gcv"].item(), rel=1e-5)
+            np.testing.assert_allclose(grads[b]["dlogh"].cpu().numpy(), r["dlogh"].cpu().numpy(),
+                                       rtol=1e-4, atol=1e-9 * abs(r["gcv"].item()))
+            dy_a, dy_b = grads[b]["dy"].double(), r["dy"].double()
+            assert (dy_a - dy_b).abs().sum().item() <= 1e-4 * dy_b.abs().sum().item()
