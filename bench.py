@@ -65,7 +65,7 @@ def parse():
 
 
 def hbm_peak():
-    """HBM peak: the driver's measured copy bandwidth (MEASURED_PEAKS.json)."""
+    """HBM peak: the measured STREAM-style copy bandwidth in MEASURED_PEAKS.json."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"
