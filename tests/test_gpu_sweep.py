@@ -188,7 +188,12 @@ def test_sweep_backward_and_log_variance_equal_group_plans():
             r = p.backward(yt, 4, probes=z, b=b - b0)
             p.sync()
             assert grads[b]["gcv"].item() == pytest.approx(r["gcv"].item(), rel=1e-5)
-            np.testing.assert_allclose(grads[b]["dlogh"].cpu().numpy(), r["dlogh"].cpu().numpy(),
-                                       rtol=1e-4, atol=1e-9 * abs(r["gcv"].item()))
+            # FP32 fine grids are sums of atomic adds in no fixed order, so two
+            # runs of one call differ by rounding; a component that is a small
+            # difference of large terms (the weak direction of this y) carries
+            # that rounding relative to the gradient's size: normwise, as dy
+            dl_a = grads[b]["dlogh"].cpu().numpy()
+            dl_b = r["dlogh"].cpu().numpy()
+            assert np.max(np.abs(dl_a - dl_b)) <= 1e-4 * np.max(np.abs(dl_b)), (b, dl_a, dl_b)
             dy_a, dy_b = grads[b]["dy"].double(), r["dy"].double()
             assert (dy_a - dy_b).abs().sum().item() <= 1e-4 * dy_b.abs().sum().item()
