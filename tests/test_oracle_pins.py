@@ -119,6 +119,24 @@ def test_local_linear_reproduces_linear_m(d):
     assert np.max(np.abs(r0["mhat"][:, 0] - (a + q @ b))) > 1e-3
 
 
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_local_linear_reproduces_linear_m_where_the_solve_pivots(d):
+    # query points well outside the sample cloud: a first moment of eq. 3's
+    # system exceeds s_0 (|sum_i K (x_i - q)_a| > sum_i K), so the elimination
+    # swaps rows; local linear still reproduces a line exactly there
+    rng = np.random.default_rng(80 + d)
+    n = 60
+    x = rng.random((n, d))
+    H = rand_spd(rng, d, 1.0)          # wide enough that far queries see the samples
+    a, b = 0.3, rng.standard_normal(d)
+    y = a + x @ b
+    q = 3.0 + rng.random((10, d))
+    r = oracle.smooth_at(x, y[None], H, 1, q)
+    first = r["s"][:, 1:d + 1]          # monomial order: 1, then z_1 .. z_d
+    assert np.all(np.max(np.abs(first), axis=1) > r["s"][:, 0])
+    np.testing.assert_allclose(r["mhat"][:, 0], a + q @ b, rtol=1e-9, atol=1e-10)
+
+
 @pytest.mark.parametrize("d", [1, 2])
 def test_local_quadratic_reproduces_quadratic_m(d):
     # order 2 (the paper's LQ): exact for any quadratic m, where LL is not
