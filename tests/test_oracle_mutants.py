@@ -47,6 +47,7 @@ PRED = [("test_predict_reproduces_polynomials", (d,)) for d in (1, 2)]
 CSMOOTH = [("test_compact_kernel_smoothing", (k,)) for k in ("uniform", "epanechnikov")]
 CFULL = [("test_compact_kernel_full_bandwidth_matrix", (k,)) for k in ("epanechnikov",)]
 CDENS = [("test_compact_kernels_are_densities", ("epanechnikov",))]
+SCALE = [("test_scale_field_is_the_absolute_strength_sum", (d,)) for d in (1, 2)]
 
 MUTANTS = [
     # ---- oracle.c: kernel and moment sums (eq. 9); occurrence 0 is the plain
@@ -110,6 +111,9 @@ MUTANTS = [
     Mutant("f32_box_muller_radius_without_2", "c",
            "const float r = sqrtf(-2.0f * logf(u1)), t = 2.0f * (float)M_PI * u2;",
            "const float r = sqrtf(-logf(u1)), t = 2.0f * (float)M_PI * u2;", 1, 0, PROBES),
+    Mutant("f32_uniform_from_23_bits", "c",
+           "const float u1 = (float)((uint32_t)(a >> 40) + 1u) * 0x1.0p-24f;",
+           "const float u1 = (float)((uint32_t)(a >> 41) + 1u) * 0x1.0p-24f;", 1, 0, PROBES),
     Mutant("pair_takes_cosine_twice", "c",
            "out[(int64_t)p * n + i] = (p & 1) ? r * sin(t) : r * cos(t);",
            "out[(int64_t)p * n + i] = r * cos(t);", 1, 0, PROBES),
@@ -126,6 +130,24 @@ MUTANTS = [
            "return (rss / n) / (1.0 - tr / n)", 1, 0, GCV + GCVG),
     Mutant("grid_spacing_over_M", "py", "((b - a) / (m - 1))", "((b - a) / m)", 1, 0,
            [("test_grid_points_eq6", ())] + KDE),
+    Mutant("scale_field_signed", "py",
+           "return moment_sums(x, np.abs(np.atleast_2d(c)), H, 0, q, nthreads, cutoff)[:, :, 0]",
+           "return moment_sums(x, np.atleast_2d(c), H, 0, q, nthreads, cutoff)[:, :, 0]", 1, 0,
+           SCALE),
+    Mutant("scale_field_inflated", "py",
+           "return moment_sums(x, np.abs(np.atleast_2d(c)), H, 0, q, nthreads, cutoff)[:, :, 0]",
+           "return 10.0 * moment_sums(x, np.abs(np.atleast_2d(c)), H, 0, q, nthreads, cutoff)[:, :, 0]",
+           1, 0, SCALE),
+    Mutant("triangle_constant", "py", "k, c = 1.0 - np.sqrt(np.clip(r2, 0.0, None)), (d + 1) / vd",
+           "k, c = 1.0 - np.sqrt(np.clip(r2, 0.0, None)), (d + 2) / vd", 1, 0,
+           [("test_compact_kernels_are_densities", ("triangle",))]),
+    Mutant("biweight_constant", "py", "k, c = (1.0 - r2) ** 2, (d + 2) * (d + 4) / (8.0 * vd)",
+           "k, c = (1.0 - r2) ** 2, (d + 2) * (d + 4) / (6.0 * vd)", 1, 0,
+           [("test_compact_kernels_are_densities", ("biweight",))]),
+    Mutant("triweight_profile_power", "py",
+           "k, c = (1.0 - r2) ** 3, (d + 2) * (d + 4) * (d + 6) / (48.0 * vd)",
+           "k, c = (1.0 - r2) ** 2, (d + 2) * (d + 4) * (d + 6) / (48.0 * vd)", 1, 0,
+           [("test_compact_kernels_are_densities", ("triweight",))]),
     Mutant("epanechnikov_constant", "py", "k, c = 1.0 - r2, (d + 2) / (2.0 * vd)",
            "k, c = 1.0 - r2, (d + 2) / vd", 1, 0, CDENS + CSMOOTH),
     Mutant("compact_scale_det_not_sqrt", "py", "scale = 1.0 / math.sqrt(np.linalg.det(H))",
@@ -142,6 +164,10 @@ MUTANTS = [
            "kappa = 1.0 / np.mean(r.T, axis=0)", 1, 0, [("test_log_variance_closed_forms", ())]),
     Mutant("interval_one_sided_quantile", "py", "z = norm.ppf(1.0 - 0.5 * alpha)",
            "z = norm.ppf(1.0 - alpha)", 1, 0, [("test_interval_eq28", ())]),
+    Mutant("interval_uses_variance_as_sd", "py",
+           "sd = np.where(v >= 0, np.sqrt(np.where(v >= 0, v, 0.0)), np.nan)",
+           "sd = np.where(v >= 0, np.where(v >= 0, v, 0.0), np.nan)", 1, 0,
+           [("test_interval_eq28", ())]),
     Mutant("keys_parameter", "py", "def _keys_weights(t: float, a: float = -0.5):",
            "def _keys_weights(t: float, a: float = -0.75):", 1, 0, PRED),
     Mutant("keys_boundary_row_linear", "py", "for c, off in ((3, 0), (-3, 1), (1, 2)):",
@@ -157,9 +183,20 @@ MUTANTS = [
     Mutant("vjp_kernel_gradient_sign", "py",
            "grad = K[:, None] * (dP - P[:, None] * z * hinv[None, :])",
            "grad = K[:, None] * (dP + P[:, None] * z * hinv[None, :])", 1, 0, VJP),
+    Mutant("vjp_target_side_dropped", "py", "dx[qi] -= np.sum(grad, axis=0)", "pass", 1, 0,
+           VJP),
+    Mutant("vjp_s_adjoint_sign", "py",
+           "sbar = np.array([-sum(a[u] * bbar[v] for u, v in pr) for pr in pair])",
+           "sbar = np.array([sum(a[u] * bbar[v] for u, v in pr) for pr in pair])", 1, 0, VJP),
+    Mutant("gcv_grad_explicit_dy_sign", "py", '"dy": g["dY"][0] + 2.0 * L_rss * r',
+           '"dy": g["dY"][0] - 2.0 * L_rss * r', 1, 0, GCVG),
     Mutant("gcv_grad_trace_adjoint_power", "py", "L_tr = 2.0 * (rss / n) / (n * den ** 3)",
            "L_tr = 2.0 * (rss / n) / (n * den ** 2)", 1, 0, GCVG),
     Mutant("select_h_ties_to_smaller", "py", "return int(ok.max())", "return int(ok.min())", 1, 0,
+           [("test_select_h_dstd_rule", ())]),
+    Mutant("select_h_dstd_in_variance_units", "py",
+           "thr = np.nanmin(g) + dstd * (np.nanstd(g) if dstd else 0.0)",
+           "thr = np.nanmin(g) + dstd * (np.nanvar(g) if dstd else 0.0)", 1, 0,
            [("test_select_h_dstd_rule", ())]),
     Mutant("hlist_linear_for_log", "py",
            "return 10.0 ** np.linspace(math.log10(lo), math.log10(hi), n)",

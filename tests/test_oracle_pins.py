@@ -53,6 +53,20 @@ def test_single_point_numerator_is_the_gaussian_density(d):
     np.testing.assert_allclose(t, ref, rtol=1e-13)
 
 
+@pytest.mark.parametrize("d", [1, 2])
+def test_scale_field_is_the_absolute_strength_sum(d):
+    # the natural size a(q) = sum_i K_H(x_i - q) |c_i| that normalises every
+    # field error: scipy's density times |c|, for strengths of both signs
+    rng = np.random.default_rng(15 + d)
+    H = rand_spd(rng, d, 0.12)
+    x = rng.random((30, d))
+    c = np.stack([rng.standard_normal(30), np.ones(30)])
+    q = rng.random((9, d))
+    a = oracle.scale_field(x, c, H, q)
+    K = np.stack([stats.multivariate_normal(mean=x[i], cov=H).pdf(q) for i in range(30)], axis=1)
+    np.testing.assert_allclose(a, K @ np.abs(c).T, rtol=1e-12)
+
+
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_first_and_second_moments_are_density_derivatives(d):
     # grad_q s_0 = H^-1 s_(1) and H (grad grad^T s_0) H = s_(2) - H s_0, where
