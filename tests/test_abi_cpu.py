@@ -73,6 +73,35 @@ def test_geometry_covers_tail_and_spectrum(lib):
         assert g["inv_h"][j] == pytest.approx(g["nf"][j] / g["period"][j], rel=1e-7)
 
 
+@pytest.mark.parametrize("d,tol,order", [(d, t, o) for d in (1, 2, 3) for t in (1e-6, 1e-9, 1e-12)
+                                          for o in (0, 1, 2) if not (d == 3 and o == 2)])
+def test_geometry_invariants_across_configurations(lib, d, tol, order):
+    # for every accepted plan: the period leaves room for the Gaussian tail to
+    # fall below tol before it wraps into the box (exp(-r^2/2) < tol), the
+    # largest kept mode's Gaussian multiplier is below tol, the fine grid is
+    # oversampled by at least 2, the ES width follows tol, and a fine grid
+    # beyond the size limit is refused as UNSUPPORTED, not planned
+    need = math.sqrt(2 * math.log(1 / tol))
+    for sig in (0.002, 0.005, 0.01, 0.03, 0.1, 0.3):
+        for grid in (64, 256):
+            kw = dict(d=d, order=order, grid_n=(grid,) * d, lo=(0.0,) * d, hi=(1.0,) * d,
+                      H=np.eye(d) * sig * sig, tol=tol, precision="f64" if tol < 1e-7 else "f32")
+            try:
+                g = fkreg.geometry(**kw)
+            except fkreg.FkregError as e:
+                assert "UNSUPPORTED" in str(e) and d == 3 and sig < 0.005, (kw, e)
+                continue
+            assert g["w"] == math.ceil(math.log10(1 / tol)) + 1
+            for j in range(d):
+                P, K, nf = g["period"][j], g["modes"][j], g["nf"][j]
+                assert (P - 1.0) / sig >= need, (kw, j, P)
+                assert P == pytest.approx(g["ldft"][j] / (grid - 1))
+                xi = (K // 2 - 1) / P
+                assert math.exp(-2 * math.pi ** 2 * sig ** 2 * xi ** 2) < tol, (kw, j, K)
+                assert nf >= 2 * K and nf % 2 == 0
+                assert g["inv_h"][j] == pytest.approx(nf / P, rel=1e-7)
+
+
 def test_direct_geometry_for_compact_kernels(lib):
     # compact kernels: bins on the output lattice (n_f = M), cells of the
     # grid spacing, a quarter of the widest support half-width per bin
