@@ -503,13 +503,35 @@ class Plan:
             setattr(s, k, o[k].data_ptr() if k in o else None)
         return s
 
+    def _need(self, a, count: int, what: str):
+        """The C call reads ``count`` values of ``a``: refuse a smaller tensor,
+        which the device would read past its end."""
+        if a.numel() < count:
+            raise FkregError(f"INVALID_ARG: {what} holds {a.numel()} values where the call "
+                             f"reads {count}")
+
     def _y(self, y):
         y = self._as_dev(y, complex_ok=self.y_complex)
         if self.y_complex and y.dim() == 2:      # [n, 2] from a 1-D complex vector
             y = y.unsqueeze(0)
         if not self.y_complex and y.dim() == 1:
             y = y.unsqueeze(0)
+        self._need(y, self.n_rhs * self.n * (2 if self.y_complex else 1),
+                   "y ([n_rhs, n] responses)")
         return y.contiguous()
+
+    def _probes(self, probes, n_probes: int):
+        if probes is None:
+            return None
+        pr = self._as_dev(probes)
+        self._need(pr, max(int(n_probes), 0) * self.n, "probes ([n_probes, n])")
+        return pr
+
+    def _mhat_at_x(self, mhat_at_x, complex_ok: bool):
+        mh = self._as_dev(mhat_at_x, complex_ok=complex_ok)
+        self._need(mh, self.n_bw * self.n_rhs * self.n * (2 if self.y_complex else 1),
+                   "mhat_at_x ([n_bw, n_rhs, n])")
+        return mh
 
     def smooth(self, y, want=("mhat_grid", "mask")) -> Dict[str, object]:
         y = self._y(y)
@@ -523,9 +545,7 @@ class Plan:
     def df(self, y, n_probes: int, seed: int = 0, probes=None,
            want=("mhat_grid", "mask")) -> Dict[str, object]:
         y = self._y(y)
-        pr = None
-        if probes is not None:
-            pr = self._as_dev(probes)
+        pr = self._probes(probes, n_probes)
         o = self._outputs(want, df=True)
         s = self._struct(o)
         self._check(self.L.fkreg_df(self.h, ctypes.c_void_p(y.data_ptr()), int(n_probes),
@@ -540,7 +560,7 @@ class Plan:
         """GCV of bandwidth b and its gradient (fkreg_backward)."""
         t = self.torch
         y = self._y(y)
-        pr = None if probes is None else self._as_dev(probes)
+        pr = self._probes(probes, n_probes)
         n = max(self.n, 1)
         out = {"gcv": t.empty(1, dtype=t.float64, device=self.device)}
         if "dlogh" in want:
@@ -582,7 +602,7 @@ class Plan:
     def variance(self, y, mhat_at_x):
         t = self.torch
         y = self._y(y)
-        mh = self._as_dev(mhat_at_x, complex_ok=self.y_complex)
+        mh = self._mhat_at_x(mhat_at_x, complex_ok=self.y_complex)
         out = t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
         self._check(self.L.fkreg_variance(self.h, ctypes.c_void_p(y.data_ptr()),
                                           ctypes.c_void_p(mh.data_ptr()),
@@ -595,7 +615,7 @@ class Plan:
         kappa per bandwidth and response, and sigma^2 = exp(v) / kappa on the grid."""
         t = self.torch
         y = self._y(y)
-        mh = self._as_dev(mhat_at_x)
+        mh = self._mhat_at_x(mhat_at_x, complex_ok=False)
         v_grid = t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
         v_x = t.empty((self.n_bw, self.n_rhs, self.n), dtype=self.dtype, device=self.device)
         kappa = t.empty((self.n_bw, self.n_rhs), dtype=t.float64, device=self.device)
@@ -1031,7 +1051,7 @@ class Sweep(Plan):
     def df(self, y, n_probes: int, seed: int = 0, probes=None,
            want=("mhat_grid", "mask")) -> Dict[str, object]:
         y = self._y(y)
-        pr = None if probes is None else self._as_dev(probes)
+        pr = self._probes(probes, n_probes)
         o = self._outputs(want, df=True)
         s = self._struct(o)
         self._check(self.L.fkreg_sweep_df(self.h, ctypes.c_void_p(y.data_ptr()), int(n_probes),
@@ -1044,7 +1064,7 @@ class Sweep(Plan):
     def variance(self, y, mhat_at_x):
         t = self.torch
         y = self._y(y)
-        mh = self._as_dev(mhat_at_x, complex_ok=self.y_complex)
+        mh = self._mhat_at_x(mhat_at_x, complex_ok=self.y_complex)
         out = t.empty((self.n_bw, self.n_rhs) + self.grid_n, dtype=self.dtype, device=self.device)
         self._check(self.L.fkreg_sweep_variance(self.h, ctypes.c_void_p(y.data_ptr()),
                                                 ctypes.c_void_p(mh.data_ptr()),

@@ -249,3 +249,51 @@ def test_sweep_picks_direct_sums_only_where_they_pay():
     with pytest.raises(fkreg.FkregError):
         fkreg.geometry(d=2, order=1, grid_n=(128, 128), lo=(0, 0), hi=(1, 1), H=H[1:2],
                        kernel="gaussian_direct", flags=fkreg.FKREG_WANT_BACKWARD)
+
+
+def _standin_plan(n, n_rhs=1, n_bw=1, y_complex=False, d=2):
+    # a Plan object without a device plan: only the argument marshalling runs
+    import torch
+    p = fkreg.Plan.__new__(fkreg.Plan)
+    p.torch = torch
+    p.device = torch.device("cpu")
+    p.d, p.n_rhs, p.n_bw, p.n = d, n_rhs, n_bw, n
+    p.y_complex = y_complex
+    p.dtype, p.cdtype = torch.float32, torch.complex64
+    return p
+
+
+def test_inputs_smaller_than_the_call_reads_are_refused():
+    # the C calls read [n_rhs, n] responses, [n_probes, n] probes and
+    # [n_bw, n_rhs, n] at-sample estimates from device memory by size alone:
+    # the binding refuses a tensor with fewer values, which the device would
+    # read past its end, and accepts every shape the plan calls produce
+    import torch
+    p = _standin_plan(10)
+    assert tuple(p._y(torch.zeros(10)).shape) == (1, 10)
+    assert tuple(p._y(np.zeros((1, 10))).shape) == (1, 10)
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: y"):
+        p._y(torch.zeros(9))
+    p2 = _standin_plan(10, n_rhs=2, n_bw=3)
+    assert tuple(p2._y(torch.zeros(2, 10)).shape) == (2, 10)
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: y"):
+        p2._y(torch.zeros(10))
+    assert p2._probes(None, 4) is None
+    assert tuple(p2._probes(torch.zeros(4, 10), 4).shape) == (4, 10)
+    assert tuple(p2._probes(torch.zeros(5, 10), 4).shape) == (5, 10)
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: probes"):
+        p2._probes(torch.zeros(3, 10), 4)
+    assert p2._mhat_at_x(torch.zeros(3, 2, 10), False).numel() == 60
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: mhat_at_x"):
+        p2._mhat_at_x(torch.zeros(1, 2, 10), False)
+    # complex responses: interleaved (re, im), twice the values
+    pc = _standin_plan(10, y_complex=True)
+    assert tuple(pc._y(torch.zeros(10, dtype=torch.complex64)).shape) == (1, 10, 2)
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: y"):
+        pc._y(torch.zeros(10))
+    assert pc._mhat_at_x(torch.zeros(1, 1, 10, dtype=torch.complex64), True).numel() == 20
+    # no samples yet (or none at all): nothing is read, the outputs of a
+    # plan with n = 0 (one padding value) pass
+    p0 = _standin_plan(0)
+    assert p0._y(torch.zeros(0)).numel() == 0
+    assert p0._mhat_at_x(torch.zeros(1, 1, 1), False).numel() == 1
