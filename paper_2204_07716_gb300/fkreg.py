@@ -432,10 +432,18 @@ class Plan:
                 raise FkregError("complex locations are a vector of n points")
         else:
             x = self._as_dev(x)
-        n = int(x.shape[0])
+        n = self._sample_count(x)
         self._x = x
         self._check(self.L.fkreg_set_points(self.h, n, ctypes.c_void_p(x.data_ptr()), self._stream()))
         self.n = n
+
+    def _sample_count(self, x) -> int:
+        """n of samples x [n, d] (or [n] when d = 1); the C call reads n * d values."""
+        n = int(x.shape[0]) if x.dim() > 0 else 0
+        if (x.dim() == 2 and int(x.shape[1]) != self.d) or x.dim() > 2:
+            raise FkregError(f"INVALID_ARG: samples of shape {tuple(x.shape)} for a {self.d}-D plan")
+        self._need(x, n * self.d, f"x ([n, {self.d}] samples)")
+        return n
 
     def sync(self):
         self._check(self.L.fkreg_sync_status(self.h, self._stream()))
@@ -1018,7 +1026,7 @@ class Sweep(Plan):
 
     def set_points(self, x):
         x = self._as_dev(x)
-        n = int(x.shape[0])
+        n = self._sample_count(x)
         self._x = x
         self._check(self.L.fkreg_sweep_set_points(self.h, n, ctypes.c_void_p(x.data_ptr()),
                                                   self._stream()))

@@ -297,3 +297,16 @@ def test_inputs_smaller_than_the_call_reads_are_refused():
     p0 = _standin_plan(0)
     assert p0._y(torch.zeros(0)).numel() == 0
     assert p0._mhat_at_x(torch.zeros(1, 1, 1), False).numel() == 1
+
+
+def test_sample_arrays_must_match_the_plan_dimension():
+    import torch
+    p = _standin_plan(0, d=2)
+    assert p._sample_count(torch.zeros(7, 2)) == 7
+    assert p._sample_count(torch.zeros(0, 2)) == 0
+    for bad in (torch.zeros(7, 3), torch.zeros(7), torch.zeros(7, 2, 1)):
+        with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
+            p._sample_count(bad)
+    p1 = _standin_plan(0, d=1)
+    assert p1._sample_count(torch.zeros(7)) == 7
+    assert p1._sample_count(torch.zeros(7, 1)) == 7
