@@ -1138,7 +1138,11 @@ class Batch:
         """Record the batch; xs, ys are device tensors per problem (kept alive)."""
         t = self.torch
         n = len(self.problems)
-        self._inputs = (list(xs), list(ys))
+        xs, ys = list(xs), list(ys)
+        if len(xs) != n or len(ys) != n:
+            raise FkregError(f"INVALID_ARG: {n} problems, {len(xs)} sample and {len(ys)} "
+                             "response tensors")
+        self._inputs = (xs, ys)
         outs = []
         arr_out = (Outputs * n)()
         nn = (ctypes.c_int64 * n)()
@@ -1155,6 +1159,17 @@ class Batch:
             nbw = np.asarray(p["H"]).reshape(-1, d, d).shape[0]
             x = xs[i]
             ni = int(x.shape[0])
+            # the recorded kernels read these pointers by size alone: each
+            # tensor must live on the batch's device, in the problem's
+            # precision, contiguous and at least as large as the call reads
+            for name, a, count in (("x", x, ni * d), ("y", ys[i], ni * (2 if cplx else 1))):
+                real = t.view_as_real(a) if a.is_complex() else a
+                if (a.device != self.device or real.dtype != dt or not a.is_contiguous()
+                        or real.numel() < count or (name == "x" and x.dim() == 2
+                                                    and int(x.shape[1]) != d)):
+                    raise FkregError(f"INVALID_ARG: problem {i}: {name} must be a contiguous "
+                                     f"{dt} tensor on {self.device} with at least {count} "
+                                     f"values (got {tuple(a.shape)} {a.dtype} on {a.device})")
             o = {"mhat_grid": t.empty((nbw, 1) + grid, dtype=cdt if cplx else dt, device=self.device),
                  "mask": t.empty((nbw,) + grid, dtype=t.uint8, device=self.device),
                  "mhat_at_x": t.empty((nbw, 1, max(ni, 1)), dtype=cdt if cplx else dt,

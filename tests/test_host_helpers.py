@@ -310,3 +310,36 @@ def test_sample_arrays_must_match_the_plan_dimension():
     p1 = _standin_plan(0, d=1)
     assert p1._sample_count(torch.zeros(7)) == 7
     assert p1._sample_count(torch.zeros(7, 1)) == 7
+
+
+def test_batch_capture_refuses_inputs_the_kernels_cannot_read(monkeypatch):
+    # Batch.capture hands raw pointers to the recorded kernels: every tensor
+    # must be on the batch's device, in the problem's precision, contiguous
+    # and large enough; the check runs before anything is recorded
+    import types
+    import torch
+    monkeypatch.setattr(torch.cuda, "current_stream",
+                        lambda *a, **k: types.SimpleNamespace(cuda_stream=0))
+    b = fkreg.Batch.__new__(fkreg.Batch)
+    b.torch, b.device, b.h = torch, torch.device("cpu"), None
+    b.problems = [dict(d=2, grid_n=(8, 8), H=np.eye(2) * 0.01, y_complex=True, precision="f32")]
+    reached = []
+
+    class StandInLib:
+        def fkreg_batch_capture(self, *a):
+            reached.append(a)
+            return 0
+
+    b.L = StandInLib()
+    x, y = torch.zeros(5, 2), torch.zeros(5, 2)            # y: (re, im) pairs
+    b.capture([x], [y])
+    b.capture([x], [torch.zeros(5, dtype=torch.complex64)])
+    assert len(reached) == 2
+    for xs, ys in (([torch.zeros(5, 2, dtype=torch.float64)], [y]),      # wrong precision
+                   ([torch.zeros(5, 3)], [y]),                            # wrong dimension
+                   ([torch.zeros(2, 5).t()], [y]),                        # not contiguous
+                   ([x], [torch.zeros(5)]),                               # complex needs 2n values
+                   ([x, x], [y, y])):                                     # one problem only
+        with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
+            b.capture(xs, ys)
+    assert len(reached) == 2
