@@ -882,8 +882,10 @@ def interval(mhat, var, alpha: float = 0.05):
     float64): returns (lower, upper) = mhat -/+ z_(1-alpha/2) sqrt(var)."""
     import torch
     L = load()
+    if not (mhat.is_cuda and mhat.dtype in (torch.float32, torch.float64)):
+        raise FkregError("interval: mhat must be a float32 or float64 CUDA tensor")
     m = mhat.contiguous()
-    v = var.to(m.dtype).contiguous()
+    v = torch.as_tensor(var).to(device=m.device, dtype=m.dtype).contiguous()
     if v.shape != m.shape:
         v = v.expand(m.shape).contiguous()
     lo, hi = torch.empty_like(m), torch.empty_like(m)
@@ -900,19 +902,25 @@ def interval(mhat, var, alpha: float = 0.05):
 def predict(grid, grid_n, lo, hi, xq, method: str = "linear"):
     """Values of grid estimates at new points (device tensors).
 
-    grid: [..., M_1..M_d] (leading dims flattened into count); xq: [nq, d] of
-    the same dtype.  method "linear" or "cubic".  Returns [..., nq].
+    grid: [..., M_1..M_d] float32 or float64 on the GPU (leading dims
+    flattened into count); xq: [nq, d] points, taken to the grid's device and
+    dtype.  method "linear" or "cubic".  Returns [..., nq].
     """
     import torch
     L = load()
+    if method not in ("linear", "cubic"):
+        raise FkregError(f"predict: unknown method {method!r} ('linear' or 'cubic')")
     d = len(grid_n)
     if xq.is_complex():  # complex new points on a 2-D grid: (Re z, Im z)
         if d != 2:
             raise FkregError("complex points need a 2-D grid")
         xq = torch.view_as_real(xq.reshape(-1))
+    if not (grid.is_cuda and grid.dtype in (torch.float32, torch.float64)):
+        raise FkregError("predict: grid must be a float32 or float64 CUDA tensor")
     lead = grid.shape[: grid.dim() - d]
     g = grid.reshape(-1, *grid_n).contiguous()
-    x = xq.to(g.dtype).reshape(-1, d).contiguous()
+    # the points go to the grid's device: the kernel reads both by pointer
+    x = xq.to(device=g.device, dtype=g.dtype).reshape(-1, d).contiguous()
     out = torch.empty((g.shape[0], x.shape[0]), dtype=g.dtype, device=g.device)
     gn = (ctypes.c_int64 * d)(*[int(v) for v in grid_n])
     glo = (ctypes.c_double * d)(*[float(v) for v in lo])

@@ -343,3 +343,16 @@ def test_batch_capture_refuses_inputs_the_kernels_cannot_read(monkeypatch):
         with pytest.raises(fkreg.FkregError, match="INVALID_ARG"):
             b.capture(xs, ys)
     assert len(reached) == 2
+
+
+def test_predict_and_interval_refuse_host_arrays():
+    # both hand raw pointers to a kernel: a host tensor is refused before any
+    # launch (query points on the host are copied to the grid's device)
+    import torch
+    g = torch.zeros(4, 4, dtype=torch.float64)
+    with pytest.raises(fkreg.FkregError, match="CUDA tensor"):
+        fkreg.predict(g, (4, 4), (0, 0), (1, 1), torch.zeros(3, 2))
+    with pytest.raises(fkreg.FkregError, match="unknown method"):
+        fkreg.predict(g, (4, 4), (0, 0), (1, 1), torch.zeros(3, 2), "nearest")
+    with pytest.raises(fkreg.FkregError, match="CUDA tensor"):
+        fkreg.interval(g, torch.ones(4, 4, dtype=torch.float64))
