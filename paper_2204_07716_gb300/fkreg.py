@@ -1172,7 +1172,9 @@ class Batch:
             # precision, contiguous and at least as large as the call reads
             for name, a, count in (("x", x, ni * d), ("y", ys[i], ni * (2 if cplx else 1))):
                 real = t.view_as_real(a) if a.is_complex() else a
-                if (a.device != self.device or real.dtype != dt or not a.is_contiguous()
+                other = (a.device.type != self.device.type or (
+                    self.device.index is not None and a.device.index != self.device.index))
+                if (other or real.dtype != dt or not a.is_contiguous()
                         or real.numel() < count or (name == "x" and x.dim() == 2
                                                     and int(x.shape[1]) != d)):
                     raise FkregError(f"INVALID_ARG: problem {i}: {name} must be a contiguous "
