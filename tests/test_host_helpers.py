@@ -356,3 +356,76 @@ def test_predict_and_interval_refuse_host_arrays():
         fkreg.predict(g, (4, 4), (0, 0), (1, 1), torch.zeros(3, 2), "nearest")
     with pytest.raises(fkreg.FkregError, match="CUDA tensor"):
         fkreg.interval(g, torch.ones(4, 4, dtype=torch.float64))
+
+
+def _compositions(n, k_max):
+    # every split of [0, n) into at most k_max contiguous non-empty groups
+    import itertools
+    for k in range(1, min(k_max, n) + 1):
+        for cuts in itertools.combinations(range(1, n), k - 1):
+            yield [0, *cuts, n]
+
+
+SPLIT_CASES = [  # d, samples, seed, bandwidth range, grid points per axis
+    (2, 200_000, 1, (0.0015, 0.3), 100),   # unsorted; three groups, one of direct sums
+    (2, 1_000_000, 6, (0.002, 0.25), 128),  # two groups
+    (2, 4_000_000, 2, (0.003, 0.3), 256),   # one group
+    (3, 2_000_000, 3, (0.004, 0.15), 96),   # unsorted; direct sums for the narrow group
+    (1, 50_000, 4, (0.0005, 0.3), 512),
+]
+
+
+@pytest.mark.parametrize("d,max_n,seed,srange,grid", SPLIT_CASES)
+def test_sweep_split_is_the_cheapest_contiguous_split(d, max_n, seed, srange, grid):
+    # the split's dynamic program against brute force over every contiguous
+    # split into at most K groups, each group priced by the same entry point
+    # on that sub-list alone (one group); refused groups are infeasible
+    rng = np.random.default_rng(seed)
+    n_bw = 6 if d < 3 else 5
+    sig = np.sort(np.exp(rng.uniform(np.log(srange[0]), np.log(srange[1]), n_bw)))
+    if seed % 2:
+        sig = sig[rng.permutation(n_bw)]           # the caller's order, not sorted
+    H = np.array([np.eye(d) * s * s for s in sig])
+    kw = dict(d=d, order=1 if d < 3 else 0, grid_n=(grid,) * d, lo=(0.0,) * d, hi=(1.0,) * d,
+              n_rhs=1, max_probes=4, tol=1e-6, precision="f32")
+    memo = {}
+
+    def group(a, b):
+        if (a, b) not in memo:
+            first, cost, kern = fkreg.sweep_split(max_n, 1, with_kernels=True, H=H[a:b], **kw)
+            memo[(a, b)] = (cost, kern[0]) if cost >= 0 else (None, None)
+        return memo[(a, b)]
+
+    for K in (1, 2, 3):
+        first, cost, kern = fkreg.sweep_split(max_n, K, with_kernels=True, H=H, **kw)
+        best = None
+        for split in _compositions(n_bw, K):
+            parts = [group(a, b)[0] for a, b in zip(split, split[1:])]
+            if any(p is None for p in parts):
+                continue
+            tot = sum(parts)
+            best = tot if best is None else min(best, tot)
+        assert best is not None
+        assert cost == pytest.approx(best, rel=1e-12), (K, first)
+        assert len(first) - 1 <= K and first[0] == 0 and first[-1] == n_bw
+        chosen = [group(a, b) for a, b in zip(first, first[1:])]
+        assert sum(c for c, _ in chosen) == pytest.approx(cost, rel=1e-12)
+        assert kern == [k for _, k in chosen]
+
+
+def test_the_split_cases_include_real_splits():
+    # the brute-force cases above are not all single groups
+    groups = []
+    for d, max_n, seed, srange, grid in SPLIT_CASES:
+        rng = np.random.default_rng(seed)
+        n_bw = 6 if d < 3 else 5
+        sig = np.sort(np.exp(rng.uniform(np.log(srange[0]), np.log(srange[1]), n_bw)))
+        if seed % 2:
+            sig = sig[rng.permutation(n_bw)]
+        H = np.array([np.eye(d) * s * s for s in sig])
+        first, _, kern = fkreg.sweep_split(
+            max_n, 3, with_kernels=True, d=d, order=1 if d < 3 else 0, grid_n=(grid,) * d,
+            lo=(0.0,) * d, hi=(1.0,) * d, H=H, n_rhs=1, max_probes=4, tol=1e-6, precision="f32")
+        groups.append((len(first) - 1, kern))
+    assert max(g for g, _ in groups) == 3 and any(g == 2 for g, _ in groups)
+    assert any("gaussian_direct" in k for _, k in groups)
