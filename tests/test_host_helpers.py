@@ -1,5 +1,8 @@
-"""Host-side helpers of the binding (no GPU): the candidate bandwidth lists of
-Sec. 4 (get_hList) and the dstd selection rule of Table 1."""
+"""Host-side logic of the binding (no GPU): the candidate bandwidth lists of
+Sec. 4 (get_hList), the dstd selection rule of Table 1, the orchestration of
+cv_fkreg and gcv, the sweep's split, and the marshalling of every plan call
+(input checks, shapes, the entry point reached) against stand-in libraries."""
+import ctypes
 import os
 
 import numpy as np
@@ -429,3 +432,91 @@ def test_the_split_cases_include_real_splits():
         groups.append((len(first) - 1, kern))
     assert max(g for g, _ in groups) == 3 and any(g == 2 for g, _ in groups)
     assert any("gaussian_direct" in k for _, k in groups)
+
+
+class _RecordingLib:
+    # stands in for the C library: every entry point returns FKREG_OK and is recorded
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        def call(*a):
+            self.calls.append(name)
+            return 0
+        return call
+
+
+@pytest.mark.parametrize("cls", ["Plan", "Sweep"])
+def test_plan_methods_marshal_the_shapes_the_calls_use(cls, monkeypatch):
+    # a dry run of every plan call on host tensors with a stand-in library:
+    # the marshalling (shapes, the size checks, the entry point each call
+    # reaches) runs exactly as on the GPU, no kernel does
+    import types
+    import torch
+    monkeypatch.setattr(torch.cuda, "current_stream",
+                        lambda *a, **k: types.SimpleNamespace(cuda_stream=0))
+    p = getattr(fkreg, cls).__new__(getattr(fkreg, cls))
+    p.torch, p.device = torch, torch.device("cpu")
+    p.d, p.order, p.n_rhs, p.n_bw, p.n = 2, 1, 1, 2, 0
+    p.grid_n, p.M, p.ns, p.nt, p.max_probes = (8, 8), 64, 6, 3, 4
+    p.y_complex, p.precision = False, "f32"
+    p.dtype, p.cdtype = torch.float32, torch.complex64
+    p.L, p.h = _RecordingLib(), ctypes.c_void_p(0)
+    n = 50
+    p.set_points(torch.rand(n, 2, dtype=torch.float64))
+    assert p.n == n
+    y = torch.randn(n)
+    o = p.smooth(y, want=("mhat_grid", "mask", "mhat_at_x"))
+    assert o["mhat_at_x"].shape == (2, 1, n)
+    o = p.df(y, 4, probes=torch.randn(4, n), want=("mhat_grid", "mhat_at_x"))
+    assert o["gcv"].shape == (2, 1) and o["trace"].shape == (2, 3)
+    p.df(y, 4)
+    s2 = p.variance(y, o["mhat_at_x"])
+    assert s2.shape == (2, 1, 8, 8)
+    lv = p.log_variance(y, o["mhat_at_x"])
+    assert lv["v_at_x"].shape == (2, 1, n) and lv["kappa"].shape == (2, 1)
+    g = p.backward(y, 4, probes=torch.randn(4, n), b=1)
+    assert g["dy"].shape == (n,) and g["dx"].shape == (n, 2) and g["dlogh"].shape == (2,)
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: probes"):
+        p.df(y, 4, probes=torch.randn(3, n))
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: mhat_at_x"):
+        p.variance(y, o["mhat_at_x"][:1])
+    if cls == "Plan":
+        r = p.backward_grid(y, torch.zeros(8, 8), b=0)
+        assert r["dy"].shape == (1, n)
+        names = ["fkreg_set_points", "fkreg_smooth", "fkreg_df", "fkreg_df", "fkreg_variance",
+                 "fkreg_log_variance", "fkreg_backward", "fkreg_backward_grid"]
+    else:
+        names = ["fkreg_sweep_set_points", "fkreg_sweep_smooth", "fkreg_sweep_df",
+                 "fkreg_sweep_df", "fkreg_sweep_variance", "fkreg_sweep_log_variance",
+                 "fkreg_sweep_backward"]
+    assert p.L.calls == names
+    p.h = None                                   # nothing to destroy
+
+
+def test_complex_plan_marshals_interleaved_values(monkeypatch):
+    # complex responses and complex locations go to the C calls as (re, im)
+    # pairs; the at-sample estimates a smooth returns feed the variance pass
+    import types
+    import torch
+    monkeypatch.setattr(torch.cuda, "current_stream",
+                        lambda *a, **k: types.SimpleNamespace(cuda_stream=0))
+    p = fkreg.Plan.__new__(fkreg.Plan)
+    p.torch, p.device = torch, torch.device("cpu")
+    p.d, p.order, p.n_rhs, p.n_bw, p.n = 2, 1, 1, 1, 0
+    p.grid_n, p.M, p.ns, p.nt, p.max_probes = (8, 8), 64, 6, 3, 0
+    p.y_complex, p.precision = True, "f64"
+    p.dtype, p.cdtype = torch.float64, torch.complex128
+    p.L, p.h = _RecordingLib(), ctypes.c_void_p(0)
+    n = 30
+    p.set_points(torch.rand(n, dtype=torch.float64) + 1j * torch.rand(n, dtype=torch.float64))
+    assert p.n == n and tuple(p._x.shape) == (n, 2)
+    y = torch.randn(n, dtype=torch.complex128)
+    o = p.smooth(y, want=("mhat_grid", "mhat_at_x"))
+    assert o["mhat_at_x"].dtype == torch.complex128 and o["mhat_at_x"].shape == (1, 1, n)
+    s2 = p.variance(y, o["mhat_at_x"])
+    assert s2.dtype == torch.float64
+    with pytest.raises(fkreg.FkregError, match="INVALID_ARG: y"):
+        p.smooth(y.real)                          # half the values a complex call reads
+    assert p.L.calls == ["fkreg_set_points", "fkreg_smooth", "fkreg_variance"]
+    p.h = None
