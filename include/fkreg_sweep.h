@@ -109,9 +109,12 @@ fkreg_status fkreg_sweep_log_variance(fkreg_sweep S, const void* y_dev, const vo
                                       void* v_grid_dev, void* v_at_x_dev, double* kappa_dev,
                                       void* sigma2_grid_dev, void* stream);
 
-/* fkreg_backward for bandwidth b (index in the caller's list), run by the
- * plan of b's group (whose opts carry FKREG_WANT_BACKWARD if the sweep's
- * did); outputs as for the plan call. */
+/* fkreg_backward for bandwidth b (index in the caller's list): GCV of
+ * eq. 22 with the Monte-Carlo trace of Sec. 2.1 and its gradient with
+ * respect to log h, y and x, run by the plan of b's group (whose opts carry
+ * FKREG_WANT_BACKWARD if the sweep's did); arguments, outputs and the
+ * plan-level refusals as for fkreg_backward; b outside [0, n_bw) returns
+ * FKREG_ERR_INVALID_ARG before anything runs. */
 fkreg_status fkreg_sweep_backward(fkreg_sweep S, const void* y_dev, int n_probes, uint64_t seed,
                                   const void* probes_dev, int b, double* gcv_dev,
                                   double* dlogh_dev, void* dy_dev, void* dx_dev, void* stream);
