@@ -45,3 +45,29 @@ def test_short_region_falls_back_to_the_nearest_sample(fake_smi):
     c.start()
     r = c.stop()                   # a region of a few microseconds
     assert r["samples"] >= 1 and r["sm_mhz"] == 2070
+
+
+def test_reference_arm_prints_the_contract_line():
+    # bench.py --impl reference times the FP64 oracle on the host cores (no
+    # GPU): one JSON line with the contract's keys, its e2e without copies and
+    # a cpu_baseline that describes this run
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    import bench
+    assert j["impl"] == "reference" and j["metric"] == bench.METRIC and j["unit"] == bench.UNIT
+    assert j["value"] > 0 and j["ms_per_step"] > 0 and j["higher_is_better"] is True
+    assert (j["n_gpus"], j["steps"], j["warmup"]) == (1, 1, 0)
+    assert j["config"]["workload"] == bench.WORKLOAD and j["data"] == "synthetic"
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == j["value"]
+    assert isinstance(cb["sample"], str) and cb["sample"]
+    assert j["e2e"] == {"value": j["value"], "unit": j["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
