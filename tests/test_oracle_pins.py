@@ -350,14 +350,14 @@ def test_interval_eq28():
     assert np.isnan(lo[0]) and np.isnan(hi[0])
 
 
-@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("d", [1, 2, 3])
 def test_predict_reproduces_polynomials(d):
     # multilinear interpolation is exact for affine functions (also when it
     # extends past the box); cubic convolution with Keys' boundary rows is
     # exact for quadratics anywhere in the box and returns node values at nodes
     rng = np.random.default_rng(60 + d)
-    grid_n = (9, 7)[:d]
-    lo, hi = (0.0, -1.0)[:d], (2.0, 1.0)[:d]
+    grid_n = (9, 7, 6)[:d]
+    lo, hi = (0.0, -1.0, 0.5)[:d], (2.0, 1.0, 1.5)[:d]
     gp = oracle.grid_points(grid_n, lo, hi)
     b = rng.standard_normal(d)
     C = rng.standard_normal((d, d))
